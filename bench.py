@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the IEWPF hot path on one GB300.
+
+A step is one IEWPF cycle on the 512 x 512, 100-particle, 64-drifter
+workload: 5 model steps of 60 s (scheme steps from the CFL condition, model
+error after the first 4) followed by one two-stage IEWPF analysis against
+64 drifter observations.  Throughput is particle.cell-steps/s
+(sum over particles of scheme steps x 512^2 cells per second); the cycle time
+is ms_per_step.  The state (2 x 315 MB) exceeds the 129 MB L2, so no flush
+is needed between timed steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (there is no other implementation to run).
+Under torchrun each rank runs an independent replica (own seed).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle·cell-steps/s"
+UNIT = "particle*cell*step/s"
+BYTES_PER_CELL_STEP = 24          # read (eta, hu, hv) + write (eta, hu, hv), float32
+FLOPS_PER_CELL_STEP = 490         # FP32 operations of one scheme step per cell
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def make_observations(cfg, n_cycles, rank):
+    """Synthetic truth: one particle carrying 64 drifters, run with model
+    error; drifter observations (eq. drifterObservation) every 5 minutes."""
+    from paper_1910_01031_gb300 import iewpf, synth
+    tcfg = synth.Config(**{**cfg.as_dict(), "n_particles": 1, "seed": cfg.seed + 7919 * (rank + 1)})
+    truth = iewpf.Ensemble(iewpf.params_from_config(tcfg, n_drifters_max=cfg.n_obs))
+    truth.set_state(synth.initial_state(tcfg, 1, seed=1000 + rank).astype(np.float32))
+    xy = synth.drifter_positions(cfg)[None]
+    truth.set_drifters(xy)
+    obs = []
+    dt = cfg.obs_every_steps * cfg.dt_model
+    for k in range(n_cycles):
+        prev = truth.get_drifters()[0].copy()
+        truth.forecast(cfg.obs_every_steps, True)
+        cur = truth.get_drifters()[0].copy()
+        val = (cur - prev) / dt * cfg.H + synth.obs_noise(cfg, cfg.n_obs, k, seed=17 + rank)
+        obs.append((cur, val))
+    truth.close()
+    return obs
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1910_01031_gb300 import build, iewpf, synth
+
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    cfg = synth.config2(seed=0x1910_01031 + 104729 * rank)
+    ne, N = cfg.n_particles, cfg.nx * cfg.ny
+    P = iewpf.params_from_config(cfg)
+    P.instance_id = rank
+    ens = iewpf.Ensemble(P)
+    ens.set_state(synth.initial_state(cfg, ne, seed=7 + rank).astype(np.float32))
+    obs = make_observations(cfg, args.warmup + args.steps, rank)
+    # pinned host buffers for the per-step inputs and outputs (end-to-end leg)
+    pin_xy = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs]
+    pin_val = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs]
+    for k, (xy, val) in enumerate(obs):
+        pin_xy[k].numpy()[:] = xy
+        pin_val[k].numpy()[:] = val
+    stream = torch.cuda.ExternalStream(ens.stream())
+
+    def cycle(k):
+        ens.forecast(cfg.obs_every_steps - 1, True)
+        ens.forecast(1, False)
+        return ens.assimilate(pin_xy[k].numpy(), pin_val[k].numpy())
+
+    for k in range(args.warmup):
+        cycle(k)
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    w0, l0 = ens.work(), ens.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        d = cycle(k)
+    e1.record(stream)
+    e1.synchronize()
+    h1 = time.perf_counter()
+    torch.cuda.synchronize()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    host_s = h1 - h0
+    work = ens.work() - w0
+    launches = ens.launch_count() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    # slowest rank sets the job time
+    t = torch.tensor([dev_s, host_s, float(work)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tw = t.clone()
+        torch.distributed.all_reduce(t[:2], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tw[2:], op=torch.distributed.ReduceOp.SUM)
+        t[2] = tw[2]
+    dev_s, host_s, work_all = float(t[0]), float(t[1]), float(t[2])
+    value = work_all * N / dev_s
+    e2e_value = work_all * N / host_s
+    # the dominant kernel: bare scheme steps, CUDA events on the context stream
+    nsub_probe = 26
+    dt_probe = cfg.dt_model / 13.0
+    ens.substeps(2, dt_probe)           # warm
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    ens.substeps(nsub_probe, dt_probe)
+    f1.record(stream)
+    f1.synchronize()
+    launch_s = f0.elapsed_time(f1) / 1e3 / nsub_probe
+    cells = ne * N
+    achieved_gbs = BYTES_PER_CELL_STEP * cells / launch_s / 1e9
+    achieved_tflops = FLOPS_PER_CELL_STEP * cells / launch_s / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s, FMA = 2
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "rk2_traffic.json")))
+        if prof.get("kernel_sha") == _kernel_sha():
+            traffic = prof["bytes_per_cell_step"] * cells
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4), "traffic": traffic,
+                "kernel": "rk2_kernel (fused SSP-RK2 scheme step)",
+                "per_launch_ms": round(launch_s * 1e3, 4),
+                "alu": {"achieved": round(achieved_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                        "frac": round(achieved_tflops / fp32_peak, 4)}}
+    if rank != 0:
+        return
+    cpu = cpu_baseline(args) if world == 1 else None
+    h2d = 2 * cfg.n_obs * 2 * 8
+    d2h = 6 * ne * 8 + 2 * 8
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dev_s / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, f64 weights", "data": "synthetic",
+        "config": {"workload": "iewpf_cycle_512x512_ne100_64drifters", "nx": cfg.nx, "ny": cfg.ny,
+                   "particles": ne, "drifters": cfg.n_obs, "model_steps_per_cycle": cfg.obs_every_steps,
+                   "dt_model_s": cfg.dt_model, "c_omega": cfg.c_omega, "courant": cfg.courant,
+                   "particle_substeps_timed": int(work_all), "l2": "inputs larger than L2 (state 2x315 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iewpf_cycle_ms": round(dev_s / args.steps * 1e3, 3),
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "timing": "host wall clock through the C ABI, pinned obs buffers"},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "last_beta": d["beta"] if d else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _kernel_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("stepper.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1910_01031_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def oracle_sample(n_particles=4, seed_rank=0):
+    """One IEWPF cycle of the FP64 oracle on n_particles of the 512^2
+    workload; returns (particle.cell-steps, seconds, threads)."""
+    from oracle import oracle as O
+    from paper_1910_01031_gb300 import synth
+    cfg = synth.config2()
+    P = O.Problem(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, g=cfg.g, f=cfg.f, H=cfg.H, theta=cfg.theta,
+                  courant=cfg.courant, dt_model=cfg.dt_model, c_omega=cfg.c_omega, q0=cfg.q0, L0=cfg.L0,
+                  seed=cfg.seed, obs_sigma=cfg.obs_sigma)
+    U = synth.initial_state(cfg, n_particles, seed=7 + seed_rank)
+    xy = synth.drifter_positions(cfg)
+    cells = [O.obs_cell(P, *p) for p in xy]
+    truth = synth.initial_state(cfg, 1, seed=3)[0]
+    y = synth.obs_from_state(cfg, truth, np.array(cells), synth.obs_noise(cfg, len(cells), 0))
+    K = O.pull_stencil(P)
+    M = O.local_block_sqrt(P)
+    t0 = time.perf_counter()
+    U, nsub, _ = O.forecast(P, U, cfg.obs_every_steps, [1] * (cfg.obs_every_steps - 1) + [0], t0=0)
+    U, _ = O.assimilate(P, U, cells, y, t=0, K=K, Msq=M)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return float(nsub.sum()) * cfg.nx * cfg.ny, dt, min(threads, os.cpu_count() or 1, n_particles)
+
+
+def cpu_baseline(args):
+    try:
+        from oracle import build as ob
+        ob.build()
+        n = min(100, 2 * (os.cpu_count() or 1))
+        work, secs, threads = oracle_sample(n)
+        return {"value": round(work / secs, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": "1 IEWPF cycle (5 model steps + analysis, 64 drifters) of %d of the 100 particles "
+                          "of the 512x512 workload, FP64, OpenMP over particles" % n,
+                "seconds": round(secs, 2)}
+    except Exception as e:  # the GPU number stands without it
+        return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": "failed: %s" % e}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    total_work, total_s = 0.0, 0.0
+    threads = 1
+    for k in range(args.warmup + args.steps):
+        work, secs, threads = oracle_sample(2, seed_rank=k)
+        if k >= args.warmup:
+            total_work += work
+            total_s += secs
+    value = total_work / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "iewpf_cycle_512x512_ne100_64drifters", "sample_particles_per_step": 2},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "each step: 1 IEWPF cycle of 2 of the 100 particles of the 512x512 workload"},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

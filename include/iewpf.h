@@ -1,0 +1,246 @@
+/*
+ * iewpf.h - C ABI of the GB300 implementation of the two-stage implicit
+ * equal-weights particle filter (IEWPF) for a rotating shallow-water ocean
+ * model with drifter and mooring observations (arXiv 1910.01031).
+ *
+ * All calls return IEWPF_OK (0) or a negative error code; a message for the
+ * last error of a context is available from iewpf_last_error().  No C++
+ * exception crosses this interface.  A NULL context gives IEWPF_EINVAL.
+ *
+ * Memory: a context owns every device buffer it allocates.  Host pointers
+ * passed in are read (or written) during the call only.  Device pointers
+ * passed in are borrowed for the duration of the call and are used on the
+ * context's stream; the context never frees caller memory.
+ *
+ * Layouts: a field is [ny][nx] with x fastest; a particle state is
+ * [3][ny][nx] holding (eta, hu, hv); an ensemble is [N_e][3][ny][nx] float32.
+ * Positions are metres, unwrapped (a drifter that crosses the periodic
+ * boundary keeps counting); the cell of (x, y) is
+ * (floor(x/dx) mod nx, floor(y/dy) mod ny).
+ *
+ * Threading: a context is not thread-safe; different contexts may be used
+ * from different threads.  All work of a context runs on its own CUDA stream.
+ */
+#ifndef IEWPF_H
+#define IEWPF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IEWPF_API __attribute__((visibility("default")))
+#else
+#define IEWPF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IEWPF_OK 0
+#define IEWPF_EINVAL (-1)      /* invalid argument or call order            */
+#define IEWPF_ENOMEM (-2)      /* device or host allocation failed          */
+#define IEWPF_ECUDA (-3)       /* a CUDA runtime call or launch failed      */
+#define IEWPF_ENONFINITE (-4)  /* NaN/Inf met in the state or the weights   */
+#define IEWPF_EBETA (-5)       /* beta < 0 (eq. betaTwoStage): N_y too large for N_psi */
+#define IEWPF_EDOMAIN (-6)     /* Lambert W / alpha solve out of domain     */
+#define IEWPF_ETIMEOUT (-7)    /* a bounded device wait gave up             */
+#define IEWPF_ENOTPD (-8)      /* HQH^T + R not positive definite           */
+
+#define IEWPF_OBS_DRIFTER 0
+#define IEWPF_OBS_MOORING 1
+
+/* Problem description (Secs. 3.1-3.3 and 5 of the paper).
+ * Grid: periodic nx x ny cells of dx x dy metres (eq. cell_center).
+ * Physics: gravity g, Coriolis parameter f, constant equilibrium depth H_eq
+ * (eq. swe_full).  theta: parameter of the generalized minmod limiter of the
+ * reconstruction (1 <= theta <= 2).  courant: factor in front of the
+ * 1/4 min(dx/a, dy/b) limit of eq. swecfl.  dt_model: the model step dt,
+ * subdivided into as many scheme steps as the CFL condition requires.
+ * Model error (Sec. 3.2): coarse grid of every c_omega-th cell (odd), SOAR
+ * amplitude q0 (m) and length scale L0 (m), cut-off 2 coarse cells.
+ * seed: key of the counter-based random numbers.
+ * Observations: obs_kind, at most n_obs_max per cycle, standard deviation
+ * obs_sigma in hu/hv units (m^2/s), R = obs_sigma^2 I.  dense_S = 1 keeps
+ * the couplings between nearby observations in HQH^T (dense (HQH^T+R),
+ * Cholesky in FP64); 0 keeps only each observation's 2x2 block as the paper
+ * does (Sec. 4.2).  n_drifters_max: drifters each particle may carry in a
+ * forecast (0 for none). */
+typedef struct {
+    int nx, ny;
+    double dx, dy;
+    double g, f, H_eq;
+    double theta;
+    double courant;
+    double dt_model;
+    int c_omega;
+    double q0, L0;
+    uint64_t seed;
+    int n_particles;
+    int obs_kind;
+    int n_obs_max;
+    double obs_sigma;
+    int dense_S;
+    int instance_id;
+    int n_drifters_max;
+} iewpf_params_t;
+
+/* One observation time (Sec. 3.3).  xy: [n_obs][2] observed positions;
+ * value: [n_obs][2] observed (hu, hv) in m^2/s, i.e. eq. drifterObservation
+ * or eq. buoyObservation including the observation error.  For moorings the
+ * positions must be the ones given to iewpf_create (xy may be NULL). */
+typedef struct {
+    int n_obs;
+    const double* xy;
+    const double* value;
+} iewpf_obs_t;
+
+/* Per-cycle diagnostics of iewpf_assimilate (App. A).  Each array has
+ * N_e entries and may be NULL. */
+typedef struct {
+    double c_bar;        /* w_target = mean c_i                              */
+    double beta;         /* eq. betaTwoStage                                 */
+    double* phi;         /* eq. iewpfPhi                                     */
+    double* c;           /* eq. iewpf_ci, -log w^{n-1} = log N_e             */
+    double* gamma;       /* eq. scalingGammaZeta                             */
+    double* zeta;        /* eq. scalingGammaZeta                             */
+    double* alpha;       /* eq. iewpfAlphaSol                                */
+    double* neglogw;     /* final -log w_i, equal to c_bar for every i       */
+} iewpf_diag_t;
+
+typedef struct iewpf_ctx iewpf_ctx_t;
+
+/* Create a context: validates the parameters, allocates the ensemble (two
+ * state buffers), precomputes the pull stencils of a unit hu/hv observation
+ * (eq. detailedOPDUpdate), the 49x49 local block root (eq. Psquareroot,
+ * Fig. localsvd) and, for moorings, factors HQH^T + R (eq. S_extended) in
+ * FP64 on the GPU.  mooring_xy: [n_obs_max][2] for obs_kind = MOORING,
+ * else NULL.  Errors: EINVAL (bad sizes: nx, ny must exceed 14 c_omega + 1;
+ * c_omega odd; positive spacings, depth, step), ENOMEM, ECUDA, ENOTPD.
+ * The state is zero until iewpf_set_state. */
+IEWPF_API int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_ctx_t** out);
+
+/* Free every resource of the context.  NULL is accepted. */
+IEWPF_API int iewpf_destroy(iewpf_ctx_t* ctx);
+
+/* Copy the ensemble in ([N_e][3][ny][nx] float32).  on_device: src is a
+ * device pointer (copied on the context stream, after `stream` if given). */
+IEWPF_API int iewpf_set_state(iewpf_ctx_t* ctx, const float* src, int on_device, void* stream);
+
+/* Copy the ensemble out ([N_e][3][ny][nx] float32). */
+IEWPF_API int iewpf_get_state(iewpf_ctx_t* ctx, float* dst, int on_device, void* stream);
+
+/* Ensemble forecast (eq. model_equation): n_model_steps model steps of
+ * dt_model.  Each step picks n_sub = ceil(dt / dt_cfl) scheme steps per
+ * particle from the CFL condition (eq. swecfl), runs them (advecting the
+ * particle's drifters after each, if any are set), then adds the model
+ * error Q^{1/2} xi (eq. model_error) when add_model_error != 0.  The model
+ * error of step k uses draw counter = the context's model-step counter,
+ * which advances by one per model step.  Errors: EINVAL, ECUDA,
+ * ENONFINITE (checked once per call). */
+IEWPF_API int iewpf_forecast(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error);
+
+/* As iewpf_forecast but with a fixed number of scheme steps per model step
+ * (n_sub > 0) for every particle, skipping the CFL evaluation. */
+IEWPF_API int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error, int n_sub);
+
+/* One two-stage IEWPF analysis of the current ensemble against `obs`
+ * (Sec. 4, steps 1-6; App. A): innovations and S d (FP64), c_i, the
+ * perpendicular random vectors and gamma_i, zeta_i, the ensemble-wide
+ * target weight and beta, alpha_i from the Lambert W function, and one
+ * fused update psi <- psi + Q H^T S d + P^{1/2}(beta^{1/2} nu + alpha^{1/2}
+ * xi) (eq. optUpdateEquationTwoStage).  Random draws use the context's
+ * cycle counter, which then advances by one.  diag may be NULL.
+ * Errors: EINVAL (n_obs > n_obs_max, NULL values), EBETA, EDOMAIN,
+ * ENONFINITE, ENOTPD, ECUDA. */
+IEWPF_API int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* diag);
+
+/* Drifters carried by every particle (Sec. 3.3, forward Euler with the
+ * velocity hu/(H+eta) of the containing cell after each scheme step).
+ * xy: [N_e][n][2] float64 unwrapped positions; n <= n_drifters_max.
+ * n = 0 removes them. */
+IEWPF_API int iewpf_set_drifters(iewpf_ctx_t* ctx, const double* xy, int n);
+IEWPF_API int iewpf_get_drifters(iewpf_ctx_t* ctx, double* xy);
+
+/* Drift trajectory forecast (Sec. 5.2): places drifters xy0 ([n][2]) in
+ * every particle, runs `hours` of model steps with model error and stores
+ * positions every out_every_s seconds (and at t = 0) into
+ * traj[n_out][N_e][n][2], n_out = floor(hours*3600/out_every_s) + 1.
+ * use_surrogate must be 0 (the plain stepper). */
+IEWPF_API int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours,
+                     double out_every_s, double* traj, int use_surrogate);
+
+/* Checkpoint: raw state, drifters and the two draw counters; because the
+ * random numbers are counter-based, a resumed run is bit-identical. */
+IEWPF_API int iewpf_save(const iewpf_ctx_t* ctx, const char* path);
+IEWPF_API int iewpf_load(iewpf_ctx_t* ctx, const char* path);
+
+/* Draw counters: model steps taken (model error) and cycles assimilated. */
+IEWPF_API int iewpf_get_counters(const iewpf_ctx_t* ctx, uint32_t* model_step, uint32_t* cycle);
+IEWPF_API int iewpf_set_counters(iewpf_ctx_t* ctx, uint32_t model_step, uint32_t cycle);
+
+/* Scheme steps each particle took in the last model step ([N_e] ints). */
+IEWPF_API int iewpf_last_nsub(const iewpf_ctx_t* ctx, int* n_sub);
+
+/* Message of the last error of ctx ("" if none); static text for NULL. */
+IEWPF_API const char* iewpf_last_error(const iewpf_ctx_t* ctx);
+
+/* ---- building blocks, exposed for verification --------------------- */
+
+/* Raw Philox4x32-10 blocks (Salmon et al., SC'11) computed on the GPU:
+ * block b of counter (b, p, t, stream) with key (seed lo, seed hi).
+ * out: host [n_blocks][4] uint32.  The model-error, xi and nu draws use
+ * streams 0, 1, 2 (plus 16 x instance_id). */
+IEWPF_API int iewpf_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream,
+                        int64_t n_blocks, uint32_t* out);
+
+/* Standard normals from those blocks by the Box-Muller pairing, computed
+ * on the GPU in FP64 (out64) and FP32 (out32); either may be NULL. */
+IEWPF_API int iewpf_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, int64_t n,
+                  double* out64, float* out32);
+
+/* The ensemble-wide step of the two-stage IEWPF on the GPU (App. A,
+ * eqs. betaTwoStage, cistarTwoStage, iewpfAlphaSol): from host arrays c,
+ * gamma, zeta ([ne]) and N_psi, returns c_bar and beta in out2[2] and
+ * alpha, c* and -log w in host arrays of ne (neglogw may be NULL).
+ * Errors: EINVAL, EBETA, EDOMAIN, ENONFINITE, ENOMEM, ECUDA. */
+IEWPF_API int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma,
+                  const double* zeta, double* out2, double* alpha, double* cstar,
+                  double* neglogw);
+
+/* The context's precomputed pull stencils: K[2][3][2R+1][2R+1] float64,
+ * R = 7 c_omega (unit hu, unit hv observation; fields eta, hu, hv). */
+IEWPF_API int iewpf_pull_stencil(const iewpf_ctx_t* ctx, double* K);
+
+/* The context's 49x49 local block root (row-major float64, block entries
+ * ordered (dy+3)*7 + (dx+3)). */
+IEWPF_API int iewpf_local_block(const iewpf_ctx_t* ctx, double* M);
+
+/* Add Q^{1/2} x to every particle for coarse fields x ([N_e][N_R] float32,
+ * host), the operator of eq. covarianceOperatorsDef (testing aid). */
+IEWPF_API int iewpf_add_qhalf(iewpf_ctx_t* ctx, const float* x);
+
+/* The CUDA stream (cudaStream_t) on which all work of ctx runs, so that a
+ * caller can order its own work or record timing events on it. */
+IEWPF_API int iewpf_stream(const iewpf_ctx_t* ctx, void** stream);
+
+/* n scheme steps (eq. swecfl's subdivision of the model step) of length dt
+ * seconds for every particle, without the CFL evaluation, the model error
+ * or any host synchronisation: the bare stepper (Sec. 3.1). */
+IEWPF_API int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt);
+
+/* Particle scheme steps (sum over particles of the scheme steps each took)
+ * executed by the context so far; one unit of work is a particle scheme
+ * step over nx*ny cells. */
+IEWPF_API int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps);
+
+/* Number of kernels the context has launched so far. */
+IEWPF_API int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count);
+
+/* Sizes derived from the parameters. */
+IEWPF_API int iewpf_sizes(const iewpf_ctx_t* ctx, int* nRx, int* nRy, int* stencil_R);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IEWPF_H */

@@ -1,0 +1,989 @@
+// C ABI of the IEWPF library (declared in include/iewpf.h): context
+// management, create-time precomputation (pull stencils, SOAR weight table,
+// 49x49 block root, mooring factorisation) and the orchestration of the
+// forecast and analysis kernels on the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/iewpf.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace iewpf;
+
+struct iewpf_ctx {
+    iewpf_params_t P;
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    Grid G{};
+    Coarse C{};
+    int R = 0;              // pull stencil radius (7 c)
+    long long NR = 0;
+    long long plane = 0;
+    // host precomputations (FP64)
+    std::vector<double> K64;   // [2][3][2R+1][2R+1]
+    std::vector<double> M49;   // [49][49]
+    std::vector<float> wtab;   // [tab][tab]
+    // device state
+    float* buf[2] = {nullptr, nullptr};
+    int* par = nullptr;
+    int* nsub = nullptr;
+    float* dtp = nullptr;
+    float* amax = nullptr;
+    int* maxsub = nullptr;
+    int* flag = nullptr;
+    unsigned long long* work = nullptr;   // particle scheme steps
+    float* d_wtab = nullptr;
+    float* d_K32 = nullptr;
+    double* d_K64 = nullptr;
+    float* d_M49 = nullptr;
+    // drifters carried by the particles
+    double* d_xy = nullptr;
+    int nd = 0;
+    // analysis buffers
+    int nobs_max = 0;
+    double* d_obs_xy = nullptr;
+    double* d_obs_y = nullptr;
+    int* d_cell = nullptr;
+    int* d_block0 = nullptr;
+    int ntiles = 0;
+    int tile_cap = 256;
+    int* d_tile_cnt = nullptr;
+    int* d_tile_obs = nullptr;
+    double* d_L = nullptr;      // (HQH^T + R) and its factor [Ny][Ny]
+    int* d_colptr = nullptr;
+    int* d_rowidx = nullptr;
+    double* d_d = nullptr;      // innovations [ne][Ny]
+    double* d_Sd = nullptr;     // [ne][Ny]
+    double* d_phi = nullptr;
+    double* d_c = nullptr;
+    double* d_gamma = nullptr;
+    double* d_zeta = nullptr;
+    double* d_alpha = nullptr;
+    double* d_cstar = nullptr;
+    double* d_neglogw = nullptr;
+    double* d_coef = nullptr;   // [ne][2] (a_i, length scale)
+    double* d_scal = nullptr;   // [4] (c_bar, beta)
+    double* d_partial = nullptr;
+    int dots_blk = 0;
+    float* d_r = nullptr;       // posterior coarse field [ne][N_R]
+    int* d_list = nullptr;      // observation order, grouped into non-overlapping waves
+    bool factored = false;      // mooring factor ready
+    std::vector<int> waves;     // sizes of the waves of d_list
+    // pinned staging
+    int* h_flag = nullptr;
+    int* h_maxsub = nullptr;
+    double* h_scal = nullptr;
+    // counters
+    uint32_t step = 0, cycle = 0;
+    int64_t launches = 0;    // kernels launched
+    std::string err;
+};
+
+namespace {
+
+const char* kNullMsg = "null context";
+
+int fail(iewpf_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define KL(n, call)                                                                                  \
+    do {                                                                                             \
+        CK(call);                                                                                    \
+        ctx->launches += (n);                                                                        \
+    } while (0)
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(ctx, IEWPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+template <typename T>
+int dalloc(iewpf_ctx* ctx, T** p, size_t n)
+{
+    if (n == 0) n = 1;
+    if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, IEWPF_ENOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    }
+    return IEWPF_OK;
+}
+
+int coarse_count(int n, int c) { return (n - 1 - c / 2) / c + 1; }
+
+double soar(double d, double q0, double L0) { return q0 * (1.0 + d / L0) * std::exp(-d / L0); }
+
+// Catmull-Rom weights of taps a-1 .. a+2
+void cubic(double t, double w[4])
+{
+    const double t2 = t * t, t3 = t2 * t;
+    w[0] = 0.5 * (-t3 + 2 * t2 - t);
+    w[1] = 0.5 * (3 * t3 - 5 * t2 + 2);
+    w[2] = 0.5 * (-3 * t3 + 4 * t2 + t);
+    w[3] = 0.5 * (t3 - t2);
+}
+
+// Response of the chain of eq. detailedOPDUpdate to a unit hu (comp 0) or
+// hv (comp 1) observation: point injection on the observation-centred
+// coarse lattice, adjoint geostrophic balance with spacing 2 c dx
+// (eq. adjointGeoBalance, coefficient g H / f), SOAR twice, bicubic to the
+// fine offsets, geostrophic balance on the fine grid.
+void build_stencil(const iewpf_params_t& P, int R, std::vector<double>& K)
+{
+    const int c = P.c_omega, A = 10, n = 2 * A + 1, W = 2 * R + 1, Rf = R + 1, Wf = 2 * Rf + 1;
+    const double dxc = c * P.dx, dyc = c * P.dy, s = P.g * P.H_eq / P.f;
+    double w5[5][5];
+    for (int b = -2; b <= 2; ++b)
+        for (int a = -2; a <= 2; ++a) w5[b + 2][a + 2] = soar(std::hypot(a * dxc, b * dyc), P.q0, P.L0);
+    K.assign(2 * 3 * W * W, 0.0);
+    std::vector<double> e(n * n), t(n * n), eta(Wf * Wf);
+    for (int comp = 0; comp < 2; ++comp) {
+        std::fill(e.begin(), e.end(), 0.0);
+        if (comp == 0) {
+            e[(A + 1) * n + A] = -s / (2 * dyc);
+            e[(A - 1) * n + A] = s / (2 * dyc);
+        } else {
+            e[A * n + A + 1] = s / (2 * dxc);
+            e[A * n + A - 1] = -s / (2 * dxc);
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            std::fill(t.begin(), t.end(), 0.0);
+            for (int b = 2; b < n - 2; ++b)
+                for (int a = 2; a < n - 2; ++a) {
+                    double acc = 0.0;
+                    for (int db = -2; db <= 2; ++db)
+                        for (int da = -2; da <= 2; ++da) acc += w5[db + 2][da + 2] * e[(b + db) * n + a + da];
+                    t[b * n + a] = acc;
+                }
+            e.swap(t);
+        }
+        for (int fy = -Rf; fy <= Rf; ++fy) {
+            const int by = (int)std::floor((double)fy / c);
+            double wy[4];
+            cubic((double)(fy - by * c) / c, wy);
+            for (int fx = -Rf; fx <= Rf; ++fx) {
+                const int bx = (int)std::floor((double)fx / c);
+                double wx[4];
+                cubic((double)(fx - bx * c) / c, wx);
+                double acc = 0.0;
+                for (int q = 0; q < 4; ++q) {
+                    double row = 0.0;
+                    for (int p = 0; p < 4; ++p) row += wx[p] * e[(A + by - 1 + q) * n + (A + bx - 1 + p)];
+                    acc += wy[q] * row;
+                }
+                eta[(fy + Rf) * Wf + (fx + Rf)] = acc;
+            }
+        }
+        for (int y = -R; y <= R; ++y)
+            for (int x = -R; x <= R; ++x) {
+                const int i = (y + Rf) * Wf + (x + Rf);
+                const int o = (y + R) * W + (x + R);
+                K[(comp * 3 + 0) * W * W + o] = eta[i];
+                K[(comp * 3 + 1) * W * W + o] = -s * (eta[i + Wf] - eta[i - Wf]) / (2 * P.dy);
+                K[(comp * 3 + 2) * W * W + o] = s * (eta[i + 1] - eta[i - 1]) / (2 * P.dx);
+            }
+    }
+}
+
+// Cyclic Jacobi eigensolver for a symmetric n x n matrix (row-major); on
+// return a holds the eigenvalues on its diagonal and v the eigenvectors.
+void jacobi_eigen(int n, std::vector<double>& a, std::vector<double>& v)
+{
+    v.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i) v[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double th = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = cs * akp - sn * akq;
+                    a[k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = cs * apk - sn * aqk;
+                    a[q * n + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = v[k * n + p], vkq = v[k * n + q];
+                    v[k * n + p] = cs * vkp - sn * vkq;
+                    v[k * n + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+}
+
+// Square root of the local block I - Q_SOAR Q_GB^T H^T S H Q_GB Q_SOAR of
+// eq. svdOfParenthesis on the 7x7 block of a grid with Omega^M = Omega^R
+// (spacing c dx).  With B = H Q_GB Q_SOAR (2 x 49) the block is
+// I - B^T (B B^T + R)^{-1} B; the root used is V Lambda^{1/2} V^T.
+void build_block_root(const iewpf_params_t& P, std::vector<double>& M)
+{
+    const double dxc = P.c_omega * P.dx, dyc = P.c_omega * P.dy, s = P.g * P.H_eq / P.f;
+    auto w = [&](int ax, int ay, int bx, int by) {
+        const int dx = ax - bx, dy = ay - by;
+        if (std::abs(dx) > 2 || std::abs(dy) > 2) return 0.0;
+        return soar(std::hypot(dx * dxc, dy * dyc), P.q0, P.L0);
+    };
+    double B[2][49];
+    for (int m = 0; m < 49; ++m) {
+        const int mx = m % 7 - 3, my = m / 7 - 3;
+        B[0][m] = -s / (2 * dyc) * (w(0, 1, mx, my) - w(0, -1, mx, my));
+        B[1][m] = s / (2 * dxc) * (w(1, 0, mx, my) - w(-1, 0, mx, my));
+    }
+    double C[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0.0;
+            for (int m = 0; m < 49; ++m) acc += B[i][m] * B[j][m];
+            C[i][j] = acc + (i == j ? P.obs_sigma * P.obs_sigma : 0.0);
+        }
+    const double det = C[0][0] * C[1][1] - C[0][1] * C[1][0];
+    const double S[2][2] = {{C[1][1] / det, -C[0][1] / det}, {-C[1][0] / det, C[0][0] / det}};
+    std::vector<double> a(49 * 49), v;
+    for (int i = 0; i < 49; ++i)
+        for (int j = 0; j < 49; ++j) {
+            double acc = 0.0;
+            for (int p = 0; p < 2; ++p)
+                for (int q = 0; q < 2; ++q) acc += B[p][i] * S[p][q] * B[q][j];
+            a[i * 49 + j] = (i == j ? 1.0 : 0.0) - acc;
+        }
+    for (int i = 0; i < 49; ++i)
+        for (int j = i + 1; j < 49; ++j) a[i * 49 + j] = a[j * 49 + i] = 0.5 * (a[i * 49 + j] + a[j * 49 + i]);
+    jacobi_eigen(49, a, v);
+    M.assign(49 * 49, 0.0);
+    for (int k = 0; k < 49; ++k) {
+        const double lam = a[k * 49 + k];
+        const double sl = lam > 0.0 ? std::sqrt(lam) : 0.0;
+        for (int i = 0; i < 49; ++i)
+            for (int j = 0; j < 49; ++j) M[i * 49 + j] += v[i * 49 + k] * sl * v[j * 49 + k];
+    }
+}
+
+int fdiv(double x, double d) { return (int)std::floor(x / d); }
+int posmod(int a, int n) { return ((a % n) + n) % n; }
+
+// nearest coarse point index of fine index j (ties to the lower one)
+int nearest_coarse(int j, int n, int nR, int c)
+{
+    const int o = c / 2;
+    int a = (j < o) ? -1 : std::min((j - o) / c, nR - 1);
+    auto pos = [&](int aa) {
+        const int w = aa >= 0 ? aa / nR : -((-aa + nR - 1) / nR);
+        return o + c * (aa - w * nR) + w * n;
+    };
+    const int xa = pos(a), xb = pos(a + 1);
+    return posmod((j - xa) <= (xb - j) ? a : a + 1, nR);
+}
+
+// Observations in order, split into waves whose 7x7 coarse blocks do not
+// overlap; an observation goes one wave after the last earlier observation
+// it overlaps, so applying the waves in turn equals applying the blocks in
+// observation order.
+void make_waves(iewpf_ctx* ctx, const double* xy, int nobs, std::vector<int>& order, std::vector<int>& sizes)
+{
+    const auto& P = ctx->P;
+    std::vector<int> ba(nobs), bb(nobs), wave(nobs, 0);
+    for (int l = 0; l < nobs; ++l) {
+        const int j = posmod(fdiv(xy[2 * l], P.dx), P.nx), k = posmod(fdiv(xy[2 * l + 1], P.dy), P.ny);
+        ba[l] = nearest_coarse(j, P.nx, ctx->C.nRx, P.c_omega);
+        bb[l] = nearest_coarse(k, P.ny, ctx->C.nRy, P.c_omega);
+    }
+    // bucket by coarse cell so that the overlap search stays local
+    const int cell = 7, gx = (ctx->C.nRx + cell - 1) / cell, gy = (ctx->C.nRy + cell - 1) / cell;
+    std::vector<std::vector<int>> bucket((size_t)gx * gy);
+    int nw = 0;
+    for (int l = 0; l < nobs; ++l) {
+        const int cx = ba[l] / cell, cy = bb[l] / cell;
+        int w = 0;
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                const auto& bk = bucket[(size_t)posmod(cy + dy, gy) * gx + posmod(cx + dx, gx)];
+                for (int k : bk) {
+                    int ox = std::abs(ba[l] - ba[k]), oy = std::abs(bb[l] - bb[k]);
+                    ox = std::min(ox, ctx->C.nRx - ox);
+                    oy = std::min(oy, ctx->C.nRy - oy);
+                    if (ox <= 6 && oy <= 6) w = std::max(w, wave[k] + 1);
+                }
+            }
+        wave[l] = w;
+        nw = std::max(nw, w + 1);
+        bucket[(size_t)cy * gx + cx].push_back(l);
+    }
+    order.clear();
+    sizes.assign(nw, 0);
+    for (int w = 0; w < nw; ++w)
+        for (int l = 0; l < nobs; ++l)
+            if (wave[l] == w) {
+                order.push_back(l);
+                ++sizes[w];
+            }
+}
+
+int check_flags(iewpf_ctx* ctx, int f)
+{
+    if (f & FLAG_NONFINITE) return fail(ctx, IEWPF_ENONFINITE, "non-finite values in the state or weights");
+    if (f & FLAG_NOTPD) return fail(ctx, IEWPF_ENOTPD, "HQH^T + R is not positive definite");
+    if (f & FLAG_BETA) return fail(ctx, IEWPF_EBETA, "beta < 0: too many observations for the state size");
+    if (f & FLAG_DOMAIN) return fail(ctx, IEWPF_EDOMAIN, "alpha solve (Lambert W) out of domain");
+    if (f & FLAG_TILE_OVERFLOW) return fail(ctx, IEWPF_EINVAL, "too many observations near one tile");
+    return IEWPF_OK;
+}
+
+// Factor (HQH^T + R) for the current d_cell layout.
+int factor(iewpf_ctx* ctx, int nobs)
+{
+    const int n = 2 * nobs;
+    KL(1, launch_hqht(ctx->d_K64, ctx->R, ctx->d_cell, nobs, ctx->G, ctx->P.dense_S,
+                   ctx->P.obs_sigma * ctx->P.obs_sigma, ctx->d_L, ctx->st));
+    KL(1, launch_cholesky(ctx->d_L, n, ctx->d_colptr, ctx->d_rowidx, ctx->flag, ctx->st));
+    return IEWPF_OK;
+}
+
+int upload_obs_layout(iewpf_ctx* ctx, const double* xy, int nobs)
+{
+    CK(cudaMemcpyAsync(ctx->d_obs_xy, xy, sizeof(double) * 2 * nobs, cudaMemcpyHostToDevice, ctx->st));
+    KL(2, launch_obs_setup(ctx->d_obs_xy, nobs, ctx->G, ctx->C, ctx->P.dx, ctx->P.dy, ctx->R, ctx->d_cell,
+                        ctx->d_block0, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->tile_cap, ctx->flag, ctx->st));
+    std::vector<int> order;
+    make_waves(ctx, xy, nobs, order, ctx->waves);
+    CK(cudaMemcpyAsync(ctx->d_list, order.data(), sizeof(int) * (order.empty() ? 1 : order.size()),
+                       cudaMemcpyHostToDevice, ctx->st));
+    // the host vector must outlive the copy
+    CK(cudaStreamSynchronize(ctx->st));
+    return IEWPF_OK;
+}
+
+int read_flags(iewpf_ctx* ctx)
+{
+    CK(cudaMemcpyAsync(ctx->h_flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const int f = *ctx->h_flag;
+    if (f) {
+        CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return check_flags(ctx, f);
+}
+
+int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (n_steps < 0) return fail(ctx, IEWPF_EINVAL, "n_model_steps < 0");
+    CK(cudaSetDevice(ctx->dev));
+    for (int k = 0; k < n_steps; ++k) {
+        KL(fixed > 0 ? 1 : 2, launch_cfl(ctx->buf[0], ctx->buf[1], ctx->par, ctx->amax, ctx->nsub, ctx->dtp, ctx->maxsub, ctx->G,
+                      ctx->P.courant, ctx->P.dt_model, fixed, ctx->st));
+        CK(cudaMemcpyAsync(ctx->h_maxsub, ctx->maxsub, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        const int ms = *ctx->h_maxsub;
+        if (ms < 1 || ms > 100000) return fail(ctx, IEWPF_ENONFINITE, "invalid CFL substep count");
+        for (int s = 0; s < ms; ++s) {
+            KL(1, launch_rk2(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->st));
+            if (ctx->nd > 0)
+                KL(1, launch_drift(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->d_xy, ctx->nd, s,
+                                ctx->G, ctx->P.dx, ctx->P.dy, ctx->st));
+        }
+        KL(1, launch_par_update(ctx->par, ctx->nsub, ctx->G.ne, ctx->work, ctx->st));
+        if (add_err) {
+            QhalfArgs A{};
+            A.b0 = ctx->buf[0];
+            A.b1 = ctx->buf[1];
+            A.par = ctx->par;
+            A.wtab = ctx->d_wtab;
+            A.from_philox = 1;
+            A.seed = ctx->P.seed;
+            A.t = ctx->step;
+            A.stream = 0u + 16u * (uint32_t)ctx->P.instance_id;
+            KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+        }
+        ctx->step++;
+    }
+    KL(1, launch_nonfinite(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, ctx->flag, ctx->st));
+    return read_flags(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_ctx_t** out)
+{
+    if (!params || !out) return IEWPF_EINVAL;
+    *out = nullptr;
+    const iewpf_params_t& P = *params;
+    const int c = P.c_omega;
+    if (c < 1 || c % 2 == 0 || c > 15 || P.nx <= 14 * c + 1 || P.ny <= 14 * c + 1 || !(P.dx > 0) ||
+        !(P.dy > 0) || !(P.H_eq > 0) || !(P.g > 0) || P.f == 0.0 || !(P.dt_model > 0) || !(P.courant > 0) ||
+        !(P.q0 >= 0) || !(P.L0 > 0) || P.n_particles < 1 || P.n_particles > 65535 || P.n_obs_max < 0 ||
+        !(P.obs_sigma > 0) || P.theta < 1.0 || P.theta > 2.0 || P.n_drifters_max < 0 ||
+        (P.obs_kind != IEWPF_OBS_DRIFTER && P.obs_kind != IEWPF_OBS_MOORING) ||
+        (P.obs_kind == IEWPF_OBS_MOORING && P.n_obs_max > 0 && !mooring_xy) || P.instance_id < 0 ||
+        P.instance_id > 0x0FFFFFFF)
+        return IEWPF_EINVAL;
+    iewpf_ctx* ctx = new (std::nothrow) iewpf_ctx();
+    if (!ctx) return IEWPF_ENOMEM;
+    ctx->P = P;
+    auto bail = [&](int code) {
+        iewpf_destroy(ctx);
+        return code;
+    };
+    if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(IEWPF_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) return bail(IEWPF_ECUDA);
+    Grid& G = ctx->G;
+    G.nx = P.nx;
+    G.ny = P.ny;
+    G.dx = (float)P.dx;
+    G.dy = (float)P.dy;
+    G.g = (float)P.g;
+    G.f = (float)P.f;
+    G.H = (float)P.H_eq;
+    G.theta = (float)P.theta;
+    G.inv_dx = (float)(1.0 / P.dx);
+    G.inv_dy = (float)(1.0 / P.dy);
+    G.fdx = (float)(P.f * P.dx);
+    G.fdy = (float)(P.f * P.dy);
+    G.fdx_half = (float)(0.5 * P.f * P.dx);
+    G.fdy_half = (float)(0.5 * P.f * P.dy);
+    G.inv_2g = (float)(0.5 / P.g);
+    G.sgh = (float)(P.g * P.H_eq / P.f);
+    G.inv_2dx = (float)(0.5 / P.dx);
+    G.inv_2dy = (float)(0.5 / P.dy);
+    G.ne = P.n_particles;
+    G.plane = (long long)P.nx * P.ny;
+    ctx->plane = G.plane;
+    Coarse& C = ctx->C;
+    C.c = c;
+    C.o = c / 2;
+    C.nRx = coarse_count(P.nx, c);
+    C.nRy = coarse_count(P.ny, c);
+    C.tab = 3 * c;
+    ctx->NR = (long long)C.nRx * C.nRy;
+    ctx->R = 7 * c;
+    // SOAR weights by fine-cell offset
+    ctx->wtab.resize(C.tab * C.tab);
+    for (int y = 0; y < C.tab; ++y)
+        for (int x = 0; x < C.tab; ++x)
+            ctx->wtab[y * C.tab + x] = (float)soar(std::hypot(x * P.dx, y * P.dy), P.q0, P.L0);
+    build_stencil(P, ctx->R, ctx->K64);
+    build_block_root(P, ctx->M49);
+    const size_t ne = P.n_particles;
+    const size_t state = ne * 3 * (size_t)G.plane;
+    int rc;
+    if ((rc = dalloc(ctx, &ctx->buf[0], state)) || (rc = dalloc(ctx, &ctx->buf[1], state)) ||
+        (rc = dalloc(ctx, &ctx->par, ne)) || (rc = dalloc(ctx, &ctx->nsub, ne)) ||
+        (rc = dalloc(ctx, &ctx->dtp, ne)) || (rc = dalloc(ctx, &ctx->amax, ne)) ||
+        (rc = dalloc(ctx, &ctx->maxsub, 1)) || (rc = dalloc(ctx, &ctx->flag, 1)) || (rc = dalloc(ctx, &ctx->work, 1)) ||
+        (rc = dalloc(ctx, &ctx->d_wtab, ctx->wtab.size())) || (rc = dalloc(ctx, &ctx->d_K32, ctx->K64.size())) ||
+        (rc = dalloc(ctx, &ctx->d_K64, ctx->K64.size())) || (rc = dalloc(ctx, &ctx->d_M49, 49 * 49)))
+        return bail(rc);
+    if (cudaMallocHost((void**)&ctx->h_flag, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_maxsub, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_scal, 4 * sizeof(double)) != cudaSuccess)
+        return bail(IEWPF_ENOMEM);
+    std::vector<float> K32(ctx->K64.begin(), ctx->K64.end());
+    std::vector<float> M32(ctx->M49.begin(), ctx->M49.end());
+    if (cudaMemsetAsync(ctx->buf[0], 0, state * sizeof(float), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->buf[1], 0, state * sizeof(float), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->par, 0, ne * sizeof(int), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->work, 0, sizeof(unsigned long long), ctx->st) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->d_wtab, ctx->wtab.data(), ctx->wtab.size() * 4, cudaMemcpyHostToDevice, ctx->st) ||
+        cudaMemcpyAsync(ctx->d_K32, K32.data(), K32.size() * 4, cudaMemcpyHostToDevice, ctx->st) ||
+        cudaMemcpyAsync(ctx->d_K64, ctx->K64.data(), ctx->K64.size() * 8, cudaMemcpyHostToDevice, ctx->st) ||
+        cudaMemcpyAsync(ctx->d_M49, M32.data(), M32.size() * 4, cudaMemcpyHostToDevice, ctx->st) ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess)
+        return bail(IEWPF_ECUDA);
+    // analysis buffers
+    const int nobs = P.n_obs_max;
+    ctx->nobs_max = nobs;
+    const size_t ny = 2 * (size_t)std::max(nobs, 1);
+    ctx->ntiles = ((P.nx + TW - 1) / TW) * ((P.ny + TH - 1) / TH);
+    ctx->dots_blk = rand_dots_blocks((int)ctx->NR);
+    if ((rc = dalloc(ctx, &ctx->d_obs_xy, ny)) || (rc = dalloc(ctx, &ctx->d_obs_y, ny)) ||
+        (rc = dalloc(ctx, &ctx->d_cell, ny)) || (rc = dalloc(ctx, &ctx->d_block0, ny)) ||
+        (rc = dalloc(ctx, &ctx->d_list, ny / 2)) || (rc = dalloc(ctx, &ctx->d_tile_cnt, ctx->ntiles)) ||
+        (rc = dalloc(ctx, &ctx->d_tile_obs, (size_t)ctx->ntiles * ctx->tile_cap)) ||
+        (rc = dalloc(ctx, &ctx->d_L, ny * ny)) || (rc = dalloc(ctx, &ctx->d_colptr, ny + 1)) ||
+        (rc = dalloc(ctx, &ctx->d_rowidx, ny * (ny - 1) / 2 + ny)) || (rc = dalloc(ctx, &ctx->d_d, ne * ny)) ||
+        (rc = dalloc(ctx, &ctx->d_Sd, ne * ny)) || (rc = dalloc(ctx, &ctx->d_phi, ne)) ||
+        (rc = dalloc(ctx, &ctx->d_c, ne)) || (rc = dalloc(ctx, &ctx->d_gamma, ne)) ||
+        (rc = dalloc(ctx, &ctx->d_zeta, ne)) || (rc = dalloc(ctx, &ctx->d_alpha, ne)) ||
+        (rc = dalloc(ctx, &ctx->d_cstar, ne)) || (rc = dalloc(ctx, &ctx->d_neglogw, ne)) ||
+        (rc = dalloc(ctx, &ctx->d_coef, 2 * ne)) || (rc = dalloc(ctx, &ctx->d_scal, 4)) ||
+        (rc = dalloc(ctx, &ctx->d_partial, ne * ctx->dots_blk * 3)) ||
+        (rc = dalloc(ctx, &ctx->d_r, ne * (size_t)ctx->NR)))
+        return bail(rc);
+    if (P.n_drifters_max > 0 && (rc = dalloc(ctx, &ctx->d_xy, ne * 2 * (size_t)P.n_drifters_max)))
+        return bail(rc);
+    if (P.obs_kind == IEWPF_OBS_MOORING && nobs > 0) {
+        if ((rc = upload_obs_layout(ctx, mooring_xy, nobs)) || (rc = factor(ctx, nobs)) ||
+            (rc = read_flags(ctx)))
+            return bail(rc);
+        ctx->factored = true;
+    }
+    *out = ctx;
+    return IEWPF_OK;
+}
+
+int iewpf_destroy(iewpf_ctx_t* ctx)
+{
+    if (!ctx) return IEWPF_OK;
+    cudaSetDevice(ctx->dev);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    void* ptrs[] = {ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->amax, ctx->maxsub, ctx->flag, ctx->work,
+                    ctx->d_wtab, ctx->d_K32, ctx->d_K64, ctx->d_M49, ctx->d_xy, ctx->d_obs_xy, ctx->d_obs_y,
+                    ctx->d_cell, ctx->d_block0, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
+                    ctx->d_rowidx, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
+                    ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
+                    ctx->d_r, ctx->d_list};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
+    if (ctx->h_maxsub) cudaFreeHost(ctx->h_maxsub);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->st) cudaStreamDestroy(ctx->st);
+    delete ctx;
+    return IEWPF_OK;
+}
+
+static int copy_state(iewpf_ctx_t* ctx, float* host_or_dev, int on_device, void* stream, bool in)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!host_or_dev) return fail(ctx, IEWPF_EINVAL, "null state pointer");
+    CK(cudaSetDevice(ctx->dev));
+    cudaStream_t user = (cudaStream_t)stream;
+    if (user) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, user));
+        CK(cudaStreamWaitEvent(ctx->st, ev, 0));
+        CK(cudaEventDestroy(ev));
+    }
+    const size_t per = 3 * (size_t)ctx->plane;
+    std::vector<int> par(ctx->G.ne);
+    if (!in) {
+        CK(cudaMemcpyAsync(par.data(), ctx->par, sizeof(int) * par.size(), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    const cudaMemcpyKind kind = in ? (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                                   : (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    if (in) {
+        CK(cudaMemcpyAsync(ctx->buf[0], host_or_dev, sizeof(float) * per * ctx->G.ne, kind, ctx->st));
+        CK(cudaMemsetAsync(ctx->par, 0, sizeof(int) * ctx->G.ne, ctx->st));
+    } else {
+        // contiguous runs of particles that live in the same buffer
+        int p = 0;
+        while (p < ctx->G.ne) {
+            int q = p;
+            while (q < ctx->G.ne && par[q] == par[p]) ++q;
+            CK(cudaMemcpyAsync(host_or_dev + per * p, ctx->buf[par[p]] + per * p, sizeof(float) * per * (q - p),
+                               kind, ctx->st));
+            p = q;
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return IEWPF_OK;
+}
+
+int iewpf_set_state(iewpf_ctx_t* ctx, const float* src, int on_device, void* stream)
+{
+    return copy_state(ctx, const_cast<float*>(src), on_device, stream, true);
+}
+
+int iewpf_get_state(iewpf_ctx_t* ctx, float* dst, int on_device, void* stream)
+{
+    return copy_state(ctx, dst, on_device, stream, false);
+}
+
+int iewpf_forecast(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error)
+{
+    return forecast_impl(ctx, n_model_steps, add_model_error, 0);
+}
+
+int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error, int n_sub)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (n_sub < 1) return fail(ctx, IEWPF_EINVAL, "n_sub < 1");
+    return forecast_impl(ctx, n_model_steps, add_model_error, n_sub);
+}
+
+int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* diag)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max || !obs->value)
+        return fail(ctx, IEWPF_EINVAL, "bad observation set");
+    const bool mooring = ctx->P.obs_kind == IEWPF_OBS_MOORING;
+    if (!mooring && !obs->xy) return fail(ctx, IEWPF_EINVAL, "drifter observations need positions");
+    if (mooring && obs->n_obs != ctx->nobs_max)
+        return fail(ctx, IEWPF_EINVAL, "mooring observations must cover every mooring");
+    CK(cudaSetDevice(ctx->dev));
+    const int nobs = obs->n_obs, n = 2 * nobs, ne = ctx->G.ne;
+    int rc;
+    if (!mooring) {
+        if ((rc = upload_obs_layout(ctx, obs->xy, nobs))) return rc;
+    }
+    CK(cudaMemcpyAsync(ctx->d_obs_y, obs->value, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+    // 1-2: innovations, S d, phi
+    KL(1, launch_innovate(ctx->buf[0], ctx->buf[1], ctx->par, ctx->d_cell, ctx->d_obs_y, nobs, ctx->G,
+                       ctx->P.H_eq, ctx->d_d, ctx->st));
+    if (!mooring && (rc = factor(ctx, nobs))) return rc;
+    KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, n, ctx->d_d, ctx->d_Sd, ctx->d_phi, ne, ctx->st));
+    // 3: random vectors
+    const uint32_t sb = 16u * (uint32_t)ctx->P.instance_id;
+    KL(1, launch_rand_dots(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_partial,
+                        ctx->dots_blk, ctx->st));
+    // 4-5: target weight, beta, alpha
+    KL(1, launch_sync_alpha(ctx->d_phi, ctx->d_partial, ctx->dots_blk, ne, (double)ctx->NR, 3.0 * ctx->plane,
+                         std::log((double)ne), ctx->d_c, ctx->d_gamma, ctx->d_zeta, ctx->d_alpha, ctx->d_cstar,
+                         ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->flag, ctx->st));
+    // 6: posterior coarse field, local block roots, fused update with the pull
+    KL(1, launch_form_r(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_coef, ctx->d_scal,
+                     ctx->d_alpha, ctx->d_r, ctx->st));
+    int off = 0;
+    for (int w : ctx->waves) {
+        KL(w > 0 ? 1 : 0, launch_block_apply(ctx->d_r, (int)ctx->NR, ne, ctx->d_M49, ctx->d_block0, ctx->d_list + off, w,
+                              ctx->C.nRx, ctx->C.nRy, ctx->st));
+        off += w;
+    }
+    QhalfArgs A{};
+    A.b0 = ctx->buf[0];
+    A.b1 = ctx->buf[1];
+    A.par = ctx->par;
+    A.wtab = ctx->d_wtab;
+    A.from_philox = 0;
+    A.x = ctx->d_r;
+    A.with_pull = 1;
+    A.K = ctx->d_K32;
+    A.R = ctx->R;
+    A.obs_cell = ctx->d_cell;
+    A.Sd = ctx->d_Sd;
+    A.nobs = nobs;
+    A.tile_cnt = ctx->d_tile_cnt;
+    A.tile_obs = ctx->d_tile_obs;
+    A.tile_cap = ctx->tile_cap;
+    KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+    // diagnostics
+    CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if (diag) {
+        double* dst[] = {diag->phi, diag->c, diag->gamma, diag->zeta, diag->alpha, diag->neglogw};
+        double* src[] = {ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta, ctx->d_alpha, ctx->d_neglogw};
+        for (int i = 0; i < 6; ++i)
+            if (dst[i]) CK(cudaMemcpyAsync(dst[i], src[i], sizeof(double) * ne, cudaMemcpyDeviceToHost, ctx->st));
+    }
+    rc = read_flags(ctx);
+    if (diag) {
+        diag->c_bar = ctx->h_scal[0];
+        diag->beta = ctx->h_scal[1];
+    }
+    ctx->cycle++;
+    return rc;
+}
+
+int iewpf_set_drifters(iewpf_ctx_t* ctx, const double* xy, int n)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (n < 0 || n > ctx->P.n_drifters_max || (n > 0 && !xy)) return fail(ctx, IEWPF_EINVAL, "bad drifters");
+    CK(cudaSetDevice(ctx->dev));
+    ctx->nd = n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(ctx->d_xy, xy, sizeof(double) * 2 * n * ctx->G.ne, cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return IEWPF_OK;
+}
+
+int iewpf_get_drifters(iewpf_ctx_t* ctx, double* xy)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!xy) return fail(ctx, IEWPF_EINVAL, "null pointer");
+    CK(cudaSetDevice(ctx->dev));
+    if (ctx->nd > 0) {
+        CK(cudaMemcpyAsync(xy, ctx->d_xy, sizeof(double) * 2 * ctx->nd * ctx->G.ne, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return IEWPF_OK;
+}
+
+int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s, double* traj,
+                     int use_surrogate)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (use_surrogate) return fail(ctx, IEWPF_EINVAL, "the surrogate forecast is not available");
+    if (!xy0 || !traj || n < 1 || n > ctx->P.n_drifters_max || !(hours >= 0) || !(out_every_s > 0))
+        return fail(ctx, IEWPF_EINVAL, "bad drifter forecast arguments");
+    const double ratio = out_every_s / ctx->P.dt_model;
+    const int every = (int)std::lround(ratio);
+    if (every < 1 || std::fabs(ratio - every) > 1e-9)
+        return fail(ctx, IEWPF_EINVAL, "out_every_s must be a multiple of dt_model");
+    const int n_out = (int)std::floor(hours * 3600.0 / out_every_s + 1e-9) + 1;
+    const int ne = ctx->G.ne;
+    std::vector<double> rep((size_t)ne * n * 2);
+    for (int p = 0; p < ne; ++p) std::memcpy(&rep[(size_t)p * n * 2], xy0, sizeof(double) * 2 * n);
+    int rc;
+    if ((rc = iewpf_set_drifters(ctx, rep.data(), n))) return rc;
+    const size_t per = (size_t)ne * n * 2;
+    std::memcpy(traj, rep.data(), sizeof(double) * per);
+    for (int o = 1; o < n_out; ++o) {
+        if ((rc = iewpf_forecast(ctx, every, 1))) return rc;
+        if ((rc = iewpf_get_drifters(ctx, traj + per * o))) return rc;
+    }
+    return IEWPF_OK;
+}
+
+int iewpf_save(const iewpf_ctx_t* cctx, const char* path)
+{
+    iewpf_ctx* ctx = const_cast<iewpf_ctx*>(cctx);
+    if (!ctx) return IEWPF_EINVAL;
+    if (!path) return fail(ctx, IEWPF_EINVAL, "null path");
+    const size_t nstate = (size_t)ctx->G.ne * 3 * ctx->plane;
+    std::vector<float> st(nstate);
+    int rc = iewpf_get_state(ctx, st.data(), 0, nullptr);
+    if (rc) return rc;
+    std::vector<double> xy((size_t)ctx->G.ne * 2 * std::max(ctx->nd, 0));
+    if (ctx->nd > 0 && (rc = iewpf_get_drifters(ctx, xy.data()))) return rc;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, IEWPF_EINVAL, std::string("cannot open ") + path);
+    const uint32_t magic = 0x46505749u;   // "IWPF"
+    const int32_t hdr[5] = {ctx->P.nx, ctx->P.ny, ctx->G.ne, ctx->nd, 1};
+    bool ok = std::fwrite(&magic, 4, 1, f) == 1 && std::fwrite(hdr, 4, 5, f) == 5 &&
+              std::fwrite(&ctx->step, 4, 1, f) == 1 && std::fwrite(&ctx->cycle, 4, 1, f) == 1 &&
+              std::fwrite(st.data(), 4, nstate, f) == nstate &&
+              (xy.empty() || std::fwrite(xy.data(), 8, xy.size(), f) == xy.size());
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? IEWPF_OK : fail(ctx, IEWPF_EINVAL, "write failed");
+}
+
+int iewpf_load(iewpf_ctx_t* ctx, const char* path)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!path) return fail(ctx, IEWPF_EINVAL, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, IEWPF_EINVAL, std::string("cannot open ") + path);
+    uint32_t magic = 0, step = 0, cyc = 0;
+    int32_t hdr[5] = {0};
+    bool ok = std::fread(&magic, 4, 1, f) == 1 && std::fread(hdr, 4, 5, f) == 5 &&
+              std::fread(&step, 4, 1, f) == 1 && std::fread(&cyc, 4, 1, f) == 1;
+    if (!ok || magic != 0x46505749u || hdr[0] != ctx->P.nx || hdr[1] != ctx->P.ny || hdr[2] != ctx->G.ne ||
+        hdr[3] < 0 || hdr[3] > ctx->P.n_drifters_max) {
+        std::fclose(f);
+        return fail(ctx, IEWPF_EINVAL, "checkpoint does not match this context");
+    }
+    const size_t nstate = (size_t)ctx->G.ne * 3 * ctx->plane;
+    std::vector<float> st(nstate);
+    std::vector<double> xy((size_t)ctx->G.ne * 2 * hdr[3]);
+    ok = std::fread(st.data(), 4, nstate, f) == nstate && (xy.empty() || std::fread(xy.data(), 8, xy.size(), f) == xy.size());
+    std::fclose(f);
+    if (!ok) return fail(ctx, IEWPF_EINVAL, "truncated checkpoint");
+    int rc = iewpf_set_state(ctx, st.data(), 0, nullptr);
+    if (rc) return rc;
+    if ((rc = iewpf_set_drifters(ctx, xy.data(), hdr[3]))) return rc;
+    ctx->step = step;
+    ctx->cycle = cyc;
+    return IEWPF_OK;
+}
+
+int iewpf_get_counters(const iewpf_ctx_t* ctx, uint32_t* model_step, uint32_t* cycle)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (model_step) *model_step = ctx->step;
+    if (cycle) *cycle = ctx->cycle;
+    return IEWPF_OK;
+}
+
+int iewpf_set_counters(iewpf_ctx_t* ctx, uint32_t model_step, uint32_t cycle)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    ctx->step = model_step;
+    ctx->cycle = cycle;
+    return IEWPF_OK;
+}
+
+int iewpf_last_nsub(const iewpf_ctx_t* cctx, int* n_sub)
+{
+    iewpf_ctx* ctx = const_cast<iewpf_ctx*>(cctx);
+    if (!ctx) return IEWPF_EINVAL;
+    if (!n_sub) return fail(ctx, IEWPF_EINVAL, "null pointer");
+    CK(cudaSetDevice(ctx->dev));
+    CK(cudaMemcpyAsync(n_sub, ctx->nsub, sizeof(int) * ctx->G.ne, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return IEWPF_OK;
+}
+
+const char* iewpf_last_error(const iewpf_ctx_t* ctx)
+{
+    return ctx ? ctx->err.c_str() : kNullMsg;
+}
+
+int iewpf_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, int64_t n_blocks, uint32_t* out)
+{
+    if (!out || n_blocks < 0) return IEWPF_EINVAL;
+    uint32_t* d = nullptr;
+    if (cudaMalloc((void**)&d, sizeof(uint32_t) * 4 * (size_t)std::max<int64_t>(n_blocks, 1)) != cudaSuccess)
+        return IEWPF_ENOMEM;
+    int rc = IEWPF_OK;
+    if (launch_philox_blocks(seed, p, t, stream, n_blocks, d, 0) != cudaSuccess ||
+        cudaMemcpy(out, d, sizeof(uint32_t) * 4 * (size_t)n_blocks, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = IEWPF_ECUDA;
+    cudaFree(d);
+    return rc;
+}
+
+int iewpf_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, int64_t n, double* out64, float* out32)
+{
+    if (n < 0 || (!out64 && !out32)) return IEWPF_EINVAL;
+    double* d64 = nullptr;
+    float* d32 = nullptr;
+    const size_t m = (size_t)std::max<int64_t>(n, 1);
+    if ((out64 && cudaMalloc((void**)&d64, 8 * m) != cudaSuccess) ||
+        (out32 && cudaMalloc((void**)&d32, 4 * m) != cudaSuccess)) {
+        if (d64) cudaFree(d64);
+        return IEWPF_ENOMEM;
+    }
+    int rc = IEWPF_OK;
+    if (launch_normals(seed, p, t, stream, n, d64, d32, 0) != cudaSuccess ||
+        (out64 && cudaMemcpy(out64, d64, 8 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (out32 && cudaMemcpy(out32, d32, 4 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess))
+        rc = IEWPF_ECUDA;
+    if (d64) cudaFree(d64);
+    if (d32) cudaFree(d32);
+    return rc;
+}
+
+int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, const double* zeta, double* out2,
+                  double* alpha, double* cstar, double* neglogw)
+{
+    if (ne < 1 || !(N_psi > 0) || !c || !gamma || !zeta || !out2 || !alpha || !cstar) return IEWPF_EINVAL;
+    double* d = nullptr;
+    int* flag = nullptr;
+    const size_t n = (size_t)ne;
+    if (cudaMalloc((void**)&d, sizeof(double) * (6 * n + 4)) != cudaSuccess) return IEWPF_ENOMEM;
+    if (cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess) {
+        cudaFree(d);
+        return IEWPF_ENOMEM;
+    }
+    double *dc = d, *dg = d + n, *dz = d + 2 * n, *da = d + 3 * n, *ds = d + 4 * n, *dw = d + 5 * n,
+           *dsc = d + 6 * n;
+    int rc = IEWPF_OK, hf = 0;
+    if (cudaMemset(flag, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(dc, c, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dg, gamma, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dz, zeta, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        launch_weights_only(dc, dg, dz, ne, N_psi, da, ds, dw, dsc, flag, 0) != cudaSuccess ||
+        cudaMemcpy(out2, dsc, 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(alpha, da, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(cstar, ds, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (neglogw && cudaMemcpy(neglogw, dw, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = IEWPF_ECUDA;
+    cudaFree(d);
+    cudaFree(flag);
+    if (rc == IEWPF_OK && hf) {
+        if (hf & FLAG_NONFINITE) rc = IEWPF_ENONFINITE;
+        else if (hf & FLAG_BETA) rc = IEWPF_EBETA;
+        else if (hf & FLAG_DOMAIN) rc = IEWPF_EDOMAIN;
+    }
+    return rc;
+}
+
+int iewpf_pull_stencil(const iewpf_ctx_t* ctx, double* K)
+{
+    if (!ctx || !K) return IEWPF_EINVAL;
+    std::memcpy(K, ctx->K64.data(), sizeof(double) * ctx->K64.size());
+    return IEWPF_OK;
+}
+
+int iewpf_local_block(const iewpf_ctx_t* ctx, double* M)
+{
+    if (!ctx || !M) return IEWPF_EINVAL;
+    std::memcpy(M, ctx->M49.data(), sizeof(double) * ctx->M49.size());
+    return IEWPF_OK;
+}
+
+int iewpf_add_qhalf(iewpf_ctx_t* ctx, const float* x)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!x) return fail(ctx, IEWPF_EINVAL, "null pointer");
+    CK(cudaSetDevice(ctx->dev));
+    CK(cudaMemcpyAsync(ctx->d_r, x, sizeof(float) * ctx->NR * ctx->G.ne, cudaMemcpyHostToDevice, ctx->st));
+    QhalfArgs A{};
+    A.b0 = ctx->buf[0];
+    A.b1 = ctx->buf[1];
+    A.par = ctx->par;
+    A.wtab = ctx->d_wtab;
+    A.from_philox = 0;
+    A.x = ctx->d_r;
+    KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return IEWPF_OK;
+}
+
+int iewpf_stream(const iewpf_ctx_t* ctx, void** stream)
+{
+    if (!ctx || !stream) return IEWPF_EINVAL;
+    *stream = (void*)ctx->st;
+    return IEWPF_OK;
+}
+
+int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (n < 0 || !(dt > 0)) return fail(ctx, IEWPF_EINVAL, "bad substep arguments");
+    CK(cudaSetDevice(ctx->dev));
+    std::vector<int> ones(ctx->G.ne, n);
+    std::vector<float> dts(ctx->G.ne, (float)dt);
+    CK(cudaMemcpyAsync(ctx->nsub, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->dtp, dts.data(), sizeof(float) * dts.size(), cudaMemcpyHostToDevice, ctx->st));
+    for (int s = 0; s < n; ++s) KL(1, launch_rk2(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->st));
+    KL(1, launch_par_update(ctx->par, ctx->nsub, ctx->G.ne, ctx->work, ctx->st));
+    // the host vectors must outlive the copies
+    CK(cudaStreamSynchronize(ctx->st));
+    return IEWPF_OK;
+}
+
+int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps)
+{
+    if (!ctx || !particle_substeps) return IEWPF_EINVAL;
+    CK(cudaSetDevice(ctx->dev));
+    unsigned long long w = 0;
+    CK(cudaMemcpyAsync(&w, ctx->work, sizeof(w), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *particle_substeps = (int64_t)w;
+    return IEWPF_OK;
+}
+
+int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count)
+{
+    if (!ctx || !count) return IEWPF_EINVAL;
+    *count = ctx->launches;
+    return IEWPF_OK;
+}
+
+int iewpf_sizes(const iewpf_ctx_t* ctx, int* nRx, int* nRy, int* stencil_R)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (nRx) *nRx = ctx->C.nRx;
+    if (nRy) *nRy = ctx->C.nRy;
+    if (stencil_R) *stencil_R = ctx->R;
+    return IEWPF_OK;
+}
+
+}  // extern "C"

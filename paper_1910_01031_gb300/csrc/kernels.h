@@ -1,0 +1,90 @@
+// Host-side launchers of the IEWPF device kernels (internal interface
+// between the C ABI in api.cu and the kernel translation units).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace iewpf {
+
+// ---- stepper.cu -----------------------------------------------------------
+size_t rk2_smem_bytes();
+cudaError_t launch_rk2(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
+                       const Grid& G, cudaStream_t st);
+cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* amax, int* nsub, float* dtp,
+                       int* maxsub, const Grid& G, double courant, double dt_model, int fixed,
+                       cudaStream_t st);
+cudaError_t launch_par_update(int* par, const int* nsub, int ne, unsigned long long* work, cudaStream_t st);
+cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const int* nsub, const float* dtp,
+                         double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st);
+cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, const Grid& G, int* flag,
+                             cudaStream_t st);
+
+// ---- qhalf.cu -------------------------------------------------------------
+// psi += Q^{1/2} x (+ the optimal-proposal pull) for every particle.
+struct QhalfArgs {
+    float* b0;
+    float* b1;
+    const int* par;
+    const float* wtab;        // SOAR weights by fine offset [tab][tab]
+    // source of the coarse field: Philox (model error) or a device array
+    int from_philox;
+    uint64_t seed;
+    uint32_t t;
+    uint32_t stream;
+    const float* x;           // [ne][N_R]
+    // optimal-proposal pull (may be disabled)
+    int with_pull;
+    const float* K;           // [2][3][2R+1][2R+1]
+    int R;
+    const int* obs_cell;      // [nobs][2]
+    const double* Sd;         // [ne][2 nobs]
+    int nobs;
+    const int* tile_cnt;      // [ntiles]
+    const int* tile_obs;      // [ntiles][tile_cap]
+    int tile_cap;
+};
+cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cudaStream_t st);
+
+// ---- analysis.cu ----------------------------------------------------------
+cudaError_t launch_obs_setup(const double* xy, int nobs, const Grid& G, const Coarse& C, double dx, double dy,
+                             int R, int* obs_cell, int* obs_block0, int* tile_cnt, int* tile_obs, int tile_cap,
+                             int* flag, cudaStream_t st);
+cudaError_t launch_innovate(const float* b0, const float* b1, const int* par, const int* obs_cell,
+                            const double* y, int nobs, const Grid& G, double H, double* d, cudaStream_t st);
+cudaError_t launch_hqht(const double* K64, int R, const int* obs_cell, int nobs, const Grid& G, int dense,
+                        double sigma2, double* M, cudaStream_t st);
+cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, cudaStream_t st);
+cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, int n, const double* d,
+                         double* Sd, double* phi, int ne, cudaStream_t st);
+cudaError_t launch_rand_dots(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
+                             double* partial, int nblk, cudaStream_t st);
+int rand_dots_blocks(int NR);
+cudaError_t launch_sync_alpha(const double* phi, const double* partial, int nblk, int ne, double NR,
+                              double N_psi, double logNe, double* c, double* gamma, double* zeta,
+                              double* alpha, double* cstar, double* neglogw, double* coef /*[ne][2]*/,
+                              double* scal /*[4]: cbar, beta*/, int* flag, cudaStream_t st);
+cudaError_t launch_weights_only(const double* c, const double* gamma, const double* zeta, int ne, double N_psi,
+                                double* alpha, double* cstar, double* neglogw, double* scal, int* flag,
+                                cudaStream_t st);
+cudaError_t launch_form_r(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
+                          const double* coef, const double* scal, const double* alpha, float* r,
+                          cudaStream_t st);
+cudaError_t launch_block_apply(float* r, int NR, int ne, const float* M49, const int* obs_block0,
+                               const int* list, int nlist, int nRx, int nRy, cudaStream_t st);
+cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,
+                                 uint32_t* out, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n, double* o64,
+                           float* o32, cudaStream_t st);
+
+// error flags set by device code
+enum : int {
+    FLAG_NOTPD = 1,
+    FLAG_BETA = 2,
+    FLAG_DOMAIN = 4,
+    FLAG_NONFINITE = 8,
+    FLAG_TILE_OVERFLOW = 16,
+};
+
+}  // namespace iewpf

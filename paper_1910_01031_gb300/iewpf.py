@@ -1,0 +1,323 @@
+"""ctypes binding of libiewpf.so (include/iewpf.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of the library; this module
+converts numpy arrays / torch tensors to pointers and error codes to
+exceptions.  Importing it does not need a GPU; loading the library does need
+it to be built (``build.build()``), and calls fail loudly without it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IEWPF_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EBETA", -6: "EDOMAIN",
+          -7: "ETIMEOUT", -8: "ENOTPD"}
+OBS_DRIFTER, OBS_MOORING = 0, 1
+
+# every entry point declared in include/iewpf.h
+EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state", "iewpf_forecast",
+           "iewpf_forecast_fixed", "iewpf_assimilate", "iewpf_set_drifters", "iewpf_get_drifters",
+           "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
+           "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
+           "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
+           "iewpf_substeps", "iewpf_launch_count", "iewpf_work"]
+
+
+class IewpfError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("g", ctypes.c_double), ("f", ctypes.c_double), ("H_eq", ctypes.c_double),
+                ("theta", ctypes.c_double), ("courant", ctypes.c_double), ("dt_model", ctypes.c_double),
+                ("c_omega", ctypes.c_int), ("q0", ctypes.c_double), ("L0", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("n_particles", ctypes.c_int), ("obs_kind", ctypes.c_int),
+                ("n_obs_max", ctypes.c_int), ("obs_sigma", ctypes.c_double), ("dense_S", ctypes.c_int),
+                ("instance_id", ctypes.c_int), ("n_drifters_max", ctypes.c_int)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("n_obs", ctypes.c_int), ("xy", ctypes.POINTER(ctypes.c_double)),
+                ("value", ctypes.POINTER(ctypes.c_double))]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("c_bar", ctypes.c_double), ("beta", ctypes.c_double)] + \
+        [(k, ctypes.POINTER(ctypes.c_double)) for k in ("phi", "c", "gamma", "zeta", "alpha", "neglogw")]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libiewpf.so (building it first if sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libiewpf.so is not built (run paper_1910_01031_gb300.build.build())")
+    L = ctypes.CDLL(_build.LIB)
+    c = ctypes
+    L.iewpf_create.argtypes = [c.POINTER(Params), _dp, c.POINTER(c.c_void_p)]
+    L.iewpf_destroy.argtypes = [_vp]
+    L.iewpf_set_state.argtypes = [_vp, _vp, c.c_int, _vp]
+    L.iewpf_get_state.argtypes = [_vp, _vp, c.c_int, _vp]
+    L.iewpf_forecast.argtypes = [_vp, c.c_int, c.c_int]
+    L.iewpf_forecast_fixed.argtypes = [_vp, c.c_int, c.c_int, c.c_int]
+    L.iewpf_assimilate.argtypes = [_vp, c.POINTER(Obs), c.POINTER(Diag)]
+    L.iewpf_set_drifters.argtypes = [_vp, _dp, c.c_int]
+    L.iewpf_get_drifters.argtypes = [_vp, _dp]
+    L.drifter_forecast.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, c.c_int]
+    L.iewpf_save.argtypes = [_vp, c.c_char_p]
+    L.iewpf_load.argtypes = [_vp, c.c_char_p]
+    L.iewpf_get_counters.argtypes = [_vp, _u32p, _u32p]
+    L.iewpf_set_counters.argtypes = [_vp, c.c_uint32, c.c_uint32]
+    L.iewpf_last_nsub.argtypes = [_vp, _ip]
+    L.iewpf_last_error.argtypes = [_vp]
+    L.iewpf_last_error.restype = c.c_char_p
+    L.iewpf_philox_blocks.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_int64, _u32p]
+    L.iewpf_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_int64, _dp, _fp]
+    L.iewpf_weights.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.iewpf_pull_stencil.argtypes = [_vp, _dp]
+    L.iewpf_local_block.argtypes = [_vp, _dp]
+    L.iewpf_add_qhalf.argtypes = [_vp, _fp]
+    L.iewpf_sizes.argtypes = [_vp, _ip, _ip, _ip]
+    L.iewpf_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
+    L.iewpf_substeps.argtypes = [_vp, c.c_int, c.c_double]
+    L.iewpf_launch_count.argtypes = [_vp, c.POINTER(c.c_int64)]
+    L.iewpf_work.argtypes = [_vp, c.POINTER(c.c_int64)]
+    _lib = L
+    return L
+
+
+def _ptr(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def params_from_config(cfg, n_drifters_max=0, n_obs_max=None):
+    """iewpf_params_t from a synth.Config."""
+    return Params(cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.g, cfg.f, cfg.H, cfg.theta, cfg.courant, cfg.dt_model,
+                  cfg.c_omega, cfg.q0, cfg.L0, cfg.seed, cfg.n_particles, cfg.obs_kind,
+                  cfg.n_obs if n_obs_max is None else n_obs_max, cfg.obs_sigma, cfg.dense_S, 0,
+                  n_drifters_max)
+
+
+class Ensemble:
+    """An IEWPF context: the ensemble state on the GPU and its operations."""
+
+    def __init__(self, params: Params, mooring_xy=None):
+        self.L = load()
+        self.P = params
+        h = ctypes.c_void_p()
+        mx = None if mooring_xy is None else _f64(mooring_xy, (-1, 2))
+        rc = self.L.iewpf_create(ctypes.byref(params), _ptr(mx), ctypes.byref(h))
+        if rc != IEWPF_OK:
+            raise IewpfError(rc, "iewpf_create")
+        self.h = h
+        self.ne, self.nx, self.ny = params.n_particles, params.nx, params.ny
+        nrx, nry, R = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.L.iewpf_sizes(self.h, ctypes.byref(nrx), ctypes.byref(nry), ctypes.byref(R))
+        self.nRx, self.nRy, self.R = nrx.value, nry.value, R.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.iewpf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc, what):
+        if rc != IEWPF_OK:
+            msg = self.L.iewpf_last_error(self.h)
+            raise IewpfError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    @property
+    def shape(self):
+        return (self.ne, 3, self.ny, self.nx)
+
+    def set_state(self, U, stream=None):
+        """U: numpy array or CUDA torch tensor [N_e][3][ny][nx] (float32)."""
+        if hasattr(U, "data_ptr") and getattr(U, "is_cuda", False):
+            assert tuple(U.shape) == self.shape and U.is_contiguous() and str(U.dtype) == "torch.float32"
+            s = stream if stream is not None else _torch_stream()
+            self._chk(self.L.iewpf_set_state(self.h, ctypes.c_void_p(U.data_ptr()), 1, s), "set_state")
+            return
+        a = np.ascontiguousarray(U, dtype=np.float32).reshape(self.shape)
+        self._chk(self.L.iewpf_set_state(self.h, a.ctypes.data_as(_vp), 0, None), "set_state")
+
+    def get_state(self, out=None, stream=None):
+        if out is not None and hasattr(out, "data_ptr") and getattr(out, "is_cuda", False):
+            s = stream if stream is not None else _torch_stream()
+            self._chk(self.L.iewpf_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 1, s), "get_state")
+            return out
+        a = np.empty(self.shape, np.float32)
+        self._chk(self.L.iewpf_get_state(self.h, a.ctypes.data_as(_vp), 0, None), "get_state")
+        return a
+
+    def forecast(self, n_steps, add_model_error=True):
+        self._chk(self.L.iewpf_forecast(self.h, int(n_steps), int(bool(add_model_error))), "forecast")
+
+    def forecast_fixed(self, n_steps, add_model_error, n_sub):
+        self._chk(self.L.iewpf_forecast_fixed(self.h, int(n_steps), int(bool(add_model_error)), int(n_sub)),
+                  "forecast_fixed")
+
+    def assimilate(self, xy, values, diag=True):
+        values = _f64(values, (-1, 2))
+        n = values.shape[0]
+        xy = None if xy is None else _f64(xy, (-1, 2))
+        obs = Obs(n, _ptr(xy), _ptr(values))
+        out = None
+        dptr = None
+        if diag:
+            out = {k: np.zeros(self.ne) for k in ("phi", "c", "gamma", "zeta", "alpha", "neglogw")}
+            d = Diag(0.0, 0.0, *[_ptr(out[k]) for k in ("phi", "c", "gamma", "zeta", "alpha", "neglogw")])
+            dptr = ctypes.byref(d)
+        self._chk(self.L.iewpf_assimilate(self.h, ctypes.byref(obs), dptr), "assimilate")
+        if diag:
+            out["cbar"] = d.c_bar
+            out["beta"] = d.beta
+        return out
+
+    def set_drifters(self, xy):
+        xy = _f64(xy)
+        n = 0 if xy.size == 0 else xy.reshape(self.ne, -1, 2).shape[1]
+        self._chk(self.L.iewpf_set_drifters(self.h, _ptr(xy), n), "set_drifters")
+        self.nd = n
+
+    def get_drifters(self):
+        out = np.zeros((self.ne, getattr(self, "nd", 0), 2))
+        self._chk(self.L.iewpf_get_drifters(self.h, _ptr(out)), "get_drifters")
+        return out
+
+    def drifter_forecast(self, xy0, hours, out_every_s):
+        xy0 = _f64(xy0, (-1, 2))
+        n = xy0.shape[0]
+        n_out = int(np.floor(hours * 3600.0 / out_every_s + 1e-9)) + 1
+        traj = np.zeros((n_out, self.ne, n, 2))
+        self._chk(self.L.drifter_forecast(self.h, _ptr(xy0), n, float(hours), float(out_every_s), _ptr(traj), 0),
+                  "drifter_forecast")
+        self.nd = n
+        return traj
+
+    def save(self, path):
+        self._chk(self.L.iewpf_save(self.h, str(path).encode()), "save")
+
+    def load_checkpoint(self, path):
+        self._chk(self.L.iewpf_load(self.h, str(path).encode()), "load")
+
+    def counters(self):
+        a, b = ctypes.c_uint32(), ctypes.c_uint32()
+        self._chk(self.L.iewpf_get_counters(self.h, ctypes.byref(a), ctypes.byref(b)), "get_counters")
+        return a.value, b.value
+
+    def set_counters(self, step, cycle):
+        self._chk(self.L.iewpf_set_counters(self.h, int(step), int(cycle)), "set_counters")
+
+    def last_nsub(self):
+        out = np.zeros(self.ne, np.int32)
+        self._chk(self.L.iewpf_last_nsub(self.h, _ptr(out, _ip)), "last_nsub")
+        return out
+
+    def pull_stencil(self):
+        W = 2 * self.R + 1
+        K = np.zeros((2, 3, W, W))
+        self._chk(self.L.iewpf_pull_stencil(self.h, _ptr(K)), "pull_stencil")
+        return K
+
+    def local_block(self):
+        M = np.zeros((49, 49))
+        self._chk(self.L.iewpf_local_block(self.h, _ptr(M)), "local_block")
+        return M
+
+    def stream(self):
+        """The context's CUDA stream handle (an int usable by torch.cuda.ExternalStream)."""
+        s = ctypes.c_void_p()
+        self._chk(self.L.iewpf_stream(self.h, ctypes.byref(s)), "stream")
+        return s.value or 0
+
+    def substeps(self, n, dt):
+        self._chk(self.L.iewpf_substeps(self.h, int(n), float(dt)), "substeps")
+
+    def launch_count(self):
+        c = ctypes.c_int64()
+        self._chk(self.L.iewpf_launch_count(self.h, ctypes.byref(c)), "launch_count")
+        return c.value
+
+    def work(self):
+        """Particle scheme steps executed so far."""
+        c = ctypes.c_int64()
+        self._chk(self.L.iewpf_work(self.h, ctypes.byref(c)), "work")
+        return c.value
+
+    def add_qhalf(self, x):
+        x = np.ascontiguousarray(x, np.float32).reshape(self.ne, self.nRx * self.nRy)
+        self._chk(self.L.iewpf_add_qhalf(self.h, _ptr(x, _fp)), "add_qhalf")
+
+
+def _torch_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def philox_blocks(seed, p, t, stream, n_blocks):
+    L = load()
+    out = np.zeros((n_blocks, 4), np.uint32)
+    rc = L.iewpf_philox_blocks(seed, p, t, stream, n_blocks, _ptr(out, _u32p))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "philox_blocks")
+    return out
+
+
+def normals(seed, p, t, stream, n):
+    L = load()
+    o64 = np.zeros(n)
+    o32 = np.zeros(n, np.float32)
+    rc = L.iewpf_normals(seed, p, t, stream, n, _ptr(o64), _ptr(o32, _fp))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "normals")
+    return o64, o32
+
+
+def weights(c, gamma, zeta, N_psi):
+    """GPU ensemble-wide step: returns dict cbar, beta, alpha, cstar, neglogw."""
+    L = load()
+    c, gamma, zeta = _f64(c), _f64(gamma), _f64(zeta)
+    ne = c.size
+    out2 = np.zeros(2)
+    alpha, cstar, nlw = np.zeros(ne), np.zeros(ne), np.zeros(ne)
+    rc = L.iewpf_weights(ne, float(N_psi), _ptr(c), _ptr(gamma), _ptr(zeta), _ptr(out2), _ptr(alpha),
+                         _ptr(cstar), _ptr(nlw))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "weights")
+    return {"cbar": out2[0], "beta": out2[1], "alpha": alpha, "cstar": cstar, "neglogw": nlw}

@@ -66,21 +66,27 @@ class Config:
         return asdict(self)
 
 
+def _cfg(name, n, defaults, kw):
+    args = dict(defaults)
+    args.update(kw)
+    return Config(name, n, n, **args)
+
+
 def config1(**kw):
-    return Config("iewpf_64x64_ne10_1drifter", 64, 64, n_particles=10, n_obs=1, **kw)
+    return _cfg("iewpf_64x64_ne10_1drifter", 64, {"n_particles": 10, "n_obs": 1}, kw)
 
 
 def config2(**kw):
-    return Config("iewpf_512x512_ne100_64drifters", 512, 512, n_particles=100, n_obs=64, **kw)
+    return _cfg("iewpf_512x512_ne100_64drifters", 512, {"n_particles": 100, "n_obs": 64}, kw)
 
 
 def config4(**kw):
-    return Config("iewpf_1024x1024_ne1000_1521moorings", 1024, 1024, n_particles=1000,
-                  obs_kind=OBS_MOORING, n_obs=1521, **kw)
+    return _cfg("iewpf_1024x1024_ne1000_1521moorings", 1024,
+                {"n_particles": 1000, "obs_kind": OBS_MOORING, "n_obs": 1521}, kw)
 
 
 def config5(**kw):
-    return Config("surrogate_256x256_ne1000_64drifters", 256, 256, n_particles=1000, n_obs=64, **kw)
+    return _cfg("surrogate_256x256_ne1000_64drifters", 256, {"n_particles": 1000, "n_obs": 64}, kw)
 
 
 def config3(seed: int = 3, **kw):

@@ -1,0 +1,145 @@
+"""GPU parity of the IEWPF analysis against the FP64 oracle, through the C
+ABI.  Tolerances: FP64 weights 1e-10 relative on shared inputs; gamma and
+zeta (no state dependence) 1e-10; state after the analysis 1e-5 relative L2
+(FP32 state); phi and c 1e-4 relative (they inherit the FP32 state's
+rounding through innovations of a few m^2/s)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1910_01031_gb300 import iewpf, synth
+
+from gpu_common import ensemble, oracle_problem, ragged_config, rel_l2, start_state
+
+pytestmark = pytest.mark.gpu
+
+
+def test_pull_stencil_and_block_root_match_oracle():
+    for cfg in (synth.config1(), ragged_config(dy=2500.0)):
+        ens = ensemble(cfg)
+        P = oracle_problem(cfg)
+        K = O.pull_stencil(P)
+        Kg = ens.pull_stencil()
+        assert Kg.shape == K.shape
+        assert np.max(np.abs(Kg - K)) <= 1e-12 * np.max(np.abs(K))
+        M = O.local_block_sqrt(P)
+        assert np.max(np.abs(ens.local_block() - M)) <= 1e-10
+
+
+def _scalars_inputs(seed, ne, N, Ny):
+    rng = np.random.default_rng(seed)
+    c = rng.chisquare(Ny, ne) + math.log(ne)
+    gamma = N + math.sqrt(2 * N) * rng.standard_normal(ne)
+    zeta = N + math.sqrt(2 * N) * rng.standard_normal(ne)
+    return c, gamma, zeta
+
+
+@pytest.mark.parametrize("ne,N,Ny", [(10, 12288, 2), (100, 786432, 128), (1000, 3145728, 3042), (3, 60.0, 2)])
+def test_weights_stage_matches_oracle_to_1e10(ne, N, Ny):
+    c, gamma, zeta = _scalars_inputs(ne + Ny, ne, N, Ny)
+    if N < 100:        # tiny state: gamma far from N, alpha far from 1
+        gamma = np.array([40.0, 75.0, 61.0])
+        zeta = np.array([55.0, 70.0, 64.0])
+        c = np.array([3.0, 4.5, 3.7])
+    g = iewpf.weights(c, gamma, zeta, N)
+    o = O.iewpf_scalars(c, gamma, zeta, N)
+    assert math.isclose(g["cbar"], o["cbar"], rel_tol=1e-12)
+    assert math.isclose(g["beta"], o["beta"], rel_tol=1e-10)
+    assert np.allclose(g["alpha"], o["alpha"], rtol=1e-10, atol=0)
+    assert np.allclose(g["neglogw"], o["neglogw"], rtol=1e-10, atol=0)
+    # every particle reaches the target weight on the GPU as well
+    assert np.allclose(g["neglogw"], g["cbar"], rtol=1e-10, atol=0)
+
+
+def test_weights_stage_reports_negative_beta():
+    # c_bar - c_i very negative against zeta: beta < 0
+    with pytest.raises(iewpf.IewpfError) as e:
+        iewpf.weights(np.array([0.0, 1000.0, 0.0]), np.array([50.0, 50, 50]), np.array([50.0, 50, 50]), 60.0)
+    assert e.value.name == "EBETA"
+
+
+def _obs_for(cfg, U, cells, cycle=0):
+    noise = synth.obs_noise(cfg, len(cells), cycle)
+    return synth.obs_from_state(cfg, U, cells, noise)
+
+
+@pytest.mark.parametrize("dense", [1, 0])
+def test_assimilate_matches_oracle_drifters(dense):
+    cfg = synth.config1(dense_S=dense, n_obs=3)
+    ne = cfg.n_particles
+    U32, U64 = start_state(cfg, ne)
+    P = oracle_problem(cfg)
+    ens = ensemble(cfg)
+    ens.set_state(U32)
+    xy = np.array([[20.3e3, 30.1e3], [26.9e3, 34.5e3], [90.2e3, 100.7e3]])   # two close, one far
+    cells = [O.obs_cell(P, *p) for p in xy]
+    truth = synth.initial_state(cfg, 1, seed=99)[0]
+    y = _obs_for(cfg, truth, np.array(cells))
+    dg = ens.assimilate(xy, y)
+    ref, do = O.assimilate(P, U64, cells, y, t=0, dense=bool(dense))
+    assert np.allclose(dg["gamma"], do["gamma"], rtol=1e-10, atol=0)
+    assert np.allclose(dg["zeta"], do["zeta"], rtol=1e-10, atol=0)
+    assert np.allclose(dg["phi"], do["phi"], rtol=1e-4, atol=0)
+    assert np.allclose(dg["c"], do["c"], rtol=1e-4, atol=0)
+    assert math.isclose(dg["beta"], do["beta"], rel_tol=1e-6)
+    assert np.allclose(dg["alpha"], do["alpha"], rtol=1e-6, atol=0)
+    assert np.allclose(dg["neglogw"], dg["cbar"], rtol=1e-10, atol=0)
+    e = rel_l2(ens.get_state(), ref)
+    assert e < 1e-5, e
+    assert ens.counters() == (0, 1)
+
+
+def test_assimilate_matches_oracle_moorings_ragged():
+    cfg = ragged_config(obs_kind=synth.OBS_MOORING, n_obs=4)
+    ne = cfg.n_particles
+    cells = np.array([[5, 7], [36, 9], [60, 30], [20, 44]], dtype=np.int32)
+    xy = synth.cell_positions(cfg, cells)
+    U32, U64 = start_state(cfg, ne)
+    P = oracle_problem(cfg)
+    ens = ensemble(cfg, mooring_xy=xy)
+    ens.set_state(U32)
+    truth = synth.initial_state(cfg, 1, seed=5)[0]
+    ref = U64
+    for cycle in range(2):
+        y = _obs_for(cfg, truth, cells, cycle)
+        dg = ens.assimilate(None, y)
+        ref, do = O.assimilate(P, ref, [tuple(c) for c in cells], y, t=cycle, dense=True)
+        assert np.allclose(dg["gamma"], do["gamma"], rtol=1e-10, atol=0)
+        assert np.allclose(dg["phi"], do["phi"], rtol=1e-4, atol=0)
+        e = rel_l2(ens.get_state(), ref)
+        assert e < 1e-5, (cycle, e)
+
+
+def test_full_cycle_matches_oracle():
+    """Forecast 5 model steps (model error on the first 4) then assimilate,
+    twice, on the 64 x 64 ten-particle one-drifter problem."""
+    cfg = synth.config1()
+    ne = cfg.n_particles
+    U32, U64 = start_state(cfg, ne)
+    P = oracle_problem(cfg)
+    ens = ensemble(cfg)
+    ens.set_state(U32)
+    ref = U64
+    truth = synth.initial_state(cfg, 1, seed=3)[0]
+    xy = synth.drifter_positions(cfg)
+    cells = [O.obs_cell(P, *p) for p in xy]
+    step = 0
+    for cycle in range(2):
+        ens.forecast(4, True)
+        ens.forecast(1, False)
+        ref, _, _ = O.forecast(P, ref, 5, [1, 1, 1, 1, 0], t0=step)
+        step += 5
+        y = _obs_for(cfg, truth, np.array(cells), cycle)
+        ens.assimilate(xy, y)
+        ref, _ = O.assimilate(P, ref, cells, y, t=cycle)
+        e = rel_l2(ens.get_state(), ref)
+        assert e < 1e-5, (cycle, e)
+
+
+def test_assimilate_rejects_bad_observations():
+    cfg = synth.config1()
+    ens = ensemble(cfg)
+    with pytest.raises(iewpf.IewpfError):
+        ens.assimilate(np.zeros((2, 2)), np.zeros((2, 2)))     # more than n_obs_max
