@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle·cell-steps/s"
 UNIT = "particle*cell*step/s"
 BYTES_PER_CELL_STEP = 24          # read (eta, hu, hv) + write (eta, hu, hv), float32
-FLOPS_PER_CELL_STEP = 490         # FP32 operations of one scheme step per cell
+FLOPS_PER_CELL_STEP = 490         # FP32 operations of one scheme step per cell, counted from the scheme
 
 
 def _dist():

@@ -4,7 +4,7 @@
  * This file is test infrastructure.  Only tests/, __graft_entry__.smoke() and
  * bench.py's cpu_baseline leg may load it.  It shares no code with the CUDA
  * path under paper_1910_01031_gb300/csrc: both are written independently from
- * the paper (arXiv 1910.01031) and from the scheme note in the design doc.
+ * the paper (arXiv 1910.01031).
  *
  * Everything here is plain loops in double precision, in the order the paper
  * states the operations.  OpenMP is used only to run independent particles on
@@ -87,8 +87,12 @@ void orc_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream,
 
 /* ------------------------------------------------------------------------ */
 /* Rotating shallow-water stepper (Sec. 3.1, eqs. swe_full, swecfl).        */
-/* Central-upwind fluxes with the Coriolis-adjusted reconstruction of eta;  */
-/* the scheme is written out in DESIGN.md ("stepper").                      */
+/* Central-upwind fluxes (Kurganov-Petrova form) for mass and normal        */
+/* momentum, tangential momentum carried by the mass flux with the upwind   */
+/* tangential velocity, and a reconstruction of eta through the Coriolis-   */
+/* adjusted potential K = g eta - f V (V_x = v), limited by the generalized */
+/* minmod, so that a jet in discrete geostrophic balance (Sec. 3.1,         */
+/* eq. geostrophic_balance_cont) has continuous face values.                */
 /* ------------------------------------------------------------------------ */
 static inline int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
