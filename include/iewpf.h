@@ -207,6 +207,34 @@ IEWPF_API int iewpf_weights(int ne, double N_psi, const double* c, const double*
                   const double* zeta, double* out2, double* alpha, double* cstar,
                   double* neglogw);
 
+/* Largest ensemble iewpf_weights_noalloc accepts. */
+#define IEWPF_WEIGHTS_NOALLOC_MAX_NE 4096
+
+/* iewpf_weights for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a service of the library, not a step of the
+ * method.  Some callers may not call cudaMalloc: hosts whose device memory
+ * belongs to a pooling allocator (a framework's caching allocator that must
+ * see every allocation), and latency-bound loops where cudaMalloc's implicit
+ * device synchronisation is not acceptable.  This entry point computes the
+ * same results as iewpf_weights (same kernel, same arguments and errors) but
+ * allocates nothing: it calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch is a fixed array of 6 x 4096 + 8 doubles (about
+ * 192 KiB) in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.
+ *   - ne must not exceed IEWPF_WEIGHTS_NOALLOC_MAX_NE (4096); larger ensembles
+ *     get IEWPF_EINVAL before any GPU work.
+ *   - The first call on a device looks up the scratch's device address with
+ *     cudaGetSymbolAddress (with that device current) and keeps it; make that
+ *     first call before any stream capture on the device.
+ *   - Every call shares the one array, which keeps the last call's contents;
+ *     the call clears its error flag itself.  Calls whose GPU work overlaps
+ *     (from several host threads) race on the array: serialise them.
+ *   - Inputs and outputs are host arrays, copied synchronously on the legacy
+ *     default stream of the current device. */
+IEWPF_API int iewpf_weights_noalloc(int ne, double N_psi, const double* c, const double* gamma,
+                                    const double* zeta, double* out2, double* alpha, double* cstar,
+                                    double* neglogw);
+
 /* The context's precomputed pull stencils: K[2][3][2R+1][2R+1] float64,
  * R = 7 c_omega (unit hu, unit hv observation; fields eta, hu, hv). */
 IEWPF_API int iewpf_pull_stencil(const iewpf_ctx_t* ctx, double* K);

@@ -25,7 +25,8 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
-           "iewpf_substeps", "iewpf_launch_count", "iewpf_work"]
+           "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc"]
+WEIGHTS_NOALLOC_MAX_NE = 4096
 
 
 class IewpfError(RuntimeError):
@@ -98,6 +99,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_philox_blocks.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_int64, _u32p]
     L.iewpf_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_int64, _dp, _fp]
     L.iewpf_weights.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.iewpf_weights_noalloc.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_pull_stencil.argtypes = [_vp, _dp]
     L.iewpf_local_block.argtypes = [_vp, _dp]
     L.iewpf_add_qhalf.argtypes = [_vp, _fp]
@@ -309,15 +311,17 @@ def normals(seed, p, t, stream, n):
     return o64, o32
 
 
-def weights(c, gamma, zeta, N_psi):
-    """GPU ensemble-wide step: returns dict cbar, beta, alpha, cstar, neglogw."""
+def weights(c, gamma, zeta, N_psi, noalloc=False):
+    """GPU ensemble-wide step: returns dict cbar, beta, alpha, cstar, neglogw.
+    noalloc=True uses iewpf_weights_noalloc (no device allocation; at most
+    WEIGHTS_NOALLOC_MAX_NE particles)."""
     L = load()
     c, gamma, zeta = _f64(c), _f64(gamma), _f64(zeta)
     ne = c.size
     out2 = np.zeros(2)
     alpha, cstar, nlw = np.zeros(ne), np.zeros(ne), np.zeros(ne)
-    rc = L.iewpf_weights(ne, float(N_psi), _ptr(c), _ptr(gamma), _ptr(zeta), _ptr(out2), _ptr(alpha),
-                         _ptr(cstar), _ptr(nlw))
+    fn = L.iewpf_weights_noalloc if noalloc else L.iewpf_weights
+    rc = fn(ne, float(N_psi), _ptr(c), _ptr(gamma), _ptr(zeta), _ptr(out2), _ptr(alpha), _ptr(cstar), _ptr(nlw))
     if rc != IEWPF_OK:
         raise IewpfError(rc, "weights")
     return {"cbar": out2[0], "beta": out2[1], "alpha": alpha, "cstar": cstar, "neglogw": nlw}
