@@ -210,7 +210,8 @@ def run_ours(args, rank, world, local):
         pass
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": traffic,
-                "kernel": "rk2_kernel (fused SSP-RK2 scheme step)",
+                "kernel": "rk2_march_kernel (register-marching SSP-RK2 scheme step), shape (kind, nc, rows, warps) = %s"
+                          % (ens.stepper(),),
                 "per_launch_ms": round(launch_s * 1e3, 4),
                 "alu": {"achieved": round(achieved_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                         "frac": round(achieved_tflops / fp32_peak, 4)}}

@@ -261,6 +261,21 @@ IEWPF_API int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt);
  * step over nx*ny cells. */
 IEWPF_API int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps);
 
+/* Scheme-step kernel of the context (Sec. 3.1; all kinds compute the same
+ * scheme).  kind 0: shared-memory tile kernel with IEEE division and square
+ * root; kind 1: register-marching kernel with nc (2, 3 or 4) columns per
+ * lane, `rows` rows per chunk and `warps` (1..8) warps per CTA, using the
+ * hardware reciprocal and reciprocal square root.  Marching shapes give
+ * bit-identical results to one another. */
+IEWPF_API int iewpf_set_stepper(iewpf_ctx_t* ctx, int kind, int nc, int rows, int warps);
+
+/* Autotuner: times every marching shape on the context's own problem (the
+ * state is left unchanged) and keeps the fastest; shape[4] (may be NULL)
+ * receives (kind, nc, rows, warps).  Runs by itself before the first
+ * forecast unless iewpf_set_stepper was called. */
+IEWPF_API int iewpf_tune(iewpf_ctx_t* ctx, int* shape);
+IEWPF_API int iewpf_get_stepper(const iewpf_ctx_t* ctx, int* shape);
+
 /* Number of kernels the context has launched so far. */
 IEWPF_API int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count);
 

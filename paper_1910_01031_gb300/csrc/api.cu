@@ -81,6 +81,10 @@ struct iewpf_ctx {
     // counters
     uint32_t step = 0, cycle = 0;
     int64_t launches = 0;    // kernels launched
+    // scheme-step kernel: 0 = shared-memory tile kernel, 1 = register march
+    int stepper = 1;
+    MarchShape shape{2, 64, 4};
+    bool tuned = false;
     std::string err;
 };
 
@@ -278,6 +282,60 @@ void build_block_root(const iewpf_params_t& P, std::vector<double>& M)
     }
 }
 
+cudaError_t launch_step(iewpf_ctx* ctx, int s)
+{
+    if (ctx->stepper == 0)
+        return launch_rk2(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->st);
+    return launch_rk2_march(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->shape, ctx->st);
+}
+
+// Time every candidate shape of the marching kernel on the context's own
+// problem and keep the fastest.  A probe launch reads the current state and
+// writes the other buffer without flipping the parity, so the state is left
+// as it was; all shapes compute identical values.
+int tune_stepper(iewpf_ctx* ctx)
+{
+    static const int ncs[] = {2, 3, 4};
+    static const int ths[] = {16, 32, 64, 128};
+    static const int wps[] = {2, 4, 8};
+    std::vector<int> ones(ctx->G.ne, 1);
+    std::vector<float> dts(ctx->G.ne, (float)(ctx->P.dt_model / 16.0));
+    CK(cudaMemcpyAsync(ctx->nsub, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->dtp, dts.data(), sizeof(float) * dts.size(), cudaMemcpyHostToDevice, ctx->st));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    MarchShape best_shape = ctx->shape;
+    for (int nc : ncs)
+        for (int th : ths) {
+            if (th > 2 * ctx->G.ny) continue;
+            for (int w : wps) {
+                MarchShape sh{nc, th, w};
+                CK(launch_rk2_march(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, 0, ctx->G, sh, ctx->st));
+                CK(cudaEventRecord(a, ctx->st));
+                for (int r = 0; r < 3; ++r)
+                    CK(launch_rk2_march(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, 0, ctx->G, sh,
+                                        ctx->st));
+                CK(cudaEventRecord(b, ctx->st));
+                CK(cudaEventSynchronize(b));
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                ctx->launches += 4;
+                if (ms < best) {
+                    best = ms;
+                    best_shape = sh;
+                }
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->shape = best_shape;
+    ctx->stepper = 1;
+    ctx->tuned = true;
+    return IEWPF_OK;
+}
+
 int fdiv(double x, double d) { return (int)std::floor(x / d); }
 int posmod(int a, int n) { return ((a % n) + n) % n; }
 
@@ -389,6 +447,8 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
     if (!ctx) return IEWPF_EINVAL;
     if (n_steps < 0) return fail(ctx, IEWPF_EINVAL, "n_model_steps < 0");
     CK(cudaSetDevice(ctx->dev));
+    int rc;
+    if (!ctx->tuned && (rc = tune_stepper(ctx))) return rc;
     for (int k = 0; k < n_steps; ++k) {
         KL(fixed > 0 ? 1 : 2, launch_cfl(ctx->buf[0], ctx->buf[1], ctx->par, ctx->amax, ctx->nsub, ctx->dtp, ctx->maxsub, ctx->G,
                       ctx->P.courant, ctx->P.dt_model, fixed, ctx->st));
@@ -397,7 +457,7 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
         const int ms = *ctx->h_maxsub;
         if (ms < 1 || ms > 100000) return fail(ctx, IEWPF_ENONFINITE, "invalid CFL substep count");
         for (int s = 0; s < ms; ++s) {
-            KL(1, launch_rk2(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->st));
+            KL(1, launch_step(ctx, s));
             if (ctx->nd > 0)
                 KL(1, launch_drift(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->d_xy, ctx->nd, s,
                                 ctx->G, ctx->P.dx, ctx->P.dy, ctx->st));
@@ -948,11 +1008,13 @@ int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt)
     if (!ctx) return IEWPF_EINVAL;
     if (n < 0 || !(dt > 0)) return fail(ctx, IEWPF_EINVAL, "bad substep arguments");
     CK(cudaSetDevice(ctx->dev));
+    int rc;
+    if (!ctx->tuned && (rc = tune_stepper(ctx))) return rc;
     std::vector<int> ones(ctx->G.ne, n);
     std::vector<float> dts(ctx->G.ne, (float)dt);
     CK(cudaMemcpyAsync(ctx->nsub, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->dtp, dts.data(), sizeof(float) * dts.size(), cudaMemcpyHostToDevice, ctx->st));
-    for (int s = 0; s < n; ++s) KL(1, launch_rk2(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->st));
+    for (int s = 0; s < n; ++s) KL(1, launch_step(ctx, s));
     KL(1, launch_par_update(ctx->par, ctx->nsub, ctx->G.ne, ctx->work, ctx->st));
     // the host vectors must outlive the copies
     CK(cudaStreamSynchronize(ctx->st));
@@ -967,6 +1029,47 @@ int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps)
     CK(cudaMemcpyAsync(&w, ctx->work, sizeof(w), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     *particle_substeps = (int64_t)w;
+    return IEWPF_OK;
+}
+
+int iewpf_set_stepper(iewpf_ctx_t* ctx, int kind, int nc, int rows, int warps)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (kind == 0) {
+        ctx->stepper = 0;
+        ctx->tuned = true;
+        return IEWPF_OK;
+    }
+    if (kind != 1 || (nc != 2 && nc != 3 && nc != 4) || rows < 1 || warps < 1 || warps > 8)
+        return fail(ctx, IEWPF_EINVAL, "bad stepper shape");
+    ctx->stepper = 1;
+    ctx->shape = MarchShape{nc, rows, warps};
+    ctx->tuned = true;
+    return IEWPF_OK;
+}
+
+int iewpf_tune(iewpf_ctx_t* ctx, int* shape)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    CK(cudaSetDevice(ctx->dev));
+    int rc = tune_stepper(ctx);
+    if (rc) return rc;
+    if (shape) {
+        shape[0] = ctx->stepper;
+        shape[1] = ctx->shape.nc;
+        shape[2] = ctx->shape.TH;
+        shape[3] = ctx->shape.warps;
+    }
+    return IEWPF_OK;
+}
+
+int iewpf_get_stepper(const iewpf_ctx_t* ctx, int* shape)
+{
+    if (!ctx || !shape) return IEWPF_EINVAL;
+    shape[0] = ctx->stepper;
+    shape[1] = ctx->shape.nc;
+    shape[2] = ctx->shape.TH;
+    shape[3] = ctx->shape.warps;
     return IEWPF_OK;
 }
 

@@ -21,6 +21,15 @@ cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const
 cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, const Grid& G, int* flag,
                              cudaStream_t st);
 
+// ---- march.cu -------------------------------------------------------------
+// tile shape of the register-marching scheme step: NC columns per lane, TH
+// rows per chunk, warps per CTA
+struct MarchShape {
+    int nc, TH, warps;
+};
+cudaError_t launch_rk2_march(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
+                             const Grid& G, const MarchShape& shape, cudaStream_t st);
+
 // ---- qhalf.cu -------------------------------------------------------------
 // psi += Q^{1/2} x (+ the optimal-proposal pull) for every particle.
 struct QhalfArgs {

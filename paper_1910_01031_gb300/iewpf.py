@@ -25,7 +25,8 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
-           "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc"]
+           "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
+           "iewpf_get_stepper"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
 
@@ -108,6 +109,9 @@ def load(build_if_needed: bool = True):
     L.iewpf_substeps.argtypes = [_vp, c.c_int, c.c_double]
     L.iewpf_launch_count.argtypes = [_vp, c.POINTER(c.c_int64)]
     L.iewpf_work.argtypes = [_vp, c.POINTER(c.c_int64)]
+    L.iewpf_set_stepper.argtypes = [_vp, c.c_int, c.c_int, c.c_int, c.c_int]
+    L.iewpf_tune.argtypes = [_vp, _ip]
+    L.iewpf_get_stepper.argtypes = [_vp, _ip]
     _lib = L
     return L
 
@@ -275,6 +279,19 @@ class Ensemble:
         c = ctypes.c_int64()
         self._chk(self.L.iewpf_launch_count(self.h, ctypes.byref(c)), "launch_count")
         return c.value
+
+    def set_stepper(self, kind, nc=2, rows=64, warps=4):
+        self._chk(self.L.iewpf_set_stepper(self.h, int(kind), int(nc), int(rows), int(warps)), "set_stepper")
+
+    def tune(self):
+        out = np.zeros(4, np.int32)
+        self._chk(self.L.iewpf_tune(self.h, _ptr(out, _ip)), "tune")
+        return tuple(int(v) for v in out)
+
+    def stepper(self):
+        out = np.zeros(4, np.int32)
+        self._chk(self.L.iewpf_get_stepper(self.h, _ptr(out, _ip)), "get_stepper")
+        return tuple(int(v) for v in out)
 
     def work(self):
         """Particle scheme steps executed so far."""
