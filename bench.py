@@ -203,7 +203,7 @@ def run_ours(args, rank, world, local):
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s, FMA = 2
     traffic = None
     try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "rk2_traffic.json")))
+        prof = json.load(open(os.path.join(ROOT, "profiles", "rk2_march_traffic.json")))
         if prof.get("kernel_sha") == _kernel_sha():
             traffic = prof["bytes_per_cell_step"] * cells
     except Exception:
@@ -244,7 +244,7 @@ def run_ours(args, rank, world, local):
 def _kernel_sha():
     import hashlib
     h = hashlib.sha1()
-    for f in ("stepper.cu", "common.cuh"):
+    for f in ("march.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1910_01031_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
