@@ -169,6 +169,16 @@ IEWPF_API int iewpf_get_drifters(iewpf_ctx_t* ctx, double* xy);
 IEWPF_API int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours,
                      double out_every_s, double* traj, int use_surrogate);
 
+/* Drift forecast with its error measures (Sec. 5.2, eqs.
+ * errorPerEnsembleDrifter and errorNorm), computed on the GPU: as
+ * drifter_forecast, and at every output time t (t = 0 included)
+ * E(t) = sqrt(mean_d mean_i |x_{i,d} - x_true,d|^2) against truth
+ * ([n_out][n][2], unwrapped positions) and RMSE(t), the same with the
+ * ensemble-mean position in place of the truth, into E[n_out] and
+ * RMSE[n_out] (FP64).  traj ([n_out][N_e][n][2]) may be NULL. */
+IEWPF_API int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s,
+                                      const double* truth, double* E, double* RMSE, double* traj);
+
 /* Checkpoint: raw state, drifters and the two draw counters; because the
  * random numbers are counter-based, a resumed run is bit-identical. */
 IEWPF_API int iewpf_save(const iewpf_ctx_t* ctx, const char* path);

@@ -342,22 +342,26 @@ def hqht(P: Problem, K, cells, dense=True):
     dense=False keeps only the 2x2 blocks of each observation (the paper's
     block-diagonal form, Sec. 4.2).  The result is symmetrised."""
     R = stencil_radius(P)
+    cells = np.asarray(cells, dtype=np.int64).reshape(-1, 2)
     nobs = len(cells)
     M = np.zeros((2 * nobs, 2 * nobs))
-    for l in range(nobs):
-        for k in range(nobs):
-            if not dense and l != k:
+    ddx = (cells[:, None, 0] - cells[None, :, 0]) % P.nx        # [l][k]
+    ddy = (cells[:, None, 1] - cells[None, :, 1]) % P.ny
+    if not dense:
+        keep = np.eye(nobs, dtype=bool)
+    else:
+        keep = np.ones((nobs, nobs), dtype=bool)
+    for ix in range(-(R // P.nx) - 1, (R // P.nx) + 2):
+        ox = ddx + ix * P.nx
+        for iy in range(-(R // P.ny) - 1, (R // P.ny) + 2):
+            oy = ddy + iy * P.ny
+            hit = keep & (np.abs(ox) <= R) & (np.abs(oy) <= R)
+            l, k = np.nonzero(hit)
+            if len(l) == 0:
                 continue
-            ddx = (cells[l][0] - cells[k][0]) % P.nx
-            ddy = (cells[l][1] - cells[k][1]) % P.ny
-            for ix in range(-(R // P.nx) - 2, (R // P.nx) + 3):
-                for iy in range(-(R // P.ny) - 2, (R // P.ny) + 3):
-                    ox, oy = ddx + ix * P.nx, ddy + iy * P.ny
-                    if abs(ox) > R or abs(oy) > R:
-                        continue
-                    for a in range(2):
-                        for b in range(2):
-                            M[2 * l + a, 2 * k + b] += K[b, 1 + a, oy + R, ox + R]
+            for a in range(2):
+                for b in range(2):
+                    np.add.at(M, (2 * l + a, 2 * k + b), K[b, 1 + a, oy[l, k] + R, ox[l, k] + R])
     return 0.5 * (M + M.T)
 
 

@@ -809,6 +809,57 @@ int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, d
     return IEWPF_OK;
 }
 
+int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s,
+                            const double* truth, double* E, double* RMSE, double* traj)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!xy0 || !truth || !E || !RMSE || n < 1 || n > ctx->P.n_drifters_max || !(hours >= 0) || !(out_every_s > 0))
+        return fail(ctx, IEWPF_EINVAL, "bad drifter forecast arguments");
+    const double ratio = out_every_s / ctx->P.dt_model;
+    const int every = (int)std::lround(ratio);
+    if (every < 1 || std::fabs(ratio - every) > 1e-9)
+        return fail(ctx, IEWPF_EINVAL, "out_every_s must be a multiple of dt_model");
+    CK(cudaSetDevice(ctx->dev));
+    const int n_out = (int)std::floor(hours * 3600.0 / out_every_s + 1e-9) + 1;
+    const int ne = ctx->G.ne;
+    const size_t per = (size_t)ne * n * 2;
+    std::vector<double> rep(per);
+    for (int p = 0; p < ne; ++p) std::memcpy(&rep[(size_t)p * n * 2], xy0, sizeof(double) * 2 * n);
+    int rc;
+    if ((rc = iewpf_set_drifters(ctx, rep.data(), n))) return rc;
+    double *d_truth = nullptr, *d_err = nullptr, *d_traj = nullptr;
+    auto cleanup = [&]() {
+        if (d_truth) cudaFree(d_truth);
+        if (d_err) cudaFree(d_err);
+        if (d_traj) cudaFree(d_traj);
+    };
+    if ((rc = dalloc(ctx, &d_truth, (size_t)n_out * n * 2)) || (rc = dalloc(ctx, &d_err, 2 * (size_t)n_out)) ||
+        (traj && (rc = dalloc(ctx, &d_traj, per * n_out)))) {
+        cleanup();
+        return rc;
+    }
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(d_truth, truth, sizeof(double) * n_out * n * 2, cudaMemcpyHostToDevice, ctx->st));
+        for (int o = 0; o < n_out; ++o) {
+            int r;
+            if (o > 0 && (r = iewpf_forecast(ctx, every, 1))) return r;
+            KL(1, launch_drift_errors(ctx->d_xy, d_truth + (size_t)o * n * 2, ne, n, d_err + o, d_err + n_out + o,
+                                      ctx->st));
+            if (traj)
+                CK(cudaMemcpyAsync(d_traj + per * o, ctx->d_xy, sizeof(double) * per, cudaMemcpyDeviceToDevice,
+                                   ctx->st));
+        }
+        CK(cudaMemcpyAsync(E, d_err, sizeof(double) * n_out, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(RMSE, d_err + n_out, sizeof(double) * n_out, cudaMemcpyDeviceToHost, ctx->st));
+        if (traj) CK(cudaMemcpyAsync(traj, d_traj, sizeof(double) * per * n_out, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        return IEWPF_OK;
+    };
+    rc = body();
+    cleanup();
+    return rc;
+}
+
 int iewpf_save(const iewpf_ctx_t* cctx, const char* path)
 {
     iewpf_ctx* ctx = const_cast<iewpf_ctx*>(cctx);

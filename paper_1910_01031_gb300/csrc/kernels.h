@@ -18,6 +18,8 @@ cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* 
 cudaError_t launch_par_update(int* par, const int* nsub, int ne, unsigned long long* work, cudaStream_t st);
 cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const int* nsub, const float* dtp,
                          double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st);
+cudaError_t launch_drift_errors(const double* xy, const double* truth, int ne, int nd, double* E, double* RMSE,
+                                cudaStream_t st);
 cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, const Grid& G, int* flag,
                              cudaStream_t st);
 

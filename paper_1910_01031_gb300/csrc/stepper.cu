@@ -279,7 +279,61 @@ __global__ void nonfinite_kernel(const float* __restrict__ buf0, const float* __
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, (int)FLAG_NONFINITE);
 }
 
+// E(t) and RMSE(t) of the drifters against the truth (eqs.
+// errorPerEnsembleDrifter, errorNorm): one CTA, one warp per drifter at a
+// time, FP64, fixed summation order
+__global__ void __launch_bounds__(256)
+drift_errors_kernel(const double* __restrict__ xy, const double* __restrict__ truth, int ne, int nd,
+                    double* __restrict__ E, double* __restrict__ RMSE)
+{
+    __shared__ double se[8], sr[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double accE = 0.0, accR = 0.0;
+    for (int d = w; d < nd; d += 8) {
+        double mx = 0.0, my = 0.0, e = 0.0;
+        for (int i = lane; i < ne; i += 32) {
+            const double x = xy[((long long)i * nd + d) * 2], y = xy[((long long)i * nd + d) * 2 + 1];
+            mx += x;
+            my += y;
+            const double ex = x - truth[2 * d], ey = y - truth[2 * d + 1];
+            e += ex * ex + ey * ey;
+        }
+        mx = warp_sum(mx) / ne;
+        my = warp_sum(my) / ne;
+        e = warp_sum(e);
+        double r = 0.0;
+        for (int i = lane; i < ne; i += 32) {
+            const double ex = xy[((long long)i * nd + d) * 2] - mx, ey = xy[((long long)i * nd + d) * 2 + 1] - my;
+            r += ex * ex + ey * ey;
+        }
+        r = warp_sum(r);
+        accE += e / ne;
+        accR += r / ne;
+    }
+    if (lane == 0) {
+        se[w] = accE;
+        sr[w] = accR;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            a += se[i];
+            b += sr[i];
+        }
+        *E = sqrt(a / nd);
+        *RMSE = sqrt(b / nd);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_drift_errors(const double* xy, const double* truth, int ne, int nd, double* E, double* RMSE,
+                                cudaStream_t st)
+{
+    drift_errors_kernel<<<1, 256, 0, st>>>(xy, truth, ne, nd, E, RMSE);
+    return cudaGetLastError();
+}
 
 size_t rk2_smem_bytes() { return sizeof(Smem); }
 

@@ -26,7 +26,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
-           "iewpf_get_stepper"]
+           "iewpf_get_stepper", "drifter_forecast_errors"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
 
@@ -90,6 +90,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_set_drifters.argtypes = [_vp, _dp, c.c_int]
     L.iewpf_get_drifters.argtypes = [_vp, _dp]
     L.drifter_forecast.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, c.c_int]
+    L.drifter_forecast_errors.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, _dp, _dp, _dp]
     L.iewpf_save.argtypes = [_vp, c.c_char_p]
     L.iewpf_load.argtypes = [_vp, c.c_char_p]
     L.iewpf_get_counters.argtypes = [_vp, _u32p, _u32p]
@@ -235,6 +236,19 @@ class Ensemble:
                   "drifter_forecast")
         self.nd = n
         return traj
+
+    def drifter_forecast_errors(self, xy0, hours, out_every_s, truth, want_traj=False):
+        """Returns (E[n_out], RMSE[n_out], traj or None)."""
+        xy0 = _f64(xy0, (-1, 2))
+        n = xy0.shape[0]
+        n_out = int(np.floor(hours * 3600.0 / out_every_s + 1e-9)) + 1
+        truth = _f64(truth, (n_out, n, 2))
+        E, R = np.zeros(n_out), np.zeros(n_out)
+        traj = np.zeros((n_out, self.ne, n, 2)) if want_traj else None
+        self._chk(self.L.drifter_forecast_errors(self.h, _ptr(xy0), n, float(hours), float(out_every_s), _ptr(truth),
+                                                 _ptr(E), _ptr(R), _ptr(traj)), "drifter_forecast_errors")
+        self.nd = n
+        return E, R, traj
 
     def save(self, path):
         self._chk(self.L.iewpf_save(self.h, str(path).encode()), "save")

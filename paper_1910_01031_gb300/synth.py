@@ -104,12 +104,7 @@ def config3(seed: int = 3, **kw):
     return out
 
 
-def initial_state(cfg: Config, ne: int, seed: int = 7, dtype=np.float64):
-    """Two opposite zonal jets: eta(y) = A/2 [tanh((y - Ly/4)/w) -
-    tanh((y - 3Ly/4)/w)] minus its mean, with (hu, hv) from the continuous
-    geostrophic balance hu = -(g H / f) d eta/dy evaluated analytically, and
-    i.i.d. N(0, noise_std^2) added to eta of every particle (numpy's Philox
-    bit generator).  Returns [ne][3][ny][nx]."""
+def _jet(cfg: Config):
     Ly = cfg.ny * cfg.dy
     w = cfg.jet_width_cells * cfg.dy
     y = (np.arange(cfg.ny) + 0.5) * cfg.dy
@@ -118,12 +113,29 @@ def initial_state(cfg: Config, ne: int, seed: int = 7, dtype=np.float64):
     eta_y -= eta_y.mean()
     deta_dy = 0.5 * cfg.jet_amp / w * (1.0 / np.cosh(a1) ** 2 - 1.0 / np.cosh(a2) ** 2)
     hu_y = -(cfg.g * cfg.H / cfg.f) * deta_dy
-    rng = np.random.Generator(np.random.Philox(seed))
-    U = np.zeros((ne, 3, cfg.ny, cfg.nx), dtype=np.float64)
-    U[:, 0] = eta_y[None, :, None]
-    U[:, 1] = hu_y[None, :, None]
-    U[:, 0] += cfg.noise_std * rng.standard_normal((ne, cfg.ny, cfg.nx))
+    return eta_y, hu_y
+
+
+def initial_particle(cfg: Config, i: int, seed: int = 7, dtype=np.float64):
+    """Particle i of the initial ensemble: [3][ny][nx] (see initial_state);
+    its noise comes from its own generator, so any subset of a large
+    ensemble can be produced on its own."""
+    eta_y, hu_y = _jet(cfg)
+    rng = np.random.Generator(np.random.Philox(key=seed, counter=[0, 0, 0, i]))
+    U = np.zeros((3, cfg.ny, cfg.nx), dtype=np.float64)
+    U[0] = eta_y[:, None]
+    U[1] = hu_y[:, None]
+    U[0] += cfg.noise_std * rng.standard_normal((cfg.ny, cfg.nx))
     return U.astype(dtype)
+
+
+def initial_state(cfg: Config, ne: int, seed: int = 7, dtype=np.float64):
+    """Two opposite zonal jets: eta(y) = A/2 [tanh((y - Ly/4)/w) -
+    tanh((y - 3Ly/4)/w)] minus its mean, with (hu, hv) from the continuous
+    geostrophic balance hu = -(g H / f) d eta/dy evaluated analytically, and
+    i.i.d. N(0, noise_std^2) added to eta of every particle (numpy's Philox
+    bit generator, one counter per particle).  Returns [ne][3][ny][nx]."""
+    return np.stack([initial_particle(cfg, i, seed, dtype) for i in range(ne)])
 
 
 def drifter_positions(cfg: Config, n: int | None = None):

@@ -1,0 +1,117 @@
+"""Parity at the full sizes of the experiment configurations, in the launch
+configuration bench.py uses (autotuned marching stepper), on outputs the
+oracle can afford: sampled particles for the state, all particles for the
+FP64 weights.
+
+* 512 x 512, 100 particles: one model step with model error, two sampled
+  particles against the oracle.
+* 1024 x 1024, 1000 particles, 1521 moorings every 26 cells: one analysis
+  from the initial ensemble.  phi_i of every particle, gamma_i and zeta_i,
+  beta and alpha_i from the oracle's own inputs, and the updated state of two
+  sampled particles."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1910_01031_gb300 import iewpf, synth
+
+from gpu_common import ensemble, oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _device_ensemble(cfg, ne, keep=(), cells=None, seed=7):
+    """The initial ensemble on the GPU, built particle by particle; returns
+    the device tensor, the float64 states of the `keep` particles and the
+    (eta, hu, hv) values of every particle at `cells`."""
+    U = torch.empty((ne, 3, cfg.ny, cfg.nx), dtype=torch.float32, device="cuda")
+    kept = {}
+    at = None if cells is None else np.zeros((ne, len(cells), 3))
+    for i in range(ne):
+        x = synth.initial_particle(cfg, i, seed=seed, dtype=np.float32)
+        U[i].copy_(torch.from_numpy(x))
+        if i in keep:
+            kept[i] = x.astype(np.float64)
+        if cells is not None:
+            at[i] = x[:, cells[:, 1], cells[:, 0]].T.astype(np.float64)
+    torch.cuda.synchronize()
+    return U, kept, at
+
+
+def test_config2_forecast_sampled_particles():
+    cfg = synth.config2()
+    P = oracle_problem(cfg)
+    sample = (0, 57)
+    U, kept, _ = _device_ensemble(cfg, cfg.n_particles, keep=sample)
+    ens = ensemble(cfg)
+    ens.set_state(U)
+    ens.forecast(1, True)
+    nsub = ens.last_nsub()
+    out = torch.empty_like(U)
+    ens.get_state(out)
+    torch.cuda.synchronize()
+    for i in sample:
+        # particle i draws its model error with its own index
+        ref, ns, _ = _forecast_as_particle(P, kept[i], i)
+        assert ns[0, 0] == nsub[i]
+        assert rel_l2(out[i].cpu().numpy(), ref[0]) < 1e-5
+
+
+def _forecast_as_particle(P, U, i):
+    """One model step of particle i alone (its model error uses stream 0 of
+    particle i)."""
+    n = O.n_sub(P, U)
+    V = U.copy()
+    dt = P.dt_model / n
+    for _ in range(n):
+        V = O.swe_substep(P, V, dt)
+    V = O.model_error(P, V, i, 0)
+    return V[None], np.array([[n]]), None
+
+
+def test_config4_analysis_full_size():
+    cfg = synth.config4()
+    ne = cfg.n_particles
+    P = oracle_problem(cfg)
+    cells = synth.mooring_cells(cfg)
+    assert len(cells) == 1521
+    xy = synth.cell_positions(cfg, cells)
+    sample = (3, 998)
+    U, kept, at = _device_ensemble(cfg, ne, keep=sample, cells=cells)
+    truth = synth.initial_particle(cfg, 123456, seed=99)
+    y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), 0))
+    ens = ensemble(cfg, mooring_xy=xy)
+    ens.set_state(U)
+    dg = ens.assimilate(None, y)
+    # the oracle's own innovations, S d and phi for every particle
+    s = (cfg.H + at[:, :, 0]) / cfg.H
+    d = np.stack([y[None, :, 0] * s - at[:, :, 1], y[None, :, 1] * s - at[:, :, 2]], axis=2).reshape(ne, -1)
+    K = O.pull_stencil(P)
+    A = O.s_matrix(P, K, [tuple(c) for c in cells], dense=True)
+    Sd = O.cholesky_solve(A, d.T).T
+    phi = np.einsum("ij,ij->i", d, Sd)
+    assert np.allclose(dg["phi"], phi, rtol=1e-9, atol=0)
+    c = phi + math.log(ne)
+    rv = O.rand_vectors(P, ne, t=0)
+    assert np.allclose(dg["gamma"], rv["gamma"], rtol=1e-10, atol=0)
+    assert np.allclose(dg["zeta"], rv["zeta"], rtol=1e-10, atol=0)
+    sc = O.iewpf_scalars(c, rv["gamma"], rv["zeta"], P.N_psi)
+    assert math.isclose(dg["beta"], sc["beta"], rel_tol=1e-9)
+    assert np.allclose(dg["alpha"], sc["alpha"], rtol=1e-9, atol=0)
+    assert np.allclose(dg["neglogw"], dg["cbar"], rtol=1e-10, atol=0)
+    # updated state of the sampled particles
+    out = torch.empty_like(U)
+    ens.get_state(out)
+    torch.cuda.synchronize()
+    Msq = O.local_block_sqrt(P)
+    for i in sample:
+        r = math.sqrt(sc["beta"]) * rv["nu"][i] + math.sqrt(sc["alpha"][i]) * rv["xi"][i]
+        for cl in cells:
+            idx = O.block_indices(P, cl)
+            r[idx] = Msq @ r[idx]
+        ref = O.add_pull(P, K, cells, Sd[i].reshape(-1, 2), kept[i])
+        ref = O.add_qhalf(P, r, ref)
+        assert rel_l2(out[i].cpu().numpy(), ref) < 1e-5
