@@ -17,10 +17,13 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libiewpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "--ptxas-options=-v"]
-# march.cu writes every fused multiply-add out, so its results do not depend
-# on how the compiler would contract each tile-shape instantiation
-FILE_FLAGS = {"march.cu": ["--fmad=false"]}
+# --fmad=false: the kernels write every fused multiply-add out themselves, so
+# their results do not depend on how the compiler would contract each
+# instantiation (tile shapes, single-problem and batched launches agree bit
+# for bit)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+         "--ptxas-options=-v"]
+FILE_FLAGS = {}
 
 
 def nvcc() -> str:

@@ -1,0 +1,451 @@
+// Device code of the IEWPF analysis (Sec. 4 and App. A of arXiv 1910.01031):
+// observation set-up, eta-compensated innovations, assembly and FP64
+// Cholesky factorisation of HQH^T + R, the S d solves with phi_i, the
+// perpendicular random vectors' dot products, the ensemble-wide target
+// weight / beta / Lambert-W alpha step, the posterior coarse field and the
+// local 49x49 block root applied around each observation.  Each function
+// does the work of one thread, warp or CTA (as named) for one problem, so
+// that single-problem and batched kernels share it.
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace iewpf {
+namespace ana {
+
+__device__ __forceinline__ int min_image(int d, int n)
+{
+    d = pmod(d, n);
+    return d > n / 2 ? d - n : d;
+}
+
+// cell and nearest coarse point (ties to the lower one) of observation l
+__device__ __forceinline__ void obs_cell_one(const double* __restrict__ xy, int l, const Grid& G, const Coarse& C,
+                                             double dx, double dy, int* __restrict__ cell, int* __restrict__ block0)
+{
+    const int j = pmod((int)floor(xy[2 * l] / dx), G.nx);
+    const int k = pmod((int)floor(xy[2 * l + 1] / dy), G.ny);
+    cell[2 * l] = j;
+    cell[2 * l + 1] = k;
+    float t;
+    int a = coarse_interval(j, C.nRx, C.c, C.o, G.nx, t);
+    int xa = coarse_pos(a, C.nRx, C.c, C.o, G.nx), xb = coarse_pos(a + 1, C.nRx, C.c, C.o, G.nx);
+    block0[2 * l] = pmod((j - xa) <= (xb - j) ? a : a + 1, C.nRx);
+    int b = coarse_interval(k, C.nRy, C.c, C.o, G.ny, t);
+    int ya = coarse_pos(b, C.nRy, C.c, C.o, G.ny), yb = coarse_pos(b + 1, C.nRy, C.c, C.o, G.ny);
+    block0[2 * l + 1] = pmod((k - ya) <= (yb - k) ? b : b + 1, C.nRy);
+}
+
+// CTA of NTHREADS: observations whose stencil box meets `tile`, listed in
+// observation order (deterministic sums in the update kernel)
+__device__ __forceinline__ void tile_bin_cta(const int* __restrict__ cell, int nobs, const Grid& G, int R, int tile,
+                                             int* __restrict__ cnt, int* __restrict__ list, int cap,
+                                             int* __restrict__ flag)
+{
+    __shared__ int base;
+    __shared__ int warp_tot[NTHREADS / 32];
+    const int tx = tile % ((G.nx + TW - 1) / TW), ty = tile / ((G.nx + TW - 1) / TW);
+    const int cx = tx * TW + TW / 2, cy = ty * TH + TH / 2;
+    __syncthreads();
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int l0 = 0; l0 < nobs; l0 += NTHREADS) {
+        const int l = l0 + threadIdx.x;
+        bool hit = false;
+        if (l < nobs) {
+            const int ox = min_image(cell[2 * l] - cx, G.nx), oy = min_image(cell[2 * l + 1] - cy, G.ny);
+            hit = abs(ox) <= R + TW / 2 + 1 && abs(oy) <= R + TH / 2 + 1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) warp_tot[w] = __popc(m);
+        __syncthreads();
+        int off = base;
+        for (int i = 0; i < w; ++i) off += warp_tot[i];
+        off += __popc(m & ((1u << lane) - 1u));
+        if (hit) {
+            if (off < cap) list[tile * cap + off] = l;
+            else atomicOr(flag, FLAG_TILE_OVERFLOW);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int i = 0; i < NTHREADS / 32; ++i) tot += warp_tot[i];
+            base += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cnt[tile] = base < cap ? base : cap;
+}
+
+// d = y (H + eta)/H - (hu, hv) at the observed cell (eq. etaCompensatedInnovation)
+__device__ __forceinline__ void innovate_one(const float* __restrict__ b0, const float* __restrict__ b1,
+                                             const int* __restrict__ par, const int* __restrict__ cell,
+                                             const double* __restrict__ y, int nobs, const Grid& G, double H,
+                                             double* __restrict__ d, int i)
+{
+    const int p = i / nobs, l = i % nobs;
+    const float* __restrict__ U = (par[p] ? b1 : b0) + (long long)p * 3 * G.plane;
+    const long long c = (long long)cell[2 * l + 1] * G.nx + cell[2 * l];
+    const double s = (H + (double)U[c]) / H;
+    d[(long long)i * 2] = fma(y[2 * l], s, -(double)U[G.plane + c]);
+    d[(long long)i * 2 + 1] = fma(y[2 * l + 1], s, -(double)U[2 * G.plane + c]);
+}
+
+// (HQH^T)_{(l,a),(k,b)}: component a of the response to a unit b observation
+// at obs k, read at obs l's cell
+__device__ __forceinline__ double kval(const double* K, int R, const int* cell, int l, int a, int k, int b,
+                                       const Grid& G)
+{
+    const int ox = min_image(cell[2 * l] - cell[2 * k], G.nx);
+    const int oy = min_image(cell[2 * l + 1] - cell[2 * k + 1], G.ny);
+    if (abs(ox) > R || abs(oy) > R) return 0.0;
+    const int W = 2 * R + 1;
+    return K[((b * 3 + 1 + a) * W + (oy + R)) * W + (ox + R)];
+}
+
+// entry i of the symmetrised HQH^T + sigma^2 I
+__device__ __forceinline__ void hqht_one(const double* __restrict__ K, int R, const int* __restrict__ cell, int nobs,
+                                         const Grid& G, int dense, double sigma2, double* __restrict__ M, long long i)
+{
+    const int n = 2 * nobs;
+    const int r = (int)(i / n), c = (int)(i % n);
+    const int l = r >> 1, a = r & 1, k = c >> 1, b = c & 1;
+    double v = 0.0;
+    if (dense || l == k) v = 0.5 * (kval(K, R, cell, l, a, k, b, G) + kval(K, R, cell, k, b, l, a, G));
+    if (r == c) v += sigma2;
+    M[i] = v;
+}
+
+// Right-looking Cholesky of a dense SPD matrix in place (lower triangle), one
+// CTA; the update of column k touches only rows with a non-zero in it, so
+// block-diagonal and banded matrices cost their fill, not n^3/3.  Then the
+// factor's columns are listed (CSC of the strictly lower part).
+__device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int* __restrict__ colptr,
+                                             int* __restrict__ rowidx, int* __restrict__ flag,
+                                             int* __restrict__ nzlist)
+{
+    __shared__ int nnz;
+    __shared__ double piv;
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0) bad = 0;
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const double dkk = A[(long long)k * n + k];
+            if (!(dkk > 0.0)) bad = 1;
+            piv = dkk > 0.0 ? sqrt(dkk) : 1.0;
+            A[(long long)k * n + k] = piv;
+            nnz = 0;
+        }
+        __syncthreads();
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const double v = A[(long long)i * n + k];
+            if (v != 0.0) {
+                A[(long long)i * n + k] = v / piv;
+                nzlist[atomicAdd(&nnz, 1)] = i;
+            }
+        }
+        __syncthreads();
+        const int m = nnz;
+        const long long pairs = (long long)m * m;
+        for (long long q = threadIdx.x; q < pairs; q += blockDim.x) {
+            const int i = nzlist[q / m], j = nzlist[q % m];
+            if (j <= i) A[(long long)i * n + j] = fma(-A[(long long)i * n + k], A[(long long)j * n + k], A[(long long)i * n + j]);
+        }
+        __syncthreads();
+    }
+    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+        const int i = (int)(q / n), j = (int)(q % n);
+        if (j > i) A[q] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int pos = 0;
+        for (int k = 0; k < n; ++k) {
+            colptr[k] = pos;
+            for (int i = k + 1; i < n; ++i)
+                if (A[(long long)i * n + k] != 0.0) rowidx[pos++] = i;
+        }
+        colptr[n] = pos;
+        if (bad) atomicOr(flag, FLAG_NOTPD);
+    }
+}
+
+// warp: S d = (L L^T)^{-1} d for particle w and phi_w = d^T S d
+__device__ __forceinline__ void solve_warp(const double* __restrict__ L, const int* __restrict__ colptr,
+                                           const int* __restrict__ rowidx, int n, const double* __restrict__ d,
+                                           double* __restrict__ x, double* __restrict__ phi, int w)
+{
+    const int lane = threadIdx.x & 31;
+    double* xp = x + (long long)w * n;
+    const double* dp = d + (long long)w * n;
+    for (int i = lane; i < n; i += 32) xp[i] = dp[i];
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const double yk = xp[k] / L[(long long)k * n + k];
+        __syncwarp();
+        if (lane == 0) xp[k] = yk;
+        for (int q = colptr[k] + lane; q < colptr[k + 1]; q += 32) {
+            const int i = rowidx[q];
+            xp[i] = fma(-L[(long long)i * n + k], yk, xp[i]);
+        }
+        __syncwarp();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double acc = 0.0;
+        for (int q = colptr[k] + lane; q < colptr[k + 1]; q += 32) {
+            const int i = rowidx[q];
+            acc = fma(L[(long long)i * n + k], xp[i], acc);
+        }
+        acc = warp_sum(acc);
+        const double xk = (xp[k] - acc) / L[(long long)k * n + k];
+        __syncwarp();
+        if (lane == 0) xp[k] = xk;
+        __syncwarp();
+    }
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) acc = fma(dp[i], xp[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) phi[w] = acc;
+}
+
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_BLOCKS_PER_CTA = 8;
+
+// CTA of DOT_THREADS: partial sums of xi^T xi, nu~^T nu~, nu~^T xi (FP64
+// normals) of particle p over the Philox blocks of slice bx
+__device__ __forceinline__ void rand_dots_cta(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR,
+                                              double* __restrict__ partial, int nblk, int p, int bx)
+{
+    const uint2 key = seed_key(seed);
+    const int nq = (NR + 3) / 4;
+    double xx = 0.0, nn = 0.0, nx = 0.0;
+    for (int b = bx * DOT_THREADS + threadIdx.x; b < nq; b += nblk * DOT_THREADS) {
+        const uint4 wx = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)p, t, s_xi), key);
+        const uint4 wn = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)p, t, s_nu), key);
+        double x[4], v[4];
+        box_muller64(wx.x, wx.y, x[0], x[1]);
+        box_muller64(wx.z, wx.w, x[2], x[3]);
+        box_muller64(wn.x, wn.y, v[0], v[1]);
+        box_muller64(wn.z, wn.w, v[2], v[3]);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (4 * b + l < NR) {
+                xx = fma(x[l], x[l], xx);
+                nn = fma(v[l], v[l], nn);
+                nx = fma(v[l], x[l], nx);
+            }
+        }
+    }
+    __shared__ double red[3][DOT_THREADS / 32];
+    xx = warp_sum(xx);
+    nn = warp_sum(nn);
+    nx = warp_sum(nx);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = xx;
+        red[1][threadIdx.x >> 5] = nn;
+        red[2][threadIdx.x >> 5] = nx;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < DOT_THREADS / 32; ++w) s += red[threadIdx.x][w];
+        partial[((long long)p * nblk + bx) * 3 + threadIdx.x] = s;
+    }
+}
+
+// -s - log(1 - s) for s in [0, 1): power series below 0.1, closed form above
+__device__ __forceinline__ double phi_s(double s)
+{
+    if (s < 0.1) {
+        double acc = 0.0, term = s * s;
+        for (int n = 2; n < 40; ++n) {
+            acc += term / n;
+            term *= s;
+        }
+        return acc;
+    }
+    return -s - log1p(-s);
+}
+
+// alpha of eq. iewpfAlphaSol with W_0 solved through its defining equation
+// u - 1 - log u = q (u = -W_0), q = (x - 1 - log x) + c*/N_psi, x = gamma/N_psi:
+// Newton in s = 1 - u started from the branch-point series
+// s = p - p^2/3 + 11 p^3/72 - 43 p^4/540, p = sqrt(2 (1 + e z)) (Corless et
+// al. 1996), or in u itself for q > 1/2.  Returns alpha, or NaN on failure.
+__device__ __forceinline__ double alpha_lambert(double gamma, double cstar, double N)
+{
+    const double x = gamma / N;
+    const double dl = x - 1.0;
+    double q = (dl - log1p(dl)) + fmax(cstar, 0.0) / N;
+    if (!(q >= 0.0) || !isfinite(q)) return nan("");
+    double u;
+    if (q == 0.0) {
+        u = 1.0;
+    } else if (q <= 0.5) {
+        const double pp = sqrt(-2.0 * expm1(-q));
+        double s = pp * (1.0 + pp * (-1.0 / 3.0 + pp * (11.0 / 72.0 - pp * (43.0 / 540.0))));
+        s = fmin(fmax(s, 0.0), 0.999);
+        for (int it = 0; it < 8; ++it) {
+            const double f = phi_s(s) - q;
+            const double fp = s / (1.0 - s);
+            if (fp <= 0.0) break;
+            double sn = s - f / fp;
+            if (sn <= 0.0) sn = 0.5 * s;
+            if (sn >= 1.0) sn = 0.5 * (s + 1.0);
+            if (sn == s) break;
+            s = sn;
+        }
+        u = 1.0 - s;
+    } else {
+        u = exp(-1.0 - q);
+        for (int it = 0; it < 60; ++it) {
+            const double f = u - 1.0 - log(u) - q;
+            const double fp = 1.0 - 1.0 / u;
+            double un = u - f / fp;
+            if (un <= 0.0) un = 0.5 * u;
+            if (un >= 1.0) un = 0.5 * (u + 1.0);
+            if (un == u) break;
+            u = un;
+        }
+    }
+    return u / x;
+}
+
+__device__ __forceinline__ void block_sum_min(double v_sum, double v_min, double* s_out, double* m_out)
+{
+    __shared__ double ws[32], wm[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double s = warp_sum(v_sum);
+    double m = v_min;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (lane == 0) {
+        ws[w] = s;
+        wm[w] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tm = INFINITY;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            ts += ws[i];
+            tm = fmin(tm, wm[i]);
+        }
+        *s_out = ts;
+        *m_out = tm;
+    }
+    __syncthreads();
+}
+
+// CTA: the ensemble-wide step, c_bar = w_target, beta, c*, alpha, -log w
+__device__ __forceinline__ void weights_cta(const double* c, const double* gamma, const double* zeta, int ne,
+                                            double N, double* alpha, double* cstar, double* neglogw, double* scal,
+                                            int* flag)
+{
+    __shared__ double s_sum, s_min;
+    double acc = 0.0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+        acc += c[i];
+        bad |= !isfinite(c[i]) || !isfinite(gamma[i]) || !isfinite(zeta[i]);
+    }
+    bad = __syncthreads_or(bad);
+    block_sum_min(acc, INFINITY, &s_sum, &s_min);
+    const double cbar = s_sum / ne;
+    double mn = INFINITY;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) mn = fmin(mn, (cbar - c[i]) / zeta[i] + 1.0);
+    block_sum_min(0.0, mn, &s_sum, &s_min);
+    const double beta = s_min;
+    bool dom = false;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+        const double cs = cbar - c[i] - (beta - 1.0) * zeta[i];
+        const double a = alpha_lambert(gamma[i], cs, N);
+        dom |= !(a > 0.0) || !isfinite(a);
+        alpha[i] = a;
+        cstar[i] = cs;
+        if (neglogw) neglogw[i] = (a - 1.0) * gamma[i] - N * log(a) + (beta - 1.0) * zeta[i] + c[i];
+    }
+    dom = __syncthreads_or(dom);
+    if (threadIdx.x == 0) {
+        scal[0] = cbar;
+        scal[1] = beta;
+        int f = 0;
+        if (bad) f |= FLAG_NONFINITE;
+        if (!(beta >= 0.0)) f |= FLAG_BETA;
+        if (dom) f |= FLAG_DOMAIN;
+        if (f) atomicOr(flag, f);
+    }
+}
+
+// CTA: gamma, zeta, a, the length scale and c from the partial dot products,
+// then the weights step
+__device__ __forceinline__ void sync_alpha_cta(const double* __restrict__ phi, const double* __restrict__ partial,
+                                               int nblk, int ne, double NR, double N, double logNe, double* c,
+                                               double* gamma, double* zeta, double* alpha, double* cstar,
+                                               double* neglogw, double* coef, double* scal, int* flag)
+{
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+        double xx = 0.0, nn = 0.0, nx = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            xx += partial[((long long)i * nblk + b) * 3 + 0];
+            nn += partial[((long long)i * nblk + b) * 3 + 1];
+            nx += partial[((long long)i * nblk + b) * 3 + 2];
+        }
+        const double a = nx / xx;                                    // eq. nuPerpendicular
+        coef[2 * i] = a;
+        coef[2 * i + 1] = sqrt(nn / (nn - a * nx));
+        gamma[i] = xx * N / NR;                                      // eq. scalingGammaZeta
+        zeta[i] = nn * N / NR;
+        c[i] = phi[i] + logNe;                                       // eq. iewpf_ci
+    }
+    __syncthreads();
+    weights_cta(c, gamma, zeta, ne, N, alpha, cstar, neglogw, scal, flag);
+}
+
+// r = beta^{1/2} nu + alpha^{1/2} xi at coarse point m of particle p,
+// nu = s (nu~ - a xi)
+__device__ __forceinline__ void form_r_one(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR,
+                                           const double* __restrict__ coef, const double* __restrict__ scal,
+                                           const double* __restrict__ alpha, float* __restrict__ r, int p, int m)
+{
+    const uint2 key = seed_key(seed);
+    const float xi = normal32(key, (uint32_t)p, t, s_xi, (uint32_t)m);
+    const float nut = normal32(key, (uint32_t)p, t, s_nu, (uint32_t)m);
+    const float a = (float)coef[2 * p], sc = (float)coef[2 * p + 1];
+    const float sb = (float)sqrt(fmax(scal[1], 0.0)), sa = (float)sqrt(alpha[p]);
+    r[(long long)p * NR + m] = fmaf(sb, sc * fmaf(-a, xi, nut), sa * xi);
+}
+
+// CTA of at least 64 threads: the 7x7 block roots of every observation of
+// particle p applied in observation order (eq. Psquareroot, Sec. 4.6)
+__device__ __forceinline__ void block_seq_cta(float* __restrict__ r, int NR, const float* __restrict__ M49,
+                                              const int* __restrict__ block0, int nobs, int nRx, int nRy, int p)
+{
+    __shared__ float v[49];
+    __shared__ int idx[49];
+    float* rp = r + (long long)p * NR;
+    const int t = threadIdx.x;
+    for (int l = 0; l < nobs; ++l) {
+        __syncthreads();
+        if (t < 49) {
+            const int dxo = t % 7 - 3, dyo = t / 7 - 3;
+            const int a = pmod(block0[2 * l] + dxo, nRx), b = pmod(block0[2 * l + 1] + dyo, nRy);
+            idx[t] = b * nRx + a;
+            v[t] = rp[idx[t]];
+        }
+        __syncthreads();
+        if (t < 49) {
+            float acc = 0.0f;
+#pragma unroll 7
+            for (int j = 0; j < 49; ++j) acc = fmaf(M49[t * 49 + j], v[j], acc);
+            rp[idx[t]] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace ana
+}  // namespace iewpf

@@ -71,9 +71,7 @@ struct iewpf_ctx {
     double* d_partial = nullptr;
     int dots_blk = 0;
     float* d_r = nullptr;       // posterior coarse field [ne][N_R]
-    int* d_list = nullptr;      // observation order, grouped into non-overlapping waves
     bool factored = false;      // mooring factor ready
-    std::vector<int> waves;     // sizes of the waves of d_list
     // pinned staging
     int* h_flag = nullptr;
     int* h_maxsub = nullptr;
@@ -336,66 +334,6 @@ int tune_stepper(iewpf_ctx* ctx)
     return IEWPF_OK;
 }
 
-int fdiv(double x, double d) { return (int)std::floor(x / d); }
-int posmod(int a, int n) { return ((a % n) + n) % n; }
-
-// nearest coarse point index of fine index j (ties to the lower one)
-int nearest_coarse(int j, int n, int nR, int c)
-{
-    const int o = c / 2;
-    int a = (j < o) ? -1 : std::min((j - o) / c, nR - 1);
-    auto pos = [&](int aa) {
-        const int w = aa >= 0 ? aa / nR : -((-aa + nR - 1) / nR);
-        return o + c * (aa - w * nR) + w * n;
-    };
-    const int xa = pos(a), xb = pos(a + 1);
-    return posmod((j - xa) <= (xb - j) ? a : a + 1, nR);
-}
-
-// Observations in order, split into waves whose 7x7 coarse blocks do not
-// overlap; an observation goes one wave after the last earlier observation
-// it overlaps, so applying the waves in turn equals applying the blocks in
-// observation order.
-void make_waves(iewpf_ctx* ctx, const double* xy, int nobs, std::vector<int>& order, std::vector<int>& sizes)
-{
-    const auto& P = ctx->P;
-    std::vector<int> ba(nobs), bb(nobs), wave(nobs, 0);
-    for (int l = 0; l < nobs; ++l) {
-        const int j = posmod(fdiv(xy[2 * l], P.dx), P.nx), k = posmod(fdiv(xy[2 * l + 1], P.dy), P.ny);
-        ba[l] = nearest_coarse(j, P.nx, ctx->C.nRx, P.c_omega);
-        bb[l] = nearest_coarse(k, P.ny, ctx->C.nRy, P.c_omega);
-    }
-    // bucket by coarse cell so that the overlap search stays local
-    const int cell = 7, gx = (ctx->C.nRx + cell - 1) / cell, gy = (ctx->C.nRy + cell - 1) / cell;
-    std::vector<std::vector<int>> bucket((size_t)gx * gy);
-    int nw = 0;
-    for (int l = 0; l < nobs; ++l) {
-        const int cx = ba[l] / cell, cy = bb[l] / cell;
-        int w = 0;
-        for (int dy = -2; dy <= 2; ++dy)
-            for (int dx = -2; dx <= 2; ++dx) {
-                const auto& bk = bucket[(size_t)posmod(cy + dy, gy) * gx + posmod(cx + dx, gx)];
-                for (int k : bk) {
-                    int ox = std::abs(ba[l] - ba[k]), oy = std::abs(bb[l] - bb[k]);
-                    ox = std::min(ox, ctx->C.nRx - ox);
-                    oy = std::min(oy, ctx->C.nRy - oy);
-                    if (ox <= 6 && oy <= 6) w = std::max(w, wave[k] + 1);
-                }
-            }
-        wave[l] = w;
-        nw = std::max(nw, w + 1);
-        bucket[(size_t)cy * gx + cx].push_back(l);
-    }
-    order.clear();
-    sizes.assign(nw, 0);
-    for (int w = 0; w < nw; ++w)
-        for (int l = 0; l < nobs; ++l)
-            if (wave[l] == w) {
-                order.push_back(l);
-                ++sizes[w];
-            }
-}
-
 int check_flags(iewpf_ctx* ctx, int f)
 {
     if (f & FLAG_NONFINITE) return fail(ctx, IEWPF_ENONFINITE, "non-finite values in the state or weights");
@@ -421,12 +359,6 @@ int upload_obs_layout(iewpf_ctx* ctx, const double* xy, int nobs)
     CK(cudaMemcpyAsync(ctx->d_obs_xy, xy, sizeof(double) * 2 * nobs, cudaMemcpyHostToDevice, ctx->st));
     KL(2, launch_obs_setup(ctx->d_obs_xy, nobs, ctx->G, ctx->C, ctx->P.dx, ctx->P.dy, ctx->R, ctx->d_cell,
                         ctx->d_block0, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->tile_cap, ctx->flag, ctx->st));
-    std::vector<int> order;
-    make_waves(ctx, xy, nobs, order, ctx->waves);
-    CK(cudaMemcpyAsync(ctx->d_list, order.data(), sizeof(int) * (order.empty() ? 1 : order.size()),
-                       cudaMemcpyHostToDevice, ctx->st));
-    // the host vector must outlive the copy
-    CK(cudaStreamSynchronize(ctx->st));
     return IEWPF_OK;
 }
 
@@ -472,6 +404,7 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
             A.from_philox = 1;
             A.seed = ctx->P.seed;
             A.t = ctx->step;
+            A.t_dev = nullptr;
             A.stream = 0u + 16u * (uint32_t)ctx->P.instance_id;
             KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
         }
@@ -580,7 +513,7 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
     ctx->dots_blk = rand_dots_blocks((int)ctx->NR);
     if ((rc = dalloc(ctx, &ctx->d_obs_xy, ny)) || (rc = dalloc(ctx, &ctx->d_obs_y, ny)) ||
         (rc = dalloc(ctx, &ctx->d_cell, ny)) || (rc = dalloc(ctx, &ctx->d_block0, ny)) ||
-        (rc = dalloc(ctx, &ctx->d_list, ny / 2)) || (rc = dalloc(ctx, &ctx->d_tile_cnt, ctx->ntiles)) ||
+        (rc = dalloc(ctx, &ctx->d_tile_cnt, ctx->ntiles)) ||
         (rc = dalloc(ctx, &ctx->d_tile_obs, (size_t)ctx->ntiles * ctx->tile_cap)) ||
         (rc = dalloc(ctx, &ctx->d_L, ny * ny)) || (rc = dalloc(ctx, &ctx->d_colptr, ny + 1)) ||
         (rc = dalloc(ctx, &ctx->d_rowidx, ny * (ny - 1) / 2 + ny)) || (rc = dalloc(ctx, &ctx->d_d, ne * ny)) ||
@@ -614,7 +547,7 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
                     ctx->d_cell, ctx->d_block0, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
                     ctx->d_rowidx, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
                     ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
-                    ctx->d_r, ctx->d_list};
+                    ctx->d_r};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
@@ -718,12 +651,8 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     // 6: posterior coarse field, local block roots, fused update with the pull
     KL(1, launch_form_r(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_coef, ctx->d_scal,
                      ctx->d_alpha, ctx->d_r, ctx->st));
-    int off = 0;
-    for (int w : ctx->waves) {
-        KL(w > 0 ? 1 : 0, launch_block_apply(ctx->d_r, (int)ctx->NR, ne, ctx->d_M49, ctx->d_block0, ctx->d_list + off, w,
-                              ctx->C.nRx, ctx->C.nRy, ctx->st));
-        off += w;
-    }
+    KL(1, launch_block_seq(ctx->d_r, (int)ctx->NR, ne, ctx->d_M49, ctx->d_block0, nobs, ctx->C.nRx, ctx->C.nRy,
+                           ctx->st));
     QhalfArgs A{};
     A.b0 = ctx->buf[0];
     A.b1 = ctx->buf[1];

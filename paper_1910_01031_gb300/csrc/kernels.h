@@ -43,6 +43,7 @@ struct QhalfArgs {
     int from_philox;
     uint64_t seed;
     uint32_t t;
+    const uint32_t* t_dev;    // if set, the draw counter is read from device memory
     uint32_t stream;
     const float* x;           // [ne][N_R]
     // optimal-proposal pull (may be disabled)
@@ -82,8 +83,8 @@ cudaError_t launch_weights_only(const double* c, const double* gamma, const doub
 cudaError_t launch_form_r(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
                           const double* coef, const double* scal, const double* alpha, float* r,
                           cudaStream_t st);
-cudaError_t launch_block_apply(float* r, int NR, int ne, const float* M49, const int* obs_block0,
-                               const int* list, int nlist, int nRx, int nRy, cudaStream_t st);
+cudaError_t launch_block_seq(float* r, int NR, int ne, const float* M49, const int* obs_block0, int nobs, int nRx,
+                             int nRy, cudaStream_t st);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,
                                  uint32_t* out, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n, double* o64,

@@ -1,0 +1,261 @@
+// Device code of the register-marching scheme step (Sec. 3.1 of arXiv 1910.01031):
+// the same central-upwind fluxes, Coriolis-adjusted reconstruction and SSP-RK2
+// as rk2_kernel, organised for issue efficiency on GB300.
+//
+// Each warp owns a strip of 32*NC columns (NC per lane) and marches down a
+// chunk of rows.  Rows above and below live in a three-row rolling window in
+// registers; x-neighbours come from the adjacent lanes by warp shuffles.  Both
+// Runge-Kutta stages run in the same march, the second two rows behind the
+// first, so a cell is read once and written once per scheme step, with no
+// shared memory and no block barriers.  The 4 outermost columns on each side
+// of a strip are halo (recomputed by the neighbouring strip) and 8 extra rows
+// fill the pipeline of each chunk.  Divisions and square roots use the
+// hardware approximations (rcp, rsqrt; a few ulp).  The file is compiled
+// without automatic multiply-add contraction and every fused multiply-add is
+// written out, so each cell's arithmetic is the same whatever the tile shape.
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace iewpf {
+namespace march {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float fsqrt(float x) { return x * rsqrtf(x); }
+
+__device__ __forceinline__ float gmm(float a, float b, float th)
+{
+    const float x = th * a, y = 0.5f * (a + b), z = th * b;   // no contraction here
+    const float mn = fminf(x, fminf(y, z));
+    const float mx = fmaxf(x, fmaxf(y, z));
+    return mn > 0.0f ? mn : (mx < 0.0f ? mx : 0.0f);
+}
+
+// central-upwind flux, normal momentum qn, tangential qt carried by the mass
+// flux with the upwind tangential velocity
+__device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, float qnR, float qtR, const Grid& G,
+                                     float& F0, float& F1, float& F2)
+{
+    const float hL = G.H + eL, hR = G.H + eR;
+    const float rL = frcp(hL), rR = frcp(hR);
+    const float unL = qnL * rL, unR = qnR * rR;
+    const float cL = fsqrt(G.g * hL), cR = fsqrt(G.g * hR);
+    const float ap = fmaxf(fmaxf(unL + cL, unR + cR), 0.0f);
+    const float am = fminf(fminf(unL - cL, unR - cR), 0.0f);
+    const float inv = frcp(ap - am);
+    const float apam = ap * am;
+    F0 = fmaf(apam, eR - eL, fmaf(ap, qnL, -(am * qnR))) * inv;
+    const float pL = fmaf(0.5f, eL, G.H) * (G.g * eL);
+    const float pR = fmaf(0.5f, eR, G.H) * (G.g * eR);
+    const float mL = fmaf(qnL, unL, pL), mR = fmaf(qnR, unR, pR);
+    F1 = fmaf(apam, qnR - qnL, fmaf(ap, mL, -(am * mR))) * inv;
+    F2 = F0 * ((F0 >= 0.0f) ? qtL * rL : qtR * rR);
+}
+
+template <int NC>
+struct Marcher {
+    // rolling window: 0 = oldest (row being emitted), 1, 2 = newest
+    float e[3][NC], qu[3][NC], qv[3][NC], u[3][NC];
+    float dLp[NC];                  // dL on the face between rows 0 and 1
+    float sL[NC], su[NC], sv[NC];   // y-slopes of row 0
+    float G0[NC], Gu[NC], Gv[NC];   // y-flux on the face below row 0
+
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) e[r][k] = qu[r][k] = qv[r][k] = u[r][k] = 0.0f;
+            dLp[k] = sL[k] = su[k] = sv[k] = G0[k] = Gu[k] = Gv[k] = 0.0f;
+        }
+    }
+
+    // Push the next row; returns L(U) of the row that leaves the window (two
+    // rows behind the pushed one) and that row's state.
+    __device__ __forceinline__ void push(const float* ne, const float* nqu, const float* nqv, const Grid& G,
+                                         float* L0, float* L1, float* L2, float* oe, float* oqu, float* oqv)
+    {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            e[0][k] = e[1][k]; qu[0][k] = qu[1][k]; qv[0][k] = qv[1][k]; u[0][k] = u[1][k];
+            e[1][k] = e[2][k]; qu[1][k] = qu[2][k]; qv[1][k] = qv[2][k]; u[1][k] = u[2][k];
+            e[2][k] = ne[k]; qu[2][k] = nqu[k]; qv[2][k] = nqv[k];
+            u[2][k] = nqu[k] * frcp(G.H + ne[k]);
+        }
+        // y direction: slopes of row 1, flux on the face between rows 0 and 1
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const float dLn = fmaf(G.fdy_half, u[1][k] + u[2][k], G.g * (e[2][k] - e[1][k]));
+            const float s1L = gmm(dLp[k], dLn, G.theta);
+            const float s1u = gmm(qu[1][k] - qu[0][k], qu[2][k] - qu[1][k], G.theta);
+            const float s1v = gmm(qv[1][k] - qv[0][k], qv[2][k] - qv[1][k], G.theta);
+            const float eB = fmaf(fmaf(-G.fdy, u[0][k], sL[k]), G.inv_2g, e[0][k]);
+            const float eT = fmaf(fmaf(-G.fdy, u[1][k], s1L), -G.inv_2g, e[1][k]);
+            float g0, gv, gu;
+            flux(eB, fmaf(0.5f, sv[k], qv[0][k]), fmaf(0.5f, su[k], qu[0][k]), eT, fmaf(-0.5f, s1v, qv[1][k]),
+                 fmaf(-0.5f, s1u, qu[1][k]), G, g0, gv, gu);
+            L0[k] = (G0[k] - g0) * G.inv_dy;
+            L1[k] = (Gu[k] - gu) * G.inv_dy;
+            L2[k] = (Gv[k] - gv) * G.inv_dy;
+            dLp[k] = dLn;
+            sL[k] = s1L; su[k] = s1u; sv[k] = s1v;
+            G0[k] = g0; Gu[k] = gu; Gv[k] = gv;
+        }
+        // x direction on row 0: neighbours from the adjacent lanes
+        float E[NC + 2], QU[NC + 2], QV[NC + 2], V[NC + 2];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            E[k + 1] = e[0][k]; QU[k + 1] = qu[0][k]; QV[k + 1] = qv[0][k];
+            V[k + 1] = qv[0][k] * frcp(G.H + e[0][k]);
+        }
+        E[0] = __shfl_up_sync(FULL, E[NC], 1);
+        QU[0] = __shfl_up_sync(FULL, QU[NC], 1);
+        QV[0] = __shfl_up_sync(FULL, QV[NC], 1);
+        V[0] = __shfl_up_sync(FULL, V[NC], 1);
+        E[NC + 1] = __shfl_down_sync(FULL, E[1], 1);
+        QU[NC + 1] = __shfl_down_sync(FULL, QU[1], 1);
+        QV[NC + 1] = __shfl_down_sync(FULL, QV[1], 1);
+        V[NC + 1] = __shfl_down_sync(FULL, V[1], 1);
+        float dK[NC + 1];
+#pragma unroll
+        for (int f = 0; f <= NC; ++f) dK[f] = fmaf(-G.fdx_half, V[f] + V[f + 1], G.g * (E[f + 1] - E[f]));
+        float eE[NC], eW[NC], uE[NC], uW[NC], vE[NC], vW[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const float sK = gmm(dK[k], dK[k + 1], G.theta);
+            const float sU = gmm(QU[k + 1] - QU[k], QU[k + 2] - QU[k + 1], G.theta);
+            const float sV = gmm(QV[k + 1] - QV[k], QV[k + 2] - QV[k + 1], G.theta);
+            const float ex = fmaf(G.fdx, V[k + 1], sK) * G.inv_2g;
+            eE[k] = E[k + 1] + ex; eW[k] = E[k + 1] - ex;
+            uE[k] = fmaf(0.5f, sU, QU[k + 1]); uW[k] = fmaf(-0.5f, sU, QU[k + 1]);
+            vE[k] = fmaf(0.5f, sV, QV[k + 1]); vW[k] = fmaf(-0.5f, sV, QV[k + 1]);
+        }
+        // face f lies on the left of own column f; face NC is the right edge
+        float F0[NC + 1], F1[NC + 1], F2[NC + 1];
+#pragma unroll
+        for (int f = 1; f < NC; ++f) flux(eE[f - 1], uE[f - 1], vE[f - 1], eW[f], uW[f], vW[f], G, F0[f], F1[f], F2[f]);
+        {
+            const float eRW = __shfl_down_sync(FULL, eW[0], 1);
+            const float uRW = __shfl_down_sync(FULL, uW[0], 1);
+            const float vRW = __shfl_down_sync(FULL, vW[0], 1);
+            flux(eE[NC - 1], uE[NC - 1], vE[NC - 1], eRW, uRW, vRW, G, F0[NC], F1[NC], F2[NC]);
+        }
+        F0[0] = __shfl_up_sync(FULL, F0[NC], 1);
+        F1[0] = __shfl_up_sync(FULL, F1[NC], 1);
+        F2[0] = __shfl_up_sync(FULL, F2[NC], 1);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            L0[k] = fmaf(F0[k] - F0[k + 1], G.inv_dx, L0[k]);
+            L1[k] = fmaf(F1[k] - F1[k + 1], G.inv_dx, L1[k]);
+            L2[k] = fmaf(F2[k] - F2[k + 1], G.inv_dx, L2[k]);
+            L1[k] = fmaf(G.f, qv[0][k], L1[k]);
+            L2[k] = fmaf(-G.f, qu[0][k], L2[k]);
+            oe[k] = e[0][k]; oqu[k] = qu[0][k]; oqv[k] = qv[0][k];
+        }
+    }
+};
+
+// Arguments of one scheme step of one problem.
+struct StepArgs {
+    float* buf0;
+    float* buf1;
+    const int* par;
+    const int* nsub;
+    const float* dtp;
+    Grid G;
+    int TH, n_strips, n_chunks;
+};
+
+// One warp's strip of one chunk of particle p in scheme step s.
+template <int NC>
+__device__ __forceinline__ void march_warp(const StepArgs& a, int p, int chunk, int strip, int s)
+{
+    constexpr int WUSE = 32 * NC - 8;          // useful columns per strip
+    const Grid& G = a.G;
+    const int TH = a.TH;
+    const int lane = threadIdx.x & 31;
+    if (s >= a.nsub[p]) return;
+    const int src = a.par[p] ^ (s & 1);
+    float* __restrict__ buf0 = a.buf0;
+    float* __restrict__ buf1 = a.buf1;
+    const float* __restrict__ dtp = a.dtp;
+    const float* __restrict__ in = (src ? buf1 : buf0) + (long long)p * 3 * G.plane;
+    float* __restrict__ out = (src ? buf0 : buf1) + (long long)p * 3 * G.plane;
+    const float dt = dtp[p];
+    const int y0 = chunk * TH;
+    const int rows = min(TH, G.ny - y0);
+    // columns of this lane: strip-local c = lane*NC + k, global x = strip*WUSE - 4 + c
+    int gx[NC];
+    bool keep[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int c = lane * NC + k;
+        const int x = strip * WUSE - 4 + c;
+        gx[k] = pmod(x, G.nx);
+        keep[k] = (c >= 4) && (c < 32 * NC - 4) && (x < G.nx);
+    }
+    Marcher<NC> S1, S2;
+    S1.zero();
+    S2.zero();
+    float f0e[NC], f0u[NC], f0v[NC], f1e[NC], f1u[NC], f1v[NC];   // U0 of the last two emitted rows
+#pragma unroll
+    for (int k = 0; k < NC; ++k) f0e[k] = f0u[k] = f0v[k] = f1e[k] = f1u[k] = f1v[k] = 0.0f;
+    const int n_it = rows + 8;
+    float ne[NC], nqu[NC], nqv[NC];
+    {
+        const long long r0 = (long long)pmod(y0 - 4, G.ny) * G.nx;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            ne[k] = __ldg(in + r0 + gx[k]);
+            nqu[k] = __ldg(in + G.plane + r0 + gx[k]);
+            nqv[k] = __ldg(in + 2 * G.plane + r0 + gx[k]);
+        }
+    }
+    for (int it = 0; it < n_it; ++it) {
+        // prefetch the next input row
+        float pe[NC], pqu[NC], pqv[NC];
+        if (it + 1 < n_it) {
+            const long long rn = (long long)pmod(y0 - 3 + it, G.ny) * G.nx;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                pe[k] = __ldg(in + rn + gx[k]);
+                pqu[k] = __ldg(in + G.plane + rn + gx[k]);
+                pqv[k] = __ldg(in + 2 * G.plane + rn + gx[k]);
+            }
+        }
+        // stage 1 on U0, then stage 2 on U1 = U0 + dt L(U0)
+        float L0[NC], L1[NC], L2[NC], ue[NC], uu[NC], uv[NC];
+        S1.push(ne, nqu, nqv, G, L0, L1, L2, ue, uu, uv);
+        float we[NC], wu[NC], wv[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            we[k] = fmaf(dt, L0[k], ue[k]);
+            wu[k] = fmaf(dt, L1[k], uu[k]);
+            wv[k] = fmaf(dt, L2[k], uv[k]);
+        }
+        float M0[NC], M1[NC], M2[NC], ve[NC], vu[NC], vv[NC];
+        S2.push(we, wu, wv, G, M0, M1, M2, ve, vu, vv);
+        if (it >= 8) {
+            const long long ro = (long long)(y0 + it - 8) * G.nx;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                if (keep[k]) {
+                    out[ro + gx[k]] = 0.5f * (f1e[k] + fmaf(dt, M0[k], ve[k]));
+                    out[G.plane + ro + gx[k]] = 0.5f * (f1u[k] + fmaf(dt, M1[k], vu[k]));
+                    out[2 * G.plane + ro + gx[k]] = 0.5f * (f1v[k] + fmaf(dt, M2[k], vv[k]));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            f1e[k] = f0e[k]; f1u[k] = f0u[k]; f1v[k] = f0v[k];
+            f0e[k] = ue[k]; f0u[k] = uu[k]; f0v[k] = uv[k];
+            ne[k] = pe[k]; nqu[k] = pqu[k]; nqv[k] = pqv[k];
+        }
+    }
+}
+
+}  // namespace march
+}  // namespace iewpf
