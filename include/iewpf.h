@@ -289,6 +289,47 @@ IEWPF_API int iewpf_get_stepper(const iewpf_ctx_t* ctx, int* shape);
 /* Number of kernels the context has launched so far. */
 IEWPF_API int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count);
 
+/* ---- batched problems -------------------------------------------- */
+
+/* Many independent assimilation problems of uneven grid and ensemble size
+ * advanced together (each with its own parameters, state and observations).
+ * Every phase of a cycle (CFL, scheme steps, model error, each analysis step)
+ * is one persistent launch over the work of all problems, and the whole
+ * forecast-assimilate cycle is one CUDA graph, captured at the first cycle
+ * and replayed; the CFL-chosen number of scheme steps per model step drives
+ * a conditional while-node of the graph.  Results equal those of the same
+ * problems run one by one through iewpf_forecast / iewpf_assimilate. */
+typedef struct iewpf_batch iewpf_batch_t;
+
+/* n problems; params[i] as for iewpf_create (n_obs_max >= 1, a distinct
+ * instance_id gives independent draws); mooring_xy may be NULL or hold one
+ * pointer per problem (NULL for drifter problems). */
+IEWPF_API int iewpf_batch_create(const iewpf_params_t* params, const double* const* mooring_xy, int n,
+                                 iewpf_batch_t** out);
+IEWPF_API int iewpf_batch_destroy(iewpf_batch_t* b);
+
+/* The context of problem i (owned by the batch): set or read its state,
+ * counters and per-particle diagnostics with the one-problem calls. */
+IEWPF_API int iewpf_batch_instance(iewpf_batch_t* b, int i, iewpf_ctx_t** ctx);
+
+/* Autotuner of the batched scheme step (columns per lane, rows per chunk,
+ * warps per CTA); shape[3] may be NULL.  Runs by itself before the first
+ * cycle. */
+IEWPF_API int iewpf_batch_tune(iewpf_batch_t* b, int* shape);
+
+/* One cycle of every problem: n_model_steps model steps (model error after
+ * all but the last, Sec. 4.1) and one IEWPF analysis against obs[i]
+ * (obs[i].n_obs must equal problem i's n_obs_max).  diag (may be NULL)
+ * receives [n][3] = (c_bar, beta, error flags) per problem.  Returns the
+ * first problem's error, if any. */
+IEWPF_API int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* obs, double* diag);
+IEWPF_API int iewpf_batch_stream(const iewpf_batch_t* b, void** stream);
+
+/* Particle scheme steps executed by the batch and kernel launches it
+ * enqueued (a graph replay counts the launches of one capture). */
+IEWPF_API int iewpf_batch_work(iewpf_batch_t* b, int64_t* particle_substeps, int64_t* launches);
+IEWPF_API const char* iewpf_batch_last_error(const iewpf_batch_t* b);
+
 /* Sizes derived from the parameters. */
 IEWPF_API int iewpf_sizes(const iewpf_ctx_t* ctx, int* nRx, int* nRy, int* stencil_R);
 

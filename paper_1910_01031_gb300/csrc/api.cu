@@ -11,6 +11,7 @@
 
 #include "../../include/iewpf.h"
 #include "common.cuh"
+#include "batch.h"
 #include "kernels.h"
 
 using namespace iewpf;
@@ -1067,6 +1068,215 @@ int iewpf_sizes(const iewpf_ctx_t* ctx, int* nRx, int* nRy, int* stencil_R)
     if (nRy) *nRy = ctx->C.nRy;
     if (stencil_R) *stencil_R = ctx->R;
     return IEWPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched problems
+// ---------------------------------------------------------------------------
+struct iewpf_batch {
+    std::vector<iewpf_ctx*> inst;
+    BatchImpl* impl = nullptr;
+    cudaStream_t st = nullptr, st2 = nullptr;
+    int dev = 0;
+    std::string err;
+};
+
+static int bfail(iewpf_batch* b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+#define BCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return bfail(b, IEWPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+int iewpf_batch_destroy(iewpf_batch_t* b)
+{
+    if (!b) return IEWPF_OK;
+    cudaSetDevice(b->dev);
+    if (b->st) cudaStreamSynchronize(b->st);
+    batch_delete(b->impl);
+    for (iewpf_ctx* c : b->inst) iewpf_destroy(c);
+    if (b->st) cudaStreamDestroy(b->st);
+    if (b->st2) cudaStreamDestroy(b->st2);
+    delete b;
+    return IEWPF_OK;
+}
+
+int iewpf_batch_create(const iewpf_params_t* params, const double* const* mooring_xy, int n, iewpf_batch_t** out)
+{
+    if (!params || !out || n < 1) return IEWPF_EINVAL;
+    *out = nullptr;
+    iewpf_batch* b = new (std::nothrow) iewpf_batch();
+    if (!b) return IEWPF_ENOMEM;
+    cudaGetDevice(&b->dev);
+    std::vector<BInst> desc;
+    for (int i = 0; i < n; ++i) {
+        iewpf_ctx* ctx = nullptr;
+        if (params[i].n_obs_max < 1) {
+            iewpf_batch_destroy(b);
+            return IEWPF_EINVAL;
+        }
+        int rc = iewpf_create(&params[i], mooring_xy ? mooring_xy[i] : nullptr, &ctx);
+        if (rc) {
+            iewpf_batch_destroy(b);
+            return rc;
+        }
+        b->inst.push_back(ctx);
+        BInst I{};
+        I.step = march::StepArgs{ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->G, 64, 0, 0};
+        I.b0 = ctx->buf[0];
+        I.b1 = ctx->buf[1];
+        I.par = ctx->par;
+        I.nsub = ctx->nsub;
+        I.dtp = ctx->dtp;
+        I.amax = ctx->amax;
+        I.G = ctx->G;
+        I.C = ctx->C;
+        I.courant = ctx->P.courant;
+        I.dt_model = ctx->P.dt_model;
+        I.wtab = ctx->d_wtab;
+        I.seed = ctx->P.seed;
+        I.stream_base = 16u * (uint32_t)ctx->P.instance_id;
+        I.work = ctx->work;
+        I.flag = ctx->flag;
+        I.nobs = ctx->nobs_max;
+        I.moving_obs = ctx->P.obs_kind == IEWPF_OBS_DRIFTER;
+        I.dx = ctx->P.dx;
+        I.dy = ctx->P.dy;
+        I.H = ctx->P.H_eq;
+        I.sigma2 = ctx->P.obs_sigma * ctx->P.obs_sigma;
+        I.dense = ctx->P.dense_S;
+        I.R = ctx->R;
+        I.cell = ctx->d_cell;
+        I.block0 = ctx->d_block0;
+        I.tile_cnt = ctx->d_tile_cnt;
+        I.tile_obs = ctx->d_tile_obs;
+        I.tile_cap = ctx->tile_cap;
+        I.K64 = ctx->d_K64;
+        I.K32 = ctx->d_K32;
+        I.M49 = ctx->d_M49;
+        I.L = ctx->d_L;
+        I.colptr = ctx->d_colptr;
+        I.rowidx = ctx->d_rowidx;
+        I.d = ctx->d_d;
+        I.Sd = ctx->d_Sd;
+        I.phi = ctx->d_phi;
+        I.partial = ctx->d_partial;
+        I.nblk = ctx->dots_blk;
+        I.c = ctx->d_c;
+        I.gamma = ctx->d_gamma;
+        I.zeta = ctx->d_zeta;
+        I.alpha = ctx->d_alpha;
+        I.cstar = ctx->d_cstar;
+        I.neglogw = ctx->d_neglogw;
+        I.coef = ctx->d_coef;
+        I.scal = ctx->d_scal;
+        I.r = ctx->d_r;
+        I.NR = ctx->NR;
+        I.N_psi = 3.0 * ctx->plane;
+        I.logNe = std::log((double)ctx->G.ne);
+        desc.push_back(I);
+    }
+    b->impl = batch_new();
+    if (!b->impl) {
+        iewpf_batch_destroy(b);
+        return IEWPF_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking) != cudaSuccess ||
+        batch_init(*b->impl, desc) != cudaSuccess) {
+        cudaGetLastError();
+        iewpf_batch_destroy(b);
+        return IEWPF_ENOMEM;
+    }
+    *out = b;
+    return IEWPF_OK;
+}
+
+int iewpf_batch_instance(iewpf_batch_t* b, int i, iewpf_ctx_t** ctx)
+{
+    if (!b || !ctx || i < 0 || i >= (int)b->inst.size()) return IEWPF_EINVAL;
+    *ctx = b->inst[i];
+    return IEWPF_OK;
+}
+
+int iewpf_batch_tune(iewpf_batch_t* b, int* shape)
+{
+    if (!b) return IEWPF_EINVAL;
+    BCK(cudaSetDevice(b->dev));
+    BCK(batch_tune(*b->impl, b->st));
+    if (shape) batch_shape(*b->impl, shape);
+    return IEWPF_OK;
+}
+
+int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* obs, double* diag)
+{
+    if (!b) return IEWPF_EINVAL;
+    if (n_model_steps < 1 || !obs) return bfail(b, IEWPF_EINVAL, "bad cycle arguments");
+    const int n = (int)b->inst.size();
+    for (int i = 0; i < n; ++i) {
+        const iewpf_ctx* c = b->inst[i];
+        const bool mooring = c->P.obs_kind == IEWPF_OBS_MOORING;
+        if (obs[i].n_obs != c->nobs_max || !obs[i].value || (!mooring && !obs[i].xy))
+            return bfail(b, IEWPF_EINVAL, "problem " + std::to_string(i) + ": observations must fill n_obs_max");
+    }
+    BCK(cudaSetDevice(b->dev));
+    if (!batch_tuned(*b->impl)) BCK(batch_tune(*b->impl, b->st));
+    // inputs into the pinned staging the graph reads
+    for (int i = 0; i < n; ++i) {
+        double* dst = batch_obs_staging(*b->impl, i);
+        const int m = obs[i].n_obs;
+        if (obs[i].xy) std::memcpy(dst, obs[i].xy, sizeof(double) * 2 * m);
+        else std::memset(dst, 0, sizeof(double) * 2 * m);
+        std::memcpy(dst + 2 * m, obs[i].value, sizeof(double) * 2 * m);
+        uint32_t* ctr = batch_counter_staging(*b->impl);
+        ctr[2 * i] = b->inst[i]->step;
+        ctr[2 * i + 1] = b->inst[i]->cycle;
+    }
+    BCK(batch_cycle(*b->impl, n_model_steps, b->st, b->st2));
+    BCK(cudaStreamSynchronize(b->st));
+    const double* dg = batch_diag(*b->impl);
+    int rc = IEWPF_OK;
+    for (int i = 0; i < n; ++i) {
+        iewpf_ctx* c = b->inst[i];
+        c->step += (uint32_t)n_model_steps;
+        c->cycle += 1;
+        if (diag) std::memcpy(diag + 3 * i, dg + 3 * i, 3 * sizeof(double));
+        const int f = (int)dg[3 * i + 2];
+        if (f && rc == IEWPF_OK) {
+            rc = check_flags(c, f);
+            b->err = "problem " + std::to_string(i) + ": " + c->err;
+        }
+    }
+    return rc;
+}
+
+int iewpf_batch_stream(const iewpf_batch_t* b, void** stream)
+{
+    if (!b || !stream) return IEWPF_EINVAL;
+    *stream = (void*)b->st;
+    return IEWPF_OK;
+}
+
+int iewpf_batch_work(iewpf_batch_t* b, int64_t* particle_substeps, int64_t* launches)
+{
+    if (!b) return IEWPF_EINVAL;
+    BCK(cudaSetDevice(b->dev));
+    unsigned long long w = 0;
+    BCK(batch_work(*b->impl, &w));
+    if (particle_substeps) *particle_substeps = (int64_t)w;
+    if (launches) *launches = batch_launches(*b->impl);
+    return IEWPF_OK;
+}
+
+const char* iewpf_batch_last_error(const iewpf_batch_t* b)
+{
+    return b ? b->err.c_str() : kNullMsg;
 }
 
 }  // extern "C"

@@ -1,0 +1,689 @@
+// Batched IEWPF: many independent assimilation problems of uneven grid and
+// ensemble size advanced together.  Every phase of the cycle (CFL, scheme
+// steps, model error, each analysis step) is ONE persistent launch over the
+// work items of all problems (grid sized to the resident capacity of the
+// GPU, grid-stride loop over items; an item's problem is found by binary
+// search over prefix sums).  The whole forecast-assimilate cycle is captured
+// once as a CUDA graph and replayed; the number of scheme steps of each model
+// step, which the CFL condition decides on the device, drives a conditional
+// WHILE node of the graph, so no host synchronisation sits inside a cycle.
+// The per-cell arithmetic is the device code of the one-problem kernels, so
+// batched and one-problem runs give identical results.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/iewpf.h"
+#include "analysis_dev.cuh"
+#include "batch.h"
+#include "march_dev.cuh"
+#include "qhalf_dev.cuh"
+
+namespace iewpf {
+
+namespace {
+
+// first item of problem i in each work space; item spaces end at pre[n]
+enum Space : int {
+    SP_PART = 0,   // particles
+    SP_CFL,        // CFL slices: particle x slice of the plane
+    SP_STEP,       // scheme-step warps: particle x chunk x strip
+    SP_TILE,       // fine tiles: particle x tile
+    SP_OBS,        // observations
+    SP_BIN,        // tiles of the observation lists (one per problem tile)
+    SP_INN,        // particle x observation
+    SP_HQ,         // entries of HQH^T
+    SP_DOT,        // dot-product slices: particle x slice
+    SP_FR,         // particle x coarse point
+    SP_COUNT
+};
+
+constexpr long long kCflSlice = 65536;
+constexpr int kMaxSub = 100000;    // scheme steps per model step beyond this are an error
+
+__device__ __forceinline__ int find_inst(const long long* __restrict__ pre, int n, long long item)
+{
+    int lo = 0, hi = n;                  // pre[lo] <= item < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct BatchDev {
+    const BInst* inst;
+    const long long* pre;   // [SP_COUNT][n + 1]
+    int n;
+    int* s;                 // scheme-step counter of the running model step
+    int* maxsub;            // largest n_sub of the model step over all problems
+    unsigned long long* work;
+    int fixed;
+};
+
+__device__ __forceinline__ const long long* space(const BatchDev& B, int sp) { return B.pre + (long long)sp * (B.n + 1); }
+
+// ---- forecast -------------------------------------------------------------
+__global__ void b_zero(BatchDev B)
+{
+    const long long np = space(B, SP_PART)[B.n];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(space(B, SP_PART), B.n, q);
+        B.inst[i].amax[q - space(B, SP_PART)[i]] = 0.0f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *B.maxsub = 0;
+        *B.s = 0;
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS) b_cfl(BatchDev B)
+{
+    const long long* pre = space(B, SP_CFL);
+    for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const long long slices = (I.G.plane + kCflSlice - 1) / kCflSlice;
+        const long long r = q - pre[i];
+        const int p = (int)(r / slices);
+        const long long c0 = (r % slices) * kCflSlice, c1 = min(c0 + kCflSlice, I.G.plane);
+        const float* __restrict__ U = (I.par[p] ? I.b1 : I.b0) + (long long)p * 3 * I.G.plane;
+        float m = 0.0f;
+        for (long long c = c0 + threadIdx.x; c < c1; c += NTHREADS) m = fmaxf(m, cfl_cell(U, c, I.G));
+        m = warp_max(m);
+        if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(I.amax) + p, __float_as_int(m));
+    }
+}
+
+__global__ void b_nsub(BatchDev B)
+{
+    const long long np = space(B, SP_PART)[B.n];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(space(B, SP_PART), B.n, q);
+        const BInst& I = B.inst[i];
+        const int p = (int)(q - space(B, SP_PART)[i]);
+        int n = nsub_of(I.amax[p], I.courant, I.dt_model, B.fixed);
+        if (n > kMaxSub) {
+            n = kMaxSub;
+            atomicOr(I.flag, (int)FLAG_NONFINITE);
+        }
+        I.nsub[p] = n;
+        I.dtp[p] = (float)(I.dt_model / (double)n);
+        atomicMax(B.maxsub, n);
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) b_step(BatchDev B)
+{
+    const long long* pre = space(B, SP_STEP);
+    const int s = *B.s;
+    const long long wpg = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < pre[B.n]; w += wpg) {
+        const int i = find_inst(pre, B.n, w);
+        const march::StepArgs a = B.inst[i].step;     // by value: no reloads after the state stores
+        const long long r = w - pre[i];
+        const long long per_p = (long long)a.n_strips * a.n_chunks;
+        const int p = (int)(r / per_p);
+        const int rem = (int)(r % per_p);
+        march::march_warp<NC>(a, p, rem / a.n_strips, rem % a.n_strips, s);
+    }
+}
+
+// advances the scheme-step counter and sets the WHILE condition
+__global__ void b_ctl(BatchDev B, cudaGraphConditionalHandle h)
+{
+    const int s = *B.s + 1;
+    *B.s = s;
+    cudaGraphSetConditional(h, (s < *B.maxsub && s < kMaxSub) ? 1u : 0u);
+}
+
+__global__ void b_par(BatchDev B)
+{
+    const long long np = space(B, SP_PART)[B.n];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(space(B, SP_PART), B.n, q);
+        const BInst& I = B.inst[i];
+        const int p = (int)(q - space(B, SP_PART)[i]);
+        I.par[p] ^= (I.nsub[p] & 1);
+        atomicAdd(B.work, (unsigned long long)I.nsub[p]);
+        atomicAdd(I.work, (unsigned long long)I.nsub[p]);
+    }
+}
+
+// model error (PULL = false, coarse field from Philox) or analysis update
+// (PULL = true, posterior coarse field plus the pull)
+template <bool PULL>
+__global__ void __launch_bounds__(NTHREADS) b_qhalf(BatchDev B)
+{
+    const long long* pre = space(B, SP_TILE);
+    for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const int ntx = (I.G.nx + TW - 1) / TW, nty = (I.G.ny + TH - 1) / TH;
+        const long long r = q - pre[i];
+        const int p = (int)(r / (ntx * nty));
+        const int tile = (int)(r % (ntx * nty));
+        QhalfArgs A{};
+        A.b0 = I.step.buf0;
+        A.b1 = I.step.buf1;
+        A.par = I.step.par;
+        A.wtab = I.wtab;
+        A.seed = I.seed;
+        A.stream = I.stream_base;
+        uint32_t t;
+        if (PULL) {
+            A.from_philox = 0;
+            A.x = I.r;
+            A.with_pull = 1;
+            A.K = I.K32;
+            A.R = I.R;
+            A.obs_cell = I.cell;
+            A.Sd = I.Sd;
+            A.nobs = I.nobs;
+            A.tile_cnt = I.tile_cnt;
+            A.tile_obs = I.tile_obs;
+            A.tile_cap = I.tile_cap;
+            t = *I.cycle;
+        } else {
+            A.from_philox = 1;
+            t = *I.step_ctr;
+        }
+        const Grid G = I.G;
+        const Coarse C = I.C;
+        qhalf::qhalf_tile<PULL>(A, G, C, (tile % ntx) * TW, (tile / ntx) * TH, p, tile, t);
+    }
+}
+
+__global__ void b_count(BatchDev B, int which)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B.n) {
+        if (which == 0) *B.inst[i].step_ctr += 1;
+        else *B.inst[i].cycle += 1;
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS) b_nonfinite(BatchDev B)
+{
+    const long long* pre = space(B, SP_CFL);
+    for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const long long slices = (I.G.plane + kCflSlice - 1) / kCflSlice;
+        const long long r = q - pre[i];
+        const int p = (int)(r / slices);
+        const long long c0 = (r % slices) * kCflSlice, c1 = min(c0 + kCflSlice, I.G.plane);
+        const float* __restrict__ U = (I.par[p] ? I.b1 : I.b0) + (long long)p * 3 * I.G.plane;
+        bool bad = false;
+        for (long long c = c0 + threadIdx.x; c < c1; c += NTHREADS)
+            bad |= !isfinite(U[c]) || !isfinite(U[I.G.plane + c]) || !isfinite(U[2 * I.G.plane + c]);
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(I.flag, (int)FLAG_NONFINITE);
+    }
+}
+
+// ---- analysis -------------------------------------------------------------
+__global__ void b_obs_cells(BatchDev B)
+{
+    const long long* pre = space(B, SP_OBS);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pre[B.n]; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        if (I.moving_obs) ana::obs_cell_one(I.obs_xy, (int)(q - pre[i]), I.G, I.C, I.dx, I.dy, I.cell, I.block0);
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS) b_tile_bin(BatchDev B)
+{
+    const long long* pre = space(B, SP_BIN);
+    for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        if (I.moving_obs) ana::tile_bin_cta(I.cell, I.nobs, I.G, I.R, (int)(q - pre[i]), I.tile_cnt, I.tile_obs, I.tile_cap, I.flag);
+    }
+}
+
+__global__ void b_innovate(BatchDev B)
+{
+    const long long* pre = space(B, SP_INN);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pre[B.n]; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        ana::innovate_one(I.b0, I.b1, I.par, I.cell, I.obs_y, I.nobs, I.G, I.H, I.d, (int)(q - pre[i]));
+    }
+}
+
+__global__ void b_hqht(BatchDev B)
+{
+    const long long* pre = space(B, SP_HQ);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pre[B.n]; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        if (I.moving_obs) ana::hqht_one(I.K64, I.R, I.cell, I.nobs, I.G, I.dense, I.sigma2, I.L, q - pre[i]);
+    }
+}
+
+__global__ void __launch_bounds__(1024) b_cholesky(BatchDev B)
+{
+    for (int i = blockIdx.x; i < B.n; i += gridDim.x) {
+        const BInst& I = B.inst[i];
+        if (I.moving_obs) ana::cholesky_cta(I.L, 2 * I.nobs, I.colptr, I.rowidx, I.flag, I.rowidx);
+    }
+}
+
+__global__ void b_solve(BatchDev B)
+{
+    const long long* pre = space(B, SP_PART);
+    const long long wpg = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < pre[B.n]; w += wpg) {
+        const int i = find_inst(pre, B.n, w);
+        const BInst& I = B.inst[i];
+        ana::solve_warp(I.L, I.colptr, I.rowidx, 2 * I.nobs, I.d, I.Sd, I.phi, (int)(w - pre[i]));
+    }
+}
+
+__global__ void __launch_bounds__(ana::DOT_THREADS) b_dots(BatchDev B)
+{
+    const long long* pre = space(B, SP_DOT);
+    for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const long long r = q - pre[i];
+        ana::rand_dots_cta(I.seed, *I.cycle, I.stream_base + 1, I.stream_base + 2, (int)I.NR, I.partial, I.nblk,
+                           (int)(r / I.nblk), (int)(r % I.nblk));
+    }
+}
+
+__global__ void __launch_bounds__(1024) b_sync(BatchDev B)
+{
+    for (int i = blockIdx.x; i < B.n; i += gridDim.x) {
+        const BInst& I = B.inst[i];
+        ana::sync_alpha_cta(I.phi, I.partial, I.nblk, I.G.ne, (double)I.NR, I.N_psi, I.logNe, I.c, I.gamma, I.zeta,
+                            I.alpha, I.cstar, I.neglogw, I.coef, I.scal, I.flag);
+    }
+}
+
+__global__ void b_form_r(BatchDev B)
+{
+    const long long* pre = space(B, SP_FR);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pre[B.n]; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const long long r = q - pre[i];
+        ana::form_r_one(I.seed, *I.cycle, I.stream_base + 1, I.stream_base + 2, (int)I.NR, I.coef, I.scal, I.alpha, I.r,
+                        (int)(r / I.NR), (int)(r % I.NR));
+    }
+}
+
+__global__ void b_block_seq(BatchDev B)
+{
+    const long long* pre = space(B, SP_PART);
+    for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        ana::block_seq_cta(I.r, (int)I.NR, I.M49, I.block0, I.nobs, I.C.nRx, I.C.nRy, (int)(q - pre[i]));
+    }
+}
+
+// per problem (c_bar, beta, flag) into the packed diagnostics buffer
+__global__ void b_pack_diag(BatchDev B, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B.n) {
+        const BInst& I = B.inst[i];
+        out[3 * i] = I.scal[0];
+        out[3 * i + 1] = I.scal[1];
+        out[3 * i + 2] = (double)*I.flag;
+        *I.flag = 0;
+    }
+}
+
+int resident_blocks(const void* fn, int threads)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+    return std::max(1, sms * std::max(1, per));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct BatchImpl {
+    int n = 0;
+    std::vector<BInst> h_inst;
+    BInst* d_inst = nullptr;
+    long long* d_pre = nullptr;
+    std::vector<long long> pre;       // [SP_COUNT][n+1]
+    int* d_s = nullptr;
+    int* d_maxsub = nullptr;
+    unsigned long long* d_work = nullptr;
+    double* h_obs = nullptr;          // pinned packed observations [sum 4 nobs]
+    double* d_obs = nullptr;
+    std::vector<long long> obs_off;   // offset of problem i's observations in the packed buffer
+    long long obs_total = 0;
+    double* h_diag = nullptr;         // pinned [n][3]
+    uint32_t* h_ctr = nullptr;        // pinned [n][2] draw counters copied in at the start of a cycle
+    uint32_t* d_ctr = nullptr;
+    double* d_diag = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_steps = -1;
+    int nc = 2;
+    int warps = 4;
+    int fixed = 0;
+    bool tuned = false;
+    long long launches = 0;
+};
+
+namespace {
+
+BatchDev dev_view(BatchImpl& b)
+{
+    return BatchDev{b.d_inst, b.d_pre, b.n, b.d_s, b.d_maxsub, b.d_work, b.fixed};
+}
+
+long long items(const BatchImpl& b, int sp) { return b.pre[(size_t)sp * (b.n + 1) + b.n]; }
+
+cudaError_t launch_step_nc(BatchImpl& b, cudaStream_t st)
+{
+    const BatchDev B = dev_view(b);
+    const int thr = 32 * b.warps;
+    const long long need = (items(b, SP_STEP) + b.warps - 1) / b.warps;
+    switch (b.nc) {
+    case 2: {
+        const int g = (int)std::min<long long>(need, resident_blocks((const void*)b_step<2>, thr));
+        b_step<2><<<g, thr, 0, st>>>(B);
+        break;
+    }
+    case 3: {
+        const int g = (int)std::min<long long>(need, resident_blocks((const void*)b_step<3>, thr));
+        b_step<3><<<g, thr, 0, st>>>(B);
+        break;
+    }
+    default: {
+        const int g = (int)std::min<long long>(need, resident_blocks((const void*)b_step<4>, thr));
+        b_step<4><<<g, thr, 0, st>>>(B);
+        break;
+    }
+    }
+    return cudaGetLastError();
+}
+
+template <typename K>
+int grid_for(K kern, int threads, long long work_items_per_block_units)
+{
+    const long long cap = resident_blocks((const void*)kern, threads);
+    return (int)std::max<long long>(1, std::min<long long>(cap, work_items_per_block_units));
+}
+
+}  // namespace
+
+cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps)
+{
+    b.nc = nc;
+    b.warps = warps;
+    long long acc = 0;
+    for (int i = 0; i < b.n; ++i) {
+        BInst& I = b.h_inst[i];
+        const int wuse = 32 * nc - 8;
+        I.step.TH = th;
+        I.step.n_strips = (I.G.nx + wuse - 1) / wuse;
+        I.step.n_chunks = (I.G.ny + th - 1) / th;
+        b.pre[(size_t)SP_STEP * (b.n + 1) + i] = acc;
+        acc += (long long)I.step.n_strips * I.step.n_chunks * I.G.ne;
+    }
+    b.pre[(size_t)SP_STEP * (b.n + 1) + b.n] = acc;
+    cudaError_t e = cudaMemcpy(b.d_inst, b.h_inst.data(), sizeof(BInst) * b.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(b.d_pre, b.pre.data(), sizeof(long long) * b.pre.size(), cudaMemcpyHostToDevice);
+}
+
+// Builds the prefix sums and device descriptors of the problems.
+cudaError_t batch_init(BatchImpl& b, const std::vector<BInst>& insts)
+{
+    b.n = (int)insts.size();
+    b.h_inst = insts;
+    b.pre.assign((size_t)SP_COUNT * (b.n + 1), 0);
+    long long acc[SP_COUNT] = {0};
+    b.obs_off.assign(b.n + 1, 0);
+    for (int i = 0; i < b.n; ++i) {
+        const BInst& I = insts[i];
+        const long long ne = I.G.ne;
+        const long long slices = (I.G.plane + kCflSlice - 1) / kCflSlice;
+        const long long tiles = (long long)((I.G.nx + TW - 1) / TW) * ((I.G.ny + TH - 1) / TH);
+        const long long cnt[SP_COUNT] = {ne, ne * slices, 0, ne * tiles, I.nobs, tiles, ne * I.nobs,
+                                         4LL * I.nobs * I.nobs, ne * I.nblk, ne * I.NR};
+        for (int sp = 0; sp < SP_COUNT; ++sp) {
+            b.pre[(size_t)sp * (b.n + 1) + i] = acc[sp];
+            acc[sp] += cnt[sp];
+        }
+        b.obs_off[i + 1] = b.obs_off[i] + 4LL * I.nobs;
+    }
+    for (int sp = 0; sp < SP_COUNT; ++sp) b.pre[(size_t)sp * (b.n + 1) + b.n] = acc[sp];
+    b.obs_total = b.obs_off[b.n];
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&b.d_inst, sizeof(BInst) * b.n)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_pre, sizeof(long long) * b.pre.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_s, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_maxsub, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_work, sizeof(unsigned long long))) != cudaSuccess) return e;
+    if ((e = cudaMemset(b.d_work, 0, sizeof(unsigned long long))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_obs, sizeof(double) * std::max<long long>(b.obs_total, 1))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&b.h_obs, sizeof(double) * std::max<long long>(b.obs_total, 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_diag, sizeof(double) * 3 * b.n)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&b.h_diag, sizeof(double) * 3 * b.n)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&b.d_ctr, sizeof(uint32_t) * 2 * b.n)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&b.h_ctr, sizeof(uint32_t) * 2 * b.n)) != cudaSuccess) return e;
+    for (int i = 0; i < b.n; ++i) {
+        b.h_inst[i].obs_xy = b.d_obs + b.obs_off[i];
+        b.h_inst[i].obs_y = b.d_obs + b.obs_off[i] + 2 * b.h_inst[i].nobs;
+        b.h_inst[i].step_ctr = b.d_ctr + 2 * i;
+        b.h_inst[i].cycle = b.d_ctr + 2 * i + 1;
+    }
+    return batch_set_step_shape(b, b.nc, 64, b.warps);
+}
+
+BatchImpl* batch_new() { return new (std::nothrow) BatchImpl(); }
+
+void batch_delete(BatchImpl* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    void* d[] = {b->d_inst, b->d_pre, b->d_s, b->d_maxsub, b->d_work, b->d_obs, b->d_diag, b->d_ctr};
+    for (void* p : d)
+        if (p) cudaFree(p);
+    if (b->h_obs) cudaFreeHost(b->h_obs);
+    if (b->h_diag) cudaFreeHost(b->h_diag);
+    if (b->h_ctr) cudaFreeHost(b->h_ctr);
+    delete b;
+}
+
+double* batch_obs_staging(BatchImpl& b, int i) { return b.h_obs + b.obs_off[i]; }
+uint32_t* batch_counter_staging(BatchImpl& b) { return b.h_ctr; }
+const double* batch_diag(const BatchImpl& b) { return b.h_diag; }
+long long batch_launches(const BatchImpl& b) { return b.launches; }
+
+cudaError_t batch_work(BatchImpl& b, unsigned long long* out)
+{
+    return cudaMemcpy(out, b.d_work, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+}
+
+// One model step into the stream being captured: CFL, the WHILE loop of
+// scheme steps, the parity flip and (optionally) the model error.
+static cudaError_t capture_model_step(BatchImpl& b, cudaStream_t st, cudaStream_t st2, bool err)
+{
+    const BatchDev B = dev_view(b);
+    cudaError_t e;
+    b_zero<<<grid_for(b_zero, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
+    b_cfl<<<grid_for(b_cfl, NTHREADS, items(b, SP_CFL)), NTHREADS, 0, st>>>(B);
+    b_nsub<<<grid_for(b_nsub, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    b.launches += 3;
+    // WHILE node: body = one scheme step of every problem + counter update
+    cudaStreamCaptureStatus status;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &prm)) != cudaSuccess) return e;
+    cudaGraph_t body = prm.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(st2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+    if ((e = launch_step_nc(b, st2)) != cudaSuccess) return e;
+    b_ctl<<<1, 1, 0, st2>>>(B, h);
+    b.launches += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamEndCapture(st2, &body)) != cudaSuccess) return e;
+    b_par<<<grid_for(b_par, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
+    b.launches += 1;
+    if (err) {
+        b_qhalf<false><<<grid_for(b_qhalf<false>, NTHREADS, items(b, SP_TILE)), NTHREADS, 0, st>>>(B);
+        b.launches += 1;
+    }
+    b_count<<<(b.n + 127) / 128, 128, 0, st>>>(B, 0);
+    b.launches += 1;
+    return cudaGetLastError();
+}
+
+static cudaError_t capture_analysis(BatchImpl& b, cudaStream_t st)
+{
+    const BatchDev B = dev_view(b);
+    cudaError_t e;
+    if (b.obs_total > 0 &&
+        (e = cudaMemcpyAsync(b.d_obs, b.h_obs, sizeof(double) * b.obs_total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return e;
+    b_obs_cells<<<grid_for(b_obs_cells, 128, (items(b, SP_OBS) + 127) / 128), 128, 0, st>>>(B);
+    b_tile_bin<<<grid_for(b_tile_bin, NTHREADS, items(b, SP_BIN)), NTHREADS, 0, st>>>(B);
+    b_innovate<<<grid_for(b_innovate, 128, (items(b, SP_INN) + 127) / 128), 128, 0, st>>>(B);
+    b_hqht<<<grid_for(b_hqht, 256, (items(b, SP_HQ) + 255) / 256), 256, 0, st>>>(B);
+    b_cholesky<<<b.n, 1024, 0, st>>>(B);
+    b_solve<<<grid_for(b_solve, 128, (items(b, SP_PART) + 3) / 4), 128, 0, st>>>(B);
+    b_dots<<<grid_for(b_dots, ana::DOT_THREADS, items(b, SP_DOT)), ana::DOT_THREADS, 0, st>>>(B);
+    b_sync<<<b.n, 1024, 0, st>>>(B);
+    b_form_r<<<grid_for(b_form_r, 256, (items(b, SP_FR) + 255) / 256), 256, 0, st>>>(B);
+    b_block_seq<<<grid_for(b_block_seq, 64, items(b, SP_PART)), 64, 0, st>>>(B);
+    b_qhalf<true><<<grid_for(b_qhalf<true>, NTHREADS, items(b, SP_TILE)), NTHREADS, 0, st>>>(B);
+    b_count<<<(b.n + 127) / 128, 128, 0, st>>>(B, 1);
+    b_nonfinite<<<grid_for(b_nonfinite, NTHREADS, items(b, SP_CFL)), NTHREADS, 0, st>>>(B);
+    b_pack_diag<<<(b.n + 127) / 128, 128, 0, st>>>(B, b.d_diag);
+    b.launches += 14;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemcpyAsync(b.h_diag, b.d_diag, sizeof(double) * 3 * b.n, cudaMemcpyDeviceToHost, st);
+}
+
+// Captures (if needed) and launches one cycle: n_steps model steps, model
+// error after all but the last, then the analysis.
+cudaError_t batch_cycle(BatchImpl& b, int n_steps, cudaStream_t st, cudaStream_t st2)
+{
+    cudaError_t e;
+    if (!b.exec || b.graph_steps != n_steps) {
+        if (b.exec) {
+            cudaGraphExecDestroy(b.exec);
+            b.exec = nullptr;
+        }
+        if (b.graph) {
+            cudaGraphDestroy(b.graph);
+            b.graph = nullptr;
+        }
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(b.d_ctr, b.h_ctr, sizeof(uint32_t) * 2 * b.n, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(st, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            return e;
+        }
+        for (int k = 0; k < n_steps; ++k) {
+            if ((e = capture_model_step(b, st, st2, k + 1 < n_steps)) != cudaSuccess) {
+                cudaGraph_t junk;
+                cudaStreamEndCapture(st, &junk);
+                if (junk) cudaGraphDestroy(junk);
+                return e;
+            }
+        }
+        if ((e = capture_analysis(b, st)) != cudaSuccess) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(st, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            return e;
+        }
+        if ((e = cudaStreamEndCapture(st, &b.graph)) != cudaSuccess) return e;
+        if ((e = cudaGraphInstantiate(&b.exec, b.graph, 0)) != cudaSuccess) return e;
+        b.graph_steps = n_steps;
+    }
+    return cudaGraphLaunch(b.exec, st);
+}
+
+// Times one scheme step of every problem for each candidate shape and keeps
+// the fastest (probe launches leave the state unchanged: they write the other
+// buffer without flipping the parity).
+cudaError_t batch_tune(BatchImpl& b, cudaStream_t st)
+{
+    static const int ncs[] = {2, 3, 4};
+    static const int ths[] = {32, 64, 128};
+    static const int wps[] = {2, 4, 8};
+    cudaError_t e;
+    // every particle one probe step of dt_model / 16
+    b.fixed = 16;
+    {
+        const BatchDev B = dev_view(b);
+        b_zero<<<1, 1, 0, st>>>(B);
+        b_nsub<<<grid_for(b_nsub, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
+    }
+    b.fixed = 0;
+    cudaEvent_t a, z;
+    cudaEventCreate(&a);
+    cudaEventCreate(&z);
+    float best = 1e30f;
+    int bnc = 2, bth = 64, bw = 4;
+    for (int nc : ncs)
+        for (int th : ths)
+            for (int w : wps) {
+                if ((e = batch_set_step_shape(b, nc, th, w)) != cudaSuccess) return e;
+                if ((e = launch_step_nc(b, st)) != cudaSuccess) return e;
+                cudaEventRecord(a, st);
+                if ((e = launch_step_nc(b, st)) != cudaSuccess) return e;
+                cudaEventRecord(z, st);
+                cudaEventSynchronize(z);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, a, z);
+                b.launches += 2;
+                if (ms < best) {
+                    best = ms;
+                    bnc = nc;
+                    bth = th;
+                    bw = w;
+                }
+            }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    b.tuned = true;
+    return batch_set_step_shape(b, bnc, bth, bw);
+}
+
+bool batch_tuned(const BatchImpl& b) { return b.tuned; }
+
+void batch_shape(const BatchImpl& b, int* shape)
+{
+    shape[0] = b.nc;
+    shape[1] = b.n ? b.h_inst[0].step.TH : 0;
+    shape[2] = b.warps;
+}
+
+}  // namespace iewpf

@@ -136,6 +136,25 @@ __device__ __forceinline__ void cubic_weights(float t, float w[4])
     w[3] = 0.5f * (t3 - t2);
 }
 
+// max((|u| + c)/dx, (|v| + c)/dy) of one cell, c = sqrt(g h) (eq. swecfl)
+__device__ __forceinline__ float cfl_cell(const float* __restrict__ U, long long i, const Grid& G)
+{
+    const float h = G.H + U[i];
+    const float c = sqrtf(G.g * h);
+    const float u = U[G.plane + i] / h, v = U[2 * G.plane + i] / h;
+    return fmaxf((fabsf(u) + c) * G.inv_dx, (fabsf(v) + c) * G.inv_dy);
+}
+
+// scheme steps per model step: n_sub = ceil(dt_model / dt_cfl),
+// dt_cfl = courant / 4 / amax
+__device__ __forceinline__ int nsub_of(float amax, double courant, double dt_model, int fixed)
+{
+    if (fixed > 0) return fixed;
+    const double dtc = courant * 0.25 / (double)amax;
+    int n = (int)ceil(dt_model / dtc);
+    return (n >= 1) ? n : 1;
+}
+
 __device__ __forceinline__ float warp_max(float v)
 {
 #pragma unroll

@@ -24,6 +24,19 @@ cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, c
                              cudaStream_t st);
 
 // ---- march.cu -------------------------------------------------------------
+namespace march {
+// Arguments of one scheme step of one problem.
+struct StepArgs {
+    float* buf0;
+    float* buf1;
+    const int* par;
+    const int* nsub;
+    const float* dtp;
+    Grid G;
+    int TH, n_strips, n_chunks;
+};
+}  // namespace march
+
 // tile shape of the register-marching scheme step: NC columns per lane, TH
 // rows per chunk, warps per CTA
 struct MarchShape {

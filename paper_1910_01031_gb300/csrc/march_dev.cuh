@@ -157,17 +157,6 @@ struct Marcher {
     }
 };
 
-// Arguments of one scheme step of one problem.
-struct StepArgs {
-    float* buf0;
-    float* buf1;
-    const int* par;
-    const int* nsub;
-    const float* dtp;
-    Grid G;
-    int TH, n_strips, n_chunks;
-};
-
 // One warp's strip of one chunk of particle p in scheme step s.
 template <int NC>
 __device__ __forceinline__ void march_warp(const StepArgs& a, int p, int chunk, int strip, int s)

@@ -200,10 +200,7 @@ cfl_kernel(const float* __restrict__ buf0, const float* __restrict__ buf1, const
     float m = 0.0f;
     for (long long i = (long long)blockIdx.x * NTHREADS + threadIdx.x; i < G.plane;
          i += (long long)gridDim.x * NTHREADS) {
-        const float h = G.H + U[i];
-        const float c = sqrtf(G.g * h);
-        const float u = U[G.plane + i] / h, v = U[2 * G.plane + i] / h;
-        m = fmaxf(m, fmaxf((fabsf(u) + c) * G.inv_dx, (fabsf(v) + c) * G.inv_dy));
+        m = fmaxf(m, cfl_cell(U, i, G));
     }
     m = warp_max(m);
     __shared__ float red[NTHREADS / 32];
@@ -222,14 +219,7 @@ __global__ void nsub_kernel(const float* __restrict__ amax, int* __restrict__ ns
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ne) return;
-    int n;
-    if (fixed > 0) {
-        n = fixed;
-    } else {
-        const double dtc = courant * 0.25 / (double)amax[p];
-        n = (int)ceil(dt_model / dtc);
-        if (!(n >= 1)) n = 1;
-    }
+    const int n = nsub_of(amax[p], courant, dt_model, fixed);
     nsub[p] = n;
     dtp[p] = (float)(dt_model / (double)n);
     atomicMax(maxsub, n);

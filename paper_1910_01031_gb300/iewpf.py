@@ -26,7 +26,9 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
-           "iewpf_get_stepper", "drifter_forecast_errors"]
+           "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
+           "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
+           "iewpf_batch_work", "iewpf_batch_last_error"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
 
@@ -113,6 +115,15 @@ def load(build_if_needed: bool = True):
     L.iewpf_set_stepper.argtypes = [_vp, c.c_int, c.c_int, c.c_int, c.c_int]
     L.iewpf_tune.argtypes = [_vp, _ip]
     L.iewpf_get_stepper.argtypes = [_vp, _ip]
+    L.iewpf_batch_create.argtypes = [c.POINTER(Params), c.POINTER(_dp), c.c_int, c.POINTER(c.c_void_p)]
+    L.iewpf_batch_destroy.argtypes = [_vp]
+    L.iewpf_batch_instance.argtypes = [_vp, c.c_int, c.POINTER(c.c_void_p)]
+    L.iewpf_batch_tune.argtypes = [_vp, _ip]
+    L.iewpf_batch_cycle.argtypes = [_vp, c.c_int, c.POINTER(Obs), _dp]
+    L.iewpf_batch_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
+    L.iewpf_batch_work.argtypes = [_vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
+    L.iewpf_batch_last_error.argtypes = [_vp]
+    L.iewpf_batch_last_error.restype = c.c_char_p
     _lib = L
     return L
 
@@ -139,15 +150,20 @@ def params_from_config(cfg, n_drifters_max=0, n_obs_max=None):
 class Ensemble:
     """An IEWPF context: the ensemble state on the GPU and its operations."""
 
-    def __init__(self, params: Params, mooring_xy=None):
+    def __init__(self, params: Params, mooring_xy=None, handle=None):
         self.L = load()
         self.P = params
-        h = ctypes.c_void_p()
-        mx = None if mooring_xy is None else _f64(mooring_xy, (-1, 2))
-        rc = self.L.iewpf_create(ctypes.byref(params), _ptr(mx), ctypes.byref(h))
-        if rc != IEWPF_OK:
-            raise IewpfError(rc, "iewpf_create")
-        self.h = h
+        if handle is not None:          # a context owned by a Batch
+            self.h = handle
+            self.owned = False
+        else:
+            h = ctypes.c_void_p()
+            mx = None if mooring_xy is None else _f64(mooring_xy, (-1, 2))
+            rc = self.L.iewpf_create(ctypes.byref(params), _ptr(mx), ctypes.byref(h))
+            if rc != IEWPF_OK:
+                raise IewpfError(rc, "iewpf_create")
+            self.h = h
+            self.owned = True
         self.ne, self.nx, self.ny = params.n_particles, params.nx, params.ny
         nrx, nry, R = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self.L.iewpf_sizes(self.h, ctypes.byref(nrx), ctypes.byref(nry), ctypes.byref(R))
@@ -155,7 +171,8 @@ class Ensemble:
 
     def close(self):
         if getattr(self, "h", None):
-            self.L.iewpf_destroy(self.h)
+            if getattr(self, "owned", True):
+                self.L.iewpf_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -316,6 +333,79 @@ class Ensemble:
     def add_qhalf(self, x):
         x = np.ascontiguousarray(x, np.float32).reshape(self.ne, self.nRx * self.nRy)
         self._chk(self.L.iewpf_add_qhalf(self.h, _ptr(x, _fp)), "add_qhalf")
+
+
+class Batch:
+    """Many independent problems advanced together: one persistent launch per
+    phase and the whole cycle as a CUDA graph (iewpf_batch_*)."""
+
+    def __init__(self, params_list, mooring_xy_list=None):
+        self.L = load()
+        n = len(params_list)
+        arr = (Params * n)(*params_list)
+        self._moor = None
+        mptr = None
+        if mooring_xy_list is not None:
+            self._moor = [None if m is None else _f64(m, (-1, 2)) for m in mooring_xy_list]
+            mptr = (_dp * n)(*[_ptr(m) if m is not None else None for m in self._moor])
+        h = ctypes.c_void_p()
+        rc = self.L.iewpf_batch_create(arr, mptr, n, ctypes.byref(h))
+        if rc != IEWPF_OK:
+            raise IewpfError(rc, "iewpf_batch_create")
+        self.h = h
+        self.n = n
+        self.params = list(params_list)
+        self.instances = []
+        for i in range(n):
+            ch = ctypes.c_void_p()
+            self.L.iewpf_batch_instance(self.h, i, ctypes.byref(ch))
+            self.instances.append(Ensemble(params_list[i], handle=ch))
+
+    def _chk(self, rc, what):
+        if rc != IEWPF_OK:
+            msg = self.L.iewpf_batch_last_error(self.h)
+            raise IewpfError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for e in self.instances:
+                e.h = None
+            self.L.iewpf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self):
+        out = np.zeros(3, np.int32)
+        self._chk(self.L.iewpf_batch_tune(self.h, _ptr(out, _ip)), "batch_tune")
+        return tuple(int(v) for v in out)
+
+    def cycle(self, n_steps, obs):
+        """obs: list of (xy or None, values) per problem; returns diag [n][3]."""
+        keep = []
+        arr = (Obs * self.n)()
+        for i, (xy, val) in enumerate(obs):
+            val = _f64(val, (-1, 2))
+            xy = None if xy is None else _f64(xy, (-1, 2))
+            keep += [val, xy]
+            arr[i] = Obs(val.shape[0], _ptr(xy), _ptr(val))
+        diag = np.zeros((self.n, 3))
+        self._chk(self.L.iewpf_batch_cycle(self.h, int(n_steps), arr, _ptr(diag)), "batch_cycle")
+        return diag
+
+    def stream(self):
+        s = ctypes.c_void_p()
+        self._chk(self.L.iewpf_batch_stream(self.h, ctypes.byref(s)), "batch_stream")
+        return s.value or 0
+
+    def work(self):
+        w, l = ctypes.c_int64(), ctypes.c_int64()
+        self._chk(self.L.iewpf_batch_work(self.h, ctypes.byref(w), ctypes.byref(l)), "batch_work")
+        return w.value, l.value
 
 
 def _torch_stream():
