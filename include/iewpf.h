@@ -165,7 +165,10 @@ IEWPF_API int iewpf_get_drifters(iewpf_ctx_t* ctx, double* xy);
  * every particle, runs `hours` of model steps with model error and stores
  * positions every out_every_s seconds (and at t = 0) into
  * traj[n_out][N_e][n][2], n_out = floor(hours*3600/out_every_s) + 1.
- * use_surrogate must be 0 (the plain stepper). */
+ * use_surrogate = 0 runs the plain stepper; 1 runs the surrogate attached
+ * with iewpf_set_surrogate, k model steps per call (out_every_s must then be
+ * a multiple of k dt_model), the plain stepper taking over for any k steps
+ * whose surrogate state is not finite. */
 IEWPF_API int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours,
                      double out_every_s, double* traj, int use_surrogate);
 
@@ -175,9 +178,10 @@ IEWPF_API int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, doubl
  * E(t) = sqrt(mean_d mean_i |x_{i,d} - x_true,d|^2) against truth
  * ([n_out][n][2], unwrapped positions) and RMSE(t), the same with the
  * ensemble-mean position in place of the truth, into E[n_out] and
- * RMSE[n_out] (FP64).  traj ([n_out][N_e][n][2]) may be NULL. */
+ * RMSE[n_out] (FP64).  traj ([n_out][N_e][n][2]) may be NULL; use_surrogate
+ * as for drifter_forecast. */
 IEWPF_API int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s,
-                                      const double* truth, double* E, double* RMSE, double* traj);
+                                      const double* truth, double* E, double* RMSE, double* traj, int use_surrogate);
 
 /* Checkpoint: raw state, drifters and the two draw counters; because the
  * random numbers are counter-based, a resumed run is bit-identical. */
@@ -329,6 +333,59 @@ IEWPF_API int iewpf_batch_stream(const iewpf_batch_t* b, void** stream);
  * enqueued (a graph replay counts the launches of one capture). */
 IEWPF_API int iewpf_batch_work(iewpf_batch_t* b, int64_t* particle_substeps, int64_t* launches);
 IEWPF_API const char* iewpf_batch_last_error(const iewpf_batch_t* b);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the forecast model.  The paper forecasts with the
+ * numerical scheme only (Sec. 2, Sec. 5.2); this is an addition: a map
+ * f_theta: (eta, hu, hv)(t) -> (eta, hu, hv)(t + k dt_model) used in the
+ * drift forecast in place of k plain model steps (model error is still added
+ * after each of the k steps, from the same Philox streams as the plain path).
+ *
+ * Network: `depth` periodic 3x3 convolutions, 3 -> width -> ... -> width -> 3
+ * channels, SiLU between layers, BF16 weights and activations (NHWC) with
+ * FP32 accumulation on the tensor cores; the input is the state times
+ * in_scale[c] per field and the output times out_scale[c] is the state
+ * change: U(t+k) = U(t) + out_scale * f(in_scale * U(t)).
+ * Training loss: mean over pixels and the 3 fields of
+ * (f(x) - (Y - X) / out_scale)^2.  Parameters are FP32 masters, flat, per
+ * layer l: weights [3][3][cout][cin] (cin padded to 16 for l = 0, cout
+ * padded to 16 for the last layer, padding entries zero), then bias[cout].
+ * nx and ny must be multiples of 16 and 8.  The object lives on the device
+ * current at creation and owns its stream.
+ * ------------------------------------------------------------------------ */
+typedef struct iewpf_surrogate iewpf_surrogate_t;
+
+/* width 64 (or 16), depth >= 2; He-normal weights from `seed`, zero biases,
+ * output layer scaled by 0.1. */
+IEWPF_API int iewpf_surrogate_create(int nx, int ny, int width, int depth, uint64_t seed, iewpf_surrogate_t** out);
+IEWPF_API int iewpf_surrogate_destroy(iewpf_surrogate_t* s);
+IEWPF_API int iewpf_surrogate_param_count(const iewpf_surrogate_t* s, int64_t* n);
+/* FP32 parameters in the flat layout above (host arrays, copied). */
+IEWPF_API int iewpf_surrogate_set_params(iewpf_surrogate_t* s, const float* params);
+IEWPF_API int iewpf_surrogate_get_params(const iewpf_surrogate_t* s, float* params);
+/* in_scale[3], out_scale[3] (> 0) */
+IEWPF_API int iewpf_surrogate_set_scales(iewpf_surrogate_t* s, const double* in_scale, const double* out_scale);
+IEWPF_API int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, double* out_scale);
+/* U ([n][3][ny][nx] host FP32) -> Unext (same layout), one network call. */
+IEWPF_API int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Unext);
+/* Loss and its gradient w.r.t. the FP32 parameters (grad[n_params], may be
+ * NULL) for the pairs X -> Y ([n][3][ny][nx] host FP32). */
+IEWPF_API int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, const float* Y, int n, double* loss,
+                                        float* grad);
+/* Training on n_pairs pairs (psi, M^k psi), M^k = k_steps model steps of the
+ * plain stepper of ctx without model error (the deterministic model the
+ * surrogate stands for), starting from ctx's state; between two rounds of
+ * pairs the ensemble advances k_steps steps with model error (ctx advances).  Sets the scales from the pairs, then runs `epochs`
+ * shuffled passes of Adam (beta 0.9, 0.999, eps 1e-8, step lr) in mini-batches
+ * of `batch`; epoch_loss[epochs] (may be NULL) receives the mean batch loss. */
+IEWPF_API int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs,
+                                    int batch, double lr, double* epoch_loss);
+/* Attach (s != NULL, k_steps >= 1) or detach (s = NULL) a surrogate to ctx
+ * for drifter_forecast(..., use_surrogate = 1).  Not owned by ctx. */
+IEWPF_API int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_steps);
+/* Surrogate calls made for ctx and how many fell back to the plain stepper. */
+IEWPF_API int iewpf_surrogate_stats(const iewpf_ctx_t* ctx, int64_t* calls, int64_t* fallbacks);
+IEWPF_API const char* iewpf_surrogate_last_error(const iewpf_surrogate_t* s);
 
 /* Sizes derived from the parameters. */
 IEWPF_API int iewpf_sizes(const iewpf_ctx_t* ctx, int* nRx, int* nRy, int* stencil_R);

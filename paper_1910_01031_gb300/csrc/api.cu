@@ -13,6 +13,8 @@
 #include "common.cuh"
 #include "batch.h"
 #include "kernels.h"
+#include "surrogate.h"
+#include <random>
 
 using namespace iewpf;
 
@@ -80,6 +82,9 @@ struct iewpf_ctx {
     // counters
     uint32_t step = 0, cycle = 0;
     int64_t launches = 0;    // kernels launched
+    struct iewpf_surrogate* sur = nullptr;   // learned surrogate for drift forecasts (not owned)
+    int sur_k = 0;
+    int64_t sur_calls = 0, sur_fallbacks = 0;
     // scheme-step kernel: 0 = shared-memory tile kernel, 1 = register march
     int stepper = 1;
     MarchShape shape{2, 64, 4};
@@ -417,6 +422,102 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
 
 }  // namespace
 
+struct iewpf_surrogate {
+    Surrogate net;
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    std::string err;
+    // inference scratch of an attached context
+    float* S0 = nullptr;
+    float* S1 = nullptr;
+    double* xy_save = nullptr;
+    size_t cap_state = 0, cap_xy = 0;
+    int chunk = 64;
+};
+
+namespace {
+
+// k model steps of every particle by the surrogate (Sec. 5.2 forecast with a
+// learned model): the state change of k steps from the network, drifters
+// advected with the mean of the velocities before and after, then the k
+// model errors of those steps.  A non-finite result falls back to the plain
+// scheme for the same k steps.
+int surrogate_steps(iewpf_ctx* ctx)
+{
+    iewpf_surrogate* S = ctx->sur;
+    const int ne = ctx->G.ne, k = ctx->sur_k;
+    const size_t nstate = (size_t)ne * 3 * ctx->plane;
+    CK(cudaSetDevice(ctx->dev));
+    if (S->cap_state < nstate) {
+        if (S->S0) cudaFree(S->S0);
+        if (S->S1) cudaFree(S->S1);
+        S->S0 = S->S1 = nullptr;
+        if (cudaMalloc((void**)&S->S0, nstate * 4) != cudaSuccess || cudaMalloc((void**)&S->S1, nstate * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, IEWPF_ENOMEM, "surrogate scratch");
+        }
+        S->cap_state = nstate;
+    }
+    const size_t nxy = (size_t)ne * 2 * std::max(ctx->nd, 1);
+    if (S->cap_xy < nxy) {
+        if (S->xy_save) cudaFree(S->xy_save);
+        if (cudaMalloc((void**)&S->xy_save, nxy * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, IEWPF_ENOMEM, "surrogate scratch");
+        }
+        S->cap_xy = nxy;
+    }
+    int rc;
+    if ((rc = iewpf_get_state(ctx, S->S0, 1, nullptr))) return rc;
+    CK(cudaMemcpyAsync(S->S1, S->S0, nstate * 4, cudaMemcpyDeviceToDevice, ctx->st));
+    if (ctx->nd > 0)
+        CK(cudaMemcpyAsync(S->xy_save, ctx->d_xy, sizeof(double) * 2 * ctx->nd * ne, cudaMemcpyDeviceToDevice, ctx->st));
+    const size_t per = 3 * (size_t)ctx->plane;
+    if ((rc = S->net.ensure_batch(S->chunk))) return fail(ctx, rc, "surrogate activations");
+    for (int p0 = 0; p0 < ne; p0 += S->chunk) {
+        const int nb = std::min(S->chunk, ne - p0);
+        CK(S->net.pack_input(S->S0 + per * p0, nb, ctx->st));
+        CK(S->net.forward(nb, ctx->st));
+        CK(S->net.apply(S->S1 + per * p0, nb, ctx->st));
+        ctx->launches += 2 + S->net.depth;
+    }
+    if (ctx->nd > 0)
+        KL(1, launch_sur_drift(S->S0, S->S1, ne, ctx->nd, ctx->d_xy, ctx->G, ctx->P.dx, ctx->P.dy,
+                               k * ctx->P.dt_model, ctx->st));
+    if ((rc = iewpf_set_state(ctx, S->S1, 1, nullptr))) return rc;
+    for (int i = 0; i < k; ++i) {
+        QhalfArgs A{};
+        A.b0 = ctx->buf[0];
+        A.b1 = ctx->buf[1];
+        A.par = ctx->par;
+        A.wtab = ctx->d_wtab;
+        A.from_philox = 1;
+        A.seed = ctx->P.seed;
+        A.t = ctx->step + i;
+        A.t_dev = nullptr;
+        A.stream = 16u * (uint32_t)ctx->P.instance_id;
+        KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+    }
+    KL(1, launch_nonfinite(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, ctx->flag, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->sur_calls++;
+    if (*ctx->h_flag & FLAG_NONFINITE) {
+        // fall back to the plain scheme for these k steps
+        CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+        if ((rc = iewpf_set_state(ctx, S->S0, 1, nullptr))) return rc;
+        if (ctx->nd > 0)
+            CK(cudaMemcpyAsync(ctx->d_xy, S->xy_save, sizeof(double) * 2 * ctx->nd * ne, cudaMemcpyDeviceToDevice,
+                               ctx->st));
+        ctx->sur_fallbacks++;
+        return forecast_impl(ctx, k, 1, 0);
+    }
+    ctx->step += k;
+    return IEWPF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_ctx_t** out)
@@ -717,7 +818,7 @@ int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, d
                      int use_surrogate)
 {
     if (!ctx) return IEWPF_EINVAL;
-    if (use_surrogate) return fail(ctx, IEWPF_EINVAL, "the surrogate forecast is not available");
+    if (use_surrogate && !ctx->sur) return fail(ctx, IEWPF_EINVAL, "no surrogate attached (iewpf_set_surrogate)");
     if (!xy0 || !traj || n < 1 || n > ctx->P.n_drifters_max || !(hours >= 0) || !(out_every_s > 0))
         return fail(ctx, IEWPF_EINVAL, "bad drifter forecast arguments");
     const double ratio = out_every_s / ctx->P.dt_model;
@@ -732,15 +833,22 @@ int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, d
     if ((rc = iewpf_set_drifters(ctx, rep.data(), n))) return rc;
     const size_t per = (size_t)ne * n * 2;
     std::memcpy(traj, rep.data(), sizeof(double) * per);
+    if (use_surrogate && every % ctx->sur_k != 0)
+        return fail(ctx, IEWPF_EINVAL, "out_every_s must be a multiple of the surrogate's k model steps");
     for (int o = 1; o < n_out; ++o) {
-        if ((rc = iewpf_forecast(ctx, every, 1))) return rc;
+        if (use_surrogate) {
+            for (int c = 0; c < every / ctx->sur_k; ++c)
+                if ((rc = surrogate_steps(ctx))) return rc;
+        } else if ((rc = iewpf_forecast(ctx, every, 1))) {
+            return rc;
+        }
         if ((rc = iewpf_get_drifters(ctx, traj + per * o))) return rc;
     }
     return IEWPF_OK;
 }
 
 int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s,
-                            const double* truth, double* E, double* RMSE, double* traj)
+                            const double* truth, double* E, double* RMSE, double* traj, int use_surrogate)
 {
     if (!ctx) return IEWPF_EINVAL;
     if (!xy0 || !truth || !E || !RMSE || n < 1 || n > ctx->P.n_drifters_max || !(hours >= 0) || !(out_every_s > 0))
@@ -770,9 +878,16 @@ int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double h
     }
     auto body = [&]() -> int {
         CK(cudaMemcpyAsync(d_truth, truth, sizeof(double) * n_out * n * 2, cudaMemcpyHostToDevice, ctx->st));
+        if (use_surrogate && (!ctx->sur || every % ctx->sur_k != 0))
+            return fail(ctx, IEWPF_EINVAL, "surrogate missing or k does not divide the output interval");
         for (int o = 0; o < n_out; ++o) {
             int r;
-            if (o > 0 && (r = iewpf_forecast(ctx, every, 1))) return r;
+            if (o > 0 && use_surrogate) {
+                for (int c = 0; c < every / ctx->sur_k; ++c)
+                    if ((r = surrogate_steps(ctx))) return r;
+            } else if (o > 0 && (r = iewpf_forecast(ctx, every, 1))) {
+                return r;
+            }
             KL(1, launch_drift_errors(ctx->d_xy, d_truth + (size_t)o * n * 2, ne, n, d_err + o, d_err + n_out + o,
                                       ctx->st));
             if (traj)
@@ -1277,6 +1392,290 @@ int iewpf_batch_work(iewpf_batch_t* b, int64_t* particle_substeps, int64_t* laun
 const char* iewpf_batch_last_error(const iewpf_batch_t* b)
 {
     return b ? b->err.c_str() : kNullMsg;
+}
+
+// ---------------------------------------------------------------------------
+// learned surrogate
+// ---------------------------------------------------------------------------
+static int sfail(iewpf_surrogate* s, int code, const std::string& msg)
+{
+    if (s) s->err = msg;
+    return code;
+}
+
+#define SCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return sfail(s, IEWPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+int iewpf_surrogate_destroy(iewpf_surrogate_t* s)
+{
+    if (!s) return IEWPF_OK;
+    cudaSetDevice(s->dev);
+    if (s->st) cudaStreamSynchronize(s->st);
+    if (s->S0) cudaFree(s->S0);
+    if (s->S1) cudaFree(s->S1);
+    if (s->xy_save) cudaFree(s->xy_save);
+    s->net.release();
+    if (s->st) cudaStreamDestroy(s->st);
+    delete s;
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_create(int nx, int ny, int width, int depth, uint64_t seed, iewpf_surrogate_t** out)
+{
+    if (!out) return IEWPF_EINVAL;
+    *out = nullptr;
+    iewpf_surrogate* s = new (std::nothrow) iewpf_surrogate();
+    if (!s) return IEWPF_ENOMEM;
+    cudaGetDevice(&s->dev);
+    int rc = s->net.init(nx, ny, width, depth);
+    if (rc || cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+        iewpf_surrogate_destroy(s);
+        return rc ? rc : IEWPF_ECUDA;
+    }
+    // He-normal initial weights (fan-in 9 cin), zero biases; the output layer
+    // starts small so the initial prediction is close to "no change"
+    std::mt19937_64 gen(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<float> p(s->net.n_params, 0.0f);
+    for (int l = 0; l < s->net.depth; ++l) {
+        const int cin = s->net.layer_cin(l), cout = s->net.layer_cout(l);
+        const int real_in = l == 0 ? 3 : cin, real_out = l == s->net.depth - 1 ? 3 : cout;
+        const double sd = std::sqrt(2.0 / (9.0 * real_in)) * (l == s->net.depth - 1 ? 0.1 : 1.0);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int co = 0; co < cout; ++co)
+                for (int ci = 0; ci < cin; ++ci)
+                    if (co < real_out && ci < real_in)
+                        p[s->net.w_off[l] + ((size_t)tap * cout + co) * cin + ci] = (float)(sd * nd(gen));
+    }
+    if (cudaMemcpy(s->net.master, p.data(), p.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        s->net.cast(s->st) != cudaSuccess || cudaStreamSynchronize(s->st) != cudaSuccess) {
+        iewpf_surrogate_destroy(s);
+        return IEWPF_ECUDA;
+    }
+    *out = s;
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_param_count(const iewpf_surrogate_t* s, int64_t* n)
+{
+    if (!s || !n) return IEWPF_EINVAL;
+    *n = (int64_t)s->net.n_params;
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_set_params(iewpf_surrogate_t* s, const float* params)
+{
+    if (!s || !params) return IEWPF_EINVAL;
+    SCK(cudaSetDevice(s->dev));
+    SCK(cudaMemcpy(s->net.master, params, s->net.n_params * 4, cudaMemcpyHostToDevice));
+    SCK(s->net.cast(s->st));
+    SCK(cudaStreamSynchronize(s->st));
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_get_params(const iewpf_surrogate_t* cs, float* params)
+{
+    iewpf_surrogate* s = const_cast<iewpf_surrogate*>(cs);
+    if (!s || !params) return IEWPF_EINVAL;
+    SCK(cudaSetDevice(s->dev));
+    SCK(cudaMemcpy(params, s->net.master, s->net.n_params * 4, cudaMemcpyDeviceToHost));
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_set_scales(iewpf_surrogate_t* s, const double* in_scale, const double* out_scale)
+{
+    if (!s || !in_scale || !out_scale) return IEWPF_EINVAL;
+    for (int c = 0; c < 3; ++c) {
+        if (!(in_scale[c] > 0) || !(out_scale[c] > 0)) return sfail(s, IEWPF_EINVAL, "scales must be positive");
+        s->net.in_scale[c] = (float)in_scale[c];
+        s->net.out_scale[c] = (float)out_scale[c];
+    }
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, double* out_scale)
+{
+    if (!s || !in_scale || !out_scale) return IEWPF_EINVAL;
+    for (int c = 0; c < 3; ++c) {
+        in_scale[c] = s->net.in_scale[c];
+        out_scale[c] = s->net.out_scale[c];
+    }
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Unext)
+{
+    if (!s || !U || !Unext || n < 1) return IEWPF_EINVAL;
+    SCK(cudaSetDevice(s->dev));
+    const size_t per = 3ull * s->net.nx * s->net.ny;
+    float* d = nullptr;
+    if (cudaMalloc((void**)&d, per * n * 4) != cudaSuccess) return sfail(s, IEWPF_ENOMEM, "input");
+    int rc = s->net.ensure_batch(n);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        if ((e = cudaMemcpyAsync(d, U, per * n * 4, cudaMemcpyHostToDevice, s->st)) == cudaSuccess &&
+            (e = s->net.pack_input(d, n, s->st)) == cudaSuccess && (e = s->net.forward(n, s->st)) == cudaSuccess &&
+            (e = s->net.apply(d, n, s->st)) == cudaSuccess)
+            e = cudaMemcpyAsync(Unext, d, per * n * 4, cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    }
+    cudaFree(d);
+    if (rc) return sfail(s, rc, "activations");
+    if (e != cudaSuccess) return sfail(s, IEWPF_ECUDA, cudaGetErrorString(e));
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, const float* Y, int n, double* loss, float* grad)
+{
+    if (!s || !X || !Y || n < 1) return IEWPF_EINVAL;
+    SCK(cudaSetDevice(s->dev));
+    const size_t per = 3ull * s->net.nx * s->net.ny;
+    float *dx = nullptr, *dy = nullptr;
+    if (cudaMalloc((void**)&dx, per * n * 4) != cudaSuccess || cudaMalloc((void**)&dy, per * n * 4) != cudaSuccess) {
+        if (dx) cudaFree(dx);
+        return sfail(s, IEWPF_ENOMEM, "pairs");
+    }
+    int rc = s->net.ensure_batch(n);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        if ((e = cudaMemcpyAsync(dx, X, per * n * 4, cudaMemcpyHostToDevice, s->st)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(dy, Y, per * n * 4, cudaMemcpyHostToDevice, s->st)) == cudaSuccess &&
+            (e = s->net.pack_input(dx, n, s->st)) == cudaSuccess && (e = s->net.pack_target(dx, dy, n, s->st)) == cudaSuccess &&
+            (e = s->net.forward(n, s->st)) == cudaSuccess && (e = s->net.backward(n, s->st)) == cudaSuccess) {
+            if (loss) e = cudaMemcpyAsync(loss, s->net.dloss, 8, cudaMemcpyDeviceToHost, s->st);
+            if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, s->net.grad, s->net.n_params * 4, cudaMemcpyDeviceToHost, s->st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    }
+    cudaFree(dx);
+    cudaFree(dy);
+    if (rc) return sfail(s, rc, "activations");
+    if (e != cudaSuccess) return sfail(s, IEWPF_ECUDA, cudaGetErrorString(e));
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs, int batch,
+                          double lr, double* epoch_loss)
+{
+    if (!s || !ctx || n_pairs < 1 || k_steps < 1 || epochs < 0 || batch < 1 || !(lr > 0)) return IEWPF_EINVAL;
+    if (ctx->P.nx != s->net.nx || ctx->P.ny != s->net.ny) return sfail(s, IEWPF_EINVAL, "grid mismatch");
+    SCK(cudaSetDevice(s->dev));
+    const int ne = ctx->G.ne;
+    const size_t per = 3ull * s->net.nx * s->net.ny;
+    float *X = nullptr, *Y = nullptr, *bx = nullptr, *by = nullptr;
+    auto cleanup = [&]() {
+        for (float* p : {X, Y, bx, by})
+            if (p) cudaFree(p);
+    };
+    if (cudaMalloc((void**)&X, per * n_pairs * 4) != cudaSuccess || cudaMalloc((void**)&Y, per * n_pairs * 4) != cudaSuccess ||
+        cudaMalloc((void**)&bx, per * batch * 4) != cudaSuccess || cudaMalloc((void**)&by, per * batch * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return sfail(s, IEWPF_ENOMEM, "training pairs");
+    }
+    int rc = IEWPF_OK;
+    // pairs (psi, M^k psi) of the plain scheme without model error (the
+    // surrogate stands for the deterministic model; model error is added
+    // after it); between pairs the ensemble advances k steps with model error
+    float* snap = nullptr;
+    if (cudaMalloc((void**)&snap, per * ne * 4) != cudaSuccess) {
+        cleanup();
+        return sfail(s, IEWPF_ENOMEM, "snapshot");
+    }
+    for (int got = 0; got < n_pairs && !rc;) {
+        const int take = std::min(ne, n_pairs - got);
+        if ((rc = iewpf_get_state(ctx, snap, 1, nullptr))) break;
+        if (cudaMemcpy(X + per * got, snap, per * take * 4, cudaMemcpyDeviceToDevice) != cudaSuccess) rc = IEWPF_ECUDA;
+        if (!rc && (rc = iewpf_forecast(ctx, k_steps, 0))) break;
+        if (!rc && (rc = iewpf_get_state(ctx, snap, 1, nullptr))) break;
+        if (!rc && cudaMemcpy(Y + per * got, snap, per * take * 4, cudaMemcpyDeviceToDevice) != cudaSuccess) rc = IEWPF_ECUDA;
+        if (!rc && (rc = iewpf_forecast(ctx, k_steps, 1))) break;
+        got += take;
+    }
+    cudaFree(snap);
+    if (rc) {
+        cleanup();
+        return sfail(s, rc, std::string("generating pairs: ") + ctx->err);
+    }
+    // normalisation from the data: input ~ unit spread, output change ~ unit spread
+    {
+        const size_t sample = std::min<size_t>(n_pairs, 32) * per;
+        std::vector<float> hx(sample), hy(sample);
+        cudaMemcpy(hx.data(), X, sample * 4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(hy.data(), Y, sample * 4, cudaMemcpyDeviceToHost);
+        const size_t plane = (size_t)s->net.nx * s->net.ny;
+        for (int c = 0; c < 3; ++c) {
+            double sx = 0, sxx = 0, sd = 0, sdd = 0;
+            size_t cnt = 0;
+            for (size_t b = 0; b < sample / per; ++b)
+                for (size_t i = 0; i < plane; ++i) {
+                    const double x = hx[b * per + c * plane + i], d = hy[b * per + c * plane + i] - x;
+                    sx += x; sxx += x * x; sd += d; sdd += d * d;
+                    ++cnt;
+                }
+            const double vx = sxx / cnt - (sx / cnt) * (sx / cnt), vd = sdd / cnt - (sd / cnt) * (sd / cnt);
+            s->net.in_scale[c] = (float)(1.0 / std::sqrt(std::max(vx, 1e-30)));
+            s->net.out_scale[c] = (float)std::sqrt(std::max(vd, 1e-30));
+        }
+    }
+    if ((rc = s->net.ensure_batch(batch))) {
+        cleanup();
+        return sfail(s, rc, "activations");
+    }
+    std::mt19937_64 gen(12345);
+    std::vector<int> order(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) order[i] = i;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[gen() % (uint64_t)(i + 1)]);
+        double acc = 0.0;
+        int nbat = 0;
+        for (int b0 = 0; b0 + batch <= n_pairs; b0 += batch) {
+            for (int j = 0; j < batch; ++j) {
+                SCK(cudaMemcpyAsync(bx + per * j, X + per * order[b0 + j], per * 4, cudaMemcpyDeviceToDevice, s->st));
+                SCK(cudaMemcpyAsync(by + per * j, Y + per * order[b0 + j], per * 4, cudaMemcpyDeviceToDevice, s->st));
+            }
+            SCK(s->net.pack_input(bx, batch, s->st));
+            SCK(s->net.pack_target(bx, by, batch, s->st));
+            SCK(s->net.forward(batch, s->st));
+            SCK(s->net.backward(batch, s->st));
+            SCK(s->net.adam_step((float)lr, s->st));
+            double l = 0.0;
+            SCK(cudaMemcpyAsync(&l, s->net.dloss, 8, cudaMemcpyDeviceToHost, s->st));
+            SCK(cudaStreamSynchronize(s->st));
+            acc += l;
+            ++nbat;
+        }
+        if (epoch_loss) epoch_loss[ep] = nbat ? acc / nbat : 0.0;
+    }
+    cleanup();
+    return IEWPF_OK;
+}
+
+int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_steps)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (s && (k_steps < 1 || s->net.nx != ctx->P.nx || s->net.ny != ctx->P.ny))
+        return fail(ctx, IEWPF_EINVAL, "surrogate grid or k mismatch");
+    ctx->sur = s;
+    ctx->sur_k = s ? k_steps : 0;
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_stats(const iewpf_ctx_t* ctx, int64_t* calls, int64_t* fallbacks)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (calls) *calls = ctx->sur_calls;
+    if (fallbacks) *fallbacks = ctx->sur_fallbacks;
+    return IEWPF_OK;
+}
+
+const char* iewpf_surrogate_last_error(const iewpf_surrogate_t* s)
+{
+    return s ? s->err.c_str() : kNullMsg;
 }
 
 }  // extern "C"

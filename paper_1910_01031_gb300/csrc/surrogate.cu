@@ -1,0 +1,650 @@
+// Learned surrogate of the scheme: a periodic 3x3 convolutional network (width
+// 64, BF16 weights and activations, FP32 accumulation on the tensor cores)
+// that maps the normalised state (eta, hu, hv) to the change of the state over
+// k model steps, trained on pairs the plain scheme generates.  Hand-written
+// kernels for the forward convolution (implicit GEMM, bias + SiLU fused), the
+// backward data pass (the same kernel with the flipped, transposed weights and
+// the activation derivative fused), the weight gradients (implicit GEMM over
+// pixels, deterministic two-level reduction), the loss, and Adam.
+//
+// Tensor layout: activations NHWC [batch][ny][nx][C] bf16 with C = 16
+// (network input, 3 used) or 64; weights [tap = 3 ky + kx][cout][cin] bf16.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/iewpf.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "surrogate.h"
+
+#include <cuda_bf16.h>
+
+namespace iewpf {
+
+namespace {
+
+constexpr int TROWS = 8, TCOLS = 16;      // pixel tile of the convolution kernels (128 pixels)
+constexpr int CONV_THREADS = 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+// D = A (16x16 bf16, row) * B (16x8 bf16, col) + D, fp32
+__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu(float z)
+{
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+enum ConvMode : int {
+    MODE_HIDDEN = 0,    // z = conv + b: store z and silu(z) (bf16)
+    MODE_OUT = 1,       // out = conv + b: store fp32 (first 3 channels)
+    MODE_DGRAD = 2,     // dA = conv(dZ, flipped W^T): store dZ_prev = dA * silu'(z_prev) (bf16)
+};
+
+// Implicit-GEMM 3x3 periodic convolution over 8x16 pixel tiles, all COUT
+// output channels per CTA, persistent over tiles.  CIN, COUT in {16, 64}.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(CONV_THREADS)
+conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
+            int nb, int ny, int nx, __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout,
+            float* __restrict__ fout, const __nv_bfloat16* __restrict__ zprev)
+{
+    constexpr int CP = CIN + 8;               // padded channel stride (conflict-free ldmatrix)
+    constexpr int PR = TROWS + 2, PC = TCOLS + 2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem);                  // [9][COUT][CP]
+    __nv_bfloat16* Ps = Ws + 9 * COUT * CP;                                      // [PR][PC][CP]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // weights once per CTA
+    for (int i = tid; i < 9 * COUT * (CIN / 8); i += CONV_THREADS) {
+        const int c8 = i % (CIN / 8), row = i / (CIN / 8);
+        *reinterpret_cast<uint4*>(Ws + row * CP + c8 * 8) = *reinterpret_cast<const uint4*>(W + row * CIN + c8 * 8);
+    }
+    const int tiles_x = nx / TCOLS, tiles_y = ny / TROWS;
+    const long long ntiles = (long long)nb * tiles_x * tiles_y;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = (int)(tile / (tiles_x * tiles_y));
+        const int rem = (int)(tile % (tiles_x * tiles_y));
+        const int y0 = (rem / tiles_x) * TROWS, x0 = (rem % tiles_x) * TCOLS;
+        __syncthreads();
+        for (int i = tid; i < PR * PC * (CIN / 8); i += CONV_THREADS) {
+            const int c8 = i % (CIN / 8), pix = i / (CIN / 8);
+            const int py = pix / PC, px = pix % PC;
+            const int gy = pmod(y0 - 1 + py, ny), gx = pmod(x0 - 1 + px, nx);
+            *reinterpret_cast<uint4*>(Ps + pix * CP + c8 * 8) =
+                *reinterpret_cast<const uint4*>(in + (((long long)b * ny + gy) * nx + gx) * CIN + c8 * 8);
+        }
+        __syncthreads();
+        float acc[COUT / 8][4];
+#pragma unroll
+        for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+        // warp w: pixel row w of the tile, 16 pixels
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                const int mi = lane >> 3, r = lane & 7;
+                const int pc = (mi & 1) * 8 + r + kx;
+                const uint32_t aaddr = smem_u32(Ps + ((warp + ky) * PC + pc) * CP + kc * 16 + (mi >> 1) * 8);
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4(aaddr, a0, a1, a2, a3);
+#pragma unroll
+                for (int j = 0; j < COUT / 8; j += 2) {
+                    const int n = (j + (mi >> 1)) * 8 + r;
+                    const uint32_t baddr = smem_u32(Ws + (tap * COUT + n) * CP + kc * 16 + (mi & 1) * 8);
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4(baddr, b0, b1, b2, b3);
+                    mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                    mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+        // epilogue: rows lane/4 and lane/4 + 8 of the warp's 16 pixels
+        const int gy = y0 + warp;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int gx = x0 + (lane >> 2) + half * 8;
+            const long long pix = ((long long)b * ny + gy) * nx + gx;
+#pragma unroll
+            for (int j = 0; j < COUT / 8; ++j) {
+                const int co = j * 8 + (lane & 3) * 2;
+                float v0 = acc[j][half * 2], v1 = acc[j][half * 2 + 1];
+                if (MODE == MODE_HIDDEN) {
+                    v0 += bias[co];
+                    v1 += bias[co + 1];
+                    *reinterpret_cast<__nv_bfloat162*>(zout + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
+                    *reinterpret_cast<__nv_bfloat162*>(aout + pix * COUT + co) =
+                        __floats2bfloat162_rn(silu(v0), silu(v1));
+                } else if (MODE == MODE_OUT) {
+                    if (co < 3) fout[pix * 3 + co] = v0 + bias[co];
+                    if (co + 1 < 3) fout[pix * 3 + co + 1] = v1 + bias[co + 1];
+                } else {
+                    const __nv_bfloat162 z = *reinterpret_cast<const __nv_bfloat162*>(zprev + pix * COUT + co);
+                    v0 *= dsilu(__bfloat162float(z.x));
+                    v1 *= dsilu(__bfloat162float(z.y));
+                    *reinterpret_cast<__nv_bfloat162*>(aout + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+    }
+}
+
+// Weight gradients of one tap: dW[tap][co][ci] = sum_p dZ[p][co] X[p + off(tap)][ci]
+// over the pixel tiles [t0, t1) of CTA (tap, group); partial sums per group.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(CONV_THREADS)
+wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ X, int nb, int ny, int nx,
+             int tiles_per_group, float* __restrict__ partial)
+{
+    constexpr int CPI = CIN + 8, CPO = COUT + 8;
+    constexpr int MT = COUT / 16, NT = CIN / 8;          // m16 blocks (co), n8 blocks (ci)
+    constexpr int TILES = MT * NT;                        // of the 64x64 (or smaller) output
+    constexpr int PER_WARP = (TILES + 7) / 8;
+    __shared__ __align__(16) __nv_bfloat16 Ds[TROWS * TCOLS * CPO];
+    __shared__ __align__(16) __nv_bfloat16 Xs[TROWS * TCOLS * CPI];
+    const int tap = blockIdx.y, group = blockIdx.x;
+    const int ky = tap / 3, kx = tap % 3;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = nx / TCOLS, tiles_y = ny / TROWS;
+    const long long ntiles = (long long)nb * tiles_x * tiles_y;
+    float acc[PER_WARP][4];
+#pragma unroll
+    for (int q = 0; q < PER_WARP; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0f;
+    const long long t0 = (long long)group * tiles_per_group, t1 = min(ntiles, t0 + tiles_per_group);
+    for (long long tile = t0; tile < t1; ++tile) {
+        const int b = (int)(tile / (tiles_x * tiles_y));
+        const int rem = (int)(tile % (tiles_x * tiles_y));
+        const int y0 = (rem / tiles_x) * TROWS, x0 = (rem % tiles_x) * TCOLS;
+        __syncthreads();
+        for (int i = tid; i < TROWS * TCOLS * (COUT / 8); i += CONV_THREADS) {
+            const int c8 = i % (COUT / 8), pix = i / (COUT / 8);
+            const int gy = y0 + pix / TCOLS, gx = x0 + pix % TCOLS;
+            *reinterpret_cast<uint4*>(Ds + pix * CPO + c8 * 8) =
+                *reinterpret_cast<const uint4*>(dz + (((long long)b * ny + gy) * nx + gx) * COUT + c8 * 8);
+        }
+        for (int i = tid; i < TROWS * TCOLS * (CIN / 8); i += CONV_THREADS) {
+            const int c8 = i % (CIN / 8), pix = i / (CIN / 8);
+            const int gy = pmod(y0 + pix / TCOLS + ky - 1, ny), gx = pmod(x0 + pix % TCOLS + kx - 1, nx);
+            *reinterpret_cast<uint4*>(Xs + pix * CPI + c8 * 8) =
+                *reinterpret_cast<const uint4*>(X + (((long long)b * ny + gy) * nx + gx) * CIN + c8 * 8);
+        }
+        __syncthreads();
+        // K = 128 pixels in 8 steps of 16
+#pragma unroll 1
+        for (int k0 = 0; k0 < TROWS * TCOLS; k0 += 16) {
+#pragma unroll
+            for (int q = 0; q < PER_WARP; ++q) {
+                const int t = warp * PER_WARP + q;
+                if (t < TILES) {
+                    const int mt = t / NT, nt = t % NT;
+                    const int mi = lane >> 3, r = lane & 7;
+                    // A = dZ^T (co x p): stored [p][co], transposed load
+                    const uint32_t aaddr = smem_u32(Ds + (k0 + (mi >> 1) * 8 + r) * CPO + mt * 16 + (mi & 1) * 8);
+                    uint32_t a0, a1, a2, a3;
+                    ldsm_x4_t(aaddr, a0, a1, a2, a3);
+                    // B = X (p x ci): stored [p][ci], transposed load of two 8x8 blocks
+                    const int bi = lane & 15;
+                    const uint32_t baddr = smem_u32(Xs + (k0 + (bi >> 3) * 8 + (bi & 7)) * CPI + nt * 8);
+                    uint32_t b0, b1;
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                                 : "=r"(b0), "=r"(b1)
+                                 : "r"(baddr));
+                    mma_bf16(acc[q], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+    }
+    // partial[group][tap][co][ci]
+#pragma unroll
+    for (int q = 0; q < PER_WARP; ++q) {
+        const int t = warp * PER_WARP + q;
+        if (t < TILES) {
+            const int mt = t / NT, nt = t % NT;
+            const int co = mt * 16 + (lane >> 2), ci = nt * 8 + (lane & 3) * 2;
+            float* P = partial + (((long long)group * 9 + tap) * COUT) * CIN;
+            P[co * CIN + ci] = acc[q][0];
+            P[co * CIN + ci + 1] = acc[q][1];
+            P[(co + 8) * CIN + ci] = acc[q][2];
+            P[(co + 8) * CIN + ci + 1] = acc[q][3];
+        }
+    }
+}
+
+// grad[i] = sum over groups of partial (fixed order)
+__global__ void reduce_groups_kernel(const float* __restrict__ partial, int groups, long long n, float* __restrict__ grad)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int g = 0; g < groups; ++g) s += partial[(long long)g * n + i];
+    grad[i] = s;
+}
+
+// bias gradients: db[co] = sum_p dZ[p][co]; one CTA per channel, fixed order
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dz, long long npix, int C, float* __restrict__ db)
+{
+    const int co = blockIdx.x;
+    float s = 0.0f;
+    for (long long p = threadIdx.x; p < npix; p += blockDim.x) s += __bfloat162float(dz[p * C + co]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[co] = red[0];
+}
+
+// fp32 last-layer output (3 ch) vs target (3 ch): loss partials (per block)
+// and dZ_out = 2 (out - target) / count into the 16-channel bf16 buffer
+__global__ void loss_kernel(const float* __restrict__ out, const float* __restrict__ target, long long npix,
+                            double inv_count, __nv_bfloat16* __restrict__ dz, double* __restrict__ partial)
+{
+    double s = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
+        __align__(16) __nv_bfloat16 g[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) g[c] = __float2bfloat16(0.0f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = out[p * 3 + c] - target[p * 3 + c];
+            s += (double)r * r;
+            g[c] = __float2bfloat16((float)(2.0 * inv_count) * r);
+        }
+        uint4* d = reinterpret_cast<uint4*>(dz + p * 16);
+        d[0] = *reinterpret_cast<uint4*>(&g[0]);
+        d[1] = *reinterpret_cast<uint4*>(&g[8]);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_kernel(const double* __restrict__ partial, int n, double scale, double* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += partial[i];
+        *out = s * scale;
+    }
+}
+
+// Adam on fp32 master parameters; then the bf16 copies of the weights in the
+// forward layout [tap][co][ci] and the backward-data layout [8 - tap][ci][co]
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void cast_weights_kernel(const float* __restrict__ w, int cin, int cout, __nv_bfloat16* __restrict__ wf,
+                                    __nv_bfloat16* __restrict__ wd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * cin * cout) return;
+    const int ci = i % cin, co = (i / cin) % cout, tap = i / (cin * cout);
+    const __nv_bfloat16 b = __float2bfloat16(w[i]);
+    wf[i] = b;
+    wd[((8 - tap) * cin + ci) * cout + co] = b;
+}
+
+// state [n][3][ny][nx] fp32 -> network input [n][ny][nx][16] bf16 (normalised)
+__global__ void pack_input_kernel(const float* __restrict__ U, int n, int ny, int nx, float s0, float s1, float s2,
+                                  __nv_bfloat16* __restrict__ x)
+{
+    const long long plane = (long long)ny * nx;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * plane) return;
+    const long long b = p / plane, c = p % plane;
+    __align__(16) __nv_bfloat16 g[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[k] = __float2bfloat16(0.0f);
+    g[0] = __float2bfloat16(U[(b * 3 + 0) * plane + c] * s0);
+    g[1] = __float2bfloat16(U[(b * 3 + 1) * plane + c] * s1);
+    g[2] = __float2bfloat16(U[(b * 3 + 2) * plane + c] * s2);
+    uint4* d = reinterpret_cast<uint4*>(x + p * 16);
+    d[0] = *reinterpret_cast<uint4*>(&g[0]);
+    d[1] = *reinterpret_cast<uint4*>(&g[8]);
+}
+
+// target of a pair: normalised change (Y - X) / scale, [n][ny][nx][3] fp32
+__global__ void pack_target_kernel(const float* __restrict__ X, const float* __restrict__ Y, int n, int ny, int nx,
+                                   float d0, float d1, float d2, float* __restrict__ t)
+{
+    const long long plane = (long long)ny * nx;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * plane) return;
+    const long long b = p / plane, c = p % plane;
+    t[p * 3 + 0] = (Y[(b * 3 + 0) * plane + c] - X[(b * 3 + 0) * plane + c]) * d0;
+    t[p * 3 + 1] = (Y[(b * 3 + 1) * plane + c] - X[(b * 3 + 1) * plane + c]) * d1;
+    t[p * 3 + 2] = (Y[(b * 3 + 2) * plane + c] - X[(b * 3 + 2) * plane + c]) * d2;
+}
+
+// state += change from the network output (scaled back); out [n][ny][nx][3]
+__global__ void apply_output_kernel(float* __restrict__ U, const float* __restrict__ out, int n, int ny, int nx,
+                                    float e0, float e1, float e2)
+{
+    const long long plane = (long long)ny * nx;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * plane) return;
+    const long long b = p / plane, c = p % plane;
+    U[(b * 3 + 0) * plane + c] += out[p * 3 + 0] * e0;
+    U[(b * 3 + 1) * plane + c] += out[p * 3 + 1] * e1;
+    U[(b * 3 + 2) * plane + c] += out[p * 3 + 2] * e2;
+}
+
+__global__ void sur_drift_kernel(const float* __restrict__ S0, const float* __restrict__ S1, int ne, int nd,
+                                 double* __restrict__ xy, Grid G, double dx, double dy, double T)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne * nd) return;
+    const int p = i / nd;
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    const int j = pmod((int)floor(x / dx), G.nx), k = pmod((int)floor(y / dy), G.ny);
+    const long long c = (long long)k * G.nx + j, b = (long long)p * 3 * G.plane;
+    const double h0 = G.H + S0[b + c], h1 = G.H + S1[b + c];
+    const double u = 0.5 * (S0[b + G.plane + c] / h0 + S1[b + G.plane + c] / h1);
+    const double v = 0.5 * (S0[b + 2 * G.plane + c] / h0 + S1[b + 2 * G.plane + c] / h1);
+    xy[2 * i] = x + T * u;
+    xy[2 * i + 1] = y + T * v;
+}
+
+template <int CIN, int COUT, int MODE>
+size_t conv_smem()
+{
+    return (size_t)(9 * COUT * (CIN + 8) + (TROWS + 2) * (TCOLS + 2) * (CIN + 8)) * sizeof(__nv_bfloat16);
+}
+
+template <int CIN, int COUT, int MODE>
+cudaError_t conv(const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias, int nb, int ny, int nx,
+                 __nv_bfloat16* z, __nv_bfloat16* a, float* f, const __nv_bfloat16* zprev, cudaStream_t st)
+{
+    const size_t sm = conv_smem<CIN, COUT, MODE>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conv_kernel<CIN, COUT, MODE>, CONV_THREADS, sm);
+    const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
+    const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per, 1));
+    conv_kernel<CIN, COUT, MODE><<<grid, CONV_THREADS, sm, st>>>(in, W, bias, nb, ny, nx, z, a, f, zprev);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad(const __nv_bfloat16* dz, const __nv_bfloat16* X, int nb, int ny, int nx, int groups, float* partial,
+                  float* grad, cudaStream_t st)
+{
+    const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
+    const int tpg = (int)((tiles + groups - 1) / groups);
+    wgrad_kernel<CIN, COUT><<<dim3(groups, 9), CONV_THREADS, 0, st>>>(dz, X, nb, ny, nx, tpg, partial);
+    const long long n = 9LL * CIN * COUT;
+    reduce_groups_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, groups, n, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sur_drift(const float* S0, const float* S1, int ne, int nd, double* xy, const Grid& G, double dx,
+                             double dy, double T, cudaStream_t st)
+{
+    const int n = ne * nd;
+    if (n > 0) sur_drift_kernel<<<(n + 127) / 128, 128, 0, st>>>(S0, S1, ne, nd, xy, G, dx, dy, T);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// host: the network and its training
+// ---------------------------------------------------------------------------
+Surrogate::~Surrogate() { release(); }
+
+void Surrogate::release()
+{
+    for (void* p : owned)
+        if (p) cudaFree(p);
+    owned.clear();
+}
+
+static void sfree(Surrogate& s, void* p)
+{
+    if (!p) return;
+    for (auto& q : s.owned)
+        if (q == p) {
+            cudaFree(q);
+            q = nullptr;
+        }
+}
+
+template <typename T>
+static T* salloc(Surrogate& s, size_t n)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    s.owned.push_back(p);
+    return static_cast<T*>(p);
+}
+
+int Surrogate::layer_cin(int l) const { return l == 0 ? 16 : width; }
+int Surrogate::layer_cout(int l) const { return l == depth - 1 ? 16 : width; }
+size_t Surrogate::layer_w(int l) const { return 9ull * layer_cin(l) * layer_cout(l); }
+
+int Surrogate::init(int nx_, int ny_, int width_, int depth_)
+{
+    nx = nx_;
+    ny = ny_;
+    width = width_;
+    depth = depth_;
+    if (width != 64 || depth < 2 || depth > 16 || nx % TCOLS || ny % TROWS) return IEWPF_EINVAL;
+    n_params = 0;
+    for (int l = 0; l < depth; ++l) {
+        w_off.push_back(n_params);
+        n_params += layer_w(l);
+        b_off.push_back(n_params);
+        n_params += layer_cout(l);
+    }
+    master = salloc<float>(*this, n_params);
+    grad = salloc<float>(*this, n_params);
+    adam_m = salloc<float>(*this, n_params);
+    adam_v = salloc<float>(*this, n_params);
+    for (int l = 0; l < depth; ++l) {
+        wf.push_back(salloc<__nv_bfloat16>(*this, layer_w(l)));
+        wd.push_back(salloc<__nv_bfloat16>(*this, layer_w(l)));
+    }
+    if (!master || !grad || !adam_m || !adam_v) return IEWPF_ENOMEM;
+    for (auto* p : wf)
+        if (!p) return IEWPF_ENOMEM;
+    for (auto* p : wd)
+        if (!p) return IEWPF_ENOMEM;
+    cudaMemset(adam_m, 0, n_params * sizeof(float));
+    cudaMemset(adam_v, 0, n_params * sizeof(float));
+    return IEWPF_OK;
+}
+
+int Surrogate::ensure_batch(int nb)
+{
+    if (nb <= cap_batch) return IEWPF_OK;
+    // activations per layer: input (16 ch), then z and a per hidden layer
+    const size_t pix = (size_t)nb * nx * ny;
+    for (void* p : {(void*)x_in, (void*)out, (void*)target, (void*)dz_a, (void*)dz_b, (void*)dz_out, (void*)wpartial,
+                    (void*)lpartial, (void*)dloss})
+        sfree(*this, p);
+    for (auto* p : z) sfree(*this, p);
+    for (auto* p : a) sfree(*this, p);
+    cap_batch = 0;
+    x_in = salloc<__nv_bfloat16>(*this, pix * 16);
+    z.assign(depth, nullptr);
+    a.assign(depth, nullptr);
+    for (int l = 0; l + 1 < depth; ++l) {
+        z[l] = salloc<__nv_bfloat16>(*this, pix * width);
+        a[l] = salloc<__nv_bfloat16>(*this, pix * width);
+    }
+    out = salloc<float>(*this, pix * 3);
+    target = salloc<float>(*this, pix * 3);
+    dz_a = salloc<__nv_bfloat16>(*this, pix * width);
+    dz_b = salloc<__nv_bfloat16>(*this, pix * width);
+    dz_out = salloc<__nv_bfloat16>(*this, pix * 16);
+    const int groups = wgrad_groups(nb);
+    wpartial = salloc<float>(*this, (size_t)groups * 9 * width * width);
+    lpartial = salloc<double>(*this, 1024);
+    dloss = salloc<double>(*this, 1);
+    if (!x_in || !out || !target || !dz_a || !dz_b || !dz_out || !wpartial || !lpartial || !dloss) return IEWPF_ENOMEM;
+    for (int l = 0; l + 1 < depth; ++l)
+        if (!z[l] || !a[l]) return IEWPF_ENOMEM;
+    cap_batch = nb;
+    return IEWPF_OK;
+}
+
+int Surrogate::wgrad_groups(int nb) const
+{
+    const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
+    return (int)std::max<long long>(1, std::min<long long>(256, tiles / 16));
+}
+
+cudaError_t Surrogate::cast(cudaStream_t st)
+{
+    for (int l = 0; l < depth; ++l) {
+        const int n = (int)layer_w(l);
+        cast_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(master + w_off[l], layer_cin(l), layer_cout(l), wf[l], wd[l]);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t Surrogate::forward(int nb, cudaStream_t st)
+{
+    cudaError_t e;
+    const __nv_bfloat16* in = x_in;
+    for (int l = 0; l < depth; ++l) {
+        const float* bias = master + b_off[l];
+        if (l == 0) e = conv<16, 64, MODE_HIDDEN>(in, wf[l], bias, nb, ny, nx, z[l], a[l], nullptr, nullptr, st);
+        else if (l + 1 < depth) e = conv<64, 64, MODE_HIDDEN>(in, wf[l], bias, nb, ny, nx, z[l], a[l], nullptr, nullptr, st);
+        else e = conv<64, 16, MODE_OUT>(in, wf[l], bias, nb, ny, nx, nullptr, nullptr, out, nullptr, st);
+        if (e != cudaSuccess) return e;
+        if (l + 1 < depth) in = a[l];
+    }
+    return cudaSuccess;
+}
+
+// loss of the current forward pass against `target`, gradients into grad
+cudaError_t Surrogate::backward(int nb, cudaStream_t st)
+{
+    const long long pix = (long long)nb * nx * ny;
+    loss_kernel<<<1024, 256, 0, st>>>(out, target, pix, 1.0 / (3.0 * pix), dz_out, lpartial);
+    sum_kernel<<<1, 32, 0, st>>>(lpartial, 1024, 1.0 / (3.0 * pix), dloss);
+    const int groups = wgrad_groups(nb);
+    cudaError_t e;
+    // last layer (64 -> 16)
+    const int L = depth - 1;
+    if ((e = wgrad<64, 16>(dz_out, a[L - 1], nb, ny, nx, groups, wpartial, grad + w_off[L], st)) != cudaSuccess) return e;
+    bias_grad_kernel<<<16, 256, 0, st>>>(dz_out, pix, 16, grad + b_off[L]);
+    // dZ of layer L-1 = conv(dZ_out, Wd_L) * silu'(z[L-1])
+    if ((e = conv<16, 64, MODE_DGRAD>(dz_out, wd[L], nullptr, nb, ny, nx, nullptr, dz_a, nullptr, z[L - 1], st)) !=
+        cudaSuccess)
+        return e;
+    __nv_bfloat16* cur = dz_a;
+    __nv_bfloat16* nxt = dz_b;
+    for (int l = L - 1; l >= 0; --l) {
+        const __nv_bfloat16* X = l == 0 ? x_in : a[l - 1];
+        if (l == 0) e = wgrad<16, 64>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
+        else e = wgrad<64, 64>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
+        if (e != cudaSuccess) return e;
+        bias_grad_kernel<<<64, 256, 0, st>>>(cur, pix, 64, grad + b_off[l]);
+        if (l > 0) {
+            if ((e = conv<64, 64, MODE_DGRAD>(cur, wd[l], nullptr, nb, ny, nx, nullptr, nxt, nullptr, z[l - 1], st)) !=
+                cudaSuccess)
+                return e;
+            std::swap(cur, nxt);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t Surrogate::adam_step(float lr, cudaStream_t st)
+{
+    ++t_adam;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - std::pow(b1, (float)t_adam), c2 = 1.0f - std::pow(b2, (float)t_adam);
+    adam_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, adam_m, adam_v, grad, (long long)n_params,
+                                                                   lr, b1, b2, 1e-8f, c1, c2);
+    return cast(st);
+}
+
+cudaError_t Surrogate::pack_input(const float* U, int nb, cudaStream_t st)
+{
+    const long long n = (long long)nb * nx * ny;
+    pack_input_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, nb, ny, nx, in_scale[0], in_scale[1], in_scale[2],
+                                                                  x_in);
+    return cudaGetLastError();
+}
+
+cudaError_t Surrogate::pack_target(const float* X, const float* Y, int nb, cudaStream_t st)
+{
+    const long long n = (long long)nb * nx * ny;
+    pack_target_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, Y, nb, ny, nx, 1.0f / out_scale[0],
+                                                                   1.0f / out_scale[1], 1.0f / out_scale[2], target);
+    return cudaGetLastError();
+}
+
+cudaError_t Surrogate::apply(float* U, int nb, cudaStream_t st)
+{
+    const long long n = (long long)nb * nx * ny;
+    apply_output_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, out, nb, ny, nx, out_scale[0], out_scale[1],
+                                                                    out_scale[2]);
+    return cudaGetLastError();
+}
+
+}  // namespace iewpf

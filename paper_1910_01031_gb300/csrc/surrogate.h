@@ -1,0 +1,60 @@
+// Host side of the learned surrogate (surrogate.cu): parameters, buffers and
+// the forward / backward / Adam passes of the periodic 3x3 convolutional
+// network on one nx x ny grid.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace iewpf {
+
+struct Surrogate {
+    int nx = 0, ny = 0, width = 64, depth = 6;
+    size_t n_params = 0;
+    std::vector<size_t> w_off, b_off;       // offsets of each layer's weights / bias in the flat parameters
+    float* master = nullptr;                // fp32 parameters
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int t_adam = 0;
+    std::vector<__nv_bfloat16*> wf, wd;     // bf16 weights: forward [tap][co][ci], backward-data [tap][ci][co]
+    // activations for a batch
+    int cap_batch = 0;
+    __nv_bfloat16* x_in = nullptr;          // [b][ny][nx][16]
+    std::vector<__nv_bfloat16*> z, a;       // per hidden layer [b][ny][nx][64]
+    float* out = nullptr;                   // [b][ny][nx][3]
+    float* target = nullptr;                // [b][ny][nx][3]
+    __nv_bfloat16 *dz_a = nullptr, *dz_b = nullptr, *dz_out = nullptr;
+    float* wpartial = nullptr;
+    double* lpartial = nullptr;
+    double* dloss = nullptr;
+    float in_scale[3] = {1.0f, 1.0f, 1.0f};     // network input = state * in_scale
+    float out_scale[3] = {1.0f, 1.0f, 1.0f};    // state change = output * out_scale
+    std::vector<void*> owned;
+
+    ~Surrogate();
+    void release();
+    int init(int nx, int ny, int width, int depth);
+    int ensure_batch(int nb);
+    int wgrad_groups(int nb) const;
+    int layer_cin(int l) const;
+    int layer_cout(int l) const;
+    size_t layer_w(int l) const;
+    cudaError_t cast(cudaStream_t st);
+    cudaError_t pack_input(const float* U, int nb, cudaStream_t st);
+    cudaError_t pack_target(const float* X, const float* Y, int nb, cudaStream_t st);
+    cudaError_t forward(int nb, cudaStream_t st);
+    cudaError_t backward(int nb, cudaStream_t st);
+    cudaError_t adam_step(float lr, cudaStream_t st);
+    cudaError_t apply(float* U, int nb, cudaStream_t st);
+};
+
+// drifters advected over T seconds with the mean of the cell velocities of the
+// states before (S0) and after (S1), both [ne][3][ny][nx]
+cudaError_t launch_sur_drift(const float* S0, const float* S1, int ne, int nd, double* xy, const Grid& G, double dx,
+                             double dy, double T, cudaStream_t st);
+
+}  // namespace iewpf

@@ -28,7 +28,10 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
            "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
-           "iewpf_batch_work", "iewpf_batch_last_error"]
+           "iewpf_batch_work", "iewpf_batch_last_error", "iewpf_surrogate_create", "iewpf_surrogate_destroy",
+           "iewpf_surrogate_param_count", "iewpf_surrogate_set_params", "iewpf_surrogate_get_params",
+           "iewpf_surrogate_set_scales", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_loss_grad",
+           "iewpf_surrogate_train", "iewpf_set_surrogate", "iewpf_surrogate_stats", "iewpf_surrogate_last_error"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
 
@@ -92,7 +95,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_set_drifters.argtypes = [_vp, _dp, c.c_int]
     L.iewpf_get_drifters.argtypes = [_vp, _dp]
     L.drifter_forecast.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, c.c_int]
-    L.drifter_forecast_errors.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, _dp, _dp, _dp]
+    L.drifter_forecast_errors.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, _dp, _dp, _dp, c.c_int]
     L.iewpf_save.argtypes = [_vp, c.c_char_p]
     L.iewpf_load.argtypes = [_vp, c.c_char_p]
     L.iewpf_get_counters.argtypes = [_vp, _u32p, _u32p]
@@ -124,6 +127,20 @@ def load(build_if_needed: bool = True):
     L.iewpf_batch_work.argtypes = [_vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
     L.iewpf_batch_last_error.argtypes = [_vp]
     L.iewpf_batch_last_error.restype = c.c_char_p
+    L.iewpf_surrogate_create.argtypes = [c.c_int, c.c_int, c.c_int, c.c_int, c.c_uint64, c.POINTER(c.c_void_p)]
+    L.iewpf_surrogate_destroy.argtypes = [_vp]
+    L.iewpf_surrogate_param_count.argtypes = [_vp, c.POINTER(c.c_int64)]
+    L.iewpf_surrogate_set_params.argtypes = [_vp, _fp]
+    L.iewpf_surrogate_get_params.argtypes = [_vp, _fp]
+    L.iewpf_surrogate_set_scales.argtypes = [_vp, _dp, _dp]
+    L.iewpf_surrogate_get_scales.argtypes = [_vp, _dp, _dp]
+    L.iewpf_surrogate_apply.argtypes = [_vp, _fp, c.c_int, _fp]
+    L.iewpf_surrogate_loss_grad.argtypes = [_vp, _fp, _fp, c.c_int, _dp, _fp]
+    L.iewpf_surrogate_train.argtypes = [_vp, _vp, c.c_int, c.c_int, c.c_int, c.c_int, c.c_double, _dp]
+    L.iewpf_set_surrogate.argtypes = [_vp, _vp, c.c_int]
+    L.iewpf_surrogate_stats.argtypes = [_vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
+    L.iewpf_surrogate_last_error.argtypes = [_vp]
+    L.iewpf_surrogate_last_error.restype = c.c_char_p
     _lib = L
     return L
 
@@ -244,17 +261,17 @@ class Ensemble:
         self._chk(self.L.iewpf_get_drifters(self.h, _ptr(out)), "get_drifters")
         return out
 
-    def drifter_forecast(self, xy0, hours, out_every_s):
+    def drifter_forecast(self, xy0, hours, out_every_s, use_surrogate=False):
         xy0 = _f64(xy0, (-1, 2))
         n = xy0.shape[0]
         n_out = int(np.floor(hours * 3600.0 / out_every_s + 1e-9)) + 1
         traj = np.zeros((n_out, self.ne, n, 2))
-        self._chk(self.L.drifter_forecast(self.h, _ptr(xy0), n, float(hours), float(out_every_s), _ptr(traj), 0),
-                  "drifter_forecast")
+        self._chk(self.L.drifter_forecast(self.h, _ptr(xy0), n, float(hours), float(out_every_s), _ptr(traj),
+                                          int(bool(use_surrogate))), "drifter_forecast")
         self.nd = n
         return traj
 
-    def drifter_forecast_errors(self, xy0, hours, out_every_s, truth, want_traj=False):
+    def drifter_forecast_errors(self, xy0, hours, out_every_s, truth, want_traj=False, use_surrogate=False):
         """Returns (E[n_out], RMSE[n_out], traj or None)."""
         xy0 = _f64(xy0, (-1, 2))
         n = xy0.shape[0]
@@ -263,7 +280,8 @@ class Ensemble:
         E, R = np.zeros(n_out), np.zeros(n_out)
         traj = np.zeros((n_out, self.ne, n, 2)) if want_traj else None
         self._chk(self.L.drifter_forecast_errors(self.h, _ptr(xy0), n, float(hours), float(out_every_s), _ptr(truth),
-                                                 _ptr(E), _ptr(R), _ptr(traj)), "drifter_forecast_errors")
+                                                 _ptr(E), _ptr(R), _ptr(traj), int(bool(use_surrogate))),
+                  "drifter_forecast_errors")
         self.nd = n
         return E, R, traj
 
@@ -329,6 +347,16 @@ class Ensemble:
         c = ctypes.c_int64()
         self._chk(self.L.iewpf_work(self.h, ctypes.byref(c)), "work")
         return c.value
+
+    def set_surrogate(self, sur, k_steps):
+        """Attach a Surrogate (None detaches) for drift forecasts with use_surrogate."""
+        self._chk(self.L.iewpf_set_surrogate(self.h, None if sur is None else sur.h, int(k_steps)), "set_surrogate")
+        self._sur = sur
+
+    def surrogate_stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._chk(self.L.iewpf_surrogate_stats(self.h, ctypes.byref(a), ctypes.byref(b)), "surrogate_stats")
+        return a.value, b.value
 
     def add_qhalf(self, x):
         x = np.ascontiguousarray(x, np.float32).reshape(self.ne, self.nRx * self.nRy)
@@ -406,6 +434,82 @@ class Batch:
         w, l = ctypes.c_int64(), ctypes.c_int64()
         self._chk(self.L.iewpf_batch_work(self.h, ctypes.byref(w), ctypes.byref(l)), "batch_work")
         return w.value, l.value
+
+
+class Surrogate:
+    """The learned surrogate (iewpf_surrogate_*): a periodic 3x3 conv network
+    on the GPU with its own forward, backward and Adam kernels."""
+
+    def __init__(self, nx, ny, width=64, depth=6, seed=0):
+        self.L = load()
+        h = ctypes.c_void_p()
+        rc = self.L.iewpf_surrogate_create(int(nx), int(ny), int(width), int(depth), int(seed), ctypes.byref(h))
+        if rc != IEWPF_OK:
+            raise IewpfError(rc, "iewpf_surrogate_create")
+        self.h = h
+        self.nx, self.ny, self.width, self.depth = nx, ny, width, depth
+        n = ctypes.c_int64()
+        self.L.iewpf_surrogate_param_count(self.h, ctypes.byref(n))
+        self.n_params = n.value
+
+    def _chk(self, rc, what):
+        if rc != IEWPF_OK:
+            msg = self.L.iewpf_surrogate_last_error(self.h)
+            raise IewpfError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.iewpf_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layer_shapes(self):
+        """(cin, cout) per layer, padded as stored (16 channels at the ends)."""
+        return [(16 if l == 0 else self.width, 16 if l == self.depth - 1 else self.width) for l in range(self.depth)]
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._chk(self.L.iewpf_surrogate_get_params(self.h, _ptr(out, _fp)), "get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32).reshape(self.n_params)
+        self._chk(self.L.iewpf_surrogate_set_params(self.h, _ptr(p, _fp)), "set_params")
+
+    def set_scales(self, in_scale, out_scale):
+        a, b = _f64(in_scale, (3,)), _f64(out_scale, (3,))
+        self._chk(self.L.iewpf_surrogate_set_scales(self.h, _ptr(a), _ptr(b)), "set_scales")
+
+    def scales(self):
+        a, b = np.zeros(3), np.zeros(3)
+        self._chk(self.L.iewpf_surrogate_get_scales(self.h, _ptr(a), _ptr(b)), "get_scales")
+        return a, b
+
+    def apply(self, U):
+        U = np.ascontiguousarray(U, np.float32).reshape(-1, 3, self.ny, self.nx)
+        out = np.empty_like(U)
+        self._chk(self.L.iewpf_surrogate_apply(self.h, _ptr(U, _fp), U.shape[0], _ptr(out, _fp)), "apply")
+        return out
+
+    def loss_grad(self, X, Y):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, 3, self.ny, self.nx)
+        Y = np.ascontiguousarray(Y, np.float32).reshape(X.shape)
+        loss = ctypes.c_double()
+        g = np.zeros(self.n_params, np.float32)
+        self._chk(self.L.iewpf_surrogate_loss_grad(self.h, _ptr(X, _fp), _ptr(Y, _fp), X.shape[0], ctypes.byref(loss),
+                                                   _ptr(g, _fp)), "loss_grad")
+        return loss.value, g
+
+    def train(self, ens, n_pairs, k_steps, epochs, batch, lr):
+        losses = np.zeros(epochs)
+        self._chk(self.L.iewpf_surrogate_train(self.h, ens.h, int(n_pairs), int(k_steps), int(epochs), int(batch),
+                                               float(lr), _ptr(losses)), "train")
+        return losses
 
 
 def _torch_stream():

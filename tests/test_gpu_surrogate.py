@@ -1,0 +1,203 @@
+"""GPU parity of the learned surrogate against its FP64 oracle
+(oracle/surrogate.py), through the C ABI.
+
+Tolerances follow from the arithmetic: weights are made BF16-exact before
+the comparison, so the GPU differs from FP64 by the BF16 rounding of the
+network input and of every activation (relative 2^-9 each) and by FP32
+accumulation.  Six layers of such rounding give a relative L2 error of the
+output change of a few 1e-3 (FWD_TOL = 2e-2 leaves a margin); the gradients
+also pass the BF16-rounded back-propagated signal through every layer
+(GRAD_TOL = 5e-2)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import surrogate as S
+from paper_1910_01031_gb300 import iewpf, synth
+
+from gpu_common import ensemble, oracle_problem, rel_l2, start_state
+
+pytestmark = pytest.mark.gpu
+FWD_TOL = 2e-2
+GRAD_TOL = 5e-2
+W, D = 64, 6
+
+
+def bf16_exact(a):
+    """Round FP32 values to the nearest BF16 (ties to even), kept as FP32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _fields(n, ny, nx, seed):
+    """Smooth random states of the right magnitudes: eta ~ 0.05 m, hu, hv ~ 5 m^2/s."""
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((n, 3, ny, nx))
+    for _ in range(2):                                   # light periodic smoothing
+        U = (U + np.roll(U, 1, 2) + np.roll(U, -1, 2) + np.roll(U, 1, 3) + np.roll(U, -1, 3)) / 5.0
+    U *= np.array([0.05, 5.0, 5.0])[None, :, None, None] / U.std(axis=(0, 2, 3))[None, :, None, None]
+    return U.astype(np.float32)
+
+
+SI = [1 / 0.05, 1 / 5.0, 1 / 5.0]
+SO = [0.004, 0.3, 0.3]
+
+
+def _net(nx=48, ny=40, seed=5):
+    sur = iewpf.Surrogate(nx, ny, W, D, seed=seed)
+    p = bf16_exact(sur.params())
+    sur.set_params(p)
+    sur.set_scales(SI, SO)
+    return sur, p
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_parameter_layout_and_padding():
+    sur, p = _net()
+    assert sur.n_params == S.n_params(W, D)
+    assert np.array_equal(S.pack(S.unpack(p, W, D), W, D), p)     # padding holds zeros
+
+
+def test_forward_matches_oracle():
+    sur, p = _net()
+    U = _fields(3, 40, 48, 1)
+    out = sur.apply(U)
+    ref = S.apply(p, U.astype(np.float64), SI, SO, W, D)
+    d_gpu = out.astype(np.float64) - U
+    d_ref = ref - U
+    assert np.linalg.norm(d_ref) > 0
+    assert _rel(d_gpu, d_ref) < FWD_TOL
+
+
+def test_forward_is_bitwise_translation_equivariant():
+    # a shift by whole pixel tiles (8 rows, 16 columns) maps every output to
+    # the same position in its tile: identical arithmetic
+    sur, _ = _net()
+    U = _fields(2, 40, 48, 2)
+    a = sur.apply(U)
+    b = sur.apply(np.ascontiguousarray(np.roll(U, (8, 16), axis=(2, 3))))
+    assert np.array_equal(np.roll(a, (8, 16), axis=(2, 3)), b)
+
+
+def test_loss_and_gradients_match_oracle():
+    sur, p = _net()
+    X = _fields(3, 40, 48, 3)
+    Y = X + (_fields(3, 40, 48, 4) * np.array([0.05, 0.1, 0.1], np.float32)[None, :, None, None]).astype(np.float32)
+    L, g = sur.loss_grad(X, Y)
+    Lr, gr = S.loss_grad(p, X.astype(np.float64), Y.astype(np.float64), SI, SO, W, D)
+    assert abs(L - Lr) < 1e-2 * Lr
+    lg, lr = S.unpack(g, W, D), S.unpack(gr, W, D)
+    for l in range(D):
+        assert _rel(lg[l][0], lr[l][0]) < GRAD_TOL, ("weights", l)
+        assert _rel(lg[l][1], lr[l][1]) < GRAD_TOL, ("bias", l)
+    # padding entries get exactly zero gradient
+    pad = S.pack([(np.ones_like(Wl), np.ones_like(bl)) for Wl, bl in lr], W, D) == 0
+    assert np.all(g[pad] == 0.0)
+
+
+def test_first_training_step_is_signed_learning_rate():
+    cfg = synth.config1(n_particles=4)
+    U32, _ = start_state(cfg, 4)
+    ens, ens2 = ensemble(cfg), ensemble(cfg)
+    ens.set_state(U32)
+    ens2.set_state(U32)
+    sur = iewpf.Surrogate(cfg.nx, cfg.ny, W, D, seed=9)
+    p0 = sur.params()
+    lr = 1e-3
+    sur.train(ens, n_pairs=4, k_steps=1, epochs=1, batch=4, lr=lr)
+    p1 = sur.params()
+    # the same pairs and parameters, gradient by loss_grad
+    X = ens2.get_state()
+    ens2.forecast(1, False)
+    Y = ens2.get_state()
+    sur2 = iewpf.Surrogate(cfg.nx, cfg.ny, W, D, seed=9)
+    si, so = sur.scales()
+    sur2.set_scales(si, so)
+    _, g = sur2.loss_grad(X, Y)
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    assert big.sum() > 1000
+    dp = p1.astype(np.float64) - p0
+    assert np.all(np.abs(dp[big] + lr * np.sign(g[big])) < 2e-2 * lr)
+    assert np.all(dp[g == 0] == 0)
+
+
+def test_training_reduces_the_loss():
+    cfg = synth.config1(n_particles=16)
+    U32, _ = start_state(cfg, 16)
+    ens = ensemble(cfg)
+    ens.set_state(U32)
+    sur = iewpf.Surrogate(cfg.nx, cfg.ny, W, D, seed=11)
+    losses = sur.train(ens, n_pairs=64, k_steps=2, epochs=15, batch=8, lr=2e-3)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.8 * losses[0], losses
+
+
+def test_zero_network_forecast_is_model_error_and_drift_only():
+    cfg = synth.config1(n_particles=3)
+    P = oracle_problem(cfg)
+    U32, U64 = start_state(cfg, 3)
+    ens = ensemble(cfg, n_drifters_max=2)
+    ens.set_state(U32)
+    sur = iewpf.Surrogate(cfg.nx, cfg.ny, W, D, seed=1)
+    sur.set_params(np.zeros(sur.n_params, np.float32))
+    k = 2
+    ens.set_surrogate(sur, k)
+    xy0 = np.array([[30.5e3, 61.2e3], [100.1e3, 7.7e3]])
+    every = k * cfg.dt_model
+    traj = ens.drifter_forecast(xy0, hours=2 * every / 3600.0, out_every_s=every, use_surrogate=True)
+    calls, fb = ens.surrogate_stats()
+    assert (calls, fb) == (2, 0)
+    ref_traj = [np.repeat(xy0[None], 3, axis=0)]
+    ref = U64.copy()
+    xy = ref_traj[0].copy()
+    t = 0
+    for _ in range(2):
+        for p in range(3):
+            xy[p] = O.drift(P, ref[p], k * cfg.dt_model, xy[p])
+        for _ in range(k):
+            for p in range(3):
+                ref[p] = O.model_error(P, ref[p], p, t)
+            t += 1
+        ref_traj.append(xy.copy())
+    assert rel_l2(ens.get_state(), ref) < 1e-5
+    disp = np.abs(np.array(ref_traj) - ref_traj[0]).max()
+    assert disp > 0 and np.abs(traj - np.array(ref_traj)).max() < 1e-5 * disp + 1e-6
+    assert ens.counters()[0] == 2 * k
+
+
+def test_non_finite_network_falls_back_to_the_plain_stepper_bitwise():
+    cfg = synth.config1(n_particles=3)
+    U32, _ = start_state(cfg, 3)
+    a, b = ensemble(cfg, n_drifters_max=1), ensemble(cfg, n_drifters_max=1)
+    a.set_state(U32)
+    b.set_state(U32)
+    sur = iewpf.Surrogate(cfg.nx, cfg.ny, W, D, seed=1)
+    sur.set_params(np.full(sur.n_params, np.nan, np.float32))
+    a.set_surrogate(sur, 2)
+    xy0 = np.array([[50e3, 50e3]])
+    ta = a.drifter_forecast(xy0, hours=240 / 3600.0, out_every_s=240.0, use_surrogate=True)
+    tb = b.drifter_forecast(xy0, hours=240 / 3600.0, out_every_s=240.0)
+    assert a.surrogate_stats() == (2, 2)
+    assert np.array_equal(ta, tb)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.counters() == b.counters()
+
+
+def test_surrogate_argument_errors():
+    with pytest.raises(iewpf.IewpfError):
+        iewpf.Surrogate(50, 40, W, D)                 # nx not a multiple of 16
+    cfg = synth.config1(n_particles=2)
+    ens = ensemble(cfg, n_drifters_max=1)
+    with pytest.raises(iewpf.IewpfError):
+        ens.drifter_forecast(np.array([[1e3, 1e3]]), 0.1, 60.0, use_surrogate=True)   # none attached
+    sur = iewpf.Surrogate(cfg.nx, cfg.ny, W, D)
+    ens.set_surrogate(sur, 4)
+    with pytest.raises(iewpf.IewpfError):
+        ens.drifter_forecast(np.array([[1e3, 1e3]]), 0.1, 60.0, use_surrogate=True)   # 60 s not a multiple of 4 steps
+    other = iewpf.Surrogate(32, 32, W, D)
+    with pytest.raises(iewpf.IewpfError):
+        ens.set_surrogate(other, 2)
