@@ -307,6 +307,118 @@ def run_batched(rank):
     return out
 
 
+SUR_FLOPS_PER_PIXEL = 2 * 9 * (3 * 64 + 4 * 64 * 64 + 64 * 3)   # algorithmic (unpadded) FLOPs of one network call
+
+
+def run_surrogate(rank, n_pairs=20000, epochs=4, batch=32, lr=1e-3, hours=12.0, k=10, ne=1000, train_ne=500):
+    """The learned-surrogate workload: the network is trained on n_pairs
+    pairs (psi, 10 model steps of psi) of the 64 x 64 jet model (a 500-particle
+    ensemble of it), its weights are moved to a 256 x 256 network, and a
+    12 h drift forecast of 1000 particles x 64 drifters runs twice from the
+    same ensemble and counters: with the plain stepper and with the
+    surrogate (model error from the same Philox draws in both).  Reports the
+    time of both, the RMS and largest drifter distance between the two
+    forecasts at every hour, and the tensor-core rate of a network call."""
+    import torch
+    from paper_1910_01031_gb300 import iewpf, synth
+    out = {"workload": "surrogate_256x256_ne%d_64drifters, %g h drift forecast, network 6 x conv3x3 (64 ch), "
+                       "k = %d model steps per call" % (ne, hours, k)}
+    cfg1 = synth.config1(n_particles=train_ne, seed=0x1910_01031 + 7 * rank)
+    p1 = iewpf.params_from_config(cfg1)
+    p1.instance_id = 2000 + rank
+    ens1 = iewpf.Ensemble(p1)
+    ens1.set_state(synth.initial_state(cfg1, train_ne, seed=21 + rank).astype(np.float32))
+    net = iewpf.Surrogate(cfg1.nx, cfg1.ny, 64, 6, seed=rank)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(ens1, n_pairs=n_pairs, k_steps=k, epochs=epochs, batch=batch, lr=lr)
+    train_s = time.perf_counter() - t0
+    params, (si, so) = net.params(), net.scales()
+    net.close()
+    ens1.close()
+    out["train"] = {"pairs": n_pairs, "grid": "64x64", "epochs": epochs, "batch": batch, "lr": lr,
+                    "seconds": round(train_s, 2), "epoch_loss": [round(float(v), 5) for v in losses]}
+    cfg = synth.config5(n_particles=ne, seed=0x1910_01031 + 11 * rank)
+    P = iewpf.params_from_config(cfg, n_drifters_max=cfg.n_obs)
+    P.instance_id = rank
+    ens = iewpf.Ensemble(P)
+    U0 = torch.empty((ne, 3, cfg.ny, cfg.nx), dtype=torch.float32, device="cuda")
+    for a in range(0, ne, 100):
+        b = min(ne, a + 100)
+        U0[a:b] = torch.from_numpy(np.stack([synth.initial_particle(cfg, i, seed=31 + rank, dtype=np.float32)
+                                             for i in range(a, b)]))
+    sur = iewpf.Surrogate(cfg.nx, cfg.ny, 64, 6, seed=rank)
+    sur.set_params(params)
+    sur.set_scales(si, so)
+    ens.set_surrogate(sur, k)
+    xy0 = synth.drifter_positions(cfg)
+    stream = torch.cuda.ExternalStream(ens.stream())
+    res = {}
+    for mode in ("plain", "surrogate"):
+        ens.set_state(U0)
+        ens.set_counters(0, 0)
+        torch.cuda.synchronize()
+        w0 = ens.work()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h0 = time.perf_counter()
+        traj = ens.drifter_forecast(xy0, hours, 3600.0, use_surrogate=(mode == "surrogate"))
+        e1.record(stream)
+        e1.synchronize()
+        res[mode] = (traj, time.perf_counter() - h0, e0.elapsed_time(e1) / 1e3, ens.work() - w0)
+    calls, fallbacks = ens.surrogate_stats()
+    d = np.sqrt(np.sum((res["surrogate"][0] - res["plain"][0]) ** 2, axis=-1)) / 1e3     # km, [hour][p][drifter]
+    rms = np.sqrt(np.mean(d ** 2, axis=(1, 2)))
+    model_steps = int(round(hours * 3600.0 / cfg.dt_model)) * ne
+    out["plain"] = {"seconds": round(res["plain"][1], 3), "device_s": round(res["plain"][2], 3),
+                    "particle_model_steps_per_s": round(model_steps / res["plain"][1], 1),
+                    "particle_substeps": int(res["plain"][3])}
+    out["surrogate"] = {"seconds": round(res["surrogate"][1], 3), "device_s": round(res["surrogate"][2], 3),
+                        "particle_model_steps_per_s": round(model_steps / res["surrogate"][1], 1),
+                        "network_calls": calls, "fallbacks": fallbacks,
+                        "particle_substeps_of_fallbacks": int(res["surrogate"][3])}
+    out["speedup"] = round(res["plain"][1] / res["surrogate"][1], 3)
+    out["drift_distance_km"] = {"rms_by_hour": [round(float(v), 4) for v in rms],
+                                "max_at_end": round(float(d[-1].max()), 4),
+                                "median_at_end": round(float(np.median(d[-1])), 4)}
+    out["within_1km"] = bool(rms[-1] <= 1.0)
+    # one network call over the whole ensemble, CUDA events on the surrogate stream
+    s_stream = torch.cuda.ExternalStream(sur.stream())
+    V = U0.clone()
+    sur.apply_device(V, stream=ctypes_stream(s_stream))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    f0.record(s_stream)
+    for _ in range(reps):
+        sur.apply_device(V, stream=ctypes_stream(s_stream))
+    f1.record(s_stream)
+    f1.synchronize()
+    call_s = f0.elapsed_time(f1) / 1e3 / reps
+    flops = SUR_FLOPS_PER_PIXEL * ne * cfg.nx * cfg.ny
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    out["network_call"] = {"ms_per_ensemble_call": round(call_s * 1e3, 2), "bound": "tensor",
+                           "achieved": round(flops / call_s / 1e12, 1), "peak": peak, "unit": "TFLOP/s",
+                           "frac": round(flops / call_s / 1e12 / peak, 4),
+                           "flops_per_pixel": SUR_FLOPS_PER_PIXEL}
+    ens.set_surrogate(None, 0)
+    sur.close()
+    ens.close()
+    del U0, V
+    torch.cuda.empty_cache()
+    return out
+
+
+def ctypes_stream(torch_stream):
+    import ctypes
+    return ctypes.c_void_p(torch_stream.cuda_stream)
+
+
 def _kernel_sha():
     import hashlib
     h = hashlib.sha1()

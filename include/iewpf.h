@@ -368,6 +368,13 @@ IEWPF_API int iewpf_surrogate_set_scales(iewpf_surrogate_t* s, const double* in_
 IEWPF_API int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, double* out_scale);
 /* U ([n][3][ny][nx] host FP32) -> Unext (same layout), one network call. */
 IEWPF_API int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Unext);
+/* The same on device memory: U and Unext (may be equal: in place) are
+ * device pointers [n][3][ny][nx], borrowed; the work is ordered after the
+ * work queued on `stream` (NULL: the call returns when done) and `stream`
+ * waits for it.  Particles go through the network in chunks of 64. */
+IEWPF_API int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, float* Unext, void* stream);
+/* The surrogate's own CUDA stream. */
+IEWPF_API int iewpf_surrogate_stream(const iewpf_surrogate_t* s, void** stream);
 /* Loss and its gradient w.r.t. the FP32 parameters (grad[n_params], may be
  * NULL) for the pairs X -> Y ([n][3][ny][nx] host FP32). */
 IEWPF_API int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, const float* Y, int n, double* loss,
@@ -375,13 +382,21 @@ IEWPF_API int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, co
 /* Training on n_pairs pairs (psi, M^k psi), M^k = k_steps model steps of the
  * plain stepper of ctx without model error (the deterministic model the
  * surrogate stands for), starting from ctx's state; between two rounds of
- * pairs the ensemble advances k_steps steps with model error (ctx advances).  Sets the scales from the pairs, then runs `epochs`
- * shuffled passes of Adam (beta 0.9, 0.999, eps 1e-8, step lr) in mini-batches
- * of `batch`; epoch_loss[epochs] (may be NULL) receives the mean batch loss. */
+ * pairs the ensemble advances k_steps steps with model error (ctx advances).
+ * The scales are set from up to 64 pairs spread over the set (unit spread of
+ * the input and of the change; one scale for eta, one shared by hu and hv).
+ * Then `epochs` shuffled passes of Adam (beta 0.9, 0.999, eps 1e-8, step lr)
+ * in mini-batches of `batch` (a last partial batch is skipped);
+ * epoch_loss[epochs] (may be NULL) receives the mean batch loss. */
 IEWPF_API int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs,
                                     int batch, double lr, double* epoch_loss);
 /* Attach (s != NULL, k_steps >= 1) or detach (s = NULL) a surrogate to ctx
- * for drifter_forecast(..., use_surrogate = 1).  Not owned by ctx. */
+ * for drifter_forecast(..., use_surrogate = 1).  Not owned by ctx.  Each
+ * surrogate call covers k_steps model steps of all particles; it is rejected
+ * and those steps are run by the plain stepper when the network's state is
+ * not finite or, for some particle, max|eta| exceeds 1.5 x its value before
+ * plus 0.01 m, or the largest |hu/h|, |hv/h| exceeds 1.5 x its value before
+ * plus 0.05 m/s. */
 IEWPF_API int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_steps);
 /* Surrogate calls made for ctx and how many fell back to the plain stepper. */
 IEWPF_API int iewpf_surrogate_stats(const iewpf_ctx_t* ctx, int64_t* calls, int64_t* fallbacks);

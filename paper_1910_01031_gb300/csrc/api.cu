@@ -430,18 +430,22 @@ struct iewpf_surrogate {
     // inference scratch of an attached context
     float* S0 = nullptr;
     float* S1 = nullptr;
-    double* xy_save = nullptr;
-    size_t cap_state = 0, cap_xy = 0;
+    float* stats = nullptr;
+    size_t cap_state = 0;
     int chunk = 64;
 };
 
 namespace {
 
-// k model steps of every particle by the surrogate (Sec. 5.2 forecast with a
-// learned model): the state change of k steps from the network, drifters
-// advected with the mean of the velocities before and after, then the k
-// model errors of those steps.  A non-finite result falls back to the plain
-// scheme for the same k steps.
+// k model steps of every particle by the surrogate (in place of k steps of
+// the scheme of Sec. 2 in the drift forecast of Sec. 5.2): the state change
+// of k steps from the network, drifters advected with the mean of the
+// velocities before and after, then the k model errors of those steps.  The
+// plain scheme takes over for the k steps when the network's state fails the
+// guard: non-finite, or for some particle max|eta| or the largest velocity
+// component grows by more than SUR_GROWTH (plus a small absolute slack).
+constexpr float SUR_GROWTH = 1.5f, SUR_SLACK_ETA = 0.01f, SUR_SLACK_VEL = 0.05f;
+
 int surrogate_steps(iewpf_ctx* ctx)
 {
     iewpf_surrogate* S = ctx->sur;
@@ -451,27 +455,20 @@ int surrogate_steps(iewpf_ctx* ctx)
     if (S->cap_state < nstate) {
         if (S->S0) cudaFree(S->S0);
         if (S->S1) cudaFree(S->S1);
+        if (S->stats) cudaFree(S->stats);
         S->S0 = S->S1 = nullptr;
-        if (cudaMalloc((void**)&S->S0, nstate * 4) != cudaSuccess || cudaMalloc((void**)&S->S1, nstate * 4) != cudaSuccess) {
+        S->stats = nullptr;
+        S->cap_state = 0;
+        if (cudaMalloc((void**)&S->S0, nstate * 4) != cudaSuccess || cudaMalloc((void**)&S->S1, nstate * 4) != cudaSuccess ||
+            cudaMalloc((void**)&S->stats, sizeof(float) * 4 * ne) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, IEWPF_ENOMEM, "surrogate scratch");
         }
         S->cap_state = nstate;
     }
-    const size_t nxy = (size_t)ne * 2 * std::max(ctx->nd, 1);
-    if (S->cap_xy < nxy) {
-        if (S->xy_save) cudaFree(S->xy_save);
-        if (cudaMalloc((void**)&S->xy_save, nxy * 8) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, IEWPF_ENOMEM, "surrogate scratch");
-        }
-        S->cap_xy = nxy;
-    }
     int rc;
     if ((rc = iewpf_get_state(ctx, S->S0, 1, nullptr))) return rc;
     CK(cudaMemcpyAsync(S->S1, S->S0, nstate * 4, cudaMemcpyDeviceToDevice, ctx->st));
-    if (ctx->nd > 0)
-        CK(cudaMemcpyAsync(S->xy_save, ctx->d_xy, sizeof(double) * 2 * ctx->nd * ne, cudaMemcpyDeviceToDevice, ctx->st));
     const size_t per = 3 * (size_t)ctx->plane;
     if ((rc = S->net.ensure_batch(S->chunk))) return fail(ctx, rc, "surrogate activations");
     for (int p0 = 0; p0 < ne; p0 += S->chunk) {
@@ -480,6 +477,23 @@ int surrogate_steps(iewpf_ctx* ctx)
         CK(S->net.forward(nb, ctx->st));
         CK(S->net.apply(S->S1 + per * p0, nb, ctx->st));
         ctx->launches += 2 + S->net.depth;
+    }
+    // guard: per-particle max|eta| and max velocity component before / after
+    KL(1, launch_sur_stats(S->S0, ne, ctx->G, S->stats, ctx->st));
+    KL(1, launch_sur_stats(S->S1, ne, ctx->G, S->stats + 2 * ne, ctx->st));
+    std::vector<float> st(4 * (size_t)ne);
+    CK(cudaMemcpyAsync(st.data(), S->stats, sizeof(float) * 4 * ne, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->sur_calls++;
+    bool ok = true;
+    for (int p = 0; p < ne && ok; ++p) {
+        const float e0 = st[2 * p], v0 = st[2 * p + 1], e1 = st[2 * ne + 2 * p], v1 = st[2 * ne + 2 * p + 1];
+        ok = std::isfinite(e1) && std::isfinite(v1) && e1 <= SUR_GROWTH * e0 + SUR_SLACK_ETA &&
+             v1 <= SUR_GROWTH * v0 + SUR_SLACK_VEL;
+    }
+    if (!ok) {
+        ctx->sur_fallbacks++;
+        return forecast_impl(ctx, k, 1, 0);
     }
     if (ctx->nd > 0)
         KL(1, launch_sur_drift(S->S0, S->S1, ne, ctx->nd, ctx->d_xy, ctx->G, ctx->P.dx, ctx->P.dy,
@@ -498,22 +512,9 @@ int surrogate_steps(iewpf_ctx* ctx)
         A.stream = 16u * (uint32_t)ctx->P.instance_id;
         KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
     }
-    KL(1, launch_nonfinite(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, ctx->flag, ctx->st));
-    CK(cudaMemcpyAsync(ctx->h_flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    ctx->sur_calls++;
-    if (*ctx->h_flag & FLAG_NONFINITE) {
-        // fall back to the plain scheme for these k steps
-        CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
-        if ((rc = iewpf_set_state(ctx, S->S0, 1, nullptr))) return rc;
-        if (ctx->nd > 0)
-            CK(cudaMemcpyAsync(ctx->d_xy, S->xy_save, sizeof(double) * 2 * ctx->nd * ne, cudaMemcpyDeviceToDevice,
-                               ctx->st));
-        ctx->sur_fallbacks++;
-        return forecast_impl(ctx, k, 1, 0);
-    }
     ctx->step += k;
-    return IEWPF_OK;
+    KL(1, launch_nonfinite(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, ctx->flag, ctx->st));
+    return read_flags(ctx);
 }
 
 }  // namespace
@@ -1417,7 +1418,7 @@ int iewpf_surrogate_destroy(iewpf_surrogate_t* s)
     if (s->st) cudaStreamSynchronize(s->st);
     if (s->S0) cudaFree(s->S0);
     if (s->S1) cudaFree(s->S1);
-    if (s->xy_save) cudaFree(s->xy_save);
+    if (s->stats) cudaFree(s->stats);
     s->net.release();
     if (s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -1451,7 +1452,7 @@ int iewpf_surrogate_create(int nx, int ny, int width, int depth, uint64_t seed, 
                     if (co < real_out && ci < real_in)
                         p[s->net.w_off[l] + ((size_t)tap * cout + co) * cin + ci] = (float)(sd * nd(gen));
     }
-    if (cudaMemcpy(s->net.master, p.data(), p.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpyAsync(s->net.master, p.data(), p.size() * 4, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
         s->net.cast(s->st) != cudaSuccess || cudaStreamSynchronize(s->st) != cudaSuccess) {
         iewpf_surrogate_destroy(s);
         return IEWPF_ECUDA;
@@ -1471,7 +1472,7 @@ int iewpf_surrogate_set_params(iewpf_surrogate_t* s, const float* params)
 {
     if (!s || !params) return IEWPF_EINVAL;
     SCK(cudaSetDevice(s->dev));
-    SCK(cudaMemcpy(s->net.master, params, s->net.n_params * 4, cudaMemcpyHostToDevice));
+    SCK(cudaMemcpyAsync(s->net.master, params, s->net.n_params * 4, cudaMemcpyHostToDevice, s->st));
     SCK(s->net.cast(s->st));
     SCK(cudaStreamSynchronize(s->st));
     return IEWPF_OK;
@@ -1482,7 +1483,8 @@ int iewpf_surrogate_get_params(const iewpf_surrogate_t* cs, float* params)
     iewpf_surrogate* s = const_cast<iewpf_surrogate*>(cs);
     if (!s || !params) return IEWPF_EINVAL;
     SCK(cudaSetDevice(s->dev));
-    SCK(cudaMemcpy(params, s->net.master, s->net.n_params * 4, cudaMemcpyDeviceToHost));
+    SCK(cudaMemcpyAsync(params, s->net.master, s->net.n_params * 4, cudaMemcpyDeviceToHost, s->st));
+    SCK(cudaStreamSynchronize(s->st));
     return IEWPF_OK;
 }
 
@@ -1526,6 +1528,41 @@ int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Un
     cudaFree(d);
     if (rc) return sfail(s, rc, "activations");
     if (e != cudaSuccess) return sfail(s, IEWPF_ECUDA, cudaGetErrorString(e));
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, float* Unext, void* stream)
+{
+    if (!s || !U || !Unext || n < 1) return IEWPF_EINVAL;
+    SCK(cudaSetDevice(s->dev));
+    const size_t per = 3ull * s->net.nx * s->net.ny;
+    int rc = s->net.ensure_batch(std::min(n, s->chunk));
+    if (rc) return sfail(s, rc, "activations");
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaEvent_t ev;
+    SCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    if (user) {
+        SCK(cudaEventRecord(ev, user));
+        SCK(cudaStreamWaitEvent(s->st, ev, 0));
+    }
+    if (Unext != U) SCK(cudaMemcpyAsync(Unext, U, per * n * 4, cudaMemcpyDeviceToDevice, s->st));
+    for (int p0 = 0; p0 < n; p0 += s->chunk) {
+        const int nb = std::min(s->chunk, n - p0);
+        SCK(s->net.pack_input(Unext + per * p0, nb, s->st));
+        SCK(s->net.forward(nb, s->st));
+        SCK(s->net.apply(Unext + per * p0, nb, s->st));
+    }
+    SCK(cudaEventRecord(ev, s->st));
+    if (user) SCK(cudaStreamWaitEvent(user, ev, 0));
+    else SCK(cudaEventSynchronize(ev));
+    cudaEventDestroy(ev);
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_stream(const iewpf_surrogate_t* s, void** stream)
+{
+    if (!s || !stream) return IEWPF_EINVAL;
+    *stream = (void*)s->st;
     return IEWPF_OK;
 }
 
@@ -1586,41 +1623,65 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
         cleanup();
         return sfail(s, IEWPF_ENOMEM, "snapshot");
     }
+    // every copy on ctx's stream, behind the forecasts that produce it
     for (int got = 0; got < n_pairs && !rc;) {
         const int take = std::min(ne, n_pairs - got);
         if ((rc = iewpf_get_state(ctx, snap, 1, nullptr))) break;
-        if (cudaMemcpy(X + per * got, snap, per * take * 4, cudaMemcpyDeviceToDevice) != cudaSuccess) rc = IEWPF_ECUDA;
-        if (!rc && (rc = iewpf_forecast(ctx, k_steps, 0))) break;
-        if (!rc && (rc = iewpf_get_state(ctx, snap, 1, nullptr))) break;
-        if (!rc && cudaMemcpy(Y + per * got, snap, per * take * 4, cudaMemcpyDeviceToDevice) != cudaSuccess) rc = IEWPF_ECUDA;
-        if (!rc && (rc = iewpf_forecast(ctx, k_steps, 1))) break;
+        if (cudaMemcpyAsync(X + per * got, snap, per * take * 4, cudaMemcpyDeviceToDevice, ctx->st) != cudaSuccess) {
+            rc = IEWPF_ECUDA;
+            break;
+        }
+        if ((rc = iewpf_forecast(ctx, k_steps, 0))) break;
+        if ((rc = iewpf_get_state(ctx, snap, 1, nullptr))) break;
+        if (cudaMemcpyAsync(Y + per * got, snap, per * take * 4, cudaMemcpyDeviceToDevice, ctx->st) != cudaSuccess) {
+            rc = IEWPF_ECUDA;
+            break;
+        }
+        if ((rc = iewpf_forecast(ctx, k_steps, 1))) break;
         got += take;
     }
+    if (!rc && cudaStreamSynchronize(ctx->st) != cudaSuccess) rc = IEWPF_ECUDA;
     cudaFree(snap);
     if (rc) {
         cleanup();
         return sfail(s, rc, std::string("generating pairs: ") + ctx->err);
     }
-    // normalisation from the data: input ~ unit spread, output change ~ unit spread
+    // normalisation from the data (up to 64 pairs spread over the set): input
+    // and output change of unit spread per field, one scale for both momentum
+    // components (the problem is isotropic in the horizontal)
     {
-        const size_t sample = std::min<size_t>(n_pairs, 32) * per;
-        std::vector<float> hx(sample), hy(sample);
-        cudaMemcpy(hx.data(), X, sample * 4, cudaMemcpyDeviceToHost);
-        cudaMemcpy(hy.data(), Y, sample * 4, cudaMemcpyDeviceToHost);
+        const int ns = std::min(n_pairs, 64);
         const size_t plane = (size_t)s->net.nx * s->net.ny;
-        for (int c = 0; c < 3; ++c) {
-            double sx = 0, sxx = 0, sd = 0, sdd = 0;
-            size_t cnt = 0;
-            for (size_t b = 0; b < sample / per; ++b)
+        std::vector<float> hx(per), hy(per);
+        double sx[3] = {0, 0, 0}, sxx[3] = {0, 0, 0}, sd[3] = {0, 0, 0}, sdd[3] = {0, 0, 0};
+        for (int q = 0; q < ns; ++q) {
+            const size_t pi = (size_t)q * n_pairs / ns;
+            cudaMemcpy(hx.data(), X + per * pi, per * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(hy.data(), Y + per * pi, per * 4, cudaMemcpyDeviceToHost);
+            for (int c = 0; c < 3; ++c)
                 for (size_t i = 0; i < plane; ++i) {
-                    const double x = hx[b * per + c * plane + i], d = hy[b * per + c * plane + i] - x;
-                    sx += x; sxx += x * x; sd += d; sdd += d * d;
-                    ++cnt;
+                    const double x = hx[c * plane + i], d = hy[c * plane + i] - x;
+                    sx[c] += x;
+                    sxx[c] += x * x;
+                    sd[c] += d;
+                    sdd[c] += d * d;
                 }
-            const double vx = sxx / cnt - (sx / cnt) * (sx / cnt), vd = sdd / cnt - (sd / cnt) * (sd / cnt);
-            s->net.in_scale[c] = (float)(1.0 / std::sqrt(std::max(vx, 1e-30)));
-            s->net.out_scale[c] = (float)std::sqrt(std::max(vd, 1e-30));
         }
+        const double cnt = (double)ns * plane;
+        auto spread = [&](const double* a, const double* aa, int c0, int c1) {
+            double m = 0, v = 0;
+            for (int c = c0; c <= c1; ++c) m += a[c];
+            m /= cnt * (c1 - c0 + 1);
+            for (int c = c0; c <= c1; ++c) v += aa[c];
+            v = v / (cnt * (c1 - c0 + 1)) - m * m;
+            return std::sqrt(std::max(v, 1e-30));
+        };
+        const double x_eta = spread(sx, sxx, 0, 0), x_mom = spread(sx, sxx, 1, 2);
+        const double d_eta = spread(sd, sdd, 0, 0), d_mom = spread(sd, sdd, 1, 2);
+        s->net.in_scale[0] = (float)(1.0 / x_eta);
+        s->net.in_scale[1] = s->net.in_scale[2] = (float)(1.0 / x_mom);
+        s->net.out_scale[0] = (float)d_eta;
+        s->net.out_scale[1] = s->net.out_scale[2] = (float)d_mom;
     }
     if ((rc = s->net.ensure_batch(batch))) {
         cleanup();

@@ -442,7 +442,10 @@ cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps)
     b.pre[(size_t)SP_STEP * (b.n + 1) + b.n] = acc;
     cudaError_t e = cudaMemcpy(b.d_inst, b.h_inst.data(), sizeof(BInst) * b.n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(b.d_pre, b.pre.data(), sizeof(long long) * b.pre.size(), cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(b.d_pre, b.pre.data(), sizeof(long long) * b.pre.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    // the batch streams do not synchronise with the legacy stream
+    return cudaDeviceSynchronize();
 }
 
 // Builds the prefix sums and device descriptors of the problems.
@@ -513,6 +516,8 @@ long long batch_launches(const BatchImpl& b) { return b.launches; }
 
 cudaError_t batch_work(BatchImpl& b, unsigned long long* out)
 {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
     return cudaMemcpy(out, b.d_work, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
 }
 

@@ -398,6 +398,39 @@ __global__ void sur_drift_kernel(const float* __restrict__ S0, const float* __re
     xy[2 * i + 1] = y + T * v;
 }
 
+// per particle: max |eta| and the largest |hu/h|, |hv/h| of a state
+// [ne][3][ny][nx] (non-negative floats: integer atomicMax on the bits)
+__global__ void sur_stats_kernel(const float* __restrict__ S, Grid G, float* __restrict__ out)
+{
+    const int p = blockIdx.y;
+    const float* U = S + (long long)p * 3 * G.plane;
+    float e = 0.0f, v = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < G.plane; i += (long long)gridDim.x * blockDim.x) {
+        const float eta = U[i];
+        const float h = G.H + eta;
+        e = fmaxf(e, fabsf(eta));
+        v = fmaxf(v, fmaxf(fabsf(U[G.plane + i]), fabsf(U[2 * G.plane + i])) / h);
+        if (!isfinite(eta) || !isfinite(U[G.plane + i]) || !isfinite(U[2 * G.plane + i]) || !(h > 0.0f))
+            e = __int_as_float(0x7f800000);
+    }
+    e = warp_max(e);
+    v = warp_max(v);
+    __shared__ float red[2][8];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = e;
+        red[1][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            e = fmaxf(e, red[0][w]);
+            v = fmaxf(v, red[1][w]);
+        }
+        atomicMax(reinterpret_cast<int*>(out) + 2 * p, __float_as_int(e));
+        atomicMax(reinterpret_cast<int*>(out) + 2 * p + 1, __float_as_int(v));
+    }
+}
+
 template <int CIN, int COUT, int MODE>
 size_t conv_smem()
 {
@@ -445,6 +478,15 @@ cudaError_t launch_sur_drift(const float* S0, const float* S1, int ne, int nd, d
 {
     const int n = ne * nd;
     if (n > 0) sur_drift_kernel<<<(n + 127) / 128, 128, 0, st>>>(S0, S1, ne, nd, xy, G, dx, dy, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_stats(const float* S, int ne, const Grid& G, float* out, cudaStream_t st)
+{
+    cudaMemsetAsync(out, 0, sizeof(float) * 2 * ne, st);
+    const long long blocks = (G.plane + 256 * 8 - 1) / (256 * 8);
+    dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(blocks, 1024)), ne);
+    sur_stats_kernel<<<grid, 256, 0, st>>>(S, G, out);
     return cudaGetLastError();
 }
 
@@ -512,7 +554,8 @@ int Surrogate::init(int nx_, int ny_, int width_, int depth_)
         if (!p) return IEWPF_ENOMEM;
     cudaMemset(adam_m, 0, n_params * sizeof(float));
     cudaMemset(adam_v, 0, n_params * sizeof(float));
-    return IEWPF_OK;
+    // the network's kernels run on non-blocking streams
+    return cudaDeviceSynchronize() == cudaSuccess ? IEWPF_OK : IEWPF_ECUDA;
 }
 
 int Surrogate::ensure_batch(int nb)

@@ -57,4 +57,8 @@ struct Surrogate {
 cudaError_t launch_sur_drift(const float* S0, const float* S1, int ne, int nd, double* xy, const Grid& G, double dx,
                              double dy, double T, cudaStream_t st);
 
+// per particle (max |eta|, max velocity component) of S [ne][3][ny][nx] into
+// out[ne][2]; +inf for eta when a value is not finite or a depth not positive
+cudaError_t launch_sur_stats(const float* S, int ne, const Grid& G, float* out, cudaStream_t st);
+
 }  // namespace iewpf

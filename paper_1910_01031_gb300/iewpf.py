@@ -30,7 +30,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
            "iewpf_batch_work", "iewpf_batch_last_error", "iewpf_surrogate_create", "iewpf_surrogate_destroy",
            "iewpf_surrogate_param_count", "iewpf_surrogate_set_params", "iewpf_surrogate_get_params",
-           "iewpf_surrogate_set_scales", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_loss_grad",
+           "iewpf_surrogate_set_scales", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_apply_device", "iewpf_surrogate_stream", "iewpf_surrogate_loss_grad",
            "iewpf_surrogate_train", "iewpf_set_surrogate", "iewpf_surrogate_stats", "iewpf_surrogate_last_error"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
@@ -135,6 +135,8 @@ def load(build_if_needed: bool = True):
     L.iewpf_surrogate_set_scales.argtypes = [_vp, _dp, _dp]
     L.iewpf_surrogate_get_scales.argtypes = [_vp, _dp, _dp]
     L.iewpf_surrogate_apply.argtypes = [_vp, _fp, c.c_int, _fp]
+    L.iewpf_surrogate_apply_device.argtypes = [_vp, _vp, c.c_int, _vp, _vp]
+    L.iewpf_surrogate_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
     L.iewpf_surrogate_loss_grad.argtypes = [_vp, _fp, _fp, c.c_int, _dp, _fp]
     L.iewpf_surrogate_train.argtypes = [_vp, _vp, c.c_int, c.c_int, c.c_int, c.c_int, c.c_double, _dp]
     L.iewpf_set_surrogate.argtypes = [_vp, _vp, c.c_int]
@@ -495,6 +497,20 @@ class Surrogate:
         out = np.empty_like(U)
         self._chk(self.L.iewpf_surrogate_apply(self.h, _ptr(U, _fp), U.shape[0], _ptr(out, _fp)), "apply")
         return out
+
+    def apply_device(self, U, out=None, stream=None):
+        """U: CUDA torch tensor [n][3][ny][nx] float32; out (may be U) likewise."""
+        out = U if out is None else out
+        assert U.is_cuda and U.is_contiguous() and out.is_contiguous() and tuple(out.shape) == tuple(U.shape)
+        s = stream if stream is not None else _torch_stream()
+        self._chk(self.L.iewpf_surrogate_apply_device(self.h, ctypes.c_void_p(U.data_ptr()), int(U.shape[0]),
+                                                      ctypes.c_void_p(out.data_ptr()), s), "apply_device")
+        return out
+
+    def stream(self):
+        st = ctypes.c_void_p()
+        self._chk(self.L.iewpf_surrogate_stream(self.h, ctypes.byref(st)), "surrogate_stream")
+        return st.value or 0
 
     def loss_grad(self, X, Y):
         X = np.ascontiguousarray(X, np.float32).reshape(-1, 3, self.ny, self.nx)

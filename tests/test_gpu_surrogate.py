@@ -169,14 +169,22 @@ def test_zero_network_forecast_is_model_error_and_drift_only():
     assert ens.counters()[0] == 2 * k
 
 
-def test_non_finite_network_falls_back_to_the_plain_stepper_bitwise():
+@pytest.mark.parametrize("bad", ["nan", "growth"])
+def test_rejected_network_falls_back_to_the_plain_stepper_bitwise(bad):
     cfg = synth.config1(n_particles=3)
     U32, _ = start_state(cfg, 3)
     a, b = ensemble(cfg, n_drifters_max=1), ensemble(cfg, n_drifters_max=1)
     a.set_state(U32)
     b.set_state(U32)
     sur = iewpf.Surrogate(cfg.nx, cfg.ny, W, D, seed=1)
-    sur.set_params(np.full(sur.n_params, np.nan, np.float32))
+    if bad == "nan":
+        sur.set_params(np.full(sur.n_params, np.nan, np.float32))
+    else:
+        # finite output that multiplies eta far beyond the guard: f = 0.5 in every
+        # field, scaled by 1 -> eta + 0.5 m, hu, hv + 0.5 m^2/s
+        p = np.zeros(sur.n_params, np.float32)
+        p[-16:-13] = 0.5                                # bias of the output layer
+        sur.set_params(p)
     a.set_surrogate(sur, 2)
     xy0 = np.array([[50e3, 50e3]])
     ta = a.drifter_forecast(xy0, hours=240 / 3600.0, out_every_s=240.0, use_surrogate=True)
