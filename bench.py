@@ -9,6 +9,12 @@ error after the first 4) followed by one two-stage IEWPF analysis against
 is ms_per_step.  The state (2 x 315 MB) exceeds the 129 MB L2, so no flush
 is needed between timed steps.
 
+The line also carries two further workloads, each with its own numbers:
+"batched" (32 independent problems of 128^2-1024^2 cells advanced together
+as one CUDA graph per cycle) and "surrogate" (a 12 h drift forecast of 1000
+particles x 64 drifters on 256^2 cells with the plain stepper and with the
+learned surrogate, their times and the distance between the two forecasts).
+
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores (there is no other implementation to run).
 Under torchrun each rank runs an independent replica (own seed).
@@ -220,6 +226,10 @@ def run_ours(args, rank, world, local):
         batched = run_batched(rank)
     except Exception as e:  # reported, the main number stands without it
         batched = {"error": str(e)}
+    try:
+        surrogate = run_surrogate(rank, epochs=8)
+    except Exception as e:  # reported, the main number stands without it
+        surrogate = {"error": str(e)}
     if rank != 0:
         return
     cpu = cpu_baseline(args) if world == 1 else None
@@ -240,6 +250,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "batched": batched,
+        "surrogate": surrogate,
         "cpu_baseline": cpu,
         "clocks": clk,
         "last_beta": d["beta"] if d else None,
@@ -310,7 +321,7 @@ def run_batched(rank):
 SUR_FLOPS_PER_PIXEL = 2 * 9 * (3 * 64 + 4 * 64 * 64 + 64 * 3)   # algorithmic (unpadded) FLOPs of one network call
 
 
-def run_surrogate(rank, n_pairs=20000, epochs=4, batch=32, lr=1e-3, hours=12.0, k=10, ne=1000, train_ne=500):
+def run_surrogate(rank, n_pairs=20000, epochs=8, batch=32, lr=1e-3, hours=12.0, k=10, ne=1000, train_ne=500):
     """The learned-surrogate workload: the network is trained on n_pairs
     pairs (psi, 10 model steps of psi) of the 64 x 64 jet model (a 500-particle
     ensemble of it), its weights are moved to a 256 x 256 network, and a

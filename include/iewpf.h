@@ -366,12 +366,20 @@ IEWPF_API int iewpf_surrogate_get_params(const iewpf_surrogate_t* s, float* para
 /* in_scale[3], out_scale[3] (> 0) */
 IEWPF_API int iewpf_surrogate_set_scales(iewpf_surrogate_t* s, const double* in_scale, const double* out_scale);
 IEWPF_API int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, double* out_scale);
+/* Convolution path: 0 (default) = tcgen05 tensor-core kernels where nx is a
+ * multiple of 128 and ny even, else mma.sync kernels; 1 = always mma.sync.
+ * The backward pass always uses the mma.sync kernels.  get_path tells
+ * whether the forward pass runs on tcgen05. */
+IEWPF_API int iewpf_surrogate_set_path(iewpf_surrogate_t* s, int path);
+IEWPF_API int iewpf_surrogate_get_path(const iewpf_surrogate_t* s, int* uses_tcgen05);
 /* U ([n][3][ny][nx] host FP32) -> Unext (same layout), one network call. */
 IEWPF_API int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Unext);
 /* The same on device memory: U and Unext (may be equal: in place) are
  * device pointers [n][3][ny][nx], borrowed; the work is ordered after the
  * work queued on `stream` (NULL: the call returns when done) and `stream`
- * waits for it.  Particles go through the network in chunks of 64. */
+ * waits for it.  Particles go through the network in chunks of 64.  With a
+ * stream, a timeout of a bounded wait inside the tensor-core kernel
+ * (IEWPF_ETIMEOUT) is reported by the next synchronous call. */
 IEWPF_API int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, float* Unext, void* stream);
 /* The surrogate's own CUDA stream. */
 IEWPF_API int iewpf_surrogate_stream(const iewpf_surrogate_t* s, void** stream);

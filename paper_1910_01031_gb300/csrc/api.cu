@@ -347,6 +347,7 @@ int check_flags(iewpf_ctx* ctx, int f)
     if (f & FLAG_BETA) return fail(ctx, IEWPF_EBETA, "beta < 0: too many observations for the state size");
     if (f & FLAG_DOMAIN) return fail(ctx, IEWPF_EDOMAIN, "alpha solve (Lambert W) out of domain");
     if (f & FLAG_TILE_OVERFLOW) return fail(ctx, IEWPF_EINVAL, "too many observations near one tile");
+    if (f & FLAG_TIMEOUT) return fail(ctx, IEWPF_ETIMEOUT, "a bounded wait in a kernel ran out");
     return IEWPF_OK;
 }
 
@@ -435,6 +436,24 @@ struct iewpf_surrogate {
     int chunk = 64;
 };
 
+// the timeout flag of the network's tensor-core kernels (read and cleared)
+static int sur_flag(iewpf_surrogate* s, cudaStream_t st)
+{
+    int f = 0;
+    if (cudaMemcpyAsync(&f, s->net.dflag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        s->err = "reading the kernel flag";
+        return IEWPF_ECUDA;
+    }
+    if (f) {
+        cudaMemsetAsync(s->net.dflag, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        s->err = "a bounded wait of the tensor-core convolution ran out";
+        return IEWPF_ETIMEOUT;
+    }
+    return IEWPF_OK;
+}
+
 namespace {
 
 // k model steps of every particle by the surrogate (in place of k steps of
@@ -470,11 +489,9 @@ int surrogate_steps(iewpf_ctx* ctx)
     if ((rc = iewpf_get_state(ctx, S->S0, 1, nullptr))) return rc;
     CK(cudaMemcpyAsync(S->S1, S->S0, nstate * 4, cudaMemcpyDeviceToDevice, ctx->st));
     const size_t per = 3 * (size_t)ctx->plane;
-    if ((rc = S->net.ensure_batch(S->chunk))) return fail(ctx, rc, "surrogate activations");
     for (int p0 = 0; p0 < ne; p0 += S->chunk) {
         const int nb = std::min(S->chunk, ne - p0);
-        CK(S->net.pack_input(S->S0 + per * p0, nb, ctx->st));
-        CK(S->net.forward(nb, ctx->st));
+        if ((rc = S->net.infer(S->S0 + per * p0, nb, ctx->st))) return fail(ctx, rc, "surrogate network");
         CK(S->net.apply(S->S1 + per * p0, nb, ctx->st));
         ctx->launches += 2 + S->net.depth;
     }
@@ -484,6 +501,7 @@ int surrogate_steps(iewpf_ctx* ctx)
     std::vector<float> st(4 * (size_t)ne);
     CK(cudaMemcpyAsync(st.data(), S->stats, sizeof(float) * 4 * ne, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if ((rc = sur_flag(S, ctx->st))) return fail(ctx, rc, S->err);
     ctx->sur_calls++;
     bool ok = true;
     for (int p = 0; p < ne && ok; ++p) {
@@ -1411,6 +1429,20 @@ static int sfail(iewpf_surrogate* s, int code, const std::string& msg)
             return sfail(s, IEWPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
     } while (0)
 
+int iewpf_surrogate_set_path(iewpf_surrogate_t* s, int path)
+{
+    if (!s || path < 0 || path > 1) return IEWPF_EINVAL;
+    s->net.path = path;
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_get_path(const iewpf_surrogate_t* s, int* uses_tcgen05)
+{
+    if (!s || !uses_tcgen05) return IEWPF_EINVAL;
+    *uses_tcgen05 = s->net.uses_tc() ? 1 : 0;
+    return IEWPF_OK;
+}
+
 int iewpf_surrogate_destroy(iewpf_surrogate_t* s)
 {
     if (!s) return IEWPF_OK;
@@ -1516,19 +1548,18 @@ int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Un
     const size_t per = 3ull * s->net.nx * s->net.ny;
     float* d = nullptr;
     if (cudaMalloc((void**)&d, per * n * 4) != cudaSuccess) return sfail(s, IEWPF_ENOMEM, "input");
-    int rc = s->net.ensure_batch(n);
-    cudaError_t e = cudaSuccess;
-    if (!rc) {
-        if ((e = cudaMemcpyAsync(d, U, per * n * 4, cudaMemcpyHostToDevice, s->st)) == cudaSuccess &&
-            (e = s->net.pack_input(d, n, s->st)) == cudaSuccess && (e = s->net.forward(n, s->st)) == cudaSuccess &&
-            (e = s->net.apply(d, n, s->st)) == cudaSuccess)
-            e = cudaMemcpyAsync(Unext, d, per * n * 4, cudaMemcpyDeviceToHost, s->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    int rc = IEWPF_OK;
+    cudaError_t e = cudaMemcpyAsync(d, U, per * n * 4, cudaMemcpyHostToDevice, s->st);
+    for (int p0 = 0; p0 < n && e == cudaSuccess && !rc; p0 += s->chunk) {
+        const int nb = std::min(s->chunk, n - p0);
+        if (!(rc = s->net.infer(d + per * p0, nb, s->st))) e = s->net.apply(d + per * p0, nb, s->st);
     }
+    if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(Unext, d, per * n * 4, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     cudaFree(d);
-    if (rc) return sfail(s, rc, "activations");
+    if (rc) return sfail(s, rc, "network");
     if (e != cudaSuccess) return sfail(s, IEWPF_ECUDA, cudaGetErrorString(e));
-    return IEWPF_OK;
+    return sur_flag(s, s->st);
 }
 
 int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, float* Unext, void* stream)
@@ -1536,27 +1567,23 @@ int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, fl
     if (!s || !U || !Unext || n < 1) return IEWPF_EINVAL;
     SCK(cudaSetDevice(s->dev));
     const size_t per = 3ull * s->net.nx * s->net.ny;
-    int rc = s->net.ensure_batch(std::min(n, s->chunk));
-    if (rc) return sfail(s, rc, "activations");
     cudaStream_t user = (cudaStream_t)stream;
     cudaEvent_t ev;
     SCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    if (user) {
-        SCK(cudaEventRecord(ev, user));
-        SCK(cudaStreamWaitEvent(s->st, ev, 0));
-    }
-    if (Unext != U) SCK(cudaMemcpyAsync(Unext, U, per * n * 4, cudaMemcpyDeviceToDevice, s->st));
-    for (int p0 = 0; p0 < n; p0 += s->chunk) {
+    int rc = IEWPF_OK;
+    cudaError_t e = cudaSuccess;
+    if (user && (e = cudaEventRecord(ev, user)) == cudaSuccess) e = cudaStreamWaitEvent(s->st, ev, 0);
+    if (e == cudaSuccess && Unext != U) e = cudaMemcpyAsync(Unext, U, per * n * 4, cudaMemcpyDeviceToDevice, s->st);
+    for (int p0 = 0; p0 < n && e == cudaSuccess && !rc; p0 += s->chunk) {
         const int nb = std::min(s->chunk, n - p0);
-        SCK(s->net.pack_input(Unext + per * p0, nb, s->st));
-        SCK(s->net.forward(nb, s->st));
-        SCK(s->net.apply(Unext + per * p0, nb, s->st));
+        if (!(rc = s->net.infer(Unext + per * p0, nb, s->st))) e = s->net.apply(Unext + per * p0, nb, s->st);
     }
-    SCK(cudaEventRecord(ev, s->st));
-    if (user) SCK(cudaStreamWaitEvent(user, ev, 0));
-    else SCK(cudaEventSynchronize(ev));
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s->st);
+    if (e == cudaSuccess) e = user ? cudaStreamWaitEvent(user, ev, 0) : cudaEventSynchronize(ev);
     cudaEventDestroy(ev);
-    return IEWPF_OK;
+    if (rc) return sfail(s, rc, "network");
+    if (e != cudaSuccess) return sfail(s, IEWPF_ECUDA, cudaGetErrorString(e));
+    return user ? IEWPF_OK : sur_flag(s, s->st);
 }
 
 int iewpf_surrogate_stream(const iewpf_surrogate_t* s, void** stream)
@@ -1592,7 +1619,7 @@ int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, const float*
     cudaFree(dy);
     if (rc) return sfail(s, rc, "activations");
     if (e != cudaSuccess) return sfail(s, IEWPF_ECUDA, cudaGetErrorString(e));
-    return IEWPF_OK;
+    return sur_flag(s, s->st);
 }
 
 int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs, int batch,
@@ -1713,7 +1740,7 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
         if (epoch_loss) epoch_loss[ep] = nbat ? acc / nbat : 0.0;
     }
     cleanup();
-    return IEWPF_OK;
+    return sur_flag(s, s->st);
 }
 
 int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_steps)

@@ -1,0 +1,383 @@
+// Inference forward 3x3 periodic convolution of the surrogate on the
+// 5th-generation tensor cores: operands staged by TMA
+// (cp.async.bulk.tensor), products by tcgen05.mma (BF16 from shared memory,
+// FP32 accumulators in tensor memory), epilogue through tcgen05.ld.
+//
+// Implicit GEMM per tile of 2 output rows x 128 pixels: for output row r and
+// tap (ky, kx), A is the 128 x CIN block of input pixels shifted by
+// (ky - 1, kx - 1) and B the COUT x CIN weights of the tap; each row's
+// 128 x COUT accumulator sums 9 taps x CIN/16 MMAs of K = 16.  Activations
+// live in HBM with a one-pixel periodic halo ([b][ny + 2][nx + 2][C]), so the
+// halo patch of a tile (4 rows x 130 pixels x CIN) is a single TMA box and a
+// shifted tap is a shifted start address in the matrix descriptor:
+//  * CIN = 64: 128-byte rows (one pixel, 64 channels) in the 128-byte swizzle
+//    layout (8-row atoms of 1024 bytes); the swizzle follows the absolute
+//    shared-memory address, so starts at any pixel (+128 B) or K step (+32 B)
+//    stay consistent with what TMA wrote;
+//  * CIN = 16: no swizzle, core matrices of 8 pixels x 16 bytes, staged
+//    through a tensor map whose dimensions are permuted to
+//    (8 channels, pixels, rows, channel groups).
+// Warp roles: warp 0 issues TMA, warp 1 issues MMAs (one thread each), warps
+// 2-9 drain the accumulators (warp w reads tensor-memory lanes 32 (w % 4) +
+// 0..31 of output row (w - 2) / 4).  Two shared-memory stages and two
+// accumulator sets connect them through mbarriers.  The epilogue adds the
+// bias, applies SiLU, writes BF16 outputs with their periodic halo images (or
+// the FP32 output of the last layer).  Every wait is bounded: on a timeout the
+// CTA raises an abort flag, records FLAG_TIMEOUT, waits (bounded) for its own
+// copies and products in flight and frees its tensor memory.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "surrogate.h"
+
+#include <cuda_bf16.h>
+
+namespace iewpf {
+
+namespace {
+
+constexpr int TC_PX = 128;                 // pixels of one output row segment (MMA M)
+constexpr int TC_ROWS = 2;                 // output rows per tile
+constexpr int TC_PROWS = TC_ROWS + 2;      // patch rows
+constexpr int TC_PCOLS = TC_PX + 2;        // patch columns
+constexpr int TC_WARPS = 10;
+constexpr int TC_THREADS = 32 * TC_WARPS;
+constexpr int TC_EPI_WARPS = 8;
+constexpr long long TC_WAIT_LIMIT = 1LL << 24;
+
+__device__ __forceinline__ uint32_t su32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor (K-major): layout 0 = no swizzle
+// (lbo = bytes between core matrices along K, sbo = along M/N), 2 = 128-byte
+// swizzle (sbo = bytes between 8-row atoms)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7) << 61);
+}
+
+// instruction descriptor: BF16 A and B (K-major), FP32 D, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// bounded wait for the phase of `parity`; gives up when the CTA aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+{
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// the same without the abort check (draining after an abort)
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return;
+    }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <int CIN, int COUT>
+struct TcLayout {
+    static constexpr bool SW = CIN == 64;                          // 128-byte swizzle for the A patch
+    static constexpr int W_BYTES = 9 * COUT * CIN * 2;
+    static constexpr int STAGE = TC_PROWS * TC_PCOLS * CIN * 2;    // bytes of one patch
+    static constexpr int STAGE_ALLOC = (STAGE + 1023) / 1024 * 1024;
+    static constexpr int W_OFF = 0;
+    static constexpr int A_OFF = (W_BYTES + 1023) / 1024 * 1024;
+    static constexpr int BIAS_OFF = A_OFF + 2 * STAGE_ALLOC;
+    static constexpr int BAR_OFF = BIAS_OFF + COUT * 4;            // 8 mbarriers, abort flag, tensor-memory slot
+    static constexpr int TOTAL = BAR_OFF + 128;
+    // at least 120 KB so that one CTA runs per SM: it keeps its tensor memory
+    static constexpr int REQUEST = (TOTAL > 120 * 1024 ? TOTAL : 120 * 1024) + 1024;
+    static constexpr int TMEM_COLS = 2 * TC_ROWS * COUT;
+};
+
+template <int CIN, int COUT, bool OUT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16* __restrict__ W,
+               const float* __restrict__ bias, int nb, int ny, int nx, __nv_bfloat16* __restrict__ aout,
+               float* __restrict__ fout, int* __restrict__ flag)
+{
+    using L = TcLayout<CIN, COUT>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* sbias = reinterpret_cast<float*>(smem + L::BIAS_OFF);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+    // bars: full[2], empty[2], tfull[2], tempty[2]
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + L::BAR_OFF + 64);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + 68);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = su32(smem);
+
+    // weights of every tap, once per CTA (B operand, K-major, rows = output channels)
+    if (L::SW) {
+        // 128-byte rows of 64 input channels; 16-byte chunk c of row co at chunk c ^ (co & 7)
+        for (int i = tid; i < 9 * COUT * 8; i += TC_THREADS) {
+            const int c = i & 7, co = (i >> 3) % COUT, tap = i / (8 * COUT);
+            *reinterpret_cast<uint4*>(smem + L::W_OFF + (tap * COUT + co) * 128 + ((c ^ (co & 7)) << 4)) =
+                *reinterpret_cast<const uint4*>(W + ((size_t)tap * COUT + co) * CIN + c * 8);
+        }
+    } else {
+        // core matrices of 8 output channels x 16 bytes: [tap][chunk][co][8 ch]
+        for (int i = tid; i < 9 * COUT * (CIN / 8); i += TC_THREADS) {
+            const int j = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
+            *reinterpret_cast<uint4*>(smem + L::W_OFF + ((tap * (CIN / 8) + j) * COUT + co) * 16) =
+                *reinterpret_cast<const uint4*>(W + ((size_t)tap * COUT + co) * CIN + j * 8);
+        }
+    }
+    for (int i = tid; i < COUT; i += TC_THREADS) sbias[i] = bias[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 8; ++k) {
+            const int count = (k >= 6) ? TC_EPI_WARPS : 1;     // tempty: one arrival per epilogue warp
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(&bars[k])), "r"(count));
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    const int tiles_x = nx / TC_PX, tiles_y = ny / TC_ROWS;
+    const long long ntiles = (long long)nb * tiles_x * tiles_y;
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const int nloc = first < ntiles ? (int)((ntiles - 1 - first) / stride + 1) : 0;
+    auto tile_coords = [&](int i, int& b, int& y0, int& x0) {
+        const long long t = first + (long long)i * stride;
+        b = (int)(t / ((long long)tiles_x * tiles_y));
+        const int rem = (int)(t % ((long long)tiles_x * tiles_y));
+        y0 = (rem / tiles_x) * TC_ROWS;
+        x0 = (rem % tiles_x) * TC_PX;
+    };
+    const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[2]), tfull0 = su32(&bars[4]), tempty0 = su32(&bars[6]);
+
+    if (warp == 0) {
+        // ---- TMA producer ----
+        int issued = 0;
+        if (lane == 0) {
+            for (int i = 0; i < nloc; ++i) {
+                const int s = i & 1;
+                const uint32_t k = (uint32_t)(i >> 1);
+                if (!mbar_wait(empty0 + 8 * s, (k & 1) ^ 1, abort)) break;
+                int b, y0, x0;
+                tile_coords(i, b, y0, x0);
+                const uint32_t dst = sbase + L::A_OFF + s * L::STAGE_ALLOC;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full0 + 8 * s),
+                             "r"(L::STAGE)
+                             : "memory");
+                // padded coordinates: patch row 0 = padded row y0, patch column 0 = padded column x0
+                if (L::SW)
+                    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+                                 "l"(reinterpret_cast<uint64_t>(&tmap_in)), "r"(0), "r"(x0), "r"(y0), "r"(b),
+                                 "r"(full0 + 8 * s)
+                                 : "memory");
+                else
+                    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+                                 "l"(reinterpret_cast<uint64_t>(&tmap_in)), "r"(0), "r"(x0), "r"(y0), "r"(0), "r"(b),
+                                 "r"(full0 + 8 * s)
+                                 : "memory");
+                issued = i + 1;
+            }
+            // after an abort, wait (bounded) for the copies in flight
+            if (*abort)
+                for (int i = issued >= 2 ? issued - 2 : 0; i < issued; ++i)
+                    mbar_drain(full0 + 8 * (i & 1), (uint32_t)((i >> 1) & 1));
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        int issued = 0;
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(TC_PX, COUT);
+            for (int i = 0; i < nloc; ++i) {
+                const int s = i & 1;
+                const uint32_t k = (uint32_t)(i >> 1);
+                if (!mbar_wait(full0 + 8 * s, k & 1, abort)) break;
+                if (!mbar_wait(tempty0 + 8 * s, (k & 1) ^ 1, abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = sbase + L::A_OFF + s * L::STAGE_ALLOC;
+                const uint32_t d0 = tmem + (uint32_t)(s * TC_ROWS * COUT);
+#pragma unroll 1
+                for (int r = 0; r < TC_ROWS; ++r)
+#pragma unroll 1
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+                        for (int kc = 0; kc < CIN / 16; ++kc) {
+                            uint64_t ad, bd;
+                            if (L::SW) {
+                                ad = sdesc(a0 + ((r + ky) * TC_PCOLS + kx) * 128 + kc * 32, 16, 1024, 2);
+                                bd = sdesc(sbase + L::W_OFF + tap * COUT * 128 + kc * 32, 16, 1024, 2);
+                            } else {
+                                constexpr uint32_t PLANE = TC_PROWS * TC_PCOLS * 16;
+                                ad = sdesc(a0 + 2 * kc * PLANE + ((r + ky) * TC_PCOLS + kx) * 16, PLANE, 128, 0);
+                                bd = sdesc(sbase + L::W_OFF + (tap * (CIN / 8) + 2 * kc) * COUT * 16, COUT * 16, 128, 0);
+                            }
+                            const uint32_t acc = (tap | kc) != 0;
+                            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                             d0 + (uint32_t)(r * COUT)),
+                                         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                        }
+                    }
+                // the stage is free and the accumulators are ready once these MMAs complete
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 empty0 + 8 * s)
+                             : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 tfull0 + 8 * s)
+                             : "memory");
+                issued = i + 1;
+            }
+            if (*abort && issued > 0)
+                mbar_drain(tfull0 + 8 * ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1));
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue ----
+        const int e = warp - 2, q = warp & 3, r = e >> 2;
+        for (int i = 0; i < nloc; ++i) {
+            const int s = i & 1;
+            const uint32_t k = (uint32_t)(i >> 1);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(tfull0 + 8 * s, k & 1, abort);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            int b, y0, x0;
+            tile_coords(i, b, y0, x0);
+            const int y = y0 + r, x = x0 + 32 * q + lane;
+            const uint32_t ta = tmem + (uint32_t)(s * TC_ROWS * COUT + r * COUT) + ((uint32_t)(32 * q) << 16);
+            if (OUT) {
+                float v[16];
+                tmem_ld16(ta, v);
+                const size_t pix = ((size_t)b * ny + y) * nx + x;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fout[pix * 3 + c] = v[c] + sbias[c];
+            } else {
+                // this pixel and its periodic images in the padded output
+                const size_t pw = (size_t)(nx + 2), plane = (size_t)(ny + 2) * pw;
+                const int ys[2] = {y + 1, y == 0 ? ny + 1 : (y == ny - 1 ? 0 : -1)};
+                const int xs[2] = {x + 1, x == 0 ? nx + 1 : (x == nx - 1 ? 0 : -1)};
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(ta + c0, v);
+                    __align__(16) __nv_bfloat162 hv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float z0 = v[2 * j] + sbias[c0 + 2 * j], z1 = v[2 * j + 1] + sbias[c0 + 2 * j + 1];
+                        hv[j] = __floats2bfloat162_rn(__fdividef(z0, 1.0f + __expf(-z0)),
+                                                      __fdividef(z1, 1.0f + __expf(-z1)));
+                    }
+                    const uint4 w0 = reinterpret_cast<const uint4*>(hv)[0], w1 = reinterpret_cast<const uint4*>(hv)[1];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+                            if (ys[a] >= 0 && xs[c] >= 0) {
+                                uint4* p = reinterpret_cast<uint4*>(
+                                    aout + ((size_t)b * plane + (size_t)ys[a] * pw + xs[c]) * COUT + c0);
+                                p[0] = w0;
+                                p[1] = w1;
+                            }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tempty0 + 8 * s) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && *abort) atomicOr(flag, FLAG_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::TMEM_COLS));
+}
+
+template <int CIN, int COUT, bool OUT>
+cudaError_t conv_tc(const CUtensorMap& map, const __nv_bfloat16* W, const float* bias, int nb, int ny, int nx,
+                    __nv_bfloat16* a, float* f, int* flag, cudaStream_t st)
+{
+    using L = TcLayout<CIN, COUT>;
+    static_assert(L::REQUEST <= 227 * 1024, "shared memory");
+    static_assert(L::TMEM_COLS >= 32 && (L::TMEM_COLS & (L::TMEM_COLS - 1)) == 0, "tensor memory columns");
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L::REQUEST);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (long long)nb * (nx / TC_PX) * (ny / TC_ROWS);
+    const int grid = (int)std::min<long long>(tiles, sms);
+    if (grid < 1) return cudaSuccess;
+    conv_tc_kernel<CIN, COUT, OUT><<<grid, TC_THREADS, L::REQUEST, st>>>(map, W, bias, nb, ny, nx, a, f, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv_tc_supported(int nx, int ny)
+{
+    return nx % TC_PX == 0 && ny % TC_ROWS == 0 && nx + 2 <= 65536;
+}
+
+cudaError_t launch_conv_tc(int layer_kind, const CUtensorMap& in_map, const __nv_bfloat16* W, const float* bias,
+                           int nb, int ny, int nx, __nv_bfloat16* a, float* f, int* flag, cudaStream_t st)
+{
+    if (!conv_tc_supported(nx, ny)) return cudaErrorInvalidValue;
+    switch (layer_kind) {
+    case 0: return conv_tc<16, 64, false>(in_map, W, bias, nb, ny, nx, a, f, flag, st);
+    case 1: return conv_tc<64, 64, false>(in_map, W, bias, nb, ny, nx, a, f, flag, st);
+    case 2: return conv_tc<64, 16, true>(in_map, W, bias, nb, ny, nx, a, f, flag, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace iewpf

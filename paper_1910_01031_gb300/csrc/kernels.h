@@ -110,6 +110,7 @@ enum : int {
     FLAG_DOMAIN = 4,
     FLAG_NONFINITE = 8,
     FLAG_TILE_OVERFLOW = 16,
+    FLAG_TIMEOUT = 32,          // a bounded wait of a tensor-core kernel ran out
 };
 
 }  // namespace iewpf

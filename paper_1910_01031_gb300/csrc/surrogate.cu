@@ -9,10 +9,13 @@
 //
 // Tensor layout: activations NHWC [batch][ny][nx][C] bf16 with C = 16
 // (network input, 3 used) or 64; weights [tap = 3 ky + kx][cout][cin] bf16.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "../../include/iewpf.h"
 #include "common.cuh"
@@ -47,11 +50,6 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
                  : "r"(addr));
 }
 
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
-}
-
 // D = A (16x16 bf16, row) * B (16x8 bf16, col) + D, fp32
 __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1)
@@ -62,10 +60,10 @@ __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uin
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z)
 {
-    const float s = 1.0f / (1.0f + __expf(-z));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
 }
 
@@ -356,6 +354,28 @@ __global__ void pack_input_kernel(const float* __restrict__ U, int n, int ny, in
     d[1] = *reinterpret_cast<uint4*>(&g[8]);
 }
 
+// the same into the halo-padded layout [n][ny + 2][nx + 2][16]: padded
+// position (yp, xp) holds interior cell ((yp - 1) mod ny, (xp - 1) mod nx)
+__global__ void pack_input_padded_kernel(const float* __restrict__ U, int n, int ny, int nx, float s0, float s1,
+                                         float s2, __nv_bfloat16* __restrict__ x)
+{
+    const long long pw = nx + 2, pplane = (long long)(ny + 2) * pw, plane = (long long)ny * nx;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * pplane) return;
+    const long long b = p / pplane, r = p % pplane;
+    const int yp = (int)(r / pw), xq = (int)(r % pw);
+    const long long c = (long long)pmod(yp - 1, ny) * nx + pmod(xq - 1, nx);
+    __align__(16) __nv_bfloat16 g[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[k] = __float2bfloat16(0.0f);
+    g[0] = __float2bfloat16(U[(b * 3 + 0) * plane + c] * s0);
+    g[1] = __float2bfloat16(U[(b * 3 + 1) * plane + c] * s1);
+    g[2] = __float2bfloat16(U[(b * 3 + 2) * plane + c] * s2);
+    uint4* d = reinterpret_cast<uint4*>(x + p * 16);
+    d[0] = *reinterpret_cast<uint4*>(&g[0]);
+    d[1] = *reinterpret_cast<uint4*>(&g[8]);
+}
+
 // target of a pair: normalised change (Y - X) / scale, [n][ny][nx][3] fp32
 __global__ void pack_target_kernel(const float* __restrict__ X, const float* __restrict__ Y, int n, int ny, int nx,
                                    float d0, float d1, float d2, float* __restrict__ t)
@@ -539,6 +559,7 @@ int Surrogate::init(int nx_, int ny_, int width_, int depth_)
         b_off.push_back(n_params);
         n_params += layer_cout(l);
     }
+    dflag = salloc<int>(*this, 1);
     master = salloc<float>(*this, n_params);
     grad = salloc<float>(*this, n_params);
     adam_m = salloc<float>(*this, n_params);
@@ -547,7 +568,8 @@ int Surrogate::init(int nx_, int ny_, int width_, int depth_)
         wf.push_back(salloc<__nv_bfloat16>(*this, layer_w(l)));
         wd.push_back(salloc<__nv_bfloat16>(*this, layer_w(l)));
     }
-    if (!master || !grad || !adam_m || !adam_v) return IEWPF_ENOMEM;
+    if (!master || !grad || !adam_m || !adam_v || !dflag) return IEWPF_ENOMEM;
+    cudaMemset(dflag, 0, sizeof(int));
     for (auto* p : wf)
         if (!p) return IEWPF_ENOMEM;
     for (auto* p : wd)
@@ -605,6 +627,97 @@ cudaError_t Surrogate::cast(cudaStream_t st)
         cast_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(master + w_off[l], layer_cin(l), layer_cout(l), wf[l], wd[l]);
     }
     return cudaGetLastError();
+}
+
+bool Surrogate::uses_tc() const
+{
+    return path == 0 && conv_tc_supported(nx, ny);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int Surrogate::ensure_infer(int nb)
+{
+    if (!uses_tc()) {
+        const int rc = ensure_batch(nb);
+        y_out = out;
+        return rc;
+    }
+    if (nb <= cap_infer) {
+        y_out = out_i;
+        return IEWPF_OK;
+    }
+    for (void* p : {(void*)xp, (void*)ap[0], (void*)ap[1], (void*)out_i}) sfree(*this, p);
+    cap_infer = 0;
+    const size_t pp = (size_t)nb * (nx + 2) * (ny + 2);
+    xp = salloc<__nv_bfloat16>(*this, pp * 16);
+    ap[0] = salloc<__nv_bfloat16>(*this, pp * width);
+    ap[1] = salloc<__nv_bfloat16>(*this, pp * width);
+    out_i = salloc<float>(*this, (size_t)nb * nx * ny * 3);
+    if (!xp || !ap[0] || !ap[1] || !out_i) return IEWPF_ENOMEM;
+    auto enc = tensor_map_encoder();
+    if (!enc) return IEWPF_ECUDA;
+    const cuuint64_t W2 = (cuuint64_t)nx + 2, H2 = (cuuint64_t)ny + 2;
+    {
+        // 16 channels: (8 ch, x, y, channel group, b), no swizzle
+        const cuuint64_t dims[5] = {8, W2, H2, 2, (cuuint64_t)nb};
+        const cuuint64_t strides[4] = {32, W2 * 32, 16, H2 * W2 * 32};
+        const cuuint32_t box[5] = {8, 130, 4, 2, 1};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&map_x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xp, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return IEWPF_ECUDA;
+    }
+    for (int k = 0; k < 2; ++k) {
+        // 64 channels: (64 ch, x, y, b), 128-byte swizzle
+        const cuuint64_t dims[4] = {(cuuint64_t)width, W2, H2, (cuuint64_t)nb};
+        const cuuint64_t strides[3] = {(cuuint64_t)width * 2, W2 * width * 2, H2 * W2 * width * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)width, 130, 4, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&map_a[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, ap[k], dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return IEWPF_ECUDA;
+    }
+    cap_infer = nb;
+    y_out = out_i;
+    return IEWPF_OK;
+}
+
+int Surrogate::infer(const float* U, int nb, cudaStream_t st)
+{
+    int rc = ensure_infer(nb);
+    if (rc) return rc;
+    cudaError_t e;
+    if (!uses_tc()) {
+        if ((e = pack_input(U, nb, st)) != cudaSuccess || (e = forward(nb, st)) != cudaSuccess) return IEWPF_ECUDA;
+        return IEWPF_OK;
+    }
+    const long long n = (long long)nb * (nx + 2) * (ny + 2);
+    pack_input_padded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, nb, ny, nx, in_scale[0], in_scale[1],
+                                                                         in_scale[2], xp);
+    for (int l = 0; l < depth; ++l) {
+        const float* bias = master + b_off[l];
+        const int kind = l == 0 ? 0 : (l + 1 < depth ? 1 : 2);
+        const CUtensorMap& in_map = l == 0 ? map_x : map_a[(l - 1) & 1];
+        e = launch_conv_tc(kind, in_map, wf[l], bias, nb, ny, nx, kind < 2 ? ap[l & 1] : nullptr,
+                           kind == 2 ? out_i : nullptr, dflag, st);
+        if (e != cudaSuccess) return IEWPF_ECUDA;
+    }
+    return cudaGetLastError() == cudaSuccess ? IEWPF_OK : IEWPF_ECUDA;
 }
 
 cudaError_t Surrogate::forward(int nb, cudaStream_t st)
@@ -684,9 +797,10 @@ cudaError_t Surrogate::pack_target(const float* X, const float* Y, int nb, cudaS
 
 cudaError_t Surrogate::apply(float* U, int nb, cudaStream_t st)
 {
+    if (!y_out || nb > std::max(cap_batch, cap_infer)) return cudaErrorInvalidValue;
     const long long n = (long long)nb * nx * ny;
-    apply_output_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, out, nb, ny, nx, out_scale[0], out_scale[1],
-                                                                    out_scale[2]);
+    apply_output_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, y_out, nb, ny, nx, out_scale[0],
+                                                                    out_scale[1], out_scale[2]);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // the forward / backward / Adam passes of the periodic 3x3 convolutional
 // network on one nx x ny grid.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -31,6 +32,16 @@ struct Surrogate {
     float* wpartial = nullptr;
     double* lpartial = nullptr;
     double* dloss = nullptr;
+    // inference on the tcgen05 kernels: activations with a one-pixel periodic
+    // halo, [b][ny + 2][nx + 2][C], and their TMA tensor maps
+    int cap_infer = 0;
+    __nv_bfloat16* xp = nullptr;            // network input, 16 channels
+    __nv_bfloat16* ap[2] = {nullptr, nullptr};
+    float* out_i = nullptr;                 // [b][ny][nx][3]
+    CUtensorMap map_x, map_a[2];
+    float* y_out = nullptr;                 // output of the last infer(): out or out_i
+    int path = 0;                           // inference convolutions: 0 tcgen05 where the grid allows, 1 mma.sync
+    int* dflag = nullptr;                   // FLAG_TIMEOUT of the tensor-core kernel
     float in_scale[3] = {1.0f, 1.0f, 1.0f};     // network input = state * in_scale
     float out_scale[3] = {1.0f, 1.0f, 1.0f};    // state change = output * out_scale
     std::vector<void*> owned;
@@ -46,11 +57,27 @@ struct Surrogate {
     cudaError_t cast(cudaStream_t st);
     cudaError_t pack_input(const float* U, int nb, cudaStream_t st);
     cudaError_t pack_target(const float* X, const float* Y, int nb, cudaStream_t st);
+    // training forward (mma.sync, keeps z for the backward pass); output in `out`
     cudaError_t forward(int nb, cudaStream_t st);
+    // inference: U [nb][3][ny][nx] -> y_out (tcgen05 when uses_tc()); IEWPF code
+    int infer(const float* U, int nb, cudaStream_t st);
+    int ensure_infer(int nb);
+    bool uses_tc() const;
     cudaError_t backward(int nb, cudaStream_t st);
     cudaError_t adam_step(float lr, cudaStream_t st);
     cudaError_t apply(float* U, int nb, cudaStream_t st);
 };
+
+// tcgen05 inference convolution (conv_tc.cu) on halo-padded activations:
+// layer_kind 0 = 16 -> 64 channels and 1 = 64 -> 64 (bias + SiLU into the
+// padded `a`, halo images included), 2 = 64 -> 16 (bias only, first 3 channels
+// into f as FP32 [b][ny][nx][3]).  in_map: 16 channels as a 5-D map
+// (8 ch, nx+2, ny+2, 2, b) without swizzle, box (8, 130, 4, 2, 1); 64
+// channels as a 4-D map (64 ch, nx+2, ny+2, b) with the 128-byte swizzle, box
+// (64, 130, 4, 1).  Needs nx % 128 == 0 and ny % 2 == 0.
+bool conv_tc_supported(int nx, int ny);
+cudaError_t launch_conv_tc(int layer_kind, const CUtensorMap& in_map, const __nv_bfloat16* W, const float* bias,
+                           int nb, int ny, int nx, __nv_bfloat16* a, float* f, int* flag, cudaStream_t st);
 
 // drifters advected over T seconds with the mean of the cell velocities of the
 // states before (S0) and after (S1), both [ne][3][ny][nx]

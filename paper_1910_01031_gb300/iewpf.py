@@ -30,7 +30,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
            "iewpf_batch_work", "iewpf_batch_last_error", "iewpf_surrogate_create", "iewpf_surrogate_destroy",
            "iewpf_surrogate_param_count", "iewpf_surrogate_set_params", "iewpf_surrogate_get_params",
-           "iewpf_surrogate_set_scales", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_apply_device", "iewpf_surrogate_stream", "iewpf_surrogate_loss_grad",
+           "iewpf_surrogate_set_scales", "iewpf_surrogate_set_path", "iewpf_surrogate_get_path", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_apply_device", "iewpf_surrogate_stream", "iewpf_surrogate_loss_grad",
            "iewpf_surrogate_train", "iewpf_set_surrogate", "iewpf_surrogate_stats", "iewpf_surrogate_last_error"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
@@ -134,6 +134,8 @@ def load(build_if_needed: bool = True):
     L.iewpf_surrogate_get_params.argtypes = [_vp, _fp]
     L.iewpf_surrogate_set_scales.argtypes = [_vp, _dp, _dp]
     L.iewpf_surrogate_get_scales.argtypes = [_vp, _dp, _dp]
+    L.iewpf_surrogate_set_path.argtypes = [_vp, c.c_int]
+    L.iewpf_surrogate_get_path.argtypes = [_vp, _ip]
     L.iewpf_surrogate_apply.argtypes = [_vp, _fp, c.c_int, _fp]
     L.iewpf_surrogate_apply_device.argtypes = [_vp, _vp, c.c_int, _vp, _vp]
     L.iewpf_surrogate_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
@@ -486,6 +488,15 @@ class Surrogate:
     def set_scales(self, in_scale, out_scale):
         a, b = _f64(in_scale, (3,)), _f64(out_scale, (3,))
         self._chk(self.L.iewpf_surrogate_set_scales(self.h, _ptr(a), _ptr(b)), "set_scales")
+
+    def set_path(self, path):
+        """0: tcgen05 forward convolutions where the grid allows; 1: mma.sync only."""
+        self._chk(self.L.iewpf_surrogate_set_path(self.h, int(path)), "set_path")
+
+    def uses_tcgen05(self):
+        v = ctypes.c_int()
+        self._chk(self.L.iewpf_surrogate_get_path(self.h, ctypes.byref(v)), "get_path")
+        return bool(v.value)
 
     def scales(self):
         a, b = np.zeros(3), np.zeros(3)

@@ -209,3 +209,45 @@ def test_surrogate_argument_errors():
     other = iewpf.Surrogate(32, 32, W, D)
     with pytest.raises(iewpf.IewpfError):
         ens.set_surrogate(other, 2)
+
+
+def test_tcgen05_forward_matches_oracle_and_mma_sync():
+    # 256 x 64 cells, 10 fields: 640 tiles of 2 rows x 128 pixels, several per
+    # CTA (both pipeline buffers, a ragged last round of the persistent grid)
+    sur, p = _net(nx=256, ny=64, seed=6)
+    assert sur.uses_tcgen05()
+    U = _fields(10, 64, 256, 7)
+    out_tc = sur.apply(U)
+    ref = S.apply(p, U.astype(np.float64), SI, SO, W, D)
+    assert _rel(out_tc.astype(np.float64) - U, ref - U) < FWD_TOL
+    sur.set_path(1)
+    assert not sur.uses_tcgen05()
+    out_mma = sur.apply(U)
+    # the two paths round the same activations to BF16; they differ only where
+    # a different FP32 summation order flips a rounding
+    assert _rel(out_tc.astype(np.float64) - U, out_mma.astype(np.float64) - U) < 1e-2
+
+
+def test_tcgen05_forward_small_grid_and_gradients():
+    # one tile row pair per field, fewer tiles than SMs; training forward keeps z
+    sur, p = _net(nx=128, ny=16, seed=8)
+    assert sur.uses_tcgen05()
+    X = _fields(2, 16, 128, 9)
+    Y = X + (_fields(2, 16, 128, 10) * np.array([0.05, 0.1, 0.1], np.float32)[None, :, None, None]).astype(np.float32)
+    out = sur.apply(X)
+    ref = S.apply(p, X.astype(np.float64), SI, SO, W, D)
+    assert _rel(out.astype(np.float64) - X, ref - X) < FWD_TOL
+    L, g = sur.loss_grad(X, Y)
+    Lr, gr = S.loss_grad(p, X.astype(np.float64), Y.astype(np.float64), SI, SO, W, D)
+    assert abs(L - Lr) < 1e-2 * Lr
+    lg, lr = S.unpack(g, W, D), S.unpack(gr, W, D)
+    for l in range(D):
+        assert _rel(lg[l][0], lr[l][0]) < GRAD_TOL, ("weights", l)
+
+
+def test_tcgen05_forward_is_bitwise_translation_equivariant():
+    sur, _ = _net(nx=256, ny=16, seed=12)
+    U = _fields(3, 16, 256, 13)
+    a = sur.apply(U)
+    b = sur.apply(np.ascontiguousarray(np.roll(U, (2, 128), axis=(2, 3))))
+    assert np.array_equal(np.roll(a, (2, 128), axis=(2, 3)), b)
