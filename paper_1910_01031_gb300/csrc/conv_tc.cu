@@ -18,8 +18,8 @@
 //    through a tensor map whose dimensions are permuted to
 //    (8 channels, pixels, rows, channel groups).
 // Warp roles: warp 0 issues TMA, warp 1 issues MMAs (one thread each), warps
-// 2-9 drain the accumulators (warp w reads tensor-memory lanes 32 (w % 4) +
-// 0..31 of output row (w - 2) / 4).  Two shared-memory stages and two
+// 2-17 drain the accumulators (warp w reads tensor-memory lanes 32 (w % 4) +
+// 0..31, i.e. 32 pixels, of one output row and 32 of its channels).  Two shared-memory stages and two
 // accumulator sets connect them through mbarriers.  The epilogue adds the
 // bias, applies SiLU, writes BF16 outputs with their periodic halo images (or
 // the FP32 output of the last layer).  Every wait is bounded: on a timeout the
@@ -44,9 +44,9 @@ constexpr int TC_PX = 128;                 // pixels of one output row segment (
 constexpr int TC_ROWS = 2;                 // output rows per tile
 constexpr int TC_PROWS = TC_ROWS + 2;      // patch rows
 constexpr int TC_PCOLS = TC_PX + 2;        // patch columns
-constexpr int TC_WARPS = 10;
+constexpr int TC_EPI_WARPS = 16;           // 4 lane quarters x 2 rows x 2 column halves
+constexpr int TC_WARPS = 2 + TC_EPI_WARPS;
 constexpr int TC_THREADS = 32 * TC_WARPS;
-constexpr int TC_EPI_WARPS = 8;
 constexpr long long TC_WAIT_LIMIT = 1LL << 24;
 
 __device__ __forceinline__ uint32_t su32(const void* p)
@@ -112,6 +112,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v)
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// 32 consecutive accumulator columns of the warp's 32 lanes (one register each)
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
 template <int CIN, int COUT>
@@ -244,27 +258,31 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a0 = sbase + L::A_OFF + s * L::STAGE_ALLOC;
                 const uint32_t d0 = tmem + (uint32_t)(s * TC_ROWS * COUT);
-#pragma unroll 1
+                // descriptors of the stage and of the weights; every MMA adds a
+                // compile-time offset (in 16-byte units) to the address field
+                constexpr uint32_t PLANE = TC_PROWS * TC_PCOLS * 16;
+                const uint64_t adesc = L::SW ? sdesc(a0, 16, 1024, 2) : sdesc(a0, PLANE, 128, 0);
+                const uint64_t bdesc = L::SW ? sdesc(sbase + L::W_OFF, 16, 1024, 2)
+                                             : sdesc(sbase + L::W_OFF, COUT * 16, 128, 0);
+#pragma unroll
                 for (int r = 0; r < TC_ROWS; ++r)
-#pragma unroll 1
+#pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
                         const int ky = tap / 3, kx = tap % 3;
 #pragma unroll
                         for (int kc = 0; kc < CIN / 16; ++kc) {
-                            uint64_t ad, bd;
-                            if (L::SW) {
-                                ad = sdesc(a0 + ((r + ky) * TC_PCOLS + kx) * 128 + kc * 32, 16, 1024, 2);
-                                bd = sdesc(sbase + L::W_OFF + tap * COUT * 128 + kc * 32, 16, 1024, 2);
-                            } else {
-                                constexpr uint32_t PLANE = TC_PROWS * TC_PCOLS * 16;
-                                ad = sdesc(a0 + 2 * kc * PLANE + ((r + ky) * TC_PCOLS + kx) * 16, PLANE, 128, 0);
-                                bd = sdesc(sbase + L::W_OFF + (tap * (CIN / 8) + 2 * kc) * COUT * 16, COUT * 16, 128, 0);
-                            }
-                            const uint32_t acc = (tap | kc) != 0;
-                            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                             d0 + (uint32_t)(r * COUT)),
-                                         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                            const uint32_t aoff = L::SW ? (((r + ky) * TC_PCOLS + kx) * 128 + kc * 32) >> 4
+                                                        : (2 * kc * PLANE + ((r + ky) * TC_PCOLS + kx) * 16) >> 4;
+                            const uint32_t boff = L::SW ? (tap * COUT * 128 + kc * 32) >> 4
+                                                        : ((tap * (CIN / 8) + 2 * kc) * COUT * 16) >> 4;
+                            if ((tap | kc) != 0)
+                                asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n" ::"r"(
+                                                 d0 + (uint32_t)(r * COUT)),
+                                             "l"(adesc + aoff), "l"(bdesc + boff), "r"(IDESC));
+                            else
+                                asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 0;\n" ::"r"(
+                                                 d0 + (uint32_t)(r * COUT)),
+                                             "l"(adesc + aoff), "l"(bdesc + boff), "r"(IDESC));
                         }
                     }
                 // the stage is free and the accumulators are ready once these MMAs complete
@@ -281,8 +299,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
         }
         __syncwarp();
     } else {
-        // ---- epilogue ----
-        const int e = warp - 2, q = warp & 3, r = e >> 2;
+        // ---- epilogue: warp 2 + e reads lane quarter (warp % 4) of output row
+        // (e / 8) and accumulator columns 32 ((e / 4) % 2) + 0..31 ----
+        const int e = warp - 2, q = warp & 3, r = e >> 3, h = (e >> 2) & 1;
+        const bool active = !OUT || h == 0;          // the last layer has 16 columns
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1;
             const uint32_t k = (uint32_t)(i >> 1);
@@ -293,41 +313,40 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
             int b, y0, x0;
             tile_coords(i, b, y0, x0);
             const int y = y0 + r, x = x0 + 32 * q + lane;
-            const uint32_t ta = tmem + (uint32_t)(s * TC_ROWS * COUT + r * COUT) + ((uint32_t)(32 * q) << 16);
+            const uint32_t ta = tmem + (uint32_t)(s * TC_ROWS * COUT + r * COUT + 32 * h) + ((uint32_t)(32 * q) << 16);
             if (OUT) {
-                float v[16];
-                tmem_ld16(ta, v);
-                const size_t pix = ((size_t)b * ny + y) * nx + x;
+                if (active) {
+                    float v[16];
+                    tmem_ld16(ta, v);
+                    const size_t pix = ((size_t)b * ny + y) * nx + x;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) fout[pix * 3 + c] = v[c] + sbias[c];
+                    for (int c = 0; c < 3; ++c) fout[pix * 3 + c] = v[c] + sbias[c];
+                }
             } else {
+                uint32_t v[32];
+                tmem_ld32(ta, v);
+                __align__(16) __nv_bfloat162 hv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float z0 = __uint_as_float(v[2 * j]) + sbias[32 * h + 2 * j];
+                    const float z1 = __uint_as_float(v[2 * j + 1]) + sbias[32 * h + 2 * j + 1];
+                    hv[j] = __floats2bfloat162_rn(silu_act(z0), silu_act(z1));
+                }
                 // this pixel and its periodic images in the padded output
                 const size_t pw = (size_t)(nx + 2), plane = (size_t)(ny + 2) * pw;
                 const int ys[2] = {y + 1, y == 0 ? ny + 1 : (y == ny - 1 ? 0 : -1)};
                 const int xs[2] = {x + 1, x == 0 ? nx + 1 : (x == nx - 1 ? 0 : -1)};
+                const uint4* src = reinterpret_cast<const uint4*>(hv);
 #pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(ta + c0, v);
-                    __align__(16) __nv_bfloat162 hv[8];
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float z0 = v[2 * j] + sbias[c0 + 2 * j], z1 = v[2 * j + 1] + sbias[c0 + 2 * j + 1];
-                        hv[j] = __floats2bfloat162_rn(__fdividef(z0, 1.0f + __expf(-z0)),
-                                                      __fdividef(z1, 1.0f + __expf(-z1)));
-                    }
-                    const uint4 w0 = reinterpret_cast<const uint4*>(hv)[0], w1 = reinterpret_cast<const uint4*>(hv)[1];
+                    for (int c = 0; c < 2; ++c)
+                        if (ys[a] >= 0 && xs[c] >= 0) {
+                            uint4* p = reinterpret_cast<uint4*>(
+                                aout + ((size_t)b * plane + (size_t)ys[a] * pw + xs[c]) * COUT + 32 * h);
 #pragma unroll
-                    for (int a = 0; a < 2; ++a)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c)
-                            if (ys[a] >= 0 && xs[c] >= 0) {
-                                uint4* p = reinterpret_cast<uint4*>(
-                                    aout + ((size_t)b * plane + (size_t)ys[a] * pw + xs[c]) * COUT + c0);
-                                p[0] = w0;
-                                p[1] = w1;
-                            }
-                }
+                            for (int u = 0; u < 4; ++u) p[u] = src[u];
+                        }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();

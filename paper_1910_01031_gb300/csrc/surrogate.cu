@@ -60,13 +60,6 @@ __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uin
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
-__device__ __forceinline__ float dsilu(float z)
-{
-    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
-    return s * (1.0f + z * (1.0f - s));
-}
-
 enum ConvMode : int {
     MODE_HIDDEN = 0,    // z = conv + b: store z and silu(z) (bf16)
     MODE_OUT = 1,       // out = conv + b: store fp32 (first 3 channels)
@@ -147,14 +140,14 @@ conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
                     v1 += bias[co + 1];
                     *reinterpret_cast<__nv_bfloat162*>(zout + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
                     *reinterpret_cast<__nv_bfloat162*>(aout + pix * COUT + co) =
-                        __floats2bfloat162_rn(silu(v0), silu(v1));
+                        __floats2bfloat162_rn(silu_act(v0), silu_act(v1));
                 } else if (MODE == MODE_OUT) {
                     if (co < 3) fout[pix * 3 + co] = v0 + bias[co];
                     if (co + 1 < 3) fout[pix * 3 + co + 1] = v1 + bias[co + 1];
                 } else {
                     const __nv_bfloat162 z = *reinterpret_cast<const __nv_bfloat162*>(zprev + pix * COUT + co);
-                    v0 *= dsilu(__bfloat162float(z.x));
-                    v1 *= dsilu(__bfloat162float(z.y));
+                    v0 *= silu_grad(__bfloat162float(z.x));
+                    v1 *= silu_grad(__bfloat162float(z.y));
                     *reinterpret_cast<__nv_bfloat162*>(aout + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
                 }
             }

@@ -12,6 +12,28 @@
 
 namespace iewpf {
 
+#ifdef __CUDACC__
+// SiLU(z) = z sigmoid(z) with sigmoid(z) = (1 + tanh(z / 2)) / 2 from the
+// hardware tanh approximation: h + h tanh(h), h = z / 2 (one MUFU operation)
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu_act(float z)
+{
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_approx(h), h);
+}
+// d SiLU / dz = s (1 + z (1 - s)), s = sigmoid(z)
+__device__ __forceinline__ float silu_grad(float z)
+{
+    const float s = fmaf(0.5f, tanh_approx(0.5f * z), 0.5f);
+    return s * fmaf(z, 1.0f - s, 1.0f);
+}
+#endif
+
 struct Surrogate {
     int nx = 0, ny = 0, width = 64, depth = 6;
     size_t n_params = 0;
