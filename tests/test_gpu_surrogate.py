@@ -251,3 +251,17 @@ def test_tcgen05_forward_is_bitwise_translation_equivariant():
     a = sur.apply(U)
     b = sur.apply(np.ascontiguousarray(np.roll(U, (2, 128), axis=(2, 3))))
     assert np.array_equal(np.roll(a, (2, 128), axis=(2, 3)), b)
+
+
+def test_tcgen05_many_tiles_per_cta_match_mma_sync():
+    # 8 fields of 256 x 256: 2048 tiles, about 13 consecutive tiles per CTA, so
+    # the ring of input rows wraps several times within a column strip
+    sur, _ = _net(nx=256, ny=256, seed=14)
+    U = _fields(8, 256, 256, 15)
+    out_tc = sur.apply(U)
+    sur.set_path(1)
+    out_mma = sur.apply(U)
+    d_tc = out_tc.astype(np.float64) - U
+    d_mma = out_mma.astype(np.float64) - U
+    assert np.linalg.norm(d_mma) > 0
+    assert _rel(d_tc, d_mma) < 1e-2
