@@ -22,15 +22,31 @@ namespace march {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ float fsqrt(float x) { return x * rsqrtf(x); }
+// single hardware approximations (flush-to-zero: depths and wave speeds are
+// far from the subnormal range)
+__device__ __forceinline__ float frcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float frsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fsqrt(float x) { return x * frsqrt(x); }
 
+// generalized minmod(theta a, (a + b)/2, theta b): the smallest of the three
+// when all are positive, the largest when all are negative, else 0, written
+// as max(min, 0) + min(max, 0) (one of the two terms is always zero)
 __device__ __forceinline__ float gmm(float a, float b, float th)
 {
     const float x = th * a, y = 0.5f * (a + b), z = th * b;   // no contraction here
     const float mn = fminf(x, fminf(y, z));
     const float mx = fmaxf(x, fmaxf(y, z));
-    return mn > 0.0f ? mn : (mx < 0.0f ? mx : 0.0f);
+    return fmaxf(mn, 0.0f) + fminf(mx, 0.0f);
 }
 
 // central-upwind flux, normal momentum qn, tangential qt carried by the mass
