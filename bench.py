@@ -433,7 +433,7 @@ def ctypes_stream(torch_stream):
 def _kernel_sha():
     import hashlib
     h = hashlib.sha1()
-    for f in ("march.cu", "common.cuh"):
+    for f in ("march.cu", "march_dev.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1910_01031_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
