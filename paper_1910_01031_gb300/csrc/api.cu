@@ -581,6 +581,12 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
     G.sgh = (float)(P.g * P.H_eq / P.f);
     G.inv_2dx = (float)(0.5 / P.dx);
     G.inv_2dy = (float)(0.5 / P.dy);
+    G.theta2 = 2.0f * G.theta;
+    G.fdx2 = 2.0f * G.fdx;
+    G.fdy2 = 2.0f * G.fdy;
+    G.inv_4g = 0.5f * G.inv_2g;
+    G.g_half = 0.5f * G.g;
+    G.gH = (float)(P.g * P.H_eq);
     G.ne = P.n_particles;
     G.plane = (long long)P.nx * P.ny;
     ctx->plane = G.plane;

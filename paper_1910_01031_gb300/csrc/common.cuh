@@ -22,6 +22,10 @@ struct Grid {
     float inv_2g;
     float sgh;                 // g H / f (geostrophic balance)
     float inv_2dx, inv_2dy;
+    // exact doublings / halvings of the above for the marching kernel, whose
+    // slopes are carried as twice their value; g/2 and g H for the pressure
+    float theta2, fdx2, fdy2, inv_4g;
+    float g_half, gH;
     int ne;
     long long plane;           // nx * ny
 };

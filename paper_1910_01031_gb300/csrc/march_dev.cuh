@@ -38,12 +38,14 @@ __device__ __forceinline__ float frsqrt(float x)
 }
 __device__ __forceinline__ float fsqrt(float x) { return x * frsqrt(x); }
 
-// generalized minmod(theta a, (a + b)/2, theta b): the smallest of the three
-// when all are positive, the largest when all are negative, else 0, written
-// as max(min, 0) + min(max, 0) (one of the two terms is always zero)
-__device__ __forceinline__ float gmm(float a, float b, float th)
+// twice the generalized minmod(theta a, (a + b)/2, theta b), i.e. the
+// minmod of (2 theta a, a + b, 2 theta b) with th2 = 2 theta: the smallest of
+// the three when all are positive, the largest when all are negative, else 0,
+// written as max(min, 0) + min(max, 0) (one of the two terms is always zero).
+// Every use scales the slope by a power of two, so carrying 2 sigma is exact.
+__device__ __forceinline__ float gmm2(float a, float b, float th2)
 {
-    const float x = th * a, y = 0.5f * (a + b), z = th * b;   // no contraction here
+    const float x = th2 * a, y = a + b, z = th2 * b;   // no contraction here
     const float mn = fminf(x, fminf(y, z));
     const float mx = fmaxf(x, fmaxf(y, z));
     return fmaxf(mn, 0.0f) + fminf(mx, 0.0f);
@@ -63,8 +65,9 @@ __device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, f
     const float inv = frcp(ap - am);
     const float apam = ap * am;
     F0 = fmaf(apam, eR - eL, fmaf(ap, qnL, -(am * qnR))) * inv;
-    const float pL = fmaf(0.5f, eL, G.H) * (G.g * eL);
-    const float pR = fmaf(0.5f, eR, G.H) * (G.g * eR);
+    // p(eta) = g eta (H + eta/2) = eta (g/2 eta + g H)
+    const float pL = eL * fmaf(G.g_half, eL, G.gH);
+    const float pR = eR * fmaf(G.g_half, eR, G.gH);
     const float mL = fmaf(qnL, unL, pL), mR = fmaf(qnR, unR, pR);
     F1 = fmaf(apam, qnR - qnL, fmaf(ap, mL, -(am * mR))) * inv;
     F2 = F0 * ((F0 >= 0.0f) ? qtL * rL : qtR * rR);
@@ -75,7 +78,7 @@ struct Marcher {
     // rolling window: 0 = oldest (row being emitted), 1, 2 = newest
     float e[3][NC], qu[3][NC], qv[3][NC], u[3][NC];
     float dLp[NC];                  // dL on the face between rows 0 and 1
-    float sL[NC], su[NC], sv[NC];   // y-slopes of row 0
+    float sL[NC], su[NC], sv[NC];   // y-slopes of row 0 (twice their value)
     float G0[NC], Gu[NC], Gv[NC];   // y-flux on the face below row 0
 
     __device__ __forceinline__ void zero()
@@ -104,14 +107,14 @@ struct Marcher {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float dLn = fmaf(G.fdy_half, u[1][k] + u[2][k], G.g * (e[2][k] - e[1][k]));
-            const float s1L = gmm(dLp[k], dLn, G.theta);
-            const float s1u = gmm(qu[1][k] - qu[0][k], qu[2][k] - qu[1][k], G.theta);
-            const float s1v = gmm(qv[1][k] - qv[0][k], qv[2][k] - qv[1][k], G.theta);
-            const float eB = fmaf(fmaf(-G.fdy, u[0][k], sL[k]), G.inv_2g, e[0][k]);
-            const float eT = fmaf(fmaf(-G.fdy, u[1][k], s1L), -G.inv_2g, e[1][k]);
+            const float s1L = gmm2(dLp[k], dLn, G.theta2);
+            const float s1u = gmm2(qu[1][k] - qu[0][k], qu[2][k] - qu[1][k], G.theta2);
+            const float s1v = gmm2(qv[1][k] - qv[0][k], qv[2][k] - qv[1][k], G.theta2);
+            const float eB = fmaf(fmaf(-G.fdy2, u[0][k], sL[k]), G.inv_4g, e[0][k]);
+            const float eT = fmaf(fmaf(-G.fdy2, u[1][k], s1L), -G.inv_4g, e[1][k]);
             float g0, gv, gu;
-            flux(eB, fmaf(0.5f, sv[k], qv[0][k]), fmaf(0.5f, su[k], qu[0][k]), eT, fmaf(-0.5f, s1v, qv[1][k]),
-                 fmaf(-0.5f, s1u, qu[1][k]), G, g0, gv, gu);
+            flux(eB, fmaf(0.25f, sv[k], qv[0][k]), fmaf(0.25f, su[k], qu[0][k]), eT, fmaf(-0.25f, s1v, qv[1][k]),
+                 fmaf(-0.25f, s1u, qu[1][k]), G, g0, gv, gu);
             L0[k] = (G0[k] - g0) * G.inv_dy;
             L1[k] = (Gu[k] - gu) * G.inv_dy;
             L2[k] = (Gv[k] - gv) * G.inv_dy;
@@ -140,13 +143,13 @@ struct Marcher {
         float eE[NC], eW[NC], uE[NC], uW[NC], vE[NC], vW[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            const float sK = gmm(dK[k], dK[k + 1], G.theta);
-            const float sU = gmm(QU[k + 1] - QU[k], QU[k + 2] - QU[k + 1], G.theta);
-            const float sV = gmm(QV[k + 1] - QV[k], QV[k + 2] - QV[k + 1], G.theta);
-            const float ex = fmaf(G.fdx, V[k + 1], sK) * G.inv_2g;
+            const float sK = gmm2(dK[k], dK[k + 1], G.theta2);
+            const float sU = gmm2(QU[k + 1] - QU[k], QU[k + 2] - QU[k + 1], G.theta2);
+            const float sV = gmm2(QV[k + 1] - QV[k], QV[k + 2] - QV[k + 1], G.theta2);
+            const float ex = fmaf(G.fdx2, V[k + 1], sK) * G.inv_4g;
             eE[k] = E[k + 1] + ex; eW[k] = E[k + 1] - ex;
-            uE[k] = fmaf(0.5f, sU, QU[k + 1]); uW[k] = fmaf(-0.5f, sU, QU[k + 1]);
-            vE[k] = fmaf(0.5f, sV, QV[k + 1]); vW[k] = fmaf(-0.5f, sV, QV[k + 1]);
+            uE[k] = fmaf(0.25f, sU, QU[k + 1]); uW[k] = fmaf(-0.25f, sU, QU[k + 1]);
+            vE[k] = fmaf(0.25f, sV, QV[k + 1]); vW[k] = fmaf(-0.25f, sV, QV[k + 1]);
         }
         // face f lies on the left of own column f; face NC is the right edge
         float F0[NC + 1], F1[NC + 1], F2[NC + 1];
