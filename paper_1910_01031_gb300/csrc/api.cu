@@ -74,6 +74,8 @@ struct iewpf_ctx {
     double* d_partial = nullptr;
     int dots_blk = 0;
     float* d_r = nullptr;       // posterior coarse field [ne][N_R]
+    float* d_xi = nullptr;      // coarse normals of the model error [ne][N_R]
+    float* d_soar = nullptr;    // Q_SOAR^{1/2} of a coarse field [ne][N_R]
     bool factored = false;      // mooring factor ready
     // pinned staging
     int* h_flag = nullptr;
@@ -413,7 +415,9 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
             A.t = ctx->step;
             A.t_dev = nullptr;
             A.stream = 0u + 16u * (uint32_t)ctx->P.instance_id;
-            KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+            A.xi_buf = ctx->d_xi;
+            A.soar_buf = ctx->d_soar;
+            KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
         }
         ctx->step++;
     }
@@ -528,7 +532,9 @@ int surrogate_steps(iewpf_ctx* ctx)
         A.t = ctx->step + i;
         A.t_dev = nullptr;
         A.stream = 16u * (uint32_t)ctx->P.instance_id;
-        KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+        A.xi_buf = ctx->d_xi;
+        A.soar_buf = ctx->d_soar;
+        KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
     }
     ctx->step += k;
     KL(1, launch_nonfinite(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, ctx->flag, ctx->st));
@@ -650,7 +656,8 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
         (rc = dalloc(ctx, &ctx->d_cstar, ne)) || (rc = dalloc(ctx, &ctx->d_neglogw, ne)) ||
         (rc = dalloc(ctx, &ctx->d_coef, 2 * ne)) || (rc = dalloc(ctx, &ctx->d_scal, 4)) ||
         (rc = dalloc(ctx, &ctx->d_partial, ne * ctx->dots_blk * 3)) ||
-        (rc = dalloc(ctx, &ctx->d_r, ne * (size_t)ctx->NR)))
+        (rc = dalloc(ctx, &ctx->d_r, ne * (size_t)ctx->NR)) || (rc = dalloc(ctx, &ctx->d_xi, ne * (size_t)ctx->NR)) ||
+        (rc = dalloc(ctx, &ctx->d_soar, ne * (size_t)ctx->NR)))
         return bail(rc);
     if (P.n_drifters_max > 0 && (rc = dalloc(ctx, &ctx->d_xy, ne * 2 * (size_t)P.n_drifters_max)))
         return bail(rc);
@@ -674,7 +681,7 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
                     ctx->d_cell, ctx->d_block0, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
                     ctx->d_rowidx, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
                     ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
-                    ctx->d_r};
+                    ctx->d_r, ctx->d_xi, ctx->d_soar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
@@ -796,7 +803,9 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     A.tile_cnt = ctx->d_tile_cnt;
     A.tile_obs = ctx->d_tile_obs;
     A.tile_cap = ctx->tile_cap;
-    KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+    A.xi_buf = ctx->d_xi;
+    A.soar_buf = ctx->d_soar;
+    KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
     // diagnostics
     CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     if (diag) {
@@ -1112,7 +1121,9 @@ int iewpf_add_qhalf(iewpf_ctx_t* ctx, const float* x)
     A.wtab = ctx->d_wtab;
     A.from_philox = 0;
     A.x = ctx->d_r;
-    KL(1, launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+    A.xi_buf = ctx->d_xi;
+    A.soar_buf = ctx->d_soar;
+    KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return IEWPF_OK;
 }

@@ -69,8 +69,15 @@ struct QhalfArgs {
     const int* tile_cnt;      // [ntiles]
     const int* tile_obs;      // [ntiles][tile_cap]
     int tile_cap;
+    // optional scratch [ne][N_R] (both or neither): when given, the coarse
+    // stages run once per coarse point in their own launches (normals, SOAR)
+    // and the fine tiles only interpolate; results are the same bit for bit
+    float* xi_buf;
+    float* soar_buf;
 };
+// kernels it launches: 1 fused, or 2-3 with scratch (normals only from Philox)
 cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cudaStream_t st);
+int qhalf_launches(const QhalfArgs& A);
 
 // ---- analysis.cu ----------------------------------------------------------
 cudaError_t launch_obs_setup(const double* xy, int nobs, const Grid& G, const Coarse& C, double dx, double dy,

@@ -14,14 +14,64 @@ qhalf_kernel(QhalfArgs A, Grid G, Coarse C)
                             A.t_dev ? *A.t_dev : A.t);
 }
 
+// normals of every particle, one Philox block per thread
+__global__ void coarse_normals_kernel(QhalfArgs A, long long NR)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * q >= NR) return;
+    const int p = blockIdx.y;
+    const uint32_t t = A.t_dev ? *A.t_dev : A.t;
+    qhalf::normals_block(seed_key(A.seed), (uint32_t)p, t, A.stream, (uint32_t)q, NR, A.xi_buf + (long long)p * NR);
+}
+
+// Q_SOAR^{1/2} of every coarse point of every particle
+__global__ void coarse_soar_kernel(const float* __restrict__ src, const float* __restrict__ wtab, Grid G, Coarse C,
+                                   float* __restrict__ out)
+{
+    const long long NR = (long long)C.nRx * C.nRy;
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= NR) return;
+    const int p = blockIdx.y;
+    out[(long long)p * NR + m] =
+        qhalf::soar_point(src + (long long)p * NR, wtab, C, G, (int)(m % C.nRx), (int)(m / C.nRx));
+}
+
+template <bool PULL>
+__global__ void __launch_bounds__(NTHREADS)
+qhalf_fine_kernel(QhalfArgs A, Grid G, Coarse C)
+{
+    const long long NR = (long long)C.nRx * C.nRy;
+    qhalf::fine_tile<PULL>(A, G, C, blockIdx.x * TW, blockIdx.y * TH, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x,
+                           A.soar_buf + (long long)blockIdx.z * NR);
+}
+
 }  // namespace
+
+int qhalf_launches(const QhalfArgs& A)
+{
+    if (!A.xi_buf || !A.soar_buf) return 1;
+    return A.from_philox ? 3 : 2;
+}
 
 cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cudaStream_t st)
 {
     if (C.tab > qhalf::TAB_MAX) return cudaErrorInvalidValue;
     dim3 grid((G.nx + TW - 1) / TW, (G.ny + TH - 1) / TH, G.ne);
-    if (A.with_pull) qhalf_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
-    else qhalf_kernel<false><<<grid, NTHREADS, 0, st>>>(A, G, C);
+    if (!A.xi_buf || !A.soar_buf) {
+        if (A.with_pull) qhalf_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
+        else qhalf_kernel<false><<<grid, NTHREADS, 0, st>>>(A, G, C);
+        return cudaGetLastError();
+    }
+    const long long NR = (long long)C.nRx * C.nRy;
+    const float* src = A.x;
+    if (A.from_philox) {
+        const long long nq = (NR + 3) / 4;
+        coarse_normals_kernel<<<dim3((unsigned)((nq + 255) / 256), G.ne), 256, 0, st>>>(A, NR);
+        src = A.xi_buf;
+    }
+    coarse_soar_kernel<<<dim3((unsigned)((NR + 255) / 256), G.ne), 256, 0, st>>>(src, A.wtab, G, C, A.soar_buf);
+    if (A.with_pull) qhalf_fine_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
+    else qhalf_fine_kernel<false><<<grid, NTHREADS, 0, st>>>(A, G, C);
     return cudaGetLastError();
 }
 

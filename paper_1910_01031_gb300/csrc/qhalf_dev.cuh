@@ -138,5 +138,133 @@ __device__ __forceinline__ void qhalf_tile(const QhalfArgs& A, const Grid& G, co
     }
 }
 
+// Coarse stages once per coarse point.  Normals of block q (counter q) of a
+// Philox stream: words (0, 1) and (2, 3) give the Box-Muller pairs of normals
+// 4q, 4q + 1 and 4q + 2, 4q + 3 (the same numbers normal32 returns one by one).
+__device__ __forceinline__ void normals_block(uint2 key, uint32_t p, uint32_t t, uint32_t stream, uint32_t q,
+                                              long long NR, float* __restrict__ out)
+{
+    const uint4 w = philox4x32_10(make_uint4(q, p, t, stream), key);
+    float z[4];
+    box_muller32(w.x, w.y, z[0], z[1]);
+    box_muller32(w.z, w.w, z[2], z[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (4LL * q + j < NR) out[4LL * q + j] = z[j];
+}
+
+// Q_SOAR^{1/2} at coarse point (am, bm) of field src [N_R]: the same 5 x 5 sum,
+// in the same order, as the fused tile
+__device__ __forceinline__ float soar_point(const float* __restrict__ src, const float* __restrict__ wtab,
+                                            const Coarse& C, const Grid& G, int am, int bm)
+{
+    const int x0 = coarse_pos(am, C.nRx, C.c, C.o, G.nx), y0 = coarse_pos(bm, C.nRy, C.c, C.o, G.ny);
+    float acc = 0.0f;
+#pragma unroll
+    for (int db = -2; db <= 2; ++db) {
+        const int dyf = abs(coarse_pos(bm + db, C.nRy, C.c, C.o, G.ny) - y0);
+        const int row = pmod(bm + db, C.nRy) * C.nRx;
+#pragma unroll
+        for (int da = -2; da <= 2; ++da) {
+            const int dxf = abs(coarse_pos(am + da, C.nRx, C.c, C.o, G.nx) - x0);
+            acc = fmaf(wtab[dyf * C.tab + dxf], src[row + pmod(am + da, C.nRx)], acc);
+        }
+    }
+    return acc;
+}
+
+// One fine tile from the SOAR field so_g [N_R] of particle p: bicubic to the
+// tile and its 1-cell ring, geostrophic momentum, optional pull, and the
+// read-modify-write of the state.  The interpolation runs separably (rows
+// first, the same multiply-adds in the same order as qhalf_tile).
+template <bool PULL>
+__device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, const Coarse& C, int x0, int y0, int p,
+                                          int tile, const float* __restrict__ so_g)
+{
+    __shared__ float so[SXH][SXW];
+    __shared__ float rows[SXH][FW];
+    __shared__ float deta[FH][FW];
+    __shared__ int colA[FW], rowB[FH];
+    __shared__ float colW[FW][4], rowW[FH][4];
+
+    const int tid = threadIdx.x;
+    __syncthreads();   // the shared arrays may still be in use by the previous tile
+    float tdum;
+    const int a_lo = coarse_interval(x0 - 1, C.nRx, C.c, C.o, G.nx, tdum);
+    const int a_hi = coarse_interval(x0 + TW, C.nRx, C.c, C.o, G.nx, tdum);
+    const int b_lo = coarse_interval(y0 - 1, C.nRy, C.c, C.o, G.ny, tdum);
+    const int b_hi = coarse_interval(y0 + TH, C.nRy, C.c, C.o, G.ny, tdum);
+    const int nsx = a_hi - a_lo + 4, nsy = b_hi - b_lo + 4;     // SOAR, first at a_lo - 1
+    for (int i = tid; i < FW; i += NTHREADS) {
+        float t;
+        const int a = coarse_interval(x0 - 1 + i, C.nRx, C.c, C.o, G.nx, t);
+        colA[i] = a - a_lo;
+        cubic_weights(t, colW[i]);
+    }
+    for (int i = tid; i < FH; i += NTHREADS) {
+        float t;
+        const int b = coarse_interval(y0 - 1 + i, C.nRy, C.c, C.o, G.ny, t);
+        rowB[i] = b - b_lo;
+        cubic_weights(t, rowW[i]);
+    }
+    for (int i = tid; i < nsx * nsy; i += NTHREADS) {
+        const int sx = i % nsx, sy = i / nsx;
+        so[sy][sx] = so_g[pmod(b_lo - 1 + sy, C.nRy) * C.nRx + pmod(a_lo - 1 + sx, C.nRx)];
+    }
+    __syncthreads();
+    // rows: the x-interpolation of every SOAR row at every fine column
+    for (int i = tid; i < nsy * FW; i += NTHREADS) {
+        const int fx = i % FW, sy = i / FW;
+        const int a = colA[fx];
+        float row = 0.0f;
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) row = fmaf(colW[fx][pp], so[sy][a + pp], row);
+        rows[sy][fx] = row;
+    }
+    __syncthreads();
+    for (int i = tid; i < FW * FH; i += NTHREADS) {
+        const int fx = i % FW, fy = i / FW;
+        const int b = rowB[fy];
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc = fmaf(rowW[fy][q], rows[b + q][fx], acc);
+        deta[fy][fx] = acc;
+    }
+    __syncthreads();
+    float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
+    const int W = 2 * A.R + 1;
+    for (int i = tid; i < TW * TH; i += NTHREADS) {
+        const int tx = i % TW, ty = i / TW;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= G.nx || gy >= G.ny) continue;
+        const int fx = tx + 1, fy = ty + 1;
+        float de = deta[fy][fx];
+        float dhu = -G.sgh * (deta[fy + 1][fx] - deta[fy - 1][fx]) * G.inv_2dy;
+        float dhv = G.sgh * (deta[fy][fx + 1] - deta[fy][fx - 1]) * G.inv_2dx;
+        if (PULL) {
+            const int n = A.tile_cnt[tile];
+            for (int q = 0; q < n; ++q) {
+                const int l = A.tile_obs[tile * A.tile_cap + q];
+                int ox = pmod(gx - A.obs_cell[2 * l], G.nx);
+                int oy = pmod(gy - A.obs_cell[2 * l + 1], G.ny);
+                if (ox > G.nx / 2) ox -= G.nx;
+                if (oy > G.ny / 2) oy -= G.ny;
+                if (ox < -A.R || ox > A.R || oy < -A.R || oy > A.R) continue;
+                const float su = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l];
+                const float sv = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l + 1];
+                const int o = (oy + A.R) * W + (ox + A.R);
+                const int fs = W * W;
+                de = fmaf(sv, A.K[3 * fs + o], fmaf(su, A.K[0 * fs + o], de));
+                dhu = fmaf(sv, A.K[4 * fs + o], fmaf(su, A.K[1 * fs + o], dhu));
+                dhv = fmaf(sv, A.K[5 * fs + o], fmaf(su, A.K[2 * fs + o], dhv));
+            }
+        }
+        const long long g = (long long)gy * G.nx + gx;
+        U[g] += de;
+        U[G.plane + g] += dhu;
+        U[2 * G.plane + g] += dhv;
+    }
+}
+
 }  // namespace qhalf
 }  // namespace iewpf
