@@ -76,6 +76,9 @@ struct iewpf_ctx {
     float* d_r = nullptr;       // posterior coarse field [ne][N_R]
     float* d_xi = nullptr;      // coarse normals of the model error [ne][N_R]
     float* d_soar = nullptr;    // Q_SOAR^{1/2} of a coarse field [ne][N_R]
+    // amax holds the CFL rates of the current state (left there by the last
+    // model-error or analysis update); any other change of the state clears it
+    bool cfl_ready = false;
     bool factored = false;      // mooring factor ready
     // pinned staging
     int* h_flag = nullptr;
@@ -391,8 +394,11 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
     int rc;
     if (!ctx->tuned && (rc = tune_stepper(ctx))) return rc;
     for (int k = 0; k < n_steps; ++k) {
-        KL(fixed > 0 ? 1 : 2, launch_cfl(ctx->buf[0], ctx->buf[1], ctx->par, ctx->amax, ctx->nsub, ctx->dtp, ctx->maxsub, ctx->G,
-                      ctx->P.courant, ctx->P.dt_model, fixed, ctx->st));
+        const bool have = ctx->cfl_ready && fixed <= 0;
+        KL(fixed > 0 || have ? 1 : 2, launch_cfl(ctx->buf[0], ctx->buf[1], ctx->par, ctx->amax, ctx->nsub, ctx->dtp,
+                                                 ctx->maxsub, ctx->G, ctx->P.courant, ctx->P.dt_model, fixed, ctx->st,
+                                                 have));
+        ctx->cfl_ready = false;
         CK(cudaMemcpyAsync(ctx->h_maxsub, ctx->maxsub, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
         const int ms = *ctx->h_maxsub;
@@ -417,7 +423,10 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
             A.stream = 0u + 16u * (uint32_t)ctx->P.instance_id;
             A.xi_buf = ctx->d_xi;
             A.soar_buf = ctx->d_soar;
+            A.amax = ctx->amax;
+            CK(cudaMemsetAsync(ctx->amax, 0, sizeof(float) * ctx->G.ne, ctx->st));
             KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+            ctx->cfl_ready = true;
         }
         ctx->step++;
     }
@@ -695,6 +704,7 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
 static int copy_state(iewpf_ctx_t* ctx, float* host_or_dev, int on_device, void* stream, bool in)
 {
     if (!ctx) return IEWPF_EINVAL;
+    if (in) ctx->cfl_ready = false;
     if (!host_or_dev) return fail(ctx, IEWPF_EINVAL, "null state pointer");
     CK(cudaSetDevice(ctx->dev));
     cudaStream_t user = (cudaStream_t)stream;
@@ -805,7 +815,10 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     A.tile_cap = ctx->tile_cap;
     A.xi_buf = ctx->d_xi;
     A.soar_buf = ctx->d_soar;
+    A.amax = ctx->amax;
+    CK(cudaMemsetAsync(ctx->amax, 0, sizeof(float) * ne, ctx->st));
     KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
+    ctx->cfl_ready = true;
     // diagnostics
     CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     if (diag) {
@@ -964,6 +977,7 @@ int iewpf_save(const iewpf_ctx_t* cctx, const char* path)
 
 int iewpf_load(iewpf_ctx_t* ctx, const char* path)
 {
+    if (ctx) ctx->cfl_ready = false;
     if (!ctx) return IEWPF_EINVAL;
     if (!path) return fail(ctx, IEWPF_EINVAL, "null path");
     FILE* f = std::fopen(path, "rb");
@@ -1110,6 +1124,7 @@ int iewpf_local_block(const iewpf_ctx_t* ctx, double* M)
 
 int iewpf_add_qhalf(iewpf_ctx_t* ctx, const float* x)
 {
+    if (ctx) ctx->cfl_ready = false;
     if (!ctx) return IEWPF_EINVAL;
     if (!x) return fail(ctx, IEWPF_EINVAL, "null pointer");
     CK(cudaSetDevice(ctx->dev));
@@ -1137,6 +1152,7 @@ int iewpf_stream(const iewpf_ctx_t* ctx, void** stream)
 
 int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt)
 {
+    if (ctx) ctx->cfl_ready = false;
     if (!ctx) return IEWPF_EINVAL;
     if (n < 0 || !(dt > 0)) return fail(ctx, IEWPF_EINVAL, "bad substep arguments");
     CK(cudaSetDevice(ctx->dev));
@@ -1389,6 +1405,7 @@ int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* ob
         ctr[2 * i] = b->inst[i]->step;
         ctr[2 * i + 1] = b->inst[i]->cycle;
     }
+    for (int i = 0; i < n; ++i) b->inst[i]->cfl_ready = false;
     BCK(batch_cycle(*b->impl, n_model_steps, b->st, b->st2));
     BCK(cudaStreamSynchronize(b->st));
     const double* dg = batch_diag(*b->impl);

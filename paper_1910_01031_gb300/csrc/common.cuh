@@ -141,12 +141,17 @@ __device__ __forceinline__ void cubic_weights(float t, float w[4])
 }
 
 // max((|u| + c)/dx, (|v| + c)/dy) of one cell, c = sqrt(g h) (eq. swecfl)
+__device__ __forceinline__ float cfl_of(float eta, float hu, float hv, const Grid& G)
+{
+    const float h = G.H + eta;
+    const float c = sqrtf(G.g * h);
+    const float u = hu / h, v = hv / h;
+    return fmaxf((fabsf(u) + c) * G.inv_dx, (fabsf(v) + c) * G.inv_dy);
+}
+
 __device__ __forceinline__ float cfl_cell(const float* __restrict__ U, long long i, const Grid& G)
 {
-    const float h = G.H + U[i];
-    const float c = sqrtf(G.g * h);
-    const float u = U[G.plane + i] / h, v = U[2 * G.plane + i] / h;
-    return fmaxf((fabsf(u) + c) * G.inv_dx, (fabsf(v) + c) * G.inv_dy);
+    return cfl_of(U[i], U[G.plane + i], U[2 * G.plane + i], G);
 }
 
 // scheme steps per model step: n_sub = ceil(dt_model / dt_cfl),

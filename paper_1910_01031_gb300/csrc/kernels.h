@@ -12,9 +12,11 @@ namespace iewpf {
 size_t rk2_smem_bytes();
 cudaError_t launch_rk2(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
                        const Grid& G, cudaStream_t st);
+// have_amax: amax already holds the CFL rates of the current state (left by
+// the model-error or analysis update); only n_sub is derived then
 cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* amax, int* nsub, float* dtp,
                        int* maxsub, const Grid& G, double courant, double dt_model, int fixed,
-                       cudaStream_t st);
+                       cudaStream_t st, bool have_amax = false);
 cudaError_t launch_par_update(int* par, const int* nsub, int ne, unsigned long long* work, cudaStream_t st);
 cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const int* nsub, const float* dtp,
                          double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st);
@@ -74,6 +76,9 @@ struct QhalfArgs {
     // and the fine tiles only interpolate; results are the same bit for bit
     float* xi_buf;
     float* soar_buf;
+    // optional [ne], zeroed by the caller: the split path's fine kernel also
+    // leaves the CFL rate max of the updated state here (as cfl_kernel would)
+    float* amax;
 };
 // kernels it launches: 1 fused, or 2-3 with scratch (normals only from Philox)
 cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cudaStream_t st);

@@ -233,6 +233,7 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     __syncthreads();
     float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
+    float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
     for (int i = tid; i < TW * TH; i += NTHREADS) {
         const int tx = i % TW, ty = i / TW;
         const int gx = x0 + tx, gy = y0 + ty;
@@ -260,9 +261,23 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
             }
         }
         const long long g = (long long)gy * G.nx + gx;
-        U[g] += de;
-        U[G.plane + g] += dhu;
-        U[2 * G.plane + g] += dhv;
+        const float e1 = U[g] + de, u1 = U[G.plane + g] + dhu, v1 = U[2 * G.plane + g] + dhv;
+        U[g] = e1;
+        U[G.plane + g] = u1;
+        U[2 * G.plane + g] = v1;
+        if (A.amax) m = fmaxf(m, cfl_of(e1, u1, v1, G));
+    }
+    if (A.amax) {
+        __shared__ float red[NTHREADS / 32];
+        m = warp_max(m);
+        if ((tid & 31) == 0) red[tid >> 5] = m;
+        __syncthreads();
+        if (tid < 32) {
+            float v = tid < NTHREADS / 32 ? red[tid] : 0.0f;
+            v = warp_max(v);
+            // non-negative floats order like their bit patterns
+            if (tid == 0) atomicMax(reinterpret_cast<int*>(A.amax) + p, __float_as_int(v));
+        }
     }
 }
 

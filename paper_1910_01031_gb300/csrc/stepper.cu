@@ -344,11 +344,11 @@ cudaError_t launch_rk2(float* b0, float* b1, const int* par, const int* nsub, co
 
 cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* amax, int* nsub, float* dtp,
                        int* maxsub, const Grid& G, double courant, double dt_model, int fixed,
-                       cudaStream_t st)
+                       cudaStream_t st, bool have_amax)
 {
-    cudaMemsetAsync(amax, 0, sizeof(float) * G.ne, st);
+    if (!have_amax) cudaMemsetAsync(amax, 0, sizeof(float) * G.ne, st);
     cudaMemsetAsync(maxsub, 0, sizeof(int), st);
-    if (fixed <= 0) {
+    if (fixed <= 0 && !have_amax) {
         const long long blocks = (G.plane + NTHREADS * 8 - 1) / (NTHREADS * 8);
         dim3 grid((unsigned)(blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks)), G.ne);
         cfl_kernel<<<grid, NTHREADS, 0, st>>>(b0, b1, par, amax, G);
