@@ -42,6 +42,23 @@ cholesky_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, int* __
     ana::cholesky_cta(A, n, colptr, rowidx, flag, nzlist);
 }
 
+// the same factorisation on a copy in shared memory (n * n doubles + n ints)
+__global__ void __launch_bounds__(1024)
+cholesky_small_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, int* __restrict__ rowidx,
+                      int* __restrict__ flag)
+{
+    extern __shared__ double sA[];
+    int* work = reinterpret_cast<int*>(sA + (long long)n * n);
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) sA[q] = A[q];
+    __syncthreads();
+    ana::cholesky_factor_cta(sA, n, work, &bad);
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) A[q] = sA[q];
+    ana::csc_cta(sA, n, colptr, rowidx);
+    if (threadIdx.x == 0 && bad) atomicOr(flag, FLAG_NOTPD);
+}
+
 __global__ void solve_kernel(const double* __restrict__ L, const int* __restrict__ colptr,
                              const int* __restrict__ rowidx, int n, const double* __restrict__ d,
                              double* __restrict__ x, double* __restrict__ phi, int ne)
@@ -142,6 +159,15 @@ cudaError_t launch_hqht(const double* K64, int R, const int* obs_cell, int nobs,
 
 cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, cudaStream_t st)
 {
+    // small systems (drifter layouts change every cycle) factor in shared memory
+    const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
+    if (n >= 1 && smem <= 200 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(cholesky_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        cholesky_small_kernel<<<1, 1024, smem, st>>>(M, n, colptr, rowidx, flag);
+        return cudaGetLastError();
+    }
     // rowidx doubles as the per-column work list during the factorisation
     cholesky_kernel<<<1, 1024, 0, st>>>(M, n, colptr, rowidx, flag, rowidx);
     return cudaGetLastError();

@@ -119,21 +119,17 @@ __device__ __forceinline__ void hqht_one(const double* __restrict__ K, int R, co
 
 // Right-looking Cholesky of a dense SPD matrix in place (lower triangle), one
 // CTA; the update of column k touches only rows with a non-zero in it, so
-// block-diagonal and banded matrices cost their fill, not n^3/3.  Then the
-// factor's columns are listed (CSC of the strictly lower part).
-__device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int* __restrict__ colptr,
-                                             int* __restrict__ rowidx, int* __restrict__ flag,
-                                             int* __restrict__ nzlist)
+// block-diagonal and banded matrices cost their fill, not n^3/3.  A may live
+// in global or shared memory; nzlist holds n ints.  The strict upper triangle
+// is zeroed; *bad (shared) is set for a non-positive pivot.
+__device__ __forceinline__ void cholesky_factor_cta(double* __restrict__ A, int n, int* __restrict__ nzlist, int* bad)
 {
     __shared__ int nnz;
     __shared__ double piv;
-    __shared__ int bad;
-    __syncthreads();
-    if (threadIdx.x == 0) bad = 0;
     for (int k = 0; k < n; ++k) {
         if (threadIdx.x == 0) {
             const double dkk = A[(long long)k * n + k];
-            if (!(dkk > 0.0)) bad = 1;
+            if (!(dkk > 0.0)) *bad = 1;
             piv = dkk > 0.0 ? sqrt(dkk) : 1.0;
             A[(long long)k * n + k] = piv;
             nnz = 0;
@@ -160,16 +156,55 @@ __device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int*
         if (j > i) A[q] = 0.0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int pos = 0;
-        for (int k = 0; k < n; ++k) {
-            colptr[k] = pos;
-            for (int i = k + 1; i < n; ++i)
-                if (A[(long long)i * n + k] != 0.0) rowidx[pos++] = i;
+}
+
+// The factor's columns as CSC of the strictly lower part, rows increasing:
+// one warp per column counts (ballots), a prefix sum gives colptr, and the
+// warps write the row lists in order.
+__device__ __forceinline__ void csc_cta(const double* __restrict__ L, int n, int* __restrict__ colptr,
+                                        int* __restrict__ rowidx)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < n; k += nw) {
+        int cnt = 0;
+        for (int i0 = k + 1; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            cnt += __popc(__ballot_sync(0xffffffffu, i < n && L[(long long)i * n + k] != 0.0));
         }
-        colptr[n] = pos;
-        if (bad) atomicOr(flag, FLAG_NOTPD);
+        if (lane == 0) colptr[k + 1] = cnt;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        colptr[0] = 0;
+        for (int k = 0; k < n; ++k) colptr[k + 1] += colptr[k];
+    }
+    __syncthreads();
+    for (int k = warp; k < n; k += nw) {
+        int pos = colptr[k];
+        for (int i0 = k + 1; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool nz = i < n && L[(long long)i * n + k] != 0.0;
+            const unsigned bal = __ballot_sync(0xffffffffu, nz);
+            if (nz) rowidx[pos + __popc(bal & ((1u << lane) - 1u))] = i;
+            pos += __popc(bal);
+        }
+    }
+    __syncthreads();
+}
+
+// Factor in global memory and list the factor's columns; rowidx doubles as
+// the work list during the factorisation.
+__device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int* __restrict__ colptr,
+                                             int* __restrict__ rowidx, int* __restrict__ flag,
+                                             int* __restrict__ nzlist)
+{
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    cholesky_factor_cta(A, n, nzlist, &bad);
+    csc_cta(A, n, colptr, rowidx);
+    if (threadIdx.x == 0 && bad) atomicOr(flag, FLAG_NOTPD);
 }
 
 // warp: S d = (L L^T)^{-1} d for particle w and phi_w = d^T S d
