@@ -36,13 +36,18 @@ __global__ void coarse_soar_kernel(const float* __restrict__ src, const float* _
         qhalf::soar_point(src + (long long)p * NR, wtab, C, G, (int)(m % C.nRx), (int)(m / C.nRx));
 }
 
+// model error on 64 x 32 tiles; the analysis update on the TW x TH tiles of
+// its observation lists
+constexpr int FINE_TX = 64, FINE_TY = 32;
+
 template <bool PULL>
 __global__ void __launch_bounds__(NTHREADS)
 qhalf_fine_kernel(QhalfArgs A, Grid G, Coarse C)
 {
     const long long NR = (long long)C.nRx * C.nRy;
-    qhalf::fine_tile<PULL>(A, G, C, blockIdx.x * TW, blockIdx.y * TH, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x,
-                           A.soar_buf + (long long)blockIdx.z * NR);
+    constexpr int TX = PULL ? TW : FINE_TX, TY = PULL ? TH : FINE_TY;
+    qhalf::fine_tile<PULL, TX, TY>(A, G, C, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z,
+                                   blockIdx.y * gridDim.x + blockIdx.x, A.soar_buf + (long long)blockIdx.z * NR);
 }
 
 }  // namespace
@@ -70,8 +75,12 @@ cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cud
         src = A.xi_buf;
     }
     coarse_soar_kernel<<<dim3((unsigned)((NR + 255) / 256), G.ne), 256, 0, st>>>(src, A.wtab, G, C, A.soar_buf);
-    if (A.with_pull) qhalf_fine_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
-    else qhalf_fine_kernel<false><<<grid, NTHREADS, 0, st>>>(A, G, C);
+    if (A.with_pull) {
+        qhalf_fine_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
+    } else {
+        dim3 g2((G.nx + FINE_TX - 1) / FINE_TX, (G.ny + FINE_TY - 1) / FINE_TY, G.ne);
+        qhalf_fine_kernel<false><<<g2, NTHREADS, 0, st>>>(A, G, C);
+    }
     return cudaGetLastError();
 }
 

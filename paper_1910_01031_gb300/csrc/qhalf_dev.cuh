@@ -173,14 +173,17 @@ __device__ __forceinline__ float soar_point(const float* __restrict__ src, const
     return acc;
 }
 
-// One fine tile from the SOAR field so_g [N_R] of particle p: bicubic to the
-// tile and its 1-cell ring, geostrophic momentum, optional pull, and the
+// One fine tile (TX x TY cells) from the SOAR field so_g [N_R] of particle
+// p: bicubic to the tile and its 1-cell ring, geostrophic momentum, optional
+// pull (tiles of TW x TH, which the observation lists index), and the
 // read-modify-write of the state.  The interpolation runs separably (rows
 // first, the same multiply-adds in the same order as qhalf_tile).
-template <bool PULL>
+template <bool PULL, int TX, int TY>
 __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, const Coarse& C, int x0, int y0, int p,
                                           int tile, const float* __restrict__ so_g)
 {
+    constexpr int FW = TX + 2, FH = TY + 2, SXW = FW + 3, SXH = FH + 3;
+    static_assert(!PULL || (TX == TW && TY == TH), "pull tiles follow the observation lists");
     __shared__ float so[SXH][SXW];
     __shared__ float rows[SXH][FW];
     __shared__ float deta[FH][FW];
@@ -191,9 +194,9 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     __syncthreads();   // the shared arrays may still be in use by the previous tile
     float tdum;
     const int a_lo = coarse_interval(x0 - 1, C.nRx, C.c, C.o, G.nx, tdum);
-    const int a_hi = coarse_interval(x0 + TW, C.nRx, C.c, C.o, G.nx, tdum);
+    const int a_hi = coarse_interval(x0 + TX, C.nRx, C.c, C.o, G.nx, tdum);
     const int b_lo = coarse_interval(y0 - 1, C.nRy, C.c, C.o, G.ny, tdum);
-    const int b_hi = coarse_interval(y0 + TH, C.nRy, C.c, C.o, G.ny, tdum);
+    const int b_hi = coarse_interval(y0 + TY, C.nRy, C.c, C.o, G.ny, tdum);
     const int nsx = a_hi - a_lo + 4, nsy = b_hi - b_lo + 4;     // SOAR, first at a_lo - 1
     for (int i = tid; i < FW; i += NTHREADS) {
         float t;
@@ -234,8 +237,8 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
     float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
-    for (int i = tid; i < TW * TH; i += NTHREADS) {
-        const int tx = i % TW, ty = i / TW;
+    for (int i = tid; i < TX * TY; i += NTHREADS) {
+        const int tx = i % TX, ty = i / TX;
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= G.nx || gy >= G.ny) continue;
         const int fx = tx + 1, fy = ty + 1;
