@@ -1344,6 +1344,8 @@ int iewpf_batch_create(const iewpf_params_t* params, const double* const* moorin
         I.coef = ctx->d_coef;
         I.scal = ctx->d_scal;
         I.r = ctx->d_r;
+        I.xi = ctx->d_xi;
+        I.soar = ctx->d_soar;
         I.NR = ctx->NR;
         I.N_psi = 3.0 * ctx->plane;
         I.logNe = std::log((double)ctx->G.ne);

@@ -37,6 +37,8 @@ enum Space : int {
     SP_HQ,         // entries of HQH^T
     SP_DOT,        // dot-product slices: particle x slice
     SP_FR,         // particle x coarse point
+    SP_NRM,        // particle x Philox block of the coarse normals
+    SP_FTILE,      // model-error fine tiles (FINE_TX x FINE_TY): particle x tile
     SP_COUNT
 };
 
@@ -154,16 +156,47 @@ __global__ void b_par(BatchDev B)
     }
 }
 
-// model error (PULL = false, coarse field from Philox) or analysis update
-// (PULL = true, posterior coarse field plus the pull)
-template <bool PULL>
-__global__ void __launch_bounds__(NTHREADS) b_qhalf(BatchDev B)
+// model error (coarse field from Philox) and analysis update (posterior coarse
+// field plus the pull), staged:
+// coarse normals per Philox block, SOAR per coarse point, fine tiles
+__global__ void b_normals(BatchDev B)
 {
-    const long long* pre = space(B, SP_TILE);
+    const long long* pre = space(B, SP_NRM);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pre[B.n]; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const long long nq = (I.NR + 3) / 4, r = q - pre[i];
+        const int p = (int)(r / nq);
+        qhalf::normals_block(seed_key(I.seed), (uint32_t)p, *I.step_ctr, I.stream_base, (uint32_t)(r % nq), I.NR,
+                             I.xi + (long long)p * I.NR);
+    }
+}
+
+template <bool POSTERIOR>
+__global__ void b_soar(BatchDev B)
+{
+    const long long* pre = space(B, SP_FR);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pre[B.n]; q += (long long)gridDim.x * blockDim.x) {
+        const int i = find_inst(pre, B.n, q);
+        const BInst& I = B.inst[i];
+        const long long r = q - pre[i];
+        const long long p = r / I.NR, m = r % I.NR;
+        const Grid G = I.G;
+        const Coarse C = I.C;
+        I.soar[p * I.NR + m] = qhalf::soar_point((POSTERIOR ? I.r : I.xi) + p * I.NR, I.wtab, C, G,
+                                                 (int)(m % C.nRx), (int)(m / C.nRx));
+    }
+}
+
+template <bool PULL>
+__global__ void __launch_bounds__(NTHREADS) b_fine(BatchDev B)
+{
+    constexpr int TX = PULL ? TW : qhalf::FINE_TX, TY = PULL ? TH : qhalf::FINE_TY;
+    const long long* pre = space(B, PULL ? SP_TILE : SP_FTILE);
     for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
         const int i = find_inst(pre, B.n, q);
         const BInst& I = B.inst[i];
-        const int ntx = (I.G.nx + TW - 1) / TW, nty = (I.G.ny + TH - 1) / TH;
+        const int ntx = (I.G.nx + TX - 1) / TX, nty = (I.G.ny + TY - 1) / TY;
         const long long r = q - pre[i];
         const int p = (int)(r / (ntx * nty));
         const int tile = (int)(r % (ntx * nty));
@@ -171,13 +204,7 @@ __global__ void __launch_bounds__(NTHREADS) b_qhalf(BatchDev B)
         A.b0 = I.step.buf0;
         A.b1 = I.step.buf1;
         A.par = I.step.par;
-        A.wtab = I.wtab;
-        A.seed = I.seed;
-        A.stream = I.stream_base;
-        uint32_t t;
         if (PULL) {
-            A.from_philox = 0;
-            A.x = I.r;
             A.with_pull = 1;
             A.K = I.K32;
             A.R = I.R;
@@ -187,14 +214,11 @@ __global__ void __launch_bounds__(NTHREADS) b_qhalf(BatchDev B)
             A.tile_cnt = I.tile_cnt;
             A.tile_obs = I.tile_obs;
             A.tile_cap = I.tile_cap;
-            t = *I.cycle;
-        } else {
-            A.from_philox = 1;
-            t = *I.step_ctr;
         }
         const Grid G = I.G;
         const Coarse C = I.C;
-        qhalf::qhalf_tile<PULL>(A, G, C, (tile % ntx) * TW, (tile / ntx) * TH, p, tile, t);
+        qhalf::fine_tile<PULL, TX, TY>(A, G, C, (tile % ntx) * TX, (tile / ntx) * TY, p, tile,
+                                       I.soar + (long long)p * I.NR);
     }
 }
 
@@ -461,8 +485,11 @@ cudaError_t batch_init(BatchImpl& b, const std::vector<BInst>& insts)
         const long long ne = I.G.ne;
         const long long slices = (I.G.plane + kCflSlice - 1) / kCflSlice;
         const long long tiles = (long long)((I.G.nx + TW - 1) / TW) * ((I.G.ny + TH - 1) / TH);
+        const long long ftiles = (long long)((I.G.nx + qhalf::FINE_TX - 1) / qhalf::FINE_TX) *
+                                 ((I.G.ny + qhalf::FINE_TY - 1) / qhalf::FINE_TY);
         const long long cnt[SP_COUNT] = {ne, ne * slices, 0, ne * tiles, I.nobs, tiles, ne * I.nobs,
-                                         4LL * I.nobs * I.nobs, ne * I.nblk, ne * I.NR};
+                                         4LL * I.nobs * I.nobs, ne * I.nblk, ne * I.NR, ne * ((I.NR + 3) / 4),
+                                         ne * ftiles};
         for (int sp = 0; sp < SP_COUNT; ++sp) {
             b.pre[(size_t)sp * (b.n + 1) + i] = acc[sp];
             acc[sp] += cnt[sp];
@@ -559,8 +586,10 @@ static cudaError_t capture_model_step(BatchImpl& b, cudaStream_t st, cudaStream_
     b_par<<<grid_for(b_par, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
     b.launches += 1;
     if (err) {
-        b_qhalf<false><<<grid_for(b_qhalf<false>, NTHREADS, items(b, SP_TILE)), NTHREADS, 0, st>>>(B);
-        b.launches += 1;
+        b_normals<<<grid_for(b_normals, 256, (items(b, SP_NRM) + 255) / 256), 256, 0, st>>>(B);
+        b_soar<false><<<grid_for(b_soar<false>, 256, (items(b, SP_FR) + 255) / 256), 256, 0, st>>>(B);
+        b_fine<false><<<grid_for(b_fine<false>, NTHREADS, items(b, SP_FTILE)), NTHREADS, 0, st>>>(B);
+        b.launches += 3;
     }
     b_count<<<(b.n + 127) / 128, 128, 0, st>>>(B, 0);
     b.launches += 1;
@@ -584,11 +613,12 @@ static cudaError_t capture_analysis(BatchImpl& b, cudaStream_t st)
     b_sync<<<b.n, 1024, 0, st>>>(B);
     b_form_r<<<grid_for(b_form_r, 256, (items(b, SP_FR) + 255) / 256), 256, 0, st>>>(B);
     b_block_seq<<<grid_for(b_block_seq, 64, items(b, SP_PART)), 64, 0, st>>>(B);
-    b_qhalf<true><<<grid_for(b_qhalf<true>, NTHREADS, items(b, SP_TILE)), NTHREADS, 0, st>>>(B);
+    b_soar<true><<<grid_for(b_soar<true>, 256, (items(b, SP_FR) + 255) / 256), 256, 0, st>>>(B);
+    b_fine<true><<<grid_for(b_fine<true>, NTHREADS, items(b, SP_TILE)), NTHREADS, 0, st>>>(B);
     b_count<<<(b.n + 127) / 128, 128, 0, st>>>(B, 1);
     b_nonfinite<<<grid_for(b_nonfinite, NTHREADS, items(b, SP_CFL)), NTHREADS, 0, st>>>(B);
     b_pack_diag<<<(b.n + 127) / 128, 128, 0, st>>>(B, b.d_diag);
-    b.launches += 14;
+    b.launches += 15;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaMemcpyAsync(b.h_diag, b.d_diag, sizeof(double) * 3 * b.n, cudaMemcpyDeviceToHost, st);
 }

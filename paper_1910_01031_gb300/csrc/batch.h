@@ -59,6 +59,8 @@ struct BInst {
     double* coef;
     double* scal;
     float* r;
+    float* xi;               // coarse normals [ne][N_R] (model error)
+    float* soar;             // SOAR coarse field [ne][N_R]
     long long NR;
     double N_psi, logNe;
 };

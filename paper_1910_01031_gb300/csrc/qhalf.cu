@@ -36,9 +36,10 @@ __global__ void coarse_soar_kernel(const float* __restrict__ src, const float* _
         qhalf::soar_point(src + (long long)p * NR, wtab, C, G, (int)(m % C.nRx), (int)(m / C.nRx));
 }
 
-// model error on 64 x 32 tiles; the analysis update on the TW x TH tiles of
-// its observation lists
-constexpr int FINE_TX = 64, FINE_TY = 32;
+// model error on FINE_TX x FINE_TY tiles; the analysis update on the TW x TH
+// tiles of its observation lists
+using qhalf::FINE_TX;
+using qhalf::FINE_TY;
 
 template <bool PULL>
 __global__ void __launch_bounds__(NTHREADS)

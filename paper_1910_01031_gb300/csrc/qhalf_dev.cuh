@@ -19,6 +19,7 @@ constexpr int FW = TW + 2, FH = TH + 2;       // fine eta with a 1-cell ring
 constexpr int XIW = FW + 7, XIH = FH + 7;     // normals (SOAR input)
 constexpr int SXW = FW + 3, SXH = FH + 3;     // SOAR output (bicubic taps)
 constexpr int TAB_MAX = 45;                   // 3 c for c <= 15
+constexpr int FINE_TX = 64, FINE_TY = 32;     // model-error tiles of the staged form
 
 // One fine tile (x0, y0) of particle p; `tile` indexes the per-tile
 // observation lists.  Called by whole CTAs of NTHREADS threads; a CTA may
