@@ -69,9 +69,10 @@ struct BatchDev {
 __device__ __forceinline__ const long long* space(const BatchDev& B, int sp) { return B.pre + (long long)sp * (B.n + 1); }
 
 // ---- forecast -------------------------------------------------------------
-__global__ void b_zero(BatchDev B)
+// the step counters; with `amax` also the CFL rates (before they are recomputed)
+__global__ void b_zero(BatchDev B, int amax)
 {
-    const long long np = space(B, SP_PART)[B.n];
+    const long long np = amax ? space(B, SP_PART)[B.n] : 0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np; q += (long long)gridDim.x * blockDim.x) {
         const int i = find_inst(space(B, SP_PART), B.n, q);
         B.inst[i].amax[q - space(B, SP_PART)[i]] = 0.0f;
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(NTHREADS) b_fine(BatchDev B)
         A.b0 = I.step.buf0;
         A.b1 = I.step.buf1;
         A.par = I.step.par;
+        if (!PULL) A.amax = I.amax;   // the CFL rates of the next model step
         if (PULL) {
             A.with_pull = 1;
             A.K = I.K32;
@@ -549,16 +551,21 @@ cudaError_t batch_work(BatchImpl& b, unsigned long long* out)
 }
 
 // One model step into the stream being captured: CFL, the WHILE loop of
-// scheme steps, the parity flip and (optionally) the model error.
-static cudaError_t capture_model_step(BatchImpl& b, cudaStream_t st, cudaStream_t st2, bool err)
+// scheme steps, the parity flip and (optionally) the model error, whose fine
+// kernel leaves the CFL rates of the next step (have_amax).
+static cudaError_t capture_model_step(BatchImpl& b, cudaStream_t st, cudaStream_t st2, bool err, bool have_amax)
 {
     const BatchDev B = dev_view(b);
     cudaError_t e;
-    b_zero<<<grid_for(b_zero, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
-    b_cfl<<<grid_for(b_cfl, NTHREADS, items(b, SP_CFL)), NTHREADS, 0, st>>>(B);
+    b_zero<<<grid_for(b_zero, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B, have_amax ? 0 : 1);
+    b.launches += 1;
+    if (!have_amax) {
+        b_cfl<<<grid_for(b_cfl, NTHREADS, items(b, SP_CFL)), NTHREADS, 0, st>>>(B);
+        b.launches += 1;
+    }
     b_nsub<<<grid_for(b_nsub, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    b.launches += 3;
+    b.launches += 1;
     // WHILE node: body = one scheme step of every problem + counter update
     cudaStreamCaptureStatus status;
     cudaGraph_t g = nullptr;
@@ -586,6 +593,8 @@ static cudaError_t capture_model_step(BatchImpl& b, cudaStream_t st, cudaStream_
     b_par<<<grid_for(b_par, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
     b.launches += 1;
     if (err) {
+        b_zero<<<grid_for(b_zero, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B, 1);
+        b.launches += 1;
         b_normals<<<grid_for(b_normals, 256, (items(b, SP_NRM) + 255) / 256), 256, 0, st>>>(B);
         b_soar<false><<<grid_for(b_soar<false>, 256, (items(b, SP_FR) + 255) / 256), 256, 0, st>>>(B);
         b_fine<false><<<grid_for(b_fine<false>, NTHREADS, items(b, SP_FTILE)), NTHREADS, 0, st>>>(B);
@@ -645,7 +654,7 @@ cudaError_t batch_cycle(BatchImpl& b, int n_steps, cudaStream_t st, cudaStream_t
             return e;
         }
         for (int k = 0; k < n_steps; ++k) {
-            if ((e = capture_model_step(b, st, st2, k + 1 < n_steps)) != cudaSuccess) {
+            if ((e = capture_model_step(b, st, st2, k + 1 < n_steps, k > 0)) != cudaSuccess) {
                 cudaGraph_t junk;
                 cudaStreamEndCapture(st, &junk);
                 if (junk) cudaGraphDestroy(junk);
@@ -678,7 +687,7 @@ cudaError_t batch_tune(BatchImpl& b, cudaStream_t st)
     b.fixed = 16;
     {
         const BatchDev B = dev_view(b);
-        b_zero<<<1, 1, 0, st>>>(B);
+        b_zero<<<1, 1, 0, st>>>(B, 1);
         b_nsub<<<grid_for(b_nsub, 256, (items(b, SP_PART) + 255) / 256), 256, 0, st>>>(B);
     }
     b.fixed = 0;
