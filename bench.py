@@ -9,9 +9,11 @@ error after the first 4) followed by one two-stage IEWPF analysis against
 is ms_per_step.  The state (2 x 315 MB) exceeds the 129 MB L2, so no flush
 is needed between timed steps.
 
-The line also carries two further workloads, each with its own numbers:
+The line also carries three further workloads, each with its own numbers:
 "batched" (32 independent problems of 128^2-1024^2 cells advanced together
-as one CUDA graph per cycle) and "surrogate" (a 12 h drift forecast of 1000
+as one CUDA graph per cycle), "moorings" (1024^2 cells, 1000 particles, 1521
+moored buoys: context creation with the dense FP64 factorisation, and the
+cycle time) and "surrogate" (a 12 h drift forecast of 1000
 particles x 64 drifters on 256^2 cells with the plain stepper and with the
 learned surrogate, their times and the distance between the two forecasts).
 
@@ -227,6 +229,10 @@ def run_ours(args, rank, world, local):
     except Exception as e:  # reported, the main number stands without it
         batched = {"error": str(e)}
     try:
+        moorings = run_moorings(rank)
+    except Exception as e:  # reported, the main number stands without it
+        moorings = {"error": str(e)}
+    try:
         surrogate = run_surrogate(rank, epochs=8)
     except Exception as e:  # reported, the main number stands without it
         surrogate = {"error": str(e)}
@@ -250,6 +256,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "batched": batched,
+        "moorings": moorings,
         "surrogate": surrogate,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -314,6 +321,56 @@ def run_batched(rank):
            "state_gb": round(sum(c.n_particles * c.nx * c.ny * 24 for c in cfgs) / 1e9, 1)}
     out["kernel_nodes_captured"] = int(l1)
     batch.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_moorings(rank, cycles=2):
+    """The moored-buoy workload: 1024 x 1024 cells, 1000 particles, 1521
+    equidistant moorings observing (u, v).  Times the context creation (pull
+    stencil, dense 3042 x 3042 HQH^T + R and its FP64 Cholesky on the GPU,
+    the 49 x 49 block root) and IEWPF cycles (5 model steps, model error on 4,
+    one analysis against the moorings) with CUDA events.  The particles start
+    from one synthetic state (they diverge through the model error)."""
+    import torch
+    from paper_1910_01031_gb300 import iewpf, synth
+    cfg = synth.config4(seed=0x1910_01031 + 13 * rank)
+    cells = synth.mooring_cells(cfg)
+    xy = synth.cell_positions(cfg, cells)
+    P = iewpf.params_from_config(cfg)
+    P.instance_id = rank
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens = iewpf.Ensemble(P, mooring_xy=xy)
+    create_s = time.perf_counter() - t0
+    x = torch.from_numpy(synth.initial_particle(cfg, 0, seed=41 + rank, dtype=np.float32)).cuda()
+    ens.set_state(x.unsqueeze(0).expand(cfg.n_particles, -1, -1, -1).contiguous())
+    del x
+    truth = synth.initial_particle(cfg, 1, seed=43 + rank)
+    stream = torch.cuda.ExternalStream(ens.stream())
+
+    def cycle(k):
+        ens.forecast(cfg.obs_every_steps - 1, True)
+        ens.forecast(1, False)
+        y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), k))
+        return ens.assimilate(None, y, diag=False)
+
+    cycle(0)
+    torch.cuda.synchronize()
+    w0 = ens.work()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(1, cycles + 1):
+        cycle(k)
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    work = ens.work() - w0
+    out = {"workload": "iewpf_1024x1024_ne1000_1521moorings (dense 3042 x 3042 HQH^T + R)",
+           "create_s": round(create_s, 3), "cycles_timed": cycles, "cycle_ms": round(secs / cycles * 1e3, 2),
+           "value": round(work * cfg.nx * cfg.ny / secs, 1), "unit": UNIT,
+           "state_gb": round(2 * cfg.n_particles * cfg.nx * cfg.ny * 12 / 1e9, 1)}
+    ens.close()
     torch.cuda.empty_cache()
     return out
 
