@@ -60,15 +60,15 @@ __device__ __forceinline__ uint2 seed_key(uint64_t seed)
 }
 
 // Box-Muller in double: u = (k + 1/2) 2^-32, r = sqrt(-2 ln u_a),
-// theta = 2 pi u_b; (r cos theta, r sin theta).
+// theta = 2 pi u_b; (r cos theta, r sin theta), the angle taken as pi (2 u_b)
+// (2 u_b is exact, so no rounding of 2 pi u_b enters).
 __device__ __forceinline__ void box_muller64(uint32_t a, uint32_t b, double& z0, double& z1)
 {
     const double ua = ((double)a + 0.5) * 0x1p-32;
-    const double ub = ((double)b + 0.5) * 0x1p-32;
+    const double ub2 = ((double)b + 0.5) * 0x1p-31;   // 2 u_b
     const double r = sqrt(-2.0 * log(ua));
-    const double th = 6.283185307179586 * ub;
     double s, c;
-    sincos(th, &s, &c);
+    sincospi(ub2, &s, &c);
     z0 = r * c;
     z1 = r * s;
 }

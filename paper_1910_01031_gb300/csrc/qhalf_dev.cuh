@@ -160,16 +160,19 @@ __device__ __forceinline__ float soar_point(const float* __restrict__ src, const
                                             const Coarse& C, const Grid& G, int am, int bm)
 {
     const int x0 = coarse_pos(am, C.nRx, C.c, C.o, G.nx), y0 = coarse_pos(bm, C.nRy, C.c, C.o, G.ny);
+    int dxf[5], col[5];
+#pragma unroll
+    for (int da = -2; da <= 2; ++da) {
+        dxf[da + 2] = abs(coarse_pos(am + da, C.nRx, C.c, C.o, G.nx) - x0);
+        col[da + 2] = pmod(am + da, C.nRx);
+    }
     float acc = 0.0f;
 #pragma unroll
     for (int db = -2; db <= 2; ++db) {
         const int dyf = abs(coarse_pos(bm + db, C.nRy, C.c, C.o, G.ny) - y0);
         const int row = pmod(bm + db, C.nRy) * C.nRx;
 #pragma unroll
-        for (int da = -2; da <= 2; ++da) {
-            const int dxf = abs(coarse_pos(am + da, C.nRx, C.c, C.o, G.nx) - x0);
-            acc = fmaf(wtab[dyf * C.tab + dxf], src[row + pmod(am + da, C.nRx)], acc);
-        }
+        for (int da = -2; da <= 2; ++da) acc = fmaf(wtab[dyf * C.tab + dxf[da + 2]], src[row + col[da + 2]], acc);
     }
     return acc;
 }
