@@ -143,3 +143,28 @@ def test_assimilate_rejects_bad_observations():
     ens = ensemble(cfg)
     with pytest.raises(iewpf.IewpfError):
         ens.assimilate(np.zeros((2, 2)), np.zeros((2, 2)))     # more than n_obs_max
+
+
+def test_cfl_rates_left_by_the_updates_match_a_fresh_pass():
+    """The model-error and analysis updates leave the CFL rates of the state
+    they wrote; a context that recomputes them from a copy of the same state
+    must step identically."""
+    cfg = synth.config1(n_particles=4, n_obs=2)
+    U32, _ = start_state(cfg, 4)
+    xy = synth.drifter_positions(cfg, 2)
+    a, b = ensemble(cfg), ensemble(cfg)
+    for e in (a, b):
+        e.set_state(U32)
+        e.forecast(2, True)
+    truth = synth.initial_particle(cfg, 9, seed=5)
+    cells = np.stack([np.floor(xy[:, 0] / cfg.dx) % cfg.nx, np.floor(xy[:, 1] / cfg.dy) % cfg.ny], 1).astype(int)
+    y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, 2, 0))
+    a.assimilate(xy, y)
+    b.assimilate(xy, y)
+    # b forgets its rates: a copy of its own state goes back in
+    b.set_state(b.get_state())
+    b.set_counters(*a.counters())
+    a.forecast(3, True)
+    b.forecast(3, True)
+    assert np.array_equal(a.last_nsub(), b.last_nsub())
+    assert np.array_equal(a.get_state(), b.get_state())
