@@ -125,6 +125,27 @@ def make_observations(cfg, n_cycles, rank):
     return obs
 
 
+def replica(rank):
+    """Workload of one rank: an independent replica of the 512 x 512,
+    100-particle problem with its own seed and Philox instance id."""
+    from paper_1910_01031_gb300 import synth
+    cfg = synth.config2(seed=0x1910_01031 + 104729 * rank)
+    return cfg, rank
+
+
+def combine_ranks(dev_s, host_s, work, world, device="cuda"):
+    """Job totals over the ranks: the slowest rank's device and host times,
+    the sum of the work.  Collective only for world > 1."""
+    import torch
+    t = torch.tensor([dev_s, host_s, float(work)], dtype=torch.float64, device=device)
+    if world > 1:
+        tw = t.clone()
+        torch.distributed.all_reduce(t[:2], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tw[2:], op=torch.distributed.ReduceOp.SUM)
+        t[2] = tw[2]
+    return float(t[0]), float(t[1]), float(t[2])
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1910_01031_gb300 import build, iewpf, synth
@@ -134,10 +155,10 @@ def run_ours(args, rank, world, local):
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    cfg = synth.config2(seed=0x1910_01031 + 104729 * rank)
+    cfg, instance = replica(rank)
     ne, N = cfg.n_particles, cfg.nx * cfg.ny
     P = iewpf.params_from_config(cfg)
-    P.instance_id = rank
+    P.instance_id = instance
     ens = iewpf.Ensemble(P)
     ens.set_state(synth.initial_state(cfg, ne, seed=7 + rank).astype(np.float32))
     obs = make_observations(cfg, args.warmup + args.steps, rank)
@@ -179,13 +200,7 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     clk = clocks.stop()
     # slowest rank sets the job time
-    t = torch.tensor([dev_s, host_s, float(work)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tw = t.clone()
-        torch.distributed.all_reduce(t[:2], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tw[2:], op=torch.distributed.ReduceOp.SUM)
-        t[2] = tw[2]
-    dev_s, host_s, work_all = float(t[0]), float(t[1]), float(t[2])
+    dev_s, host_s, work_all = combine_ranks(dev_s, host_s, work, world)
     value = work_all * N / dev_s
     e2e_value = work_all * N / host_s
     # the dominant kernel: bare scheme steps, CUDA events on the context stream
