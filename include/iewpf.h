@@ -49,6 +49,14 @@ extern "C" {
 #define IEWPF_OBS_DRIFTER 0
 #define IEWPF_OBS_MOORING 1
 
+/* Analysis schemes (App. A).  Two-stage: w_target = mean c_i, common beta,
+ * nu perpendicular to xi (eqs. betaTwoStage, cistarTwoStage,
+ * updateEquationTwoStageAgain).  One-stage: the original IEWPF,
+ * w_target = max c_i and no nu (eqs. iewpf_targetWeight, iewpfCStar,
+ * iewpfUpdateAgain). */
+#define IEWPF_TWO_STAGE 0
+#define IEWPF_ONE_STAGE 1
+
 /* Problem description (Secs. 3.1-3.3 and 5 of the paper).
  * Grid: periodic nx x ny cells of dx x dy metres (eq. cell_center).
  * Physics: gravity g, Coriolis parameter f, constant equilibrium depth H_eq
@@ -64,7 +72,8 @@ extern "C" {
  * the couplings between nearby observations in HQH^T (dense (HQH^T+R),
  * Cholesky in FP64); 0 keeps only each observation's 2x2 block as the paper
  * does (Sec. 4.2).  n_drifters_max: drifters each particle may carry in a
- * forecast (0 for none). */
+ * forecast (0 for none).  scheme: IEWPF_TWO_STAGE (0, the paper's method of
+ * choice) or IEWPF_ONE_STAGE (App. A); other values give IEWPF_EINVAL. */
 typedef struct {
     int nx, ny;
     double dx, dy;
@@ -82,6 +91,7 @@ typedef struct {
     int dense_S;
     int instance_id;
     int n_drifters_max;
+    int scheme;
 } iewpf_params_t;
 
 /* One observation time (Sec. 3.3).  xy: [n_obs][2] observed positions;
@@ -97,14 +107,15 @@ typedef struct {
 /* Per-cycle diagnostics of iewpf_assimilate (App. A).  Each array has
  * N_e entries and may be NULL. */
 typedef struct {
-    double c_bar;        /* w_target = mean c_i                              */
-    double beta;         /* eq. betaTwoStage                                 */
+    double c_bar;        /* mean c_i (two-stage: also w_target)              */
+    double beta;         /* eq. betaTwoStage; 0 for the one-stage scheme     */
     double* phi;         /* eq. iewpfPhi                                     */
     double* c;           /* eq. iewpf_ci, -log w^{n-1} = log N_e             */
     double* gamma;       /* eq. scalingGammaZeta                             */
     double* zeta;        /* eq. scalingGammaZeta                             */
     double* alpha;       /* eq. iewpfAlphaSol                                */
-    double* neglogw;     /* final -log w_i, equal to c_bar for every i       */
+    double* neglogw;     /* final -log w_i, equal to w_target for every i    */
+    double w_target;     /* mean c_i (two-stage) or max c_i (one-stage)      */
 } iewpf_diag_t;
 
 typedef struct iewpf_ctx iewpf_ctx_t;
@@ -221,6 +232,15 @@ IEWPF_API int iewpf_weights(int ne, double N_psi, const double* c, const double*
                   const double* zeta, double* out2, double* alpha, double* cstar,
                   double* neglogw);
 
+/* The ensemble-wide step of the one-stage IEWPF on the GPU (App. A, eqs.
+ * iewpf_targetWeight, iewpfCStar, iewpfAlphaSol): from host arrays c and
+ * gamma ([ne]) and N_psi, returns w_target = max c_i and 0 (no beta) in
+ * out2[2] and alpha, c* = w_target - c_i and -log w in host arrays of ne
+ * (neglogw may be NULL).
+ * Errors: EINVAL, EDOMAIN, ENONFINITE, ENOMEM, ECUDA. */
+IEWPF_API int iewpf_weights_one_stage(int ne, double N_psi, const double* c, const double* gamma,
+                                      double* out2, double* alpha, double* cstar, double* neglogw);
+
 /* Largest ensemble iewpf_weights_noalloc accepts. */
 #define IEWPF_WEIGHTS_NOALLOC_MAX_NE 4096
 
@@ -324,7 +344,8 @@ IEWPF_API int iewpf_batch_tune(iewpf_batch_t* b, int* shape);
 /* One cycle of every problem: n_model_steps model steps (model error after
  * all but the last, Sec. 4.1) and one IEWPF analysis against obs[i]
  * (obs[i].n_obs must equal problem i's n_obs_max).  diag (may be NULL)
- * receives [n][3] = (c_bar, beta, error flags) per problem.  Returns the
+ * receives [n][3] = (w_target, beta, error flags) per problem, w_target
+ * being c_bar for the two-stage scheme.  Returns the
  * first problem's error, if any. */
 IEWPF_API int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* obs, double* diag);
 IEWPF_API int iewpf_batch_stream(const iewpf_batch_t* b, void** stream);

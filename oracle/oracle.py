@@ -530,6 +530,31 @@ def iewpf_scalars(c, gamma, zeta, N_psi):
     return {"cbar": cbar, "beta": beta, "cstar": cstar, "alpha": alpha, "neglogw": neglogw}
 
 
+def iewpf_scalars_one_stage(c, gamma, N_psi):
+    """Target weight, c* and alpha of the one-stage IEWPF (App. A: eqs.
+    iewpf_targetWeight, iewpfCStar, iewpfAlphaSol).  There is no nu, so no
+    beta; beta is returned as 0, which removes the nu term from the
+    posterior of eq. optUpdateEquationTwoStage.
+
+    Returns dict with w_target, cbar (mean c_i), beta, cstar[i], alpha[i],
+    neglogw[i]."""
+    c = np.asarray(c, np.float64)
+    gamma = np.asarray(gamma, np.float64)
+    ne = len(c)
+    w_target = float(np.max(c))                      # eq. iewpf_targetWeight
+    cstar = w_target - c                             # eq. iewpfCStar
+    alpha = np.empty(ne)
+    for i in range(ne):
+        x = gamma[i] / N_psi
+        q = ((x - 1.0) - math.log1p(x - 1.0)) + cstar[i] / N_psi
+        alpha[i] = -lambert_w0_branch(q) / x         # eq. iewpfAlphaSol
+    # eq. implicitEquation without the derivative term (the large-N_psi form
+    # that eq. iewpfAlphaSol solves)
+    neglogw = (alpha - 1.0) * gamma - N_psi * np.log(alpha) + c
+    return {"w_target": w_target, "cbar": float(np.sum(c) / ne), "beta": 0.0, "cstar": cstar,
+            "alpha": alpha, "neglogw": neglogw}
+
+
 def rand_vectors(P: Problem, ne, t, p0=0):
     """xi, nu~ ~ N(0, I) on Omega^R (streams 1 and 2, draw t), the
     perpendicular nu (eq. nuPerpendicular) and gamma, zeta (eq.
@@ -580,9 +605,11 @@ def block_indices(P: Problem, cell):
                      for q in range(-3, 4) for p in range(-3, 4)])
 
 
-def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0):
+def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0, one_stage=False):
     """One two-stage IEWPF analysis of the forecast ensemble (Sec. 4, steps
-    1-6).  Returns (new ensemble, diagnostics dict)."""
+    1-6), or with one_stage=True the one-stage IEWPF of App. A (eq.
+    iewpfUpdateAgain: the same steps without nu).  Returns (new ensemble,
+    diagnostics dict)."""
     ens = np.array(ens, np.float64, order="C")
     ne = ens.shape[0]
     cells = [tuple(int(v) for v in cl) for cl in cells]
@@ -599,9 +626,14 @@ def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0)
     # 3: perpendicular random vectors
     rv = rand_vectors(P, ne, t, p0)
     # 4-5: target weight, beta, alpha
-    sc = iewpf_scalars(c, rv["gamma"], rv["zeta"], P.N_psi)
-    # 6: posterior (eq. optUpdateEquationTwoStage): psi^a + P^{1/2}(b^.5 nu + a^.5 xi)
-    r = math.sqrt(sc["beta"]) * rv["nu"] + np.sqrt(sc["alpha"])[:, None] * rv["xi"]
+    if one_stage:
+        sc = iewpf_scalars_one_stage(c, rv["gamma"], P.N_psi)
+        # 6: posterior (eq. iewpfUpdateAgain): psi^a + P^{1/2} a^.5 xi
+        r = np.sqrt(sc["alpha"])[:, None] * rv["xi"]
+    else:
+        sc = iewpf_scalars(c, rv["gamma"], rv["zeta"], P.N_psi)
+        # 6: posterior (eq. optUpdateEquationTwoStage): psi^a + P^{1/2}(b^.5 nu + a^.5 xi)
+        r = math.sqrt(sc["beta"]) * rv["nu"] + np.sqrt(sc["alpha"])[:, None] * rv["xi"]
     for cl in cells:                       # U Sigma^{1/2} on each 7x7 block, in order
         idx = block_indices(P, cl)
         r[:, idx] = r[:, idx] @ Msq.T

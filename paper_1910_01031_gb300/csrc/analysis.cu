@@ -76,18 +76,18 @@ rand_dots_kernel(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR
 
 __global__ void __launch_bounds__(1024)
 sync_alpha_kernel(const double* __restrict__ phi, const double* __restrict__ partial, int nblk, int ne,
-                  double NR, double N, double logNe, double* c, double* gamma, double* zeta, double* alpha,
-                  double* cstar, double* neglogw, double* coef, double* scal, int* flag)
+                  double NR, double N, double logNe, int scheme, double* c, double* gamma, double* zeta,
+                  double* alpha, double* cstar, double* neglogw, double* coef, double* scal, int* flag)
 {
-    ana::sync_alpha_cta(phi, partial, nblk, ne, NR, N, logNe, c, gamma, zeta, alpha, cstar, neglogw, coef, scal,
-                        flag);
+    ana::sync_alpha_cta(phi, partial, nblk, ne, NR, N, logNe, scheme, c, gamma, zeta, alpha, cstar, neglogw, coef,
+                        scal, flag);
 }
 
 __global__ void __launch_bounds__(1024)
-weights_kernel(const double* c, const double* gamma, const double* zeta, int ne, double N, double* alpha,
-               double* cstar, double* neglogw, double* scal, int* flag)
+weights_kernel(const double* c, const double* gamma, const double* zeta, int ne, double N, int scheme,
+               double* alpha, double* cstar, double* neglogw, double* scal, int* flag)
 {
-    ana::weights_cta(c, gamma, zeta, ne, N, alpha, cstar, neglogw, scal, flag);
+    ana::weights_cta(c, gamma, zeta, ne, N, scheme, alpha, cstar, neglogw, scal, flag);
 }
 
 __global__ void form_r_kernel(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR,
@@ -198,20 +198,20 @@ cudaError_t launch_rand_dots(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t 
 }
 
 cudaError_t launch_sync_alpha(const double* phi, const double* partial, int nblk, int ne, double NR,
-                              double N_psi, double logNe, double* c, double* gamma, double* zeta,
+                              double N_psi, double logNe, int scheme, double* c, double* gamma, double* zeta,
                               double* alpha, double* cstar, double* neglogw, double* coef, double* scal,
                               int* flag, cudaStream_t st)
 {
-    sync_alpha_kernel<<<1, 1024, 0, st>>>(phi, partial, nblk, ne, NR, N_psi, logNe, c, gamma, zeta, alpha,
-                                          cstar, neglogw, coef, scal, flag);
+    sync_alpha_kernel<<<1, 1024, 0, st>>>(phi, partial, nblk, ne, NR, N_psi, logNe, scheme, c, gamma, zeta,
+                                          alpha, cstar, neglogw, coef, scal, flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_weights_only(const double* c, const double* gamma, const double* zeta, int ne, double N_psi,
-                                double* alpha, double* cstar, double* neglogw, double* scal, int* flag,
+                                int scheme, double* alpha, double* cstar, double* neglogw, double* scal, int* flag,
                                 cudaStream_t st)
 {
-    weights_kernel<<<1, 1024, 0, st>>>(c, gamma, zeta, ne, N_psi, alpha, cstar, neglogw, scal, flag);
+    weights_kernel<<<1, 1024, 0, st>>>(c, gamma, zeta, ne, N_psi, scheme, alpha, cstar, neglogw, scal, flag);
     return cudaGetLastError();
 }
 

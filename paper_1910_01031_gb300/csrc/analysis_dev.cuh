@@ -375,38 +375,57 @@ __device__ __forceinline__ void block_sum_min(double v_sum, double v_min, double
     __syncthreads();
 }
 
-// CTA: the ensemble-wide step, c_bar = w_target, beta, c*, alpha, -log w
+// Schemes of the ensemble-wide step: the two-stage IEWPF (App. A, eqs.
+// betaTwoStage, cistarTwoStage) and the one-stage IEWPF (App. A, eqs.
+// iewpf_targetWeight, iewpfCStar), which has no nu and so no beta.
+constexpr int TWO_STAGE = 0;
+constexpr int ONE_STAGE = 1;
+
+// CTA: the ensemble-wide step.  Two-stage: w_target = mean c_i, beta, c*,
+// alpha, -log w.  One-stage: w_target = max c_i, beta reported as 0 (the nu
+// term of the posterior vanishes with it), c* = w_target - c_i, alpha, -log w.
+// scal[0] = w_target, scal[1] = beta, scal[2] = mean c_i.
 __device__ __forceinline__ void weights_cta(const double* c, const double* gamma, const double* zeta, int ne,
-                                            double N, double* alpha, double* cstar, double* neglogw, double* scal,
-                                            int* flag)
+                                            double N, int scheme, double* alpha, double* cstar, double* neglogw,
+                                            double* scal, int* flag)
 {
     __shared__ double s_sum, s_min;
-    double acc = 0.0;
+    const bool one = scheme == ONE_STAGE;
+    double acc = 0.0, mc = INFINITY;
     bool bad = false;
     for (int i = threadIdx.x; i < ne; i += blockDim.x) {
         acc += c[i];
-        bad |= !isfinite(c[i]) || !isfinite(gamma[i]) || !isfinite(zeta[i]);
+        mc = fmin(mc, -c[i]);
+        bad |= !isfinite(c[i]) || !isfinite(gamma[i]) || (!one && !isfinite(zeta[i]));
     }
     bad = __syncthreads_or(bad);
-    block_sum_min(acc, INFINITY, &s_sum, &s_min);
-    const double cbar = s_sum / ne;
-    double mn = INFINITY;
-    for (int i = threadIdx.x; i < ne; i += blockDim.x) mn = fmin(mn, (cbar - c[i]) / zeta[i] + 1.0);
-    block_sum_min(0.0, mn, &s_sum, &s_min);
-    const double beta = s_min;
+    block_sum_min(acc, mc, &s_sum, &s_min);
+    const double cmean = s_sum / ne;
+    const double target = one ? -s_min : cmean;
+    double beta = 0.0;
+    if (!one) {
+        double mn = INFINITY;
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) mn = fmin(mn, (target - c[i]) / zeta[i] + 1.0);
+        block_sum_min(0.0, mn, &s_sum, &s_min);
+        beta = s_min;
+    }
     bool dom = false;
     for (int i = threadIdx.x; i < ne; i += blockDim.x) {
-        const double cs = cbar - c[i] - (beta - 1.0) * zeta[i];
+        const double cs = one ? target - c[i] : target - c[i] - (beta - 1.0) * zeta[i];
         const double a = alpha_lambert(gamma[i], cs, N);
         dom |= !(a > 0.0) || !isfinite(a);
         alpha[i] = a;
         cstar[i] = cs;
-        if (neglogw) neglogw[i] = (a - 1.0) * gamma[i] - N * log(a) + (beta - 1.0) * zeta[i] + c[i];
+        if (neglogw) {
+            const double t = (a - 1.0) * gamma[i] - N * log(a);
+            neglogw[i] = one ? t + c[i] : t + (beta - 1.0) * zeta[i] + c[i];
+        }
     }
     dom = __syncthreads_or(dom);
     if (threadIdx.x == 0) {
-        scal[0] = cbar;
+        scal[0] = target;
         scal[1] = beta;
+        scal[2] = cmean;
         int f = 0;
         if (bad) f |= FLAG_NONFINITE;
         if (!(beta >= 0.0)) f |= FLAG_BETA;
@@ -418,7 +437,7 @@ __device__ __forceinline__ void weights_cta(const double* c, const double* gamma
 // CTA: gamma, zeta, a, the length scale and c from the partial dot products,
 // then the weights step
 __device__ __forceinline__ void sync_alpha_cta(const double* __restrict__ phi, const double* __restrict__ partial,
-                                               int nblk, int ne, double NR, double N, double logNe, double* c,
+                                               int nblk, int ne, double NR, double N, double logNe, int scheme, double* c,
                                                double* gamma, double* zeta, double* alpha, double* cstar,
                                                double* neglogw, double* coef, double* scal, int* flag)
 {
@@ -437,7 +456,7 @@ __device__ __forceinline__ void sync_alpha_cta(const double* __restrict__ phi, c
         c[i] = phi[i] + logNe;                                       // eq. iewpf_ci
     }
     __syncthreads();
-    weights_cta(c, gamma, zeta, ne, N, alpha, cstar, neglogw, scal, flag);
+    weights_cta(c, gamma, zeta, ne, N, scheme, alpha, cstar, neglogw, scal, flag);
 }
 
 // r = beta^{1/2} nu + alpha^{1/2} xi at coarse point m of particle p,

@@ -566,7 +566,7 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
         !(P.obs_sigma > 0) || P.theta < 1.0 || P.theta > 2.0 || P.n_drifters_max < 0 ||
         (P.obs_kind != IEWPF_OBS_DRIFTER && P.obs_kind != IEWPF_OBS_MOORING) ||
         (P.obs_kind == IEWPF_OBS_MOORING && P.n_obs_max > 0 && !mooring_xy) || P.instance_id < 0 ||
-        P.instance_id > 0x0FFFFFFF)
+        P.instance_id > 0x0FFFFFFF || (P.scheme != IEWPF_TWO_STAGE && P.scheme != IEWPF_ONE_STAGE))
         return IEWPF_EINVAL;
     iewpf_ctx* ctx = new (std::nothrow) iewpf_ctx();
     if (!ctx) return IEWPF_ENOMEM;
@@ -788,9 +788,9 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     const uint32_t sb = 16u * (uint32_t)ctx->P.instance_id;
     KL(1, launch_rand_dots(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_partial,
                         ctx->dots_blk, ctx->st));
-    // 4-5: target weight, beta, alpha
+    // 4-5: target weight, beta (two-stage), alpha
     KL(1, launch_sync_alpha(ctx->d_phi, ctx->d_partial, ctx->dots_blk, ne, (double)ctx->NR, 3.0 * ctx->plane,
-                         std::log((double)ne), ctx->d_c, ctx->d_gamma, ctx->d_zeta, ctx->d_alpha, ctx->d_cstar,
+                         std::log((double)ne), ctx->P.scheme, ctx->d_c, ctx->d_gamma, ctx->d_zeta, ctx->d_alpha, ctx->d_cstar,
                          ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->flag, ctx->st));
     // 6: posterior coarse field, local block roots, fused update with the pull
     KL(1, launch_form_r(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_coef, ctx->d_scal,
@@ -820,7 +820,7 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
     ctx->cfl_ready = true;
     // diagnostics
-    CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     if (diag) {
         double* dst[] = {diag->phi, diag->c, diag->gamma, diag->zeta, diag->alpha, diag->neglogw};
         double* src[] = {ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta, ctx->d_alpha, ctx->d_neglogw};
@@ -829,8 +829,9 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     }
     rc = read_flags(ctx);
     if (diag) {
-        diag->c_bar = ctx->h_scal[0];
+        diag->w_target = ctx->h_scal[0];
         diag->beta = ctx->h_scal[1];
+        diag->c_bar = ctx->h_scal[2];
     }
     ctx->cycle++;
     return rc;
@@ -1072,8 +1073,8 @@ int iewpf_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, int64_
     return rc;
 }
 
-int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, const double* zeta, double* out2,
-                  double* alpha, double* cstar, double* neglogw)
+static int weights_host(int scheme, int ne, double N_psi, const double* c, const double* gamma, const double* zeta,
+                        double* out2, double* alpha, double* cstar, double* neglogw)
 {
     if (ne < 1 || !(N_psi > 0) || !c || !gamma || !zeta || !out2 || !alpha || !cstar) return IEWPF_EINVAL;
     double* d = nullptr;
@@ -1091,7 +1092,7 @@ int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, co
         cudaMemcpy(dc, c, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dg, gamma, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dz, zeta, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-        launch_weights_only(dc, dg, dz, ne, N_psi, da, ds, dw, dsc, flag, 0) != cudaSuccess ||
+        launch_weights_only(dc, dg, dz, ne, N_psi, scheme, da, ds, dw, dsc, flag, 0) != cudaSuccess ||
         cudaMemcpy(out2, dsc, 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(alpha, da, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(cstar, ds, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -1106,6 +1107,19 @@ int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, co
         else if (hf & FLAG_DOMAIN) rc = IEWPF_EDOMAIN;
     }
     return rc;
+}
+
+int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, const double* zeta, double* out2,
+                  double* alpha, double* cstar, double* neglogw)
+{
+    return weights_host(IEWPF_TWO_STAGE, ne, N_psi, c, gamma, zeta, out2, alpha, cstar, neglogw);
+}
+
+int iewpf_weights_one_stage(int ne, double N_psi, const double* c, const double* gamma, double* out2,
+                            double* alpha, double* cstar, double* neglogw)
+{
+    // zeta is not read by the one-stage step; gamma stands in for the pointer
+    return weights_host(IEWPF_ONE_STAGE, ne, N_psi, c, gamma, gamma, out2, alpha, cstar, neglogw);
 }
 
 int iewpf_pull_stencil(const iewpf_ctx_t* ctx, double* K)
@@ -1318,6 +1332,7 @@ int iewpf_batch_create(const iewpf_params_t* params, const double* const* moorin
         I.H = ctx->P.H_eq;
         I.sigma2 = ctx->P.obs_sigma * ctx->P.obs_sigma;
         I.dense = ctx->P.dense_S;
+        I.scheme = ctx->P.scheme;
         I.R = ctx->R;
         I.cell = ctx->d_cell;
         I.block0 = ctx->d_block0;

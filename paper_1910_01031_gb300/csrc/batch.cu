@@ -327,8 +327,8 @@ __global__ void __launch_bounds__(1024) b_sync(BatchDev B)
 {
     for (int i = blockIdx.x; i < B.n; i += gridDim.x) {
         const BInst& I = B.inst[i];
-        ana::sync_alpha_cta(I.phi, I.partial, I.nblk, I.G.ne, (double)I.NR, I.N_psi, I.logNe, I.c, I.gamma, I.zeta,
-                            I.alpha, I.cstar, I.neglogw, I.coef, I.scal, I.flag);
+        ana::sync_alpha_cta(I.phi, I.partial, I.nblk, I.G.ne, (double)I.NR, I.N_psi, I.logNe, I.scheme, I.c,
+                            I.gamma, I.zeta, I.alpha, I.cstar, I.neglogw, I.coef, I.scal, I.flag);
     }
 }
 
@@ -354,7 +354,7 @@ __global__ void b_block_seq(BatchDev B)
     }
 }
 
-// per problem (c_bar, beta, flag) into the packed diagnostics buffer
+// per problem (w_target, beta, flag) into the packed diagnostics buffer
 __global__ void b_pack_diag(BatchDev B, double* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

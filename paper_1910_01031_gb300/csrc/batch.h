@@ -32,6 +32,7 @@ struct BInst {
     int moving_obs;          // drifters: cells, lists and HQH^T redone every cycle
     double dx, dy, H, sigma2;
     int dense, R;
+    int scheme;              // 0 two-stage, 1 one-stage IEWPF
     const double* obs_xy;
     const double* obs_y;
     int* cell;

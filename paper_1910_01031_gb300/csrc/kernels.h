@@ -99,11 +99,12 @@ cudaError_t launch_rand_dots(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t 
                              double* partial, int nblk, cudaStream_t st);
 int rand_dots_blocks(int NR);
 cudaError_t launch_sync_alpha(const double* phi, const double* partial, int nblk, int ne, double NR,
-                              double N_psi, double logNe, double* c, double* gamma, double* zeta,
+                              double N_psi, double logNe, int scheme /*0 two-stage, 1 one-stage*/,
+                              double* c, double* gamma, double* zeta,
                               double* alpha, double* cstar, double* neglogw, double* coef /*[ne][2]*/,
-                              double* scal /*[4]: cbar, beta*/, int* flag, cudaStream_t st);
+                              double* scal /*[4]: w_target, beta, mean c*/, int* flag, cudaStream_t st);
 cudaError_t launch_weights_only(const double* c, const double* gamma, const double* zeta, int ne, double N_psi,
-                                double* alpha, double* cstar, double* neglogw, double* scal, int* flag,
+                                int scheme, double* alpha, double* cstar, double* neglogw, double* scal, int* flag,
                                 cudaStream_t st);
 cudaError_t launch_form_r(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
                           const double* coef, const double* scal, const double* alpha, float* r,

@@ -66,7 +66,7 @@ extern "C" int iewpf_weights_noalloc(int ne, double N_psi, const double* c, cons
         cudaMemcpy(dc, c, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dg, gamma, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dz, zeta, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-        iewpf::launch_weights_only(dc, dg, dz, ne, N_psi, da, ds, dw, dsc, flag, 0) != cudaSuccess ||
+        iewpf::launch_weights_only(dc, dg, dz, ne, N_psi, 0, da, ds, dw, dsc, flag, 0) != cudaSuccess ||
         cudaMemcpy(out2, dsc, 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(alpha, da, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(cstar, ds, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||

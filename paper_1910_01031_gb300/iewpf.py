@@ -24,6 +24,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_forecast_fixed", "iewpf_assimilate", "iewpf_set_drifters", "iewpf_get_drifters",
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
+           "iewpf_weights_one_stage",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
@@ -49,7 +50,11 @@ class Params(ctypes.Structure):
                 ("c_omega", ctypes.c_int), ("q0", ctypes.c_double), ("L0", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("n_particles", ctypes.c_int), ("obs_kind", ctypes.c_int),
                 ("n_obs_max", ctypes.c_int), ("obs_sigma", ctypes.c_double), ("dense_S", ctypes.c_int),
-                ("instance_id", ctypes.c_int), ("n_drifters_max", ctypes.c_int)]
+                ("instance_id", ctypes.c_int), ("n_drifters_max", ctypes.c_int), ("scheme", ctypes.c_int)]
+
+
+TWO_STAGE = 0
+ONE_STAGE = 1
 
 
 class Obs(ctypes.Structure):
@@ -59,7 +64,8 @@ class Obs(ctypes.Structure):
 
 class Diag(ctypes.Structure):
     _fields_ = [("c_bar", ctypes.c_double), ("beta", ctypes.c_double)] + \
-        [(k, ctypes.POINTER(ctypes.c_double)) for k in ("phi", "c", "gamma", "zeta", "alpha", "neglogw")]
+        [(k, ctypes.POINTER(ctypes.c_double)) for k in ("phi", "c", "gamma", "zeta", "alpha", "neglogw")] + \
+        [("w_target", ctypes.c_double)]
 
 
 _lib = None
@@ -107,6 +113,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_normals.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_int64, _dp, _fp]
     L.iewpf_weights.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_weights_noalloc.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.iewpf_weights_one_stage.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_pull_stencil.argtypes = [_vp, _dp]
     L.iewpf_local_block.argtypes = [_vp, _dp]
     L.iewpf_add_qhalf.argtypes = [_vp, _fp]
@@ -160,12 +167,12 @@ def _f64(a, shape=None):
     return a
 
 
-def params_from_config(cfg, n_drifters_max=0, n_obs_max=None):
+def params_from_config(cfg, n_drifters_max=0, n_obs_max=None, scheme=TWO_STAGE):
     """iewpf_params_t from a synth.Config."""
     return Params(cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.g, cfg.f, cfg.H, cfg.theta, cfg.courant, cfg.dt_model,
                   cfg.c_omega, cfg.q0, cfg.L0, cfg.seed, cfg.n_particles, cfg.obs_kind,
                   cfg.n_obs if n_obs_max is None else n_obs_max, cfg.obs_sigma, cfg.dense_S, 0,
-                  n_drifters_max)
+                  n_drifters_max, scheme)
 
 
 class Ensemble:
@@ -252,6 +259,7 @@ class Ensemble:
         if diag:
             out["cbar"] = d.c_bar
             out["beta"] = d.beta
+            out["w_target"] = d.w_target
         return out
 
     def set_drifters(self, xy):
@@ -577,3 +585,18 @@ def weights(c, gamma, zeta, N_psi, noalloc=False):
     if rc != IEWPF_OK:
         raise IewpfError(rc, "weights")
     return {"cbar": out2[0], "beta": out2[1], "alpha": alpha, "cstar": cstar, "neglogw": nlw}
+
+
+def weights_one_stage(c, gamma, N_psi):
+    """GPU ensemble-wide step of the one-stage IEWPF: returns dict w_target,
+    beta (0), alpha, cstar, neglogw."""
+    L = load()
+    c, gamma = _f64(c), _f64(gamma)
+    ne = c.size
+    out2 = np.zeros(2)
+    alpha, cstar, nlw = np.zeros(ne), np.zeros(ne), np.zeros(ne)
+    rc = L.iewpf_weights_one_stage(ne, float(N_psi), _ptr(c), _ptr(gamma), _ptr(out2), _ptr(alpha), _ptr(cstar),
+                                   _ptr(nlw))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "weights_one_stage")
+    return {"w_target": out2[0], "beta": out2[1], "alpha": alpha, "cstar": cstar, "neglogw": nlw}

@@ -53,6 +53,22 @@ def test_weights_stage_matches_oracle_to_1e10(ne, N, Ny):
     assert np.allclose(g["neglogw"], g["cbar"], rtol=1e-10, atol=0)
 
 
+@pytest.mark.parametrize("ne,N,Ny", [(10, 12288, 2), (100, 786432, 128), (1000, 3145728, 3042), (5, 50.0, 2)])
+def test_one_stage_weights_match_oracle_to_1e10(ne, N, Ny):
+    c, gamma, _ = _scalars_inputs(ne + Ny + 1, ne, N, Ny)
+    if N < 100:        # tiny state: the Lambert-W argument away from -1/e
+        gamma = np.array([20.0, 35.0, 49.0, 60.0, 80.0])
+        c = np.array([4.0, 9.5, 1.0, 6.0, 2.5])
+    g = iewpf.weights_one_stage(c, gamma, N)
+    o = O.iewpf_scalars_one_stage(c, gamma, N)
+    assert g["w_target"] == o["w_target"] == c.max()
+    assert g["beta"] == 0.0
+    assert np.array_equal(g["cstar"], o["cstar"])
+    assert np.allclose(g["alpha"], o["alpha"], rtol=1e-10, atol=0)
+    assert np.allclose(g["neglogw"], o["neglogw"], rtol=1e-10, atol=0)
+    assert np.allclose(g["neglogw"], g["w_target"], rtol=1e-10, atol=0)
+
+
 def test_weights_stage_reports_negative_beta():
     # c_bar - c_i very negative against zeta: beta < 0
     with pytest.raises(iewpf.IewpfError) as e:
@@ -89,6 +105,31 @@ def test_assimilate_matches_oracle_drifters(dense):
     e = rel_l2(ens.get_state(), ref)
     assert e < 1e-5, e
     assert ens.counters() == (0, 1)
+
+
+def test_one_stage_assimilate_matches_oracle():
+    cfg = ragged_config(n_obs=3, n_particles=6)
+    ne = cfg.n_particles
+    U32, U64 = start_state(cfg, ne, seed=8)
+    P = oracle_problem(cfg)
+    ens = iewpf.Ensemble(iewpf.params_from_config(cfg, scheme=iewpf.ONE_STAGE))
+    ens.set_state(U32)
+    xy = np.array([[20.3e3, 30.1e3], [26.9e3, 34.5e3], [90.2e3, 60.7e3]])
+    cells = [O.obs_cell(P, *p) for p in xy]
+    truth = synth.initial_state(cfg, 1, seed=99)[0]
+    ref = U64
+    for cycle in range(2):
+        y = _obs_for(cfg, truth, np.array(cells), cycle)
+        dg = ens.assimilate(xy, y)
+        ref, do = O.assimilate(P, ref, cells, y, t=cycle, one_stage=True)
+        assert dg["beta"] == 0.0
+        assert dg["w_target"] == dg["c"].max()
+        assert math.isclose(dg["cbar"], np.mean(dg["c"]), rel_tol=1e-12)
+        assert np.allclose(dg["c"], do["c"], rtol=1e-4, atol=0)
+        assert np.allclose(dg["alpha"], do["alpha"], rtol=1e-6, atol=0)
+        assert np.allclose(dg["neglogw"], dg["w_target"], rtol=1e-10, atol=0)
+        e = rel_l2(ens.get_state(), ref)
+        assert e < 1e-5, (cycle, e)
 
 
 def test_assimilate_matches_oracle_moorings_ragged():

@@ -26,6 +26,7 @@ def _problems():
         p = iewpf.params_from_config(c)
         p.instance_id = i
         params.append(p)
+    params[2].scheme = iewpf.ONE_STAGE       # one problem runs the one-stage IEWPF
     return cfgs, params, moor
 
 
@@ -56,7 +57,9 @@ def test_batched_cycles_equal_one_by_one():
             s.forecast(4, True)
             s.forecast(1, False)
             d = s.assimilate(obs[i][0], obs[i][1])
-            assert diag[i, 0] == d["cbar"] and diag[i, 1] == d["beta"], (cycle, i)
+            assert diag[i, 0] == d["w_target"] and diag[i, 1] == d["beta"], (cycle, i)
+            if i == 2:
+                assert d["beta"] == 0.0 and d["w_target"] == d["c"].max()
             assert diag[i, 2] == 0
             a, b = batch.instances[i].get_state(), s.get_state()
             assert np.array_equal(a, b), (cycle, i, np.abs(a - b).max())

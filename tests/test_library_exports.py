@@ -43,6 +43,11 @@ def test_library_loads_and_reports_errors_without_crashing():
     bad = iewpf.Params()
     h = __import__("ctypes").c_void_p()
     assert L.iewpf_create(__import__("ctypes").byref(bad), None, __import__("ctypes").byref(h)) == -1
+    # an unknown analysis scheme is refused before any device work
+    from paper_1910_01031_gb300 import synth
+    p = iewpf.params_from_config(synth.config1())
+    p.scheme = 2
+    assert L.iewpf_create(__import__("ctypes").byref(p), None, __import__("ctypes").byref(h)) == -1
 
 
 def test_oracle_is_not_imported_by_the_product():
