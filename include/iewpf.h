@@ -165,6 +165,26 @@ IEWPF_API int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_
  * ENONFINITE, ENOTPD, ECUDA. */
 IEWPF_API int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* diag);
 
+/* Weights of the standard particle filter (Sec. 2.1, eqs.
+ * standardParticleFilter and standardParticleFilterWeight) for the current
+ * ensemble against subsets of one observation set, and how many particles
+ * residual resampling would keep for sure (normalised weight above 1/N_e,
+ * the count of the collapse experiment, Sec. 5.3).  The state is unchanged.
+ *   obs      as for iewpf_assimilate; the innovations are those of
+ *            eq. etaCompensatedInnovation.
+ *   r_scale  R = r_scale * obs_sigma^2 I (the experiment uses 1 and 10).
+ *   sets     host [n_sets][set_size] observation indices in [0, n_obs);
+ *            1 <= set_size <= n_obs.  A subset may repeat an index.
+ *   w        host [n_sets][N_e] normalised weights, or NULL.
+ *   n_kept   host [n_sets]: particles with w_i > 1/N_e.
+ * Per subset, w_i = exp(-(l_i - min l)) / sum_j exp(-(l_j - min l)) with
+ * l_i = |d_i on the subset|^2 / (2 r_scale obs_sigma^2), in FP64.  Device
+ * scratch of n_sets x (set_size x 4 + N_e x 8 + 4) bytes is allocated and
+ * freed by the call.  Errors: EINVAL (bad subsets or observations),
+ * ENOMEM, ECUDA. */
+IEWPF_API int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, int n_sets,
+                                int set_size, const int* sets, double* w, int* n_kept);
+
 /* Drifters carried by every particle (Sec. 3.3, forward Euler with the
  * velocity hu/(H+eta) of the containing cell after each scheme step).
  * xy: [N_e][n][2] float64 unwrapped positions; n <= n_drifters_max.

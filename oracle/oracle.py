@@ -644,6 +644,30 @@ def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0,
     return ens, diag
 
 
+def sir_weights(d, sets, sigma2, r_scale=1.0):
+    """Normalised weights of the standard particle filter (Sec. 2.1, eqs.
+    standardParticleFilter, standardParticleFilterWeight) for each subset of
+    observations, R = r_scale sigma2 I, and the number of particles whose
+    weight exceeds 1/N_e (kept for sure by residual resampling, Sec. 5.3).
+
+    d: innovations [N_e][n_obs][2]; sets: [n_sets][set_size] indices.
+    Returns (w [n_sets][N_e], kept [n_sets]).  exp(-l_i) is divided by
+    exp(-min_j l_j) before the normalisation, which changes nothing but keeps
+    the largest term at 1 instead of underflowing."""
+    d = np.asarray(d, np.float64)
+    ne = d.shape[0]
+    sets = np.asarray(sets)
+    w = np.empty((len(sets), ne))
+    kept = np.empty(len(sets), np.int64)
+    for s, S in enumerate(sets):
+        l = np.array([0.5 * sum(d[i, k, 0] ** 2 + d[i, k, 1] ** 2 for k in S) / (r_scale * sigma2)
+                      for i in range(ne)])
+        e = np.exp(-(l - l.min()))
+        w[s] = e / e.sum()
+        kept[s] = int(np.sum(w[s] > 1.0 / ne))
+    return w, kept
+
+
 def forecast_errors(traj, truth):
     """Drift-forecast error E(t) and RMSE(t) (eqs. errorPerEnsembleDrifter,
     errorNorm).  traj: [n_out][N_e][N_D][2] unwrapped positions; truth:

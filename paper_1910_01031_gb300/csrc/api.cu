@@ -837,6 +837,60 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     return rc;
 }
 
+int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, int n_sets, int set_size,
+                      const int* sets, double* w, int* n_kept)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max || !obs->value)
+        return fail(ctx, IEWPF_EINVAL, "bad observation set");
+    const bool mooring = ctx->P.obs_kind == IEWPF_OBS_MOORING;
+    if (!mooring && !obs->xy) return fail(ctx, IEWPF_EINVAL, "drifter observations need positions");
+    if (mooring && obs->n_obs != ctx->nobs_max)
+        return fail(ctx, IEWPF_EINVAL, "mooring observations must cover every mooring");
+    const int nobs = obs->n_obs, ne = ctx->G.ne;
+    if (!(r_scale > 0) || !std::isfinite(r_scale) || n_sets < 0 || set_size < 1 || set_size > nobs ||
+        (n_sets > 0 && (!sets || !n_kept)))
+        return fail(ctx, IEWPF_EINVAL, "bad observation subsets");
+    for (long long k = 0; k < (long long)n_sets * set_size; ++k)
+        if (sets[k] < 0 || sets[k] >= nobs) return fail(ctx, IEWPF_EINVAL, "subset index out of range");
+    if (n_sets == 0) return IEWPF_OK;
+    CK(cudaSetDevice(ctx->dev));
+    int rc;
+    if (!mooring && (rc = upload_obs_layout(ctx, obs->xy, nobs))) return rc;
+    CK(cudaMemcpyAsync(ctx->d_obs_y, obs->value, sizeof(double) * 2 * nobs, cudaMemcpyHostToDevice, ctx->st));
+    KL(1, launch_innovate(ctx->buf[0], ctx->buf[1], ctx->par, ctx->d_cell, ctx->d_obs_y, nobs, ctx->G,
+                       ctx->P.H_eq, ctx->d_d, ctx->st));
+    const size_t nidx = (size_t)n_sets * set_size, nw = (size_t)n_sets * ne;
+    int* d_sets = nullptr;
+    int* d_kept = nullptr;
+    double* d_w = nullptr;
+    if (cudaMalloc((void**)&d_sets, sizeof(int) * nidx) != cudaSuccess ||
+        cudaMalloc((void**)&d_kept, sizeof(int) * n_sets) != cudaSuccess ||
+        cudaMalloc((void**)&d_w, sizeof(double) * nw) != cudaSuccess) {
+        cudaFree(d_sets);
+        cudaFree(d_kept);
+        cudaFree(d_w);
+        cudaGetLastError();
+        return fail(ctx, IEWPF_ENOMEM, "subset buffers");
+    }
+    const double sigma2 = ctx->P.obs_sigma * ctx->P.obs_sigma;
+    cudaError_t e = cudaMemcpyAsync(d_sets, sets, sizeof(int) * nidx, cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) {
+        e = launch_sir_weights(ctx->d_d, ne, nobs, d_sets, n_sets, set_size, 0.5 / (r_scale * sigma2), d_w, d_kept,
+                               ctx->st);
+        if (e == cudaSuccess) ctx->launches += 1;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n_kept, d_kept, sizeof(int) * n_sets, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, d_w, sizeof(double) * nw, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    cudaFree(d_sets);
+    cudaFree(d_kept);
+    cudaFree(d_w);
+    if (e != cudaSuccess) return fail(ctx, IEWPF_ECUDA, cudaGetErrorString(e));
+    return read_flags(ctx);
+}
+
 int iewpf_set_drifters(iewpf_ctx_t* ctx, const double* xy, int n)
 {
     if (!ctx) return IEWPF_EINVAL;

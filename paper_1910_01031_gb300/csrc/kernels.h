@@ -25,6 +25,12 @@ cudaError_t launch_drift_errors(const double* xy, const double* truth, int ne, i
 cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, const Grid& G, int* flag,
                              cudaStream_t st);
 
+// ---- ensemble_stats.cu ----------------------------------------------------
+// standard particle filter weights of every particle against n_sets subsets
+// of the innovations d [ne][nobs][2]: w [n_sets][ne], kept [n_sets]
+cudaError_t launch_sir_weights(const double* d, int ne, int nobs, const int* sets, int n_sets, int set_size,
+                               double inv2R, double* w, int* kept, cudaStream_t st);
+
 // ---- march.cu -------------------------------------------------------------
 namespace march {
 // Arguments of one scheme step of one problem.

@@ -24,7 +24,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_forecast_fixed", "iewpf_assimilate", "iewpf_set_drifters", "iewpf_get_drifters",
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
-           "iewpf_weights_one_stage",
+           "iewpf_weights_one_stage", "iewpf_sir_weights",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
@@ -99,6 +99,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_forecast_fixed.argtypes = [_vp, c.c_int, c.c_int, c.c_int]
     L.iewpf_assimilate.argtypes = [_vp, c.POINTER(Obs), c.POINTER(Diag)]
     L.iewpf_set_drifters.argtypes = [_vp, _dp, c.c_int]
+    L.iewpf_sir_weights.argtypes = [_vp, c.POINTER(Obs), c.c_double, c.c_int, c.c_int, _ip, _dp, _ip]
     L.iewpf_get_drifters.argtypes = [_vp, _dp]
     L.drifter_forecast.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, c.c_int]
     L.drifter_forecast_errors.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, _dp, _dp, _dp, c.c_int]
@@ -261,6 +262,21 @@ class Ensemble:
             out["beta"] = d.beta
             out["w_target"] = d.w_target
         return out
+
+    def sir_weights(self, xy, values, sets, r_scale=1.0, weights=True):
+        """Standard particle filter weights against each row of sets (observation
+        indices): returns (w [n_sets][N_e] or None, n_kept [n_sets])."""
+        values = _f64(values, (-1, 2))
+        xy = None if xy is None else _f64(xy, (-1, 2))
+        sets = np.ascontiguousarray(sets, np.int32)
+        if sets.ndim != 2:
+            raise ValueError("sets must be [n_sets][set_size]")
+        obs = Obs(values.shape[0], _ptr(xy), _ptr(values))
+        w = np.zeros((sets.shape[0], self.ne)) if weights else None
+        kept = np.zeros(sets.shape[0], np.int32)
+        self._chk(self.L.iewpf_sir_weights(self.h, ctypes.byref(obs), float(r_scale), sets.shape[0], sets.shape[1],
+                                           _ptr(sets, _ip), _ptr(w), _ptr(kept, _ip)), "sir_weights")
+        return w, kept
 
     def set_drifters(self, xy):
         xy = _f64(xy)

@@ -184,3 +184,11 @@ def obs_from_state(cfg: Config, U, cells, noise):
     s = cfg.H / (cfg.H + eta)
     return np.stack([U[1][cells[:, 1], cells[:, 0]] * s, U[2][cells[:, 1], cells[:, 0]] * s],
                     axis=1) + noise
+
+
+def observation_subsets(n_obs: int, size: int, n_subsets: int, seed: int = 13):
+    """n_subsets random subsets of `size` distinct observation indices out of
+    n_obs ([n_subsets][size] int32), as drawn for the collapse experiment of
+    the standard particle filter (Sec. 5.3: 50 subsets per size)."""
+    rng = np.random.Generator(np.random.Philox(seed + 7919 * size))
+    return np.stack([np.sort(rng.choice(n_obs, size, replace=False)) for _ in range(n_subsets)]).astype(np.int32)
