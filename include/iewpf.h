@@ -261,6 +261,19 @@ IEWPF_API int iewpf_weights(int ne, double N_psi, const double* c, const double*
 IEWPF_API int iewpf_weights_one_stage(int ne, double N_psi, const double* c, const double* gamma,
                                       double* out2, double* alpha, double* cstar, double* neglogw);
 
+/* alpha of the one-stage IEWPF from the incomplete-gamma form of the
+ * implicit equation (App. A, eq. numericalEqForAlpha), which keeps the
+ * derivative term that the Lambert-W solution (eq. iewpfAlphaSol) drops:
+ * P(N_psi/2, alpha_i gamma_i/2) = exp(-c*_i/2) P(N_psi/2, gamma_i/2), P the
+ * regularised lower incomplete gamma function, solved on the GPU in FP64
+ * with logarithms throughout (no overflow for large N_psi; the cost grows
+ * like sqrt(N_psi)).  gamma ([ne], > 0) and cstar ([ne], >= 0) are host
+ * arrays; alpha (host, [ne]) receives values in (0, 1], exactly 1 where
+ * c* = 0.  Errors: EINVAL (bad arguments), EDOMAIN (no convergence or alpha
+ * below the FP64 range), ENOMEM, ECUDA. */
+IEWPF_API int iewpf_alpha_gamma(int ne, double N_psi, const double* gamma, const double* cstar,
+                                double* alpha);
+
 /* Largest ensemble iewpf_weights_noalloc accepts. */
 #define IEWPF_WEIGHTS_NOALLOC_MAX_NE 4096
 

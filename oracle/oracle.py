@@ -555,6 +555,37 @@ def iewpf_scalars_one_stage(c, gamma, N_psi):
             "alpha": alpha, "neglogw": neglogw}
 
 
+def alpha_incomplete_gamma(gamma, cstar, N_psi):
+    """alpha of the one-stage IEWPF from eq. numericalEqForAlpha (App. A):
+    the lower incomplete gamma function at (N_psi/2, alpha gamma/2) equals
+    exp(-c*/2) times its value at (N_psi/2, gamma/2).  scipy's regularised
+    gammainc gives P (the ratio is the same for the regularised form);
+    brentq finds the root of log P(s, alpha gamma/2) - log P(s, gamma/2) +
+    c*/2 for alpha in (0, 1].  Valid while P stays inside the FP64 range
+    (c* up to about 1400)."""
+    from scipy.optimize import brentq
+    from scipy.special import gammainc
+    s = 0.5 * N_psi
+    out = np.empty(len(gamma))
+    for i, (g, cs) in enumerate(zip(np.asarray(gamma, np.float64), np.asarray(cstar, np.float64))):
+        if cs == 0.0:
+            out[i] = 1.0
+            continue
+        target = math.log(gammainc(s, 0.5 * g)) - 0.5 * cs
+
+        def f(a):
+            p = gammainc(s, 0.5 * a * g)
+            return (math.log(p) if p > 0.0 else -1e300) - target
+        # bracket from alpha = 1 downwards (P underflows far below the root
+        # when N_psi is large)
+        step, lo = 1e-9, 1.0 - 1e-9
+        while f(lo) >= 0.0:
+            step *= 2.0
+            lo = max(1.0 - step, 0.5 * lo) if step < 1.0 else 0.5 * lo
+        out[i] = brentq(f, lo, 1.0, xtol=1e-300, rtol=1e-15, maxiter=500)
+    return out
+
+
 def rand_vectors(P: Problem, ne, t, p0=0):
     """xi, nu~ ~ N(0, I) on Omega^R (streams 1 and 2, draw t), the
     perpendicular nu (eq. nuPerpendicular) and gamma, zeta (eq.

@@ -1169,6 +1169,34 @@ int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, co
     return weights_host(IEWPF_TWO_STAGE, ne, N_psi, c, gamma, zeta, out2, alpha, cstar, neglogw);
 }
 
+int iewpf_alpha_gamma(int ne, double N_psi, const double* gamma, const double* cstar, double* alpha)
+{
+    if (ne < 1 || !(N_psi > 0) || !std::isfinite(N_psi) || !gamma || !cstar || !alpha) return IEWPF_EINVAL;
+    for (int i = 0; i < ne; ++i)
+        if (!(gamma[i] > 0) || !std::isfinite(gamma[i]) || !(cstar[i] >= 0) || !std::isfinite(cstar[i]))
+            return IEWPF_EINVAL;
+    double* d = nullptr;
+    int* flag = nullptr;
+    const size_t n = (size_t)ne;
+    if (cudaMalloc((void**)&d, sizeof(double) * 3 * n) != cudaSuccess) return IEWPF_ENOMEM;
+    if (cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess) {
+        cudaFree(d);
+        return IEWPF_ENOMEM;
+    }
+    int rc = IEWPF_OK, hf = 0;
+    if (cudaMemset(flag, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(d, gamma, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + n, cstar, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        launch_alpha_gamma(ne, N_psi, d, d + n, d + 2 * n, flag, 0) != cudaSuccess ||
+        cudaMemcpy(alpha, d + 2 * n, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = IEWPF_ECUDA;
+    cudaFree(d);
+    cudaFree(flag);
+    if (rc == IEWPF_OK && hf) rc = IEWPF_EDOMAIN;
+    return rc;
+}
+
 int iewpf_weights_one_stage(int ne, double N_psi, const double* c, const double* gamma, double* out2,
                             double* alpha, double* cstar, double* neglogw)
 {

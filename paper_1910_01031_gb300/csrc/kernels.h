@@ -31,6 +31,11 @@ cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, c
 cudaError_t launch_sir_weights(const double* d, int ne, int nobs, const int* sets, int n_sets, int set_size,
                                double inv2R, double* w, int* kept, cudaStream_t st);
 
+// ---- alpha_gamma.cu -------------------------------------------------------
+// alpha of the incomplete-gamma form of the implicit equation per particle
+cudaError_t launch_alpha_gamma(int ne, double N_psi, const double* gamma, const double* cstar, double* alpha,
+                               int* flag, cudaStream_t st);
+
 // ---- march.cu -------------------------------------------------------------
 namespace march {
 // Arguments of one scheme step of one problem.

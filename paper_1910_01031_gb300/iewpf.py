@@ -24,7 +24,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_forecast_fixed", "iewpf_assimilate", "iewpf_set_drifters", "iewpf_get_drifters",
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
-           "iewpf_weights_one_stage", "iewpf_sir_weights",
+           "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
@@ -115,6 +115,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_weights.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_weights_noalloc.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_weights_one_stage.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.iewpf_alpha_gamma.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp]
     L.iewpf_pull_stencil.argtypes = [_vp, _dp]
     L.iewpf_local_block.argtypes = [_vp, _dp]
     L.iewpf_add_qhalf.argtypes = [_vp, _fp]
@@ -601,6 +602,18 @@ def weights(c, gamma, zeta, N_psi, noalloc=False):
     if rc != IEWPF_OK:
         raise IewpfError(rc, "weights")
     return {"cbar": out2[0], "beta": out2[1], "alpha": alpha, "cstar": cstar, "neglogw": nlw}
+
+
+def alpha_gamma(gamma, cstar, N_psi):
+    """GPU alpha from the incomplete-gamma form of the one-stage implicit
+    equation, per particle."""
+    L = load()
+    gamma, cstar = _f64(gamma), _f64(cstar)
+    alpha = np.zeros(gamma.size)
+    rc = L.iewpf_alpha_gamma(gamma.size, float(N_psi), _ptr(gamma), _ptr(cstar), _ptr(alpha))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "alpha_gamma")
+    return alpha
 
 
 def weights_one_stage(c, gamma, N_psi):

@@ -69,6 +69,26 @@ def test_one_stage_weights_match_oracle_to_1e10(ne, N, Ny):
     assert np.allclose(g["neglogw"], g["w_target"], rtol=1e-10, atol=0)
 
 
+@pytest.mark.parametrize("N", [2.0, 4.0, 60.0, 1e4, 786432.0, 3145728.0])
+def test_incomplete_gamma_alpha_matches_oracle(N):
+    rng = np.random.default_rng(int(N) % 1000)
+    ne = 24
+    gamma = np.abs(N + math.sqrt(2 * N) * rng.standard_normal(ne)) + 0.05
+    cstar = np.concatenate([[0.0, 1e-6, 0.5, 300.0], rng.uniform(0.0, 60.0, ne - 4)])
+    g = iewpf.alpha_gamma(gamma, cstar, N)
+    o = O.alpha_incomplete_gamma(gamma, cstar, N)
+    assert g[0] == 1.0
+    assert np.all(g > 0.0) and np.all(g <= 1.0)
+    assert np.allclose(g, o, rtol=1e-9, atol=0)
+
+
+def test_incomplete_gamma_alpha_rejects_bad_arguments():
+    for gamma, cstar in (([1.0], [-0.1]), ([0.0], [1.0]), ([float("nan")], [1.0])):
+        with pytest.raises(iewpf.IewpfError) as e:
+            iewpf.alpha_gamma(gamma, cstar, 10.0)
+        assert e.value.name == "EINVAL"
+
+
 def test_weights_stage_reports_negative_beta():
     # c_bar - c_i very negative against zeta: beta < 0
     with pytest.raises(iewpf.IewpfError) as e:
