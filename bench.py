@@ -161,11 +161,11 @@ def run_ours(args, rank, world, local):
     P.instance_id = instance
     ens = iewpf.Ensemble(P)
     ens.set_state(synth.initial_state(cfg, ne, seed=7 + rank).astype(np.float32))
-    obs = make_observations(cfg, args.warmup + args.steps, rank)
+    obs = make_observations(cfg, args.warmup + args.steps + 1, rank)
     # pinned host buffers for the per-step inputs and outputs (end-to-end leg)
-    pin_xy = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs]
-    pin_val = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs]
-    for k, (xy, val) in enumerate(obs):
+    pin_xy = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs[:-1]]
+    pin_val = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs[:-1]]
+    for k, (xy, val) in enumerate(obs[:-1]):
         pin_xy[k].numpy()[:] = xy
         pin_val[k].numpy()[:] = val
     stream = torch.cuda.ExternalStream(ens.stream())
@@ -238,6 +238,10 @@ def run_ours(args, rank, world, local):
                 "per_launch_ms": round(launch_s * 1e3, 4),
                 "alu": {"achieved": round(achieved_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                         "frac": round(achieved_tflops / fp32_peak, 4)}}
+    try:
+        sir = run_sir_collapse(ens, cfg, *obs[-1])
+    except Exception as e:  # reported, the main number stands without it
+        sir = {"error": str(e)}
     ens.close()
     try:
         batched = run_batched(rank)
@@ -251,6 +255,14 @@ def run_ours(args, rank, world, local):
         surrogate = run_surrogate(rank, epochs=8)
     except Exception as e:  # reported, the main number stands without it
         surrogate = {"error": str(e)}
+    try:
+        one_stage = run_one_stage(rank)
+    except Exception as e:  # reported, the main number stands without it
+        one_stage = {"error": str(e)}
+    try:
+        ranks = run_rank_histogram(rank)
+    except Exception as e:  # reported, the main number stands without it
+        ranks = {"error": str(e)}
     if rank != 0:
         return
     cpu = cpu_baseline(args) if world == 1 else None
@@ -273,6 +285,9 @@ def run_ours(args, rank, world, local):
         "batched": batched,
         "moorings": moorings,
         "surrogate": surrogate,
+        "one_stage": one_stage,
+        "sir_collapse": sir,
+        "rank_histogram": ranks,
         "cpu_baseline": cpu,
         "clocks": clk,
         "last_beta": d["beta"] if d else None,
@@ -388,6 +403,92 @@ def run_moorings(rank, cycles=2):
     ens.close()
     torch.cuda.empty_cache()
     return out
+
+
+def run_sir_collapse(ens, cfg, xy, y):
+    """The collapse experiment of the standard particle filter (Sec. 5.3) on
+    the headline ensemble after its assimilation cycles, run on to the next
+    observation time: every size 1..64 of drifter subsets, 50 random subsets
+    each, with R and 10 R; the mean number of particles whose weight is above
+    1/N_e per size.  Timed per call (host wall clock through the C ABI: the
+    innovations, the weights of 3200 subsets, the copies)."""
+    import torch
+    from paper_1910_01031_gb300 import synth
+    ens.forecast(cfg.obs_every_steps - 1, True)
+    ens.forecast(1, False)
+    out = {"workload": "SIR weights on the 512x512 ne100 ensemble, 64 drifters, sizes 1..64 x 50 subsets, R and 10R"}
+    sets = [synth.observation_subsets(cfg.n_obs, k, 50) for k in range(1, cfg.n_obs + 1)]
+    for r_scale in (1.0, 10.0):
+        means = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for S in sets:
+            _, kept = ens.sir_weights(xy, y, S, r_scale, weights=False)
+            means.append(round(float(kept.mean()), 2))
+        secs = time.perf_counter() - t0
+        out["R" if r_scale == 1.0 else "10R"] = {"mean_kept_by_size": means, "seconds": round(secs, 4),
+                                                 "subsets_per_s": round(len(sets) * 50 / secs, 1)}
+    return out
+
+
+def run_one_stage(rank, cycles=3):
+    """The one-stage IEWPF (App. A) on the headline workload: cycle time
+    with CUDA events, and per cycle its target max c_i against the two-stage
+    target mean c_i.  The incomplete-gamma alpha (eq. numericalEqForAlpha) of
+    the last cycle's particles is solved on the GPU as well and compared with
+    the Lambert-W alpha the scheme used."""
+    import torch
+    from paper_1910_01031_gb300 import iewpf, synth
+    cfg, instance = replica(rank)
+    P = iewpf.params_from_config(cfg, scheme=iewpf.ONE_STAGE)
+    P.instance_id = instance
+    ens = iewpf.Ensemble(P)
+    ens.set_state(synth.initial_state(cfg, cfg.n_particles, seed=7 + rank).astype(np.float32))
+    obs = make_observations(cfg, cycles + 1, rank)
+    stream = torch.cuda.ExternalStream(ens.stream())
+
+    def cycle(k):
+        ens.forecast(cfg.obs_every_steps - 1, True)
+        ens.forecast(1, False)
+        return ens.assimilate(*obs[k])
+
+    cycle(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gaps = []
+    e0.record(stream)
+    for k in range(1, cycles + 1):
+        d = cycle(k)
+        gaps.append(round(d["w_target"] - d["cbar"], 3))
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    N = 3.0 * cfg.nx * cfg.ny
+    cstar = d["w_target"] - d["c"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ag = iewpf.alpha_gamma(d["gamma"], cstar, N)
+    g_s = time.perf_counter() - t0
+    moved = cstar > 0
+    ratio = (1.0 - ag[moved]) / (1.0 - d["alpha"][moved]) if moved.any() else np.array([1.0])
+    out = {"workload": "iewpf_cycle_512x512_ne100_64drifters, one-stage scheme",
+           "cycles_timed": cycles, "cycle_ms": round(secs / cycles * 1e3, 3),
+           "w_target_minus_cbar": gaps,
+           "alpha_gamma": {"particles": int(len(ag)), "N_psi": N, "seconds": round(g_s, 4),
+                           "min_alpha": float(ag.min()),
+                           "one_minus_alpha_ratio_gamma_over_lambert": {
+                               "min": round(float(ratio.min()), 4), "median": round(float(np.median(ratio)), 4),
+                               "max": round(float(ratio.max()), 4)}}}
+    ens.close()
+    return out
+
+
+def run_rank_histogram(rank):
+    """The rank-histogram experiment (Sec. 5.1) at a reduced count: 64
+    experiments x 40 members on 500 x 300 cells, 120 moorings, 1 h of
+    assimilation and a 1 h forecast (the paper: 1222 experiments, 6 h)."""
+    from paper_1910_01031_gb300 import rank_histogram
+    return rank_histogram.run(experiments=64, ne=40, hours_da=1.0, hours_fc=1.0, seed=2019 + 31 * rank)
 
 
 SUR_FLOPS_PER_PIXEL = 2 * 9 * (3 * 64 + 4 * 64 * 64 + 64 * 3)   # algorithmic (unpadded) FLOPs of one network call

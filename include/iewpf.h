@@ -185,6 +185,19 @@ IEWPF_API int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_d
 IEWPF_API int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, int n_sets,
                                 int set_size, const int* sets, double* w, int* n_kept);
 
+/* Ranks of observed values within the ensemble (Sec. 5.1, rank histograms):
+ * for point m (cell cells[m] = (j, k), 0 <= j < nx, 0 <= k < ny) and
+ * component c (0: hu, 1: hv), ranks[m][c] = #{i : (hu or hv)_i at the cell
+ * + obs_sigma eps_{i,m,c} < y[m][c]}, in 0..N_e: the position the observed
+ * value takes in the sorted list of the members perturbed by the
+ * observation error.  eps_{i,m,c} is the FP64 normal number 2m + c of
+ * particle i in Philox stream 3 (+ 16 x instance_id), draw `draw`.  All
+ * arrays are host memory: cells [n_pts][2], y [n_pts][2], ranks [n_pts][2].
+ * The state is unchanged.  Errors: EINVAL (a point outside the grid or a
+ * non-finite value), ENOMEM, ECUDA. */
+IEWPF_API int iewpf_rank(iewpf_ctx_t* ctx, int n_pts, const int* cells, const double* y, uint32_t draw,
+                         int* ranks);
+
 /* Drifters carried by every particle (Sec. 3.3, forward Euler with the
  * velocity hu/(H+eta) of the containing cell after each scheme step).
  * xy: [N_e][n][2] float64 unwrapped positions; n <= n_drifters_max.
@@ -234,7 +247,8 @@ IEWPF_API const char* iewpf_last_error(const iewpf_ctx_t* ctx);
 /* Raw Philox4x32-10 blocks (Salmon et al., SC'11) computed on the GPU:
  * block b of counter (b, p, t, stream) with key (seed lo, seed hi).
  * out: host [n_blocks][4] uint32.  The model-error, xi and nu draws use
- * streams 0, 1, 2 (plus 16 x instance_id). */
+ * streams 0, 1, 2 and the rank perturbations stream 3 (plus 16 x
+ * instance_id). */
 IEWPF_API int iewpf_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream,
                         int64_t n_blocks, uint32_t* out);
 

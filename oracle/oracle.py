@@ -134,7 +134,7 @@ class Problem:
 # ---------------------------------------------------------------------------
 # Random numbers
 # ---------------------------------------------------------------------------
-STREAM_MODEL_ERROR, STREAM_XI, STREAM_NU = 0, 1, 2
+STREAM_MODEL_ERROR, STREAM_XI, STREAM_NU, STREAM_RANK = 0, 1, 2, 3
 
 
 def philox(ctr, key):
@@ -555,34 +555,57 @@ def iewpf_scalars_one_stage(c, gamma, N_psi):
             "alpha": alpha, "neglogw": neglogw}
 
 
+def log_gamma_p(s, x):
+    """log P(s, x), P the regularised lower incomplete gamma function, from
+    its power series (Abramowitz & Stegun 6.5.4 with 6.5.29):
+        P(s, x) = x^s e^{-x} / Gamma(s + 1) * sum_{n>=0} x^n / ((s+1)...(s+n)),
+    the terms formed by a running product and summed in FP64 (numpy's
+    pairwise sum) until they fall below 1e-17 of the sum.  Beyond
+    x = s + 30 sqrt(s) + 30 the upper function is below 1e-190 and log P is
+    0 to FP64 precision."""
+    if x <= 0.0:
+        return -math.inf
+    if x > s + 30.0 * math.sqrt(s) + 30.0:
+        return 0.0
+    n = int(max(x - s, 0.0) + 40.0 * math.sqrt(max(s, 1.0)) + 100.0)
+    while True:
+        terms = np.cumprod(x / (s + np.arange(1, n + 1, dtype=np.float64)))
+        total = 1.0 + float(np.sum(terms))
+        if terms[-1] < 1e-17 * total:
+            break
+        n *= 2
+    return s * math.log(x) - x - math.lgamma(s + 1.0) + math.log(total)
+
+
 def alpha_incomplete_gamma(gamma, cstar, N_psi):
     """alpha of the one-stage IEWPF from eq. numericalEqForAlpha (App. A):
     the lower incomplete gamma function at (N_psi/2, alpha gamma/2) equals
-    exp(-c*/2) times its value at (N_psi/2, gamma/2).  scipy's regularised
-    gammainc gives P (the ratio is the same for the regularised form);
-    brentq finds the root of log P(s, alpha gamma/2) - log P(s, gamma/2) +
-    c*/2 for alpha in (0, 1].  Valid while P stays inside the FP64 range
-    (c* up to about 1400)."""
-    from scipy.optimize import brentq
-    from scipy.special import gammainc
+    exp(-c*/2) times its value at (N_psi/2, gamma/2); the ratio is the same
+    for the regularised form P.  Solved in logarithms (log_gamma_p), by
+    bisection on alpha in (0, 1] where log P(s, alpha gamma/2) is increasing."""
     s = 0.5 * N_psi
     out = np.empty(len(gamma))
     for i, (g, cs) in enumerate(zip(np.asarray(gamma, np.float64), np.asarray(cstar, np.float64))):
         if cs == 0.0:
             out[i] = 1.0
             continue
-        target = math.log(gammainc(s, 0.5 * g)) - 0.5 * cs
-
-        def f(a):
-            p = gammainc(s, 0.5 * a * g)
-            return (math.log(p) if p > 0.0 else -1e300) - target
-        # bracket from alpha = 1 downwards (P underflows far below the root
-        # when N_psi is large)
+        target = log_gamma_p(s, 0.5 * g) - 0.5 * cs
+        f = lambda a: log_gamma_p(s, 0.5 * a * g) - target
+        # bracket from alpha = 1 downwards
         step, lo = 1e-9, 1.0 - 1e-9
         while f(lo) >= 0.0:
             step *= 2.0
             lo = max(1.0 - step, 0.5 * lo) if step < 1.0 else 0.5 * lo
-        out[i] = brentq(f, lo, 1.0, xtol=1e-300, rtol=1e-15, maxiter=500)
+        hi = 1.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if mid <= lo or mid >= hi:
+                break
+            if f(mid) < 0.0:
+                lo = mid
+            else:
+                hi = mid
+        out[i] = 0.5 * (lo + hi)
     return out
 
 
@@ -697,6 +720,29 @@ def sir_weights(d, sets, sigma2, r_scale=1.0):
         w[s] = e / e.sum()
         kept[s] = int(np.sum(w[s] > 1.0 / ne))
     return w, kept
+
+
+def ranks(P: Problem, ens, cells, y, t, p0=0):
+    """Rank of each observed value within the ensemble (Sec. 5.1): members'
+    hu (comp 0) or hv (comp 1) at the cell plus the observation error
+    obs_sigma eps, eps the normal number 2m + comp of the particle's stream
+    STREAM_RANK (draw t); the rank is the number of perturbed members below
+    the observed value, i.e. its insertion position in their sorted list.
+    cells [n][2] integer (j, k); y [n][2].  Returns int array [n][2]."""
+    ens = np.asarray(ens, np.float64)
+    ne = ens.shape[0]
+    cells = np.asarray(cells).reshape(-1, 2)
+    y = np.asarray(y, np.float64).reshape(-1, 2)
+    eps = np.stack([normals(P.seed, p0 + i, t, STREAM_RANK, 2 * len(cells)) for i in range(ne)])
+    out = np.zeros((len(cells), 2), np.int64)
+    for m, (j, k) in enumerate(cells):
+        for comp in (0, 1):
+            below = 0
+            for i in range(ne):
+                if ens[i, 1 + comp, k, j] + P.obs_sigma * eps[i, 2 * m + comp] < y[m, comp]:
+                    below += 1
+            out[m, comp] = below
+    return out
 
 
 def forecast_errors(traj, truth):

@@ -891,6 +891,45 @@ int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, 
     return read_flags(ctx);
 }
 
+int iewpf_rank(iewpf_ctx_t* ctx, int n_pts, const int* cells, const double* y, uint32_t draw, int* ranks)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    if (n_pts < 1 || !cells || !y || !ranks) return fail(ctx, IEWPF_EINVAL, "bad rank points");
+    for (int m = 0; m < n_pts; ++m)
+        if (cells[2 * m] < 0 || cells[2 * m] >= ctx->G.nx || cells[2 * m + 1] < 0 || cells[2 * m + 1] >= ctx->G.ny ||
+            !std::isfinite(y[2 * m]) || !std::isfinite(y[2 * m + 1]))
+            return fail(ctx, IEWPF_EINVAL, "rank point outside the grid or non-finite value");
+    CK(cudaSetDevice(ctx->dev));
+    int* d_cells = nullptr;
+    int* d_ranks = nullptr;
+    double* d_y = nullptr;
+    if (cudaMalloc((void**)&d_cells, sizeof(int) * 2 * n_pts) != cudaSuccess ||
+        cudaMalloc((void**)&d_ranks, sizeof(int) * 2 * n_pts) != cudaSuccess ||
+        cudaMalloc((void**)&d_y, sizeof(double) * 2 * n_pts) != cudaSuccess) {
+        cudaFree(d_cells);
+        cudaFree(d_ranks);
+        cudaFree(d_y);
+        cudaGetLastError();
+        return fail(ctx, IEWPF_ENOMEM, "rank buffers");
+    }
+    const uint32_t stream = 16u * (uint32_t)ctx->P.instance_id + 3u;
+    cudaError_t e = cudaMemcpyAsync(d_cells, cells, sizeof(int) * 2 * n_pts, cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, y, sizeof(double) * 2 * n_pts, cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) {
+        e = launch_rank(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, d_cells, d_y, n_pts, ctx->P.seed, draw, stream,
+                        ctx->P.obs_sigma, d_ranks, ctx->st);
+        if (e == cudaSuccess) ctx->launches += 1;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ranks, d_ranks, sizeof(int) * 2 * n_pts, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    cudaFree(d_cells);
+    cudaFree(d_ranks);
+    cudaFree(d_y);
+    if (e != cudaSuccess) return fail(ctx, IEWPF_ECUDA, cudaGetErrorString(e));
+    return IEWPF_OK;
+}
+
 int iewpf_set_drifters(iewpf_ctx_t* ctx, const double* xy, int n)
 {
     if (!ctx) return IEWPF_EINVAL;

@@ -1,6 +1,7 @@
 // Ensemble statistics outside the IEWPF update: the weights of the standard
 // particle filter (Sec. 2.1) against many subsets of one observation set, as
-// in the collapse experiment of Sec. 5.3.
+// in the collapse experiment of Sec. 5.3, and the ranks of observed values
+// within the ensemble (Sec. 5.1, rank histograms).
 #include <math.h>
 
 #include "kernels.h"
@@ -82,7 +83,48 @@ sir_weights_kernel(const double* __restrict__ d, int ne, int nobs, const int* __
     }
 }
 
+// One warp per observed value q = 2 m + comp (point m, comp 0 for hu, 1 for
+// hv), lanes over particles.  Rank = #{i : U_i(1 + comp, cell_m) + sigma
+// eps_{i,q} < y_q}, eps_{i,q} the FP64 normal number q of particle i's
+// Philox stream (draw t): the members perturbed by the observation error
+// and the observed value inserted into their sorted list (Sec. 5.1).
+__global__ void rank_kernel(const float* __restrict__ b0, const float* __restrict__ b1, const int* __restrict__ par,
+                            Grid G, const int* __restrict__ cells, const double* __restrict__ y, int nq,
+                            uint64_t seed, uint32_t t, uint32_t stream, double sigma, int* __restrict__ ranks)
+{
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    const int m = q >> 1, comp = q & 1;
+    const long long cell = (long long)cells[2 * m + 1] * G.nx + cells[2 * m];
+    const double yq = y[q];
+    const uint2 key = seed_key(seed);
+    int cnt = 0;
+    for (int i = lane; i < G.ne; i += 32) {
+        const float* U = (par[i] ? b1 : b0) + (long long)i * 3 * G.plane;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)q >> 2, (uint32_t)i, t, stream), key);
+        const bool hi = (q & 2) != 0;
+        double z0, z1;
+        box_muller64(hi ? w.z : w.x, hi ? w.w : w.y, z0, z1);
+        const double v = fma(sigma, (q & 1) ? z1 : z0, (double)U[(long long)(1 + comp) * G.plane + cell]);
+        cnt += v < yq ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) ranks[q] = cnt;
+}
+
 }  // namespace
+
+cudaError_t launch_rank(const float* b0, const float* b1, const int* par, const Grid& G, const int* cells,
+                        const double* y, int npts, uint64_t seed, uint32_t t, uint32_t stream, double sigma,
+                        int* ranks, cudaStream_t st)
+{
+    const int nq = 2 * npts;
+    if (nq <= 0) return cudaSuccess;
+    rank_kernel<<<(nq + 7) / 8, 256, 0, st>>>(b0, b1, par, G, cells, y, nq, seed, t, stream, sigma, ranks);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sir_weights(const double* d, int ne, int nobs, const int* sets, int n_sets, int set_size,
                                double inv2R, double* w, int* kept, cudaStream_t st)

@@ -30,6 +30,12 @@ cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, c
 // of the innovations d [ne][nobs][2]: w [n_sets][ne], kept [n_sets]
 cudaError_t launch_sir_weights(const double* d, int ne, int nobs, const int* sets, int n_sets, int set_size,
                                double inv2R, double* w, int* kept, cudaStream_t st);
+// ranks [npts][2] of the observed (hu, hv) y [npts][2] at cells [npts][2]
+// among the members perturbed by sigma times normals of Philox stream
+// `stream`, draw t
+cudaError_t launch_rank(const float* b0, const float* b1, const int* par, const Grid& G, const int* cells,
+                        const double* y, int npts, uint64_t seed, uint32_t t, uint32_t stream, double sigma,
+                        int* ranks, cudaStream_t st);
 
 // ---- alpha_gamma.cu -------------------------------------------------------
 // alpha of the incomplete-gamma form of the implicit equation per particle

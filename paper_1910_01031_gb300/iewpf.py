@@ -24,7 +24,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_forecast_fixed", "iewpf_assimilate", "iewpf_set_drifters", "iewpf_get_drifters",
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
-           "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma",
+           "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma", "iewpf_rank",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
@@ -100,6 +100,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_assimilate.argtypes = [_vp, c.POINTER(Obs), c.POINTER(Diag)]
     L.iewpf_set_drifters.argtypes = [_vp, _dp, c.c_int]
     L.iewpf_sir_weights.argtypes = [_vp, c.POINTER(Obs), c.c_double, c.c_int, c.c_int, _ip, _dp, _ip]
+    L.iewpf_rank.argtypes = [_vp, c.c_int, _ip, _dp, c.c_uint32, _ip]
     L.iewpf_get_drifters.argtypes = [_vp, _dp]
     L.drifter_forecast.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, c.c_int]
     L.drifter_forecast_errors.argtypes = [_vp, _dp, c.c_int, c.c_double, c.c_double, _dp, _dp, _dp, _dp, c.c_int]
@@ -278,6 +279,18 @@ class Ensemble:
         self._chk(self.L.iewpf_sir_weights(self.h, ctypes.byref(obs), float(r_scale), sets.shape[0], sets.shape[1],
                                            _ptr(sets, _ip), _ptr(w), _ptr(kept, _ip)), "sir_weights")
         return w, kept
+
+    def rank(self, cells, values, draw):
+        """Ranks [n][2] of the observed (hu, hv) values [n][2] at integer
+        cells [n][2] among the members perturbed by the observation error."""
+        cells = np.ascontiguousarray(cells, np.int32).reshape(-1, 2)
+        values = _f64(values, (-1, 2))
+        if values.shape[0] != cells.shape[0]:
+            raise ValueError("one (hu, hv) pair per cell")
+        out = np.zeros(cells.shape, np.int32)
+        self._chk(self.L.iewpf_rank(self.h, cells.shape[0], _ptr(cells, _ip), _ptr(values), int(draw),
+                                    _ptr(out, _ip)), "rank")
+        return out
 
     def set_drifters(self, xy):
         xy = _f64(xy)

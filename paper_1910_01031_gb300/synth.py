@@ -104,6 +104,31 @@ def config3(seed: int = 3, **kw):
     return out
 
 
+def config_rank(**kw):
+    """The rank-histogram setup of Sec. 5.1 with the domain of Sec. 5: 500 x
+    300 cells of 2220 m, g = 9.806, f = 1.405e-4 1/s, Courant number 0.8,
+    q0 = 2.5e-4 m, c_omega = 5, L0 = 3/4 coarse cell; 40 particles, the
+    120 moorings of the western half."""
+    base = dict(dx=2220.0, dy=2220.0, g=9.806, f=1.405e-4, courant=0.8, q0=2.5e-4, c_omega=5,
+                n_particles=40, obs_kind=OBS_MOORING, n_obs=120)
+    base.update(kw)
+    return Config("rank_500x300", 500, 300, **base)
+
+
+def rank_moorings(cfg: Config):
+    """The western half of a 20 x 12 mooring lattice (240 moorings, Sec. 5):
+    10 x 12 = 120 cells, every nx/20 cells in x and ny/12 in y."""
+    sx, sy = cfg.nx // 20, cfg.ny // 12
+    return np.array([(sx // 2 + sx * p, sy // 2 + sy * q) for q in range(12) for p in range(10)], dtype=np.int32)
+
+
+def rank_cells(cfg: Config):
+    """Cells (100, y), y = 0, 50, ..., 250 (scaled to the grid), where the
+    ranks are taken (Sec. 5.1)."""
+    x = min(100, cfg.nx - 1)
+    return np.array([(x, y) for y in range(0, cfg.ny - 49, 50)], dtype=np.int32)
+
+
 def _jet(cfg: Config):
     Ly = cfg.ny * cfg.dy
     w = cfg.jet_width_cells * cfg.dy

@@ -1,15 +1,47 @@
 """Pins of the oracle's incomplete-gamma alpha (App. A, eq.
-numericalEqForAlpha): closed forms of the incomplete gamma function for
-N_psi = 2 and 4, a 50-digit solve with mpmath, alpha = 1 at c* = 0,
-monotonicity in c*, and agreement with the Lambert-W solution (eq.
-iewpfAlphaSol) once c* is large enough for the derivative term that the
-Lambert-W form drops to be negligible."""
+numericalEqForAlpha) and of its log P: closed forms of the incomplete gamma
+function for N_psi = 2 and 4, scipy's gammainc at moderate s, a 40-digit
+series at s = 1.57e6 (where scipy's gammainc is off by 1e-4 relative in the
+tail), a 50-digit solve with mpmath, alpha = 1 at c* = 0, monotonicity in c*,
+and agreement with the Lambert-W solution (eq. iewpfAlphaSol) once c* is
+large enough for the derivative term that the Lambert-W form drops to be
+negligible."""
 import math
 
 import numpy as np
 import pytest
 
 from oracle import oracle as O
+
+
+def test_log_p_closed_form_and_library_at_moderate_s():
+    from scipy.special import gammainc
+    # log P is a difference of terms of size s log x: it carries an absolute
+    # error of a few ulp of those (relative error of P itself)
+    for x in (1e-8, 0.3, 2.0, 17.0):
+        assert math.isclose(O.log_gamma_p(1.0, x), math.log(-math.expm1(-x)), rel_tol=1e-13, abs_tol=1e-13)
+    for s, x in ((5.0, 3.0), (30.0, 31.5), (500.0, 440.0), (500.0, 560.0)):
+        assert math.isclose(O.log_gamma_p(s, x), math.log(gammainc(s, x)), rel_tol=1e-12, abs_tol=1e-12)
+
+
+def test_log_p_at_large_s_against_a_forty_digit_series():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    s = mpmath.mpf(1572864)
+
+    def logp(x):
+        x = mpmath.mpf(x)
+        term = sm = mpmath.mpf(1)
+        n = 1
+        while term >= sm * mpmath.mpf(10) ** -45:
+            term *= x / (s + n)
+            sm += term
+            n += 1
+        return s * mpmath.log(x) - x - mpmath.loggamma(s + 1) + mpmath.log(sm)
+
+    # the median region and 6.3 standard deviations below it
+    for x in (1574639.7957679094, 1566766.59678907):
+        assert abs(O.log_gamma_p(1572864.0, x) - float(logp(x))) < 1e-8
 
 
 def test_two_dimensions_closed_form():
