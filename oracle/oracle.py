@@ -591,12 +591,12 @@ def alpha_incomplete_gamma(gamma, cstar, N_psi):
             continue
         target = log_gamma_p(s, 0.5 * g) - 0.5 * cs
         f = lambda a: log_gamma_p(s, 0.5 * a * g) - target
-        # bracket from alpha = 1 downwards
-        step, lo = 1e-9, 1.0 - 1e-9
+        # bracket [lo, hi] from alpha = 1 downwards, f(lo) < 0 <= f(hi)
+        step, hi, lo = 1e-9, 1.0, 1.0 - 1e-9
         while f(lo) >= 0.0:
+            hi = lo
             step *= 2.0
             lo = max(1.0 - step, 0.5 * lo) if step < 1.0 else 0.5 * lo
-        hi = 1.0
         for _ in range(200):
             mid = 0.5 * (lo + hi)
             if mid <= lo or mid >= hi:

@@ -46,8 +46,8 @@ def test_log_p_at_large_s_against_a_forty_digit_series():
 
 def test_two_dimensions_closed_form():
     # P(1, x) = 1 - exp(-x): alpha = -(2/gamma) log(1 - exp(-c*/2)(1 - exp(-gamma/2)))
-    g = np.array([0.3, 1.5, 3.0, 9.0])
-    cs = np.array([0.1, 0.7, 2.0, 30.0])
+    g = np.array([0.3, 1.5, 3.0, 9.0, 2.2])
+    cs = np.array([0.1, 0.7, 2.0, 30.0, 300.0])         # the last: alpha near 1e-66
     ref = -(2.0 / g) * np.log1p(-np.exp(-cs / 2) * -np.expm1(-g / 2))
     assert np.allclose(O.alpha_incomplete_gamma(g, cs, 2.0), ref, rtol=1e-12, atol=0)
 
