@@ -395,6 +395,14 @@ IEWPF_API int iewpf_batch_tune(iewpf_batch_t* b, int* shape);
  * being c_bar for the two-stage scheme.  Returns the
  * first problem's error, if any. */
 IEWPF_API int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* obs, double* diag);
+
+/* A free forecast of every problem (eq. model_equation without
+ * assimilation): n_model_steps >= 1 model steps, model error after each when
+ * add_model_error, as one CUDA graph (kept for repeated calls with the same
+ * arguments).  The states and draw counters advance exactly as n_model_steps
+ * steps of iewpf_forecast on each problem would.  Returns the first
+ * problem's error (ENONFINITE for a non-finite state), if any. */
+IEWPF_API int iewpf_batch_forecast(iewpf_batch_t* b, int n_model_steps, int add_model_error);
 IEWPF_API int iewpf_batch_stream(const iewpf_batch_t* b, void** stream);
 
 /* Particle scheme steps executed by the batch and kernel launches it

@@ -1562,6 +1562,35 @@ int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* ob
     return rc;
 }
 
+int iewpf_batch_forecast(iewpf_batch_t* b, int n_model_steps, int add_model_error)
+{
+    if (!b) return IEWPF_EINVAL;
+    if (n_model_steps < 1) return bfail(b, IEWPF_EINVAL, "n_model_steps < 1");
+    const int n = (int)b->inst.size();
+    BCK(cudaSetDevice(b->dev));
+    if (!batch_tuned(*b->impl)) BCK(batch_tune(*b->impl, b->st));
+    uint32_t* ctr = batch_counter_staging(*b->impl);
+    for (int i = 0; i < n; ++i) {
+        ctr[2 * i] = b->inst[i]->step;
+        ctr[2 * i + 1] = b->inst[i]->cycle;
+        b->inst[i]->cfl_ready = false;
+    }
+    BCK(batch_forecast(*b->impl, n_model_steps, add_model_error != 0, b->st, b->st2));
+    BCK(cudaStreamSynchronize(b->st));
+    const double* dg = batch_diag(*b->impl);
+    int rc = IEWPF_OK;
+    for (int i = 0; i < n; ++i) {
+        iewpf_ctx* c = b->inst[i];
+        c->step += (uint32_t)n_model_steps;
+        const int f = (int)dg[3 * i + 2];
+        if (f && rc == IEWPF_OK) {
+            rc = check_flags(c, f);
+            b->err = "problem " + std::to_string(i) + ": " + c->err;
+        }
+    }
+    return rc;
+}
+
 int iewpf_batch_stream(const iewpf_batch_t* b, void** stream)
 {
     if (!b || !stream) return IEWPF_EINVAL;

@@ -401,6 +401,10 @@ struct BatchImpl {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_steps = -1;
+    cudaGraph_t fgraph = nullptr;     // forecast-only graph
+    cudaGraphExec_t fexec = nullptr;
+    int fgraph_steps = -1;
+    bool fgraph_err = false;
     int nc = 2;
     int warps = 4;
     int fixed = 0;
@@ -529,6 +533,8 @@ void batch_delete(BatchImpl* b)
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->fexec) cudaGraphExecDestroy(b->fexec);
+    if (b->fgraph) cudaGraphDestroy(b->fgraph);
     void* d[] = {b->d_inst, b->d_pre, b->d_s, b->d_maxsub, b->d_work, b->d_obs, b->d_diag, b->d_ctr};
     for (void* p : d)
         if (p) cudaFree(p);
@@ -672,6 +678,49 @@ cudaError_t batch_cycle(BatchImpl& b, int n_steps, cudaStream_t st, cudaStream_t
         b.graph_steps = n_steps;
     }
     return cudaGraphLaunch(b.exec, st);
+}
+
+// Captures (if needed) and launches a free forecast: n_steps model steps of
+// every problem, model error after each when err, then the non-finite scan
+// and the flags into the diagnostics buffer (w_target and beta untouched).
+cudaError_t batch_forecast(BatchImpl& b, int n_steps, bool err, cudaStream_t st, cudaStream_t st2)
+{
+    cudaError_t e;
+    if (!b.fexec || b.fgraph_steps != n_steps || b.fgraph_err != err) {
+        if (b.fexec) {
+            cudaGraphExecDestroy(b.fexec);
+            b.fexec = nullptr;
+        }
+        if (b.fgraph) {
+            cudaGraphDestroy(b.fgraph);
+            b.fgraph = nullptr;
+        }
+        auto abandon = [&](cudaError_t err_) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(st, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            return err_;
+        };
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(b.d_ctr, b.h_ctr, sizeof(uint32_t) * 2 * b.n, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return abandon(e);
+        for (int k = 0; k < n_steps; ++k)
+            if ((e = capture_model_step(b, st, st2, err, err && k > 0)) != cudaSuccess) return abandon(e);
+        const BatchDev B = dev_view(b);
+        b_nonfinite<<<grid_for(b_nonfinite, NTHREADS, items(b, SP_CFL)), NTHREADS, 0, st>>>(B);
+        b_pack_diag<<<(b.n + 127) / 128, 128, 0, st>>>(B, b.d_diag);
+        b.launches += 2;
+        if ((e = cudaGetLastError()) != cudaSuccess) return abandon(e);
+        if ((e = cudaMemcpyAsync(b.h_diag, b.d_diag, sizeof(double) * 3 * b.n, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+            return abandon(e);
+        if ((e = cudaStreamEndCapture(st, &b.fgraph)) != cudaSuccess) return e;
+        if ((e = cudaGraphInstantiate(&b.fexec, b.fgraph, 0)) != cudaSuccess) return e;
+        b.fgraph_steps = n_steps;
+        b.fgraph_err = err;
+    }
+    return cudaGraphLaunch(b.fexec, st);
 }
 
 // Times one scheme step of every problem for each candidate shape and keeps

@@ -73,6 +73,7 @@ cudaError_t batch_init(BatchImpl& b, const std::vector<BInst>& insts);
 cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps);
 cudaError_t batch_tune(BatchImpl& b, cudaStream_t st);
 cudaError_t batch_cycle(BatchImpl& b, int n_steps, cudaStream_t st, cudaStream_t st2);
+cudaError_t batch_forecast(BatchImpl& b, int n_steps, bool err, cudaStream_t st, cudaStream_t st2);
 double* batch_obs_staging(BatchImpl& b, int i);
 uint32_t* batch_counter_staging(BatchImpl& b);
 const double* batch_diag(const BatchImpl& b);

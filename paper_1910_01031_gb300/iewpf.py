@@ -25,6 +25,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma", "iewpf_rank",
+           "iewpf_batch_forecast",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
@@ -133,6 +134,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_batch_instance.argtypes = [_vp, c.c_int, c.POINTER(c.c_void_p)]
     L.iewpf_batch_tune.argtypes = [_vp, _ip]
     L.iewpf_batch_cycle.argtypes = [_vp, c.c_int, c.POINTER(Obs), _dp]
+    L.iewpf_batch_forecast.argtypes = [_vp, c.c_int, c.c_int]
     L.iewpf_batch_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
     L.iewpf_batch_work.argtypes = [_vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
     L.iewpf_batch_last_error.argtypes = [_vp]
@@ -471,6 +473,10 @@ class Batch:
         s = ctypes.c_void_p()
         self._chk(self.L.iewpf_batch_stream(self.h, ctypes.byref(s)), "batch_stream")
         return s.value or 0
+
+    def forecast(self, n_steps, add_model_error=True):
+        """A free forecast of every problem as one CUDA graph."""
+        self._chk(self.L.iewpf_batch_forecast(self.h, int(n_steps), int(bool(add_model_error))), "batch_forecast")
 
     def work(self):
         w, l = ctypes.c_int64(), ctypes.c_int64()

@@ -100,11 +100,9 @@ def run(experiments=64, ne=40, hours_da=1.0, hours_fc=1.0, scheme=iewpf.TWO_STAG
     work_da = batch.work()[0] - work0
     t1 = time.perf_counter()
     truth.forecast(n_fc, True)
-    fc_work = 0
-    for inst in batch.instances:
-        before = inst.work()
-        inst.forecast(n_fc, True)
-        fc_work += inst.work() - before
+    before = batch.work()[0]
+    batch.forecast(n_fc, True)
+    fc_work = batch.work()[0] - before
     truth.get_state(TU)
     vals = _values_at(torch, TU, cells)
     ranks = np.zeros((experiments, len(cells), 2), np.int64)

@@ -68,6 +68,29 @@ def test_batched_cycles_equal_one_by_one():
     assert work > 0 and launches > 0
 
 
+def test_batched_forecast_equals_one_by_one():
+    cfgs, params, moor = _problems()
+    batch = iewpf.Batch(params, moor)
+    singles = [iewpf.Ensemble(p, mooring_xy=m) for p, m in zip(params, moor)]
+    for i, c in enumerate(cfgs):
+        U = synth.initial_state(c, c.n_particles, seed=50 + i).astype(np.float32)
+        batch.instances[i].set_state(U)
+        singles[i].set_state(U)
+    obs = [_obs(c, 0) for c in cfgs]
+    batch.cycle(5, obs)
+    for i, s in enumerate(singles):
+        s.forecast(4, True)
+        s.forecast(1, False)
+        s.assimilate(obs[i][0], obs[i][1])
+    for err, steps in ((True, 7), (True, 7), (False, 3)):     # the second call replays the graph
+        batch.forecast(steps, err)
+        for i, s in enumerate(singles):
+            s.forecast(steps, err)
+            a, b = batch.instances[i].get_state(), s.get_state()
+            assert np.array_equal(a, b), (err, i, np.abs(a - b).max())
+            assert batch.instances[i].counters() == s.counters()
+
+
 def test_batched_cycle_matches_oracle():
     """Instance 0 draws from the oracle's streams (0, 1, 2)."""
     cfgs, params, moor = _problems()
