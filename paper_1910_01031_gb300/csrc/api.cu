@@ -9,12 +9,39 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/iewpf.h"
 #include "common.cuh"
 #include "batch.h"
 #include "kernels.h"
 #include "surrogate.h"
 #include <random>
+
+namespace {
+// NVTX ranges (domain "iewpf") around each phase of the C ABI, for profilers
+// and for filtering a capture to one phase; free when no tool is attached.
+nvtxDomainHandle_t nvtx_domain()
+{
+    static nvtxDomainHandle_t d = nvtxDomainCreateA("iewpf");
+    return d;
+}
+
+struct Phase {
+    explicit Phase(const char* name)
+    {
+        nvtxEventAttributes_t a = {};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(nvtx_domain(), &a);
+    }
+    ~Phase() { nvtxDomainRangePop(nvtx_domain()); }
+    Phase(const Phase&) = delete;
+    Phase& operator=(const Phase&) = delete;
+};
+}  // namespace
 
 using namespace iewpf;
 
@@ -556,6 +583,7 @@ extern "C" {
 
 int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_ctx_t** out)
 {
+    Phase phase_("create");
     if (!params || !out) return IEWPF_EINVAL;
     *out = nullptr;
     const iewpf_params_t& P = *params;
@@ -753,11 +781,13 @@ int iewpf_get_state(iewpf_ctx_t* ctx, float* dst, int on_device, void* stream)
 
 int iewpf_forecast(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error)
 {
+    Phase phase_("forecast");
     return forecast_impl(ctx, n_model_steps, add_model_error, 0);
 }
 
 int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error, int n_sub)
 {
+    Phase phase_("forecast");
     if (!ctx) return IEWPF_EINVAL;
     if (n_sub < 1) return fail(ctx, IEWPF_EINVAL, "n_sub < 1");
     return forecast_impl(ctx, n_model_steps, add_model_error, n_sub);
@@ -765,6 +795,7 @@ int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_model_erro
 
 int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* diag)
 {
+    Phase phase_("assimilate");
     if (!ctx) return IEWPF_EINVAL;
     if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max || !obs->value)
         return fail(ctx, IEWPF_EINVAL, "bad observation set");
@@ -780,11 +811,15 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     }
     CK(cudaMemcpyAsync(ctx->d_obs_y, obs->value, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
     // 1-2: innovations, S d, phi
-    KL(1, launch_innovate(ctx->buf[0], ctx->buf[1], ctx->par, ctx->d_cell, ctx->d_obs_y, nobs, ctx->G,
-                       ctx->P.H_eq, ctx->d_d, ctx->st));
-    if (!mooring && (rc = factor(ctx, nobs))) return rc;
-    KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, n, ctx->d_d, ctx->d_Sd, ctx->d_phi, ne, ctx->st));
+    {
+        Phase sub_("innovations");
+        KL(1, launch_innovate(ctx->buf[0], ctx->buf[1], ctx->par, ctx->d_cell, ctx->d_obs_y, nobs, ctx->G,
+                           ctx->P.H_eq, ctx->d_d, ctx->st));
+        if (!mooring && (rc = factor(ctx, nobs))) return rc;
+        KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, n, ctx->d_d, ctx->d_Sd, ctx->d_phi, ne, ctx->st));
+    }
     // 3: random vectors
+    Phase sub_("weights_and_update");
     const uint32_t sb = 16u * (uint32_t)ctx->P.instance_id;
     KL(1, launch_rand_dots(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_partial,
                         ctx->dots_blk, ctx->st));
@@ -840,6 +875,7 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
 int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, int n_sets, int set_size,
                       const int* sets, double* w, int* n_kept)
 {
+    Phase phase_("sir_weights");
     if (!ctx) return IEWPF_EINVAL;
     if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max || !obs->value)
         return fail(ctx, IEWPF_EINVAL, "bad observation set");
@@ -893,6 +929,7 @@ int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, 
 
 int iewpf_rank(iewpf_ctx_t* ctx, int n_pts, const int* cells, const double* y, uint32_t draw, int* ranks)
 {
+    Phase phase_("rank");
     if (!ctx) return IEWPF_EINVAL;
     if (n_pts < 1 || !cells || !y || !ranks) return fail(ctx, IEWPF_EINVAL, "bad rank points");
     for (int m = 0; m < n_pts; ++m)
@@ -958,6 +995,7 @@ int iewpf_get_drifters(iewpf_ctx_t* ctx, double* xy)
 int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s, double* traj,
                      int use_surrogate)
 {
+    Phase phase_("drifter_forecast");
     if (!ctx) return IEWPF_EINVAL;
     if (use_surrogate && !ctx->sur) return fail(ctx, IEWPF_EINVAL, "no surrogate attached (iewpf_set_surrogate)");
     if (!xy0 || !traj || n < 1 || n > ctx->P.n_drifters_max || !(hours >= 0) || !(out_every_s > 0))
@@ -991,6 +1029,7 @@ int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, d
 int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s,
                             const double* truth, double* E, double* RMSE, double* traj, int use_surrogate)
 {
+    Phase phase_("drifter_forecast");
     if (!ctx) return IEWPF_EINVAL;
     if (!xy0 || !truth || !E || !RMSE || n < 1 || n > ctx->P.n_drifters_max || !(hours >= 0) || !(out_every_s > 0))
         return fail(ctx, IEWPF_EINVAL, "bad drifter forecast arguments");
@@ -1210,6 +1249,7 @@ int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, co
 
 int iewpf_alpha_gamma(int ne, double N_psi, const double* gamma, const double* cstar, double* alpha)
 {
+    Phase phase_("alpha_gamma");
     if (ne < 1 || !(N_psi > 0) || !std::isfinite(N_psi) || !gamma || !cstar || !alpha) return IEWPF_EINVAL;
     for (int i = 0; i < ne; ++i)
         if (!(gamma[i] > 0) || !std::isfinite(gamma[i]) || !(cstar[i] >= 0) || !std::isfinite(cstar[i]))
@@ -1411,6 +1451,7 @@ int iewpf_batch_destroy(iewpf_batch_t* b)
 
 int iewpf_batch_create(const iewpf_params_t* params, const double* const* mooring_xy, int n, iewpf_batch_t** out)
 {
+    Phase phase_("batch_create");
     if (!params || !out || n < 1) return IEWPF_EINVAL;
     *out = nullptr;
     iewpf_batch* b = new (std::nothrow) iewpf_batch();
@@ -1521,6 +1562,7 @@ int iewpf_batch_tune(iewpf_batch_t* b, int* shape)
 
 int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* obs, double* diag)
 {
+    Phase phase_("batch_cycle");
     if (!b) return IEWPF_EINVAL;
     if (n_model_steps < 1 || !obs) return bfail(b, IEWPF_EINVAL, "bad cycle arguments");
     const int n = (int)b->inst.size();
@@ -1564,6 +1606,7 @@ int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* ob
 
 int iewpf_batch_forecast(iewpf_batch_t* b, int n_model_steps, int add_model_error)
 {
+    Phase phase_("batch_forecast");
     if (!b) return IEWPF_EINVAL;
     if (n_model_steps < 1) return bfail(b, IEWPF_EINVAL, "n_model_steps < 1");
     const int n = (int)b->inst.size();
@@ -1744,6 +1787,7 @@ int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, dou
 
 int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Unext)
 {
+    Phase phase_("surrogate_apply");
     if (!s || !U || !Unext || n < 1) return IEWPF_EINVAL;
     SCK(cudaSetDevice(s->dev));
     const size_t per = 3ull * s->net.nx * s->net.ny;
@@ -1765,6 +1809,7 @@ int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Un
 
 int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, float* Unext, void* stream)
 {
+    Phase phase_("surrogate_apply");
     if (!s || !U || !Unext || n < 1) return IEWPF_EINVAL;
     SCK(cudaSetDevice(s->dev));
     const size_t per = 3ull * s->net.nx * s->net.ny;
@@ -1826,6 +1871,7 @@ int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, const float*
 int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs, int batch,
                           double lr, double* epoch_loss)
 {
+    Phase phase_("surrogate_train");
     if (!s || !ctx || n_pairs < 1 || k_steps < 1 || epochs < 0 || batch < 1 || !(lr > 0)) return IEWPF_EINVAL;
     if (ctx->P.nx != s->net.nx || ctx->P.ny != s->net.ny) return sfail(s, IEWPF_EINVAL, "grid mismatch");
     SCK(cudaSetDevice(s->dev));
