@@ -292,7 +292,9 @@ def run_ours(args, rank, world, local):
         "rank_histogram": ranks,
         "cpu_baseline": cpu,
         "clocks": clk,
-        "last_beta": d["beta"] if d else None,
+        "last_cycle": {"beta": d["beta"], "c_bar": d["cbar"], "alpha_min": float(np.min(d["alpha"])),
+                       "alpha_max": float(np.max(d["alpha"])),
+                       "neglogw_spread": float(np.max(d["neglogw"]) - np.min(d["neglogw"]))} if d else None,
     }
     print(json.dumps(line), flush=True)
 

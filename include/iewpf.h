@@ -159,10 +159,13 @@ IEWPF_API int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_
  * perpendicular random vectors and gamma_i, zeta_i, the ensemble-wide
  * target weight and beta, alpha_i from the Lambert W function, and one
  * fused update psi <- psi + Q H^T S d + P^{1/2}(beta^{1/2} nu + alpha^{1/2}
- * xi) (eq. optUpdateEquationTwoStage).  Random draws use the context's
- * cycle counter, which then advances by one.  diag may be NULL.
- * Errors: EINVAL (n_obs > n_obs_max, NULL values), EBETA, EDOMAIN,
- * ENONFINITE, ENOTPD, ECUDA. */
+ * xi) (eq. optUpdateEquationTwoStage); with params.scheme = IEWPF_ONE_STAGE
+ * the one-stage analysis of App. A instead (w_target = max c_i, no nu).
+ * Random draws use the context's cycle counter, which then advances by one.
+ * diag may be NULL.
+ * Errors: EINVAL (n_obs > n_obs_max, NULL values, a non-finite observed
+ * value or position: refused before any device work, the state unchanged),
+ * EBETA, EDOMAIN, ENONFINITE, ENOTPD, ECUDA. */
 IEWPF_API int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* diag);
 
 /* Weights of the standard particle filter (Sec. 2.1, eqs.

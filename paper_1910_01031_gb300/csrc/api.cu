@@ -160,6 +160,15 @@ int dalloc(iewpf_ctx* ctx, T** p, size_t n)
 
 int coarse_count(int n, int c) { return (n - 1 - c / 2) / c + 1; }
 
+// every observed value (and position, where given) finite: corrupted
+// observations are refused before any device work
+bool obs_finite(const iewpf_obs_t& o)
+{
+    for (int k = 0; k < 2 * o.n_obs; ++k)
+        if (!std::isfinite(o.value[k]) || (o.xy && !std::isfinite(o.xy[k]))) return false;
+    return true;
+}
+
 double soar(double d, double q0, double L0) { return q0 * (1.0 + d / L0) * std::exp(-d / L0); }
 
 // Catmull-Rom weights of taps a-1 .. a+2
@@ -803,6 +812,7 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     if (!mooring && !obs->xy) return fail(ctx, IEWPF_EINVAL, "drifter observations need positions");
     if (mooring && obs->n_obs != ctx->nobs_max)
         return fail(ctx, IEWPF_EINVAL, "mooring observations must cover every mooring");
+    if (!obs_finite(*obs)) return fail(ctx, IEWPF_EINVAL, "non-finite observation value or position");
     CK(cudaSetDevice(ctx->dev));
     const int nobs = obs->n_obs, n = 2 * nobs, ne = ctx->G.ne;
     int rc;
@@ -883,6 +893,7 @@ int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, 
     if (!mooring && !obs->xy) return fail(ctx, IEWPF_EINVAL, "drifter observations need positions");
     if (mooring && obs->n_obs != ctx->nobs_max)
         return fail(ctx, IEWPF_EINVAL, "mooring observations must cover every mooring");
+    if (!obs_finite(*obs)) return fail(ctx, IEWPF_EINVAL, "non-finite observation value or position");
     const int nobs = obs->n_obs, ne = ctx->G.ne;
     if (!(r_scale > 0) || !std::isfinite(r_scale) || n_sets < 0 || set_size < 1 || set_size > nobs ||
         (n_sets > 0 && (!sets || !n_kept)))
@@ -1571,6 +1582,8 @@ int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* ob
         const bool mooring = c->P.obs_kind == IEWPF_OBS_MOORING;
         if (obs[i].n_obs != c->nobs_max || !obs[i].value || (!mooring && !obs[i].xy))
             return bfail(b, IEWPF_EINVAL, "problem " + std::to_string(i) + ": observations must fill n_obs_max");
+        if (!obs_finite(obs[i]))
+            return bfail(b, IEWPF_EINVAL, "problem " + std::to_string(i) + ": non-finite observation");
     }
     BCK(cudaSetDevice(b->dev));
     if (!batch_tuned(*b->impl)) BCK(batch_tune(*b->impl, b->st));

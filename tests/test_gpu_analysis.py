@@ -229,3 +229,47 @@ def test_cfl_rates_left_by_the_updates_match_a_fresh_pass():
     b.forecast(3, True)
     assert np.array_equal(a.last_nsub(), b.last_nsub())
     assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_corrupted_observations_are_refused_and_leave_the_state():
+    cfg = synth.config1(n_particles=4, n_obs=2)
+    ens = ensemble(cfg)
+    U = synth.initial_state(cfg, 4, seed=2).astype(np.float32)
+    ens.set_state(U)
+    xy = synth.drifter_positions(cfg)
+    y = np.ones((2, 2))
+    for bad_xy, bad_y in ((xy, np.array([[1.0, np.nan], [0.0, 0.0]])),
+                          (np.array([[np.inf, 3e4], [5e4, 5e4]]), y)):
+        with pytest.raises(iewpf.IewpfError) as e:
+            ens.assimilate(bad_xy, bad_y)
+        assert e.value.name == "EINVAL"
+        assert np.array_equal(ens.get_state(), U)
+        assert ens.counters() == (0, 0)
+    ens.assimilate(xy, y)                      # still usable
+    assert ens.counters() == (0, 1)
+
+
+def test_weights_step_reports_domain_and_nonfinite_inputs():
+    c = np.array([3.0, 4.0, 5.0])
+    z = np.array([60.0, 60.0, 60.0])
+    with pytest.raises(iewpf.IewpfError) as e:       # gamma < 0: Lambert-W argument out of its domain
+        iewpf.weights(c, np.array([50.0, -5.0, 55.0]), z, 60.0)
+    assert e.value.name == "EDOMAIN"
+    with pytest.raises(iewpf.IewpfError) as e:
+        iewpf.weights(np.array([3.0, np.nan, 5.0]), np.array([50.0, 52.0, 55.0]), z, 60.0)
+    assert e.value.name == "ENONFINITE"
+    with pytest.raises(iewpf.IewpfError) as e:
+        iewpf.weights_one_stage(c, np.array([50.0, -5.0, 55.0]), 60.0)
+    assert e.value.name == "EDOMAIN"
+
+
+def test_device_allocation_failure_is_reported():
+    # about 13 TB of state: cudaMalloc refuses it, create returns ENOMEM
+    cfg = synth.Config("huge", 16384, 16384, n_particles=2000)
+    with pytest.raises(iewpf.IewpfError) as e:
+        iewpf.Ensemble(iewpf.params_from_config(cfg))
+    assert e.value.name == "ENOMEM"
+    # the device is still usable afterwards
+    small = ensemble(synth.config1(n_particles=2))
+    small.set_state(synth.initial_state(synth.config1(), 2).astype(np.float32))
+    small.forecast(1, True)
