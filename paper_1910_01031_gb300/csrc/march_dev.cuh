@@ -38,17 +38,34 @@ __device__ __forceinline__ float frsqrt(float x)
 }
 __device__ __forceinline__ float fsqrt(float x) { return x * frsqrt(x); }
 
+// three-input minimum and maximum (one instruction each on sm_100 and later)
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float y;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+    return y;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float y;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+    return y;
+}
+
 // twice the generalized minmod(theta a, (a + b)/2, theta b), i.e. the
-// minmod of (2 theta a, a + b, 2 theta b) with th2 = 2 theta: the smallest of
-// the three when all are positive, the largest when all are negative, else 0,
-// written as max(min, 0) + min(max, 0) (one of the two terms is always zero).
-// Every use scales the slope by a power of two, so carrying 2 sigma is exact.
+// minmod of (x, y, z) = (2 theta a, a + b, 2 theta b), from the scaled
+// differences x, z and the sum y: the smallest of the three when all are
+// positive, the largest when all are negative, else 0 -- the median of
+// (min, 0, max), max(min, min(max, 0)).  Every use scales the slope by a power
+// of two, so carrying 2 sigma is exact.
+__device__ __forceinline__ float gmm2s(float x, float y, float z)
+{
+    return fmaxf(fmin3(x, y, z), fminf(fmax3(x, y, z), 0.0f));
+}
+
 __device__ __forceinline__ float gmm2(float a, float b, float th2)
 {
-    const float x = th2 * a, y = a + b, z = th2 * b;   // no contraction here
-    const float mn = fminf(x, fminf(y, z));
-    const float mx = fmaxf(x, fmaxf(y, z));
-    return fmaxf(mn, 0.0f) + fminf(mx, 0.0f);
+    return gmm2s(th2 * a, a + b, th2 * b);   // no contraction here
 }
 
 // central-upwind flux, normal momentum qn, tangential qt carried by the mass
@@ -60,8 +77,8 @@ __device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, f
     const float rL = frcp(hL), rR = frcp(hR);
     const float unL = qnL * rL, unR = qnR * rR;
     const float cL = fsqrt(G.g * hL), cR = fsqrt(G.g * hR);
-    const float ap = fmaxf(fmaxf(unL + cL, unR + cR), 0.0f);
-    const float am = fminf(fminf(unL - cL, unR - cR), 0.0f);
+    const float ap = fmax3(unL + cL, unR + cR, 0.0f);
+    const float am = fmin3(unL - cL, unR - cR, 0.0f);
     const float inv = frcp(ap - am);
     const float apam = ap * am;
     F0 = fmaf(apam, eR - eL, fmaf(ap, qnL, -(am * qnR))) * inv;
@@ -78,6 +95,7 @@ struct Marcher {
     // rolling window: 0 = oldest (row being emitted), 1, 2 = newest
     float e[3][NC], qu[3][NC], qv[3][NC], u[3][NC];
     float dLp[NC];                  // dL on the face between rows 0 and 1
+    float tLp[NC], tup[NC], tvp[NC]; // 2 theta times the differences on that face (dL, hu, hv)
     float sL[NC], su[NC], sv[NC];   // y-slopes of row 0 (twice their value)
     float G0[NC], Gu[NC], Gv[NC];   // y-flux on the face below row 0
 
@@ -88,6 +106,7 @@ struct Marcher {
 #pragma unroll
             for (int r = 0; r < 3; ++r) e[r][k] = qu[r][k] = qv[r][k] = u[r][k] = 0.0f;
             dLp[k] = sL[k] = su[k] = sv[k] = G0[k] = Gu[k] = Gv[k] = 0.0f;
+            tLp[k] = tup[k] = tvp[k] = 0.0f;
         }
     }
 
@@ -107,9 +126,12 @@ struct Marcher {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float dLn = fmaf(G.fdy_half, u[1][k] + u[2][k], G.g * (e[2][k] - e[1][k]));
-            const float s1L = gmm2(dLp[k], dLn, G.theta2);
-            const float s1u = gmm2(qu[1][k] - qu[0][k], qu[2][k] - qu[1][k], G.theta2);
-            const float s1v = gmm2(qv[1][k] - qv[0][k], qv[2][k] - qv[1][k], G.theta2);
+            const float dun = qu[2][k] - qu[1][k], dvn = qv[2][k] - qv[1][k];
+            const float tLn = G.theta2 * dLn, tun = G.theta2 * dun, tvn = G.theta2 * dvn;
+            const float s1L = gmm2s(tLp[k], dLp[k] + dLn, tLn);
+            const float s1u = gmm2s(tup[k], (qu[1][k] - qu[0][k]) + dun, tun);
+            const float s1v = gmm2s(tvp[k], (qv[1][k] - qv[0][k]) + dvn, tvn);
+            tLp[k] = tLn; tup[k] = tun; tvp[k] = tvn;
             const float eB = fmaf(fmaf(-G.fdy2, u[0][k], sL[k]), G.inv_4g, e[0][k]);
             const float eT = fmaf(fmaf(-G.fdy2, u[1][k], s1L), -G.inv_4g, e[1][k]);
             float g0, gv, gu;
@@ -137,15 +159,24 @@ struct Marcher {
         QU[NC + 1] = __shfl_down_sync(FULL, QU[1], 1);
         QV[NC + 1] = __shfl_down_sync(FULL, QV[1], 1);
         V[NC + 1] = __shfl_down_sync(FULL, V[1], 1);
-        float dK[NC + 1];
+        // differences on the faces f = 0..NC (left of column f) and their
+        // 2 theta multiples, each formed once and shared by both neighbours
+        float dK[NC + 1], dU[NC + 1], dV[NC + 1], tK[NC + 1], tU[NC + 1], tV[NC + 1];
 #pragma unroll
-        for (int f = 0; f <= NC; ++f) dK[f] = fmaf(-G.fdx_half, V[f] + V[f + 1], G.g * (E[f + 1] - E[f]));
+        for (int f = 0; f <= NC; ++f) {
+            dK[f] = fmaf(-G.fdx_half, V[f] + V[f + 1], G.g * (E[f + 1] - E[f]));
+            dU[f] = QU[f + 1] - QU[f];
+            dV[f] = QV[f + 1] - QV[f];
+            tK[f] = G.theta2 * dK[f];
+            tU[f] = G.theta2 * dU[f];
+            tV[f] = G.theta2 * dV[f];
+        }
         float eE[NC], eW[NC], uE[NC], uW[NC], vE[NC], vW[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            const float sK = gmm2(dK[k], dK[k + 1], G.theta2);
-            const float sU = gmm2(QU[k + 1] - QU[k], QU[k + 2] - QU[k + 1], G.theta2);
-            const float sV = gmm2(QV[k + 1] - QV[k], QV[k + 2] - QV[k + 1], G.theta2);
+            const float sK = gmm2s(tK[k], dK[k] + dK[k + 1], tK[k + 1]);
+            const float sU = gmm2s(tU[k], dU[k] + dU[k + 1], tU[k + 1]);
+            const float sV = gmm2s(tV[k], dV[k] + dV[k + 1], tV[k + 1]);
             const float ex = fmaf(G.fdx2, V[k + 1], sK) * G.inv_4g;
             eE[k] = E[k + 1] + ex; eW[k] = E[k + 1] - ex;
             uE[k] = fmaf(0.25f, sU, QU[k + 1]); uW[k] = fmaf(-0.25f, sU, QU[k + 1]);
