@@ -507,9 +507,11 @@ def lambert_w0_branch(q):
     return -u
 
 
-def iewpf_scalars(c, gamma, zeta, N_psi):
+def iewpf_scalars(c, gamma, zeta, N_psi, only=None):
     """Target weight, beta, c* and alpha of the two-stage IEWPF
     (App. A: eqs. cistarTwoStage, betaTwoStage, iewpfAlphaSol).
+    only: indices whose alpha is solved (all when None; the others are NaN),
+    for large ensembles checked on samples.
 
     Returns dict with cbar, beta, cstar[i], alpha[i], neglogw[i]."""
     c = np.asarray(c, np.float64)
@@ -519,8 +521,8 @@ def iewpf_scalars(c, gamma, zeta, N_psi):
     cbar = float(np.sum(c) / ne)                     # w_target = mean c_i
     beta = float(np.min((cbar - c) / zeta + 1.0))    # eq. betaTwoStage
     cstar = cbar - c - (beta - 1.0) * zeta           # eq. cistarTwoStage
-    alpha = np.empty(ne)
-    for i in range(ne):
+    alpha = np.full(ne, np.nan)
+    for i in (range(ne) if only is None else only):
         x = gamma[i] / N_psi
         # W_0 argument -x e^{-x} e^{-c*/N} = -exp(-1 - q)
         q = ((x - 1.0) - math.log1p(x - 1.0)) + max(cstar[i], 0.0) / N_psi
@@ -659,11 +661,14 @@ def block_indices(P: Problem, cell):
                      for q in range(-3, 4) for p in range(-3, 4)])
 
 
-def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0, one_stage=False):
+def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0, one_stage=False, scalars=None):
     """One two-stage IEWPF analysis of the forecast ensemble (Sec. 4, steps
     1-6), or with one_stage=True the one-stage IEWPF of App. A (eq.
-    iewpfUpdateAgain: the same steps without nu).  Returns (new ensemble,
-    diagnostics dict)."""
+    iewpfUpdateAgain: the same steps without nu).  scalars: the ensemble-wide
+    step's results (dict with beta and alpha for these particles) taken as
+    given instead of computed from this ensemble, so that particles of a
+    large ensemble can be updated one by one (particle ids p0, p0 + 1, ...).
+    Returns (new ensemble, diagnostics dict)."""
     ens = np.array(ens, np.float64, order="C")
     ne = ens.shape[0]
     cells = [tuple(int(v) for v in cl) for cl in cells]
@@ -680,7 +685,10 @@ def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0,
     # 3: perpendicular random vectors
     rv = rand_vectors(P, ne, t, p0)
     # 4-5: target weight, beta, alpha
-    if one_stage:
+    if scalars is not None:
+        sc = {"beta": float(scalars["beta"]), "alpha": np.asarray(scalars["alpha"], np.float64)}
+        r = math.sqrt(sc["beta"]) * rv["nu"] + np.sqrt(sc["alpha"])[:, None] * rv["xi"]
+    elif one_stage:
         sc = iewpf_scalars_one_stage(c, rv["gamma"], P.N_psi)
         # 6: posterior (eq. iewpfUpdateAgain): psi^a + P^{1/2} a^.5 xi
         r = np.sqrt(sc["alpha"])[:, None] * rv["xi"]

@@ -273,3 +273,23 @@ def test_device_allocation_failure_is_reported():
     small = ensemble(synth.config1(n_particles=2))
     small.set_state(synth.initial_state(synth.config1(), 2).astype(np.float32))
     small.forecast(1, True)
+
+
+@pytest.mark.parametrize("scheme", [iewpf.TWO_STAGE, iewpf.ONE_STAGE])
+def test_single_particle_analysis_matches_oracle(scheme):
+    # N_e = 1: the target is the particle's own c, beta = 1 (two-stage) or 0
+    # (one-stage), c* = 0
+    cfg = synth.config1(n_particles=1, n_obs=2)
+    P = oracle_problem(cfg)
+    U32, U64 = start_state(cfg, 1, seed=3)
+    ens = iewpf.Ensemble(iewpf.params_from_config(cfg, scheme=scheme))
+    ens.set_state(U32)
+    xy = synth.drifter_positions(cfg)
+    cells = [O.obs_cell(P, *p) for p in xy]
+    y = _obs_for(cfg, synth.initial_state(cfg, 1, seed=99)[0], np.array(cells))
+    dg = ens.assimilate(xy, y)
+    ref, do = O.assimilate(P, U64, cells, y, t=0, one_stage=scheme == iewpf.ONE_STAGE)
+    assert dg["beta"] == (1.0 if scheme == iewpf.TWO_STAGE else 0.0)
+    assert dg["w_target"] == dg["c"][0] == dg["cbar"]
+    assert math.isclose(dg["alpha"][0], do["alpha"][0], rel_tol=1e-6)
+    assert rel_l2(ens.get_state(), ref) < 1e-5

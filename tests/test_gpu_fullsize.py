@@ -115,3 +115,52 @@ def test_config4_analysis_full_size():
         ref = O.add_pull(P, K, cells, Sd[i].reshape(-1, 2), kept[i])
         ref = O.add_qhalf(P, r, ref)
         assert rel_l2(out[i].cpu().numpy(), ref) < 1e-5
+
+
+def test_largest_ensemble_sampled():
+    """65 535 particles, the largest ensemble (N_e spans a grid dimension of
+    several launches), on 48 x 48 cells: one model step with model error and
+    one analysis against two drifters.  Sampled particles against the oracle
+    (forecast; gamma, zeta, phi, alpha; the updated state), the ensemble-wide
+    step on all particles."""
+    cfg = synth.Config("max_ne_48x48", 48, 48, n_particles=65535, n_obs=2)
+    P = oracle_problem(cfg)
+    ne = cfg.n_particles
+    sample = (0, 32768, 65534)
+    eta_y, hu_y = synth._jet(cfg)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    U = torch.zeros((ne, 3, cfg.ny, cfg.nx), dtype=torch.float32, device="cuda")
+    U[:, 0] = torch.as_tensor(eta_y, dtype=torch.float32, device="cuda")[None, :, None]
+    U[:, 1] = torch.as_tensor(hu_y, dtype=torch.float32, device="cuda")[None, :, None]
+    U[:, 0] += cfg.noise_std * torch.randn((ne, cfg.ny, cfg.nx), generator=g, device="cuda")
+    U0 = {i: U[i].double().cpu().numpy() for i in sample}
+    ens = ensemble(cfg)
+    ens.set_state(U)
+    ens.forecast(1, True)
+    nsub = ens.last_nsub()
+    out = torch.empty_like(U)
+    ens.get_state(out)
+    torch.cuda.synchronize()
+    F = {i: out[i].double().cpu().numpy() for i in sample}
+    for i in sample:
+        ref, ns, _ = _forecast_as_particle(P, U0[i], i)
+        assert ns[0, 0] == nsub[i]
+        assert rel_l2(F[i], ref[0]) < 1e-5, i
+    xy = synth.drifter_positions(cfg)
+    cells = [O.obs_cell(P, *p) for p in xy]
+    y = synth.obs_from_state(cfg, synth.initial_particle(cfg, 3, seed=8), np.array(cells), synth.obs_noise(cfg, 2, 0))
+    dg = ens.assimilate(xy, y)
+    ens.get_state(out)
+    torch.cuda.synchronize()
+    o = O.iewpf_scalars(dg["c"], dg["gamma"], dg["zeta"], P.N_psi, only=sample)
+    assert math.isclose(dg["cbar"], o["cbar"], rel_tol=1e-12)
+    assert math.isclose(dg["beta"], o["beta"], rel_tol=1e-10)
+    assert np.allclose(dg["neglogw"], dg["cbar"], rtol=1e-10, atol=0)
+    for i in sample:
+        post, do = O.assimilate(P, F[i][None], cells, y, t=0, p0=i,
+                                scalars={"beta": dg["beta"], "alpha": [o["alpha"][i]]})
+        assert math.isclose(dg["gamma"][i], do["gamma"][0], rel_tol=1e-10)
+        assert math.isclose(dg["zeta"][i], do["zeta"][0], rel_tol=1e-10)
+        assert math.isclose(dg["phi"][i], do["phi"][0], rel_tol=1e-4)
+        assert math.isclose(dg["alpha"][i], o["alpha"][i], rel_tol=1e-10)
+        assert rel_l2(out[i].cpu().numpy(), post[0]) < 1e-5, i
