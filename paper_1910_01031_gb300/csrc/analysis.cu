@@ -136,7 +136,7 @@ cudaError_t launch_obs_setup(const double* xy, int nobs, const Grid& G, const Co
                              int* flag, cudaStream_t st)
 {
     if (nobs > 0) obs_cells_kernel<<<(nobs + 127) / 128, 128, 0, st>>>(xy, nobs, G, C, dx, dy, obs_cell, obs_block0);
-    const int ntiles = ((G.nx + TW - 1) / TW) * ((G.ny + TH - 1) / TH);
+    const int ntiles = ((G.nx + OBS_TX - 1) / OBS_TX) * ((G.ny + OBS_TY - 1) / OBS_TY);
     tile_bin_kernel<<<ntiles, NTHREADS, 0, st>>>(obs_cell, nobs, G, R, tile_cnt, tile_obs, tile_cap, flag);
     return cudaGetLastError();
 }

@@ -44,8 +44,8 @@ __device__ __forceinline__ void tile_bin_cta(const int* __restrict__ cell, int n
 {
     __shared__ int base;
     __shared__ int warp_tot[NTHREADS / 32];
-    const int tx = tile % ((G.nx + TW - 1) / TW), ty = tile / ((G.nx + TW - 1) / TW);
-    const int cx = tx * TW + TW / 2, cy = ty * TH + TH / 2;
+    const int tx = tile % ((G.nx + OBS_TX - 1) / OBS_TX), ty = tile / ((G.nx + OBS_TX - 1) / OBS_TX);
+    const int cx = tx * OBS_TX + OBS_TX / 2, cy = ty * OBS_TY + OBS_TY / 2;
     __syncthreads();
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
@@ -54,7 +54,7 @@ __device__ __forceinline__ void tile_bin_cta(const int* __restrict__ cell, int n
         bool hit = false;
         if (l < nobs) {
             const int ox = min_image(cell[2 * l] - cx, G.nx), oy = min_image(cell[2 * l + 1] - cy, G.ny);
-            hit = abs(ox) <= R + TW / 2 + 1 && abs(oy) <= R + TH / 2 + 1;
+            hit = abs(ox) <= R + OBS_TX / 2 + 1 && abs(oy) <= R + OBS_TY / 2 + 1;
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

@@ -81,7 +81,7 @@ struct iewpf_ctx {
     int* d_cell = nullptr;
     int* d_block0 = nullptr;
     int ntiles = 0;
-    int tile_cap = 256;
+    int tile_cap = MAX_TILE_OBS;
     int* d_tile_cnt = nullptr;
     int* d_tile_obs = nullptr;
     double* d_L = nullptr;      // (HQH^T + R) and its factor [Ny][Ny]
@@ -688,7 +688,7 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
     const int nobs = P.n_obs_max;
     ctx->nobs_max = nobs;
     const size_t ny = 2 * (size_t)std::max(nobs, 1);
-    ctx->ntiles = ((P.nx + TW - 1) / TW) * ((P.ny + TH - 1) / TH);
+    ctx->ntiles = ((P.nx + OBS_TX - 1) / OBS_TX) * ((P.ny + OBS_TY - 1) / OBS_TY);
     ctx->dots_blk = rand_dots_blocks((int)ctx->NR);
     if ((rc = dalloc(ctx, &ctx->d_obs_xy, ny)) || (rc = dalloc(ctx, &ctx->d_obs_y, ny)) ||
         (rc = dalloc(ctx, &ctx->d_cell, ny)) || (rc = dalloc(ctx, &ctx->d_block0, ny)) ||

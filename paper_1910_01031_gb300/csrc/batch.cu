@@ -192,7 +192,7 @@ __global__ void b_soar(BatchDev B)
 template <bool PULL>
 __global__ void __launch_bounds__(NTHREADS) b_fine(BatchDev B)
 {
-    constexpr int TX = PULL ? TW : qhalf::FINE_TX, TY = PULL ? TH : qhalf::FINE_TY;
+    constexpr int TX = qhalf::FINE_TX, TY = qhalf::FINE_TY;
     const long long* pre = space(B, PULL ? SP_TILE : SP_FTILE);
     for (long long q = blockIdx.x; q < pre[B.n]; q += gridDim.x) {
         const int i = find_inst(pre, B.n, q);
@@ -490,7 +490,7 @@ cudaError_t batch_init(BatchImpl& b, const std::vector<BInst>& insts)
         const BInst& I = insts[i];
         const long long ne = I.G.ne;
         const long long slices = (I.G.plane + kCflSlice - 1) / kCflSlice;
-        const long long tiles = (long long)((I.G.nx + TW - 1) / TW) * ((I.G.ny + TH - 1) / TH);
+        const long long tiles = (long long)((I.G.nx + OBS_TX - 1) / OBS_TX) * ((I.G.ny + OBS_TY - 1) / OBS_TY);
         const long long ftiles = (long long)((I.G.nx + qhalf::FINE_TX - 1) / qhalf::FINE_TX) *
                                  ((I.G.ny + qhalf::FINE_TY - 1) / qhalf::FINE_TY);
         const long long cnt[SP_COUNT] = {ne, ne * slices, 0, ne * tiles, I.nobs, tiles, ne * I.nobs,

@@ -7,10 +7,17 @@
 
 namespace iewpf {
 
-// Tile of fine cells handled by one CTA of the grid kernels.
+// Tile of fine cells handled by one CTA of the shared-memory scheme step.
 constexpr int TW = 32;
 constexpr int TH = 16;
+// Tile of the fine model-error and analysis-update kernels, and of the
+// observation lists of the pull.
+constexpr int OBS_TX = 64;
+constexpr int OBS_TY = 32;
 constexpr int NTHREADS = 256;
+// Capacity of a tile's observation list (observations whose pull stencil
+// reaches the tile); more give FLAG_TILE_OVERFLOW.
+constexpr int MAX_TILE_OBS = 256;
 
 // Fine-grid constants in float, precomputed on the host.
 struct Grid {

@@ -97,7 +97,9 @@ struct QhalfArgs {
     // leaves the CFL rate max of the updated state here (as cfl_kernel would)
     float* amax;
 };
-// kernels it launches: 1 fused, or 2-3 with scratch (normals only from Philox)
+// psi += Q^{1/2} x in three stages (normals, SOAR, fine tiles; the normals
+// only when x comes from Philox), which need the coarse scratch xi_buf and
+// soar_buf (cudaErrorInvalidValue without); qhalf_launches gives the count
 cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cudaStream_t st);
 int qhalf_launches(const QhalfArgs& A);
 

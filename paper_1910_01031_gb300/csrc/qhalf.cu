@@ -6,14 +6,6 @@ namespace iewpf {
 
 namespace {
 
-template <bool PULL>
-__global__ void __launch_bounds__(NTHREADS)
-qhalf_kernel(QhalfArgs A, Grid G, Coarse C)
-{
-    qhalf::qhalf_tile<PULL>(A, G, C, blockIdx.x * TW, blockIdx.y * TH, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x,
-                            A.t_dev ? *A.t_dev : A.t);
-}
-
 // normals of every particle, one Philox block per thread
 __global__ void coarse_normals_kernel(QhalfArgs A, long long NR)
 {
@@ -36,8 +28,8 @@ __global__ void coarse_soar_kernel(const float* __restrict__ src, const float* _
         qhalf::soar_point(src + (long long)p * NR, wtab, C, G, (int)(m % C.nRx), (int)(m / C.nRx));
 }
 
-// model error on FINE_TX x FINE_TY tiles; the analysis update on the TW x TH
-// tiles of its observation lists
+// model error and analysis update on FINE_TX x FINE_TY tiles (the analysis
+// update's observation lists are binned by the same tiles)
 using qhalf::FINE_TX;
 using qhalf::FINE_TY;
 
@@ -46,7 +38,7 @@ __global__ void __launch_bounds__(NTHREADS)
 qhalf_fine_kernel(QhalfArgs A, Grid G, Coarse C)
 {
     const long long NR = (long long)C.nRx * C.nRy;
-    constexpr int TX = PULL ? TW : FINE_TX, TY = PULL ? TH : FINE_TY;
+    constexpr int TX = FINE_TX, TY = FINE_TY;
     qhalf::fine_tile<PULL, TX, TY>(A, G, C, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z,
                                    blockIdx.y * gridDim.x + blockIdx.x, A.soar_buf + (long long)blockIdx.z * NR);
 }
@@ -55,19 +47,13 @@ qhalf_fine_kernel(QhalfArgs A, Grid G, Coarse C)
 
 int qhalf_launches(const QhalfArgs& A)
 {
-    if (!A.xi_buf || !A.soar_buf) return 1;
+    if (!A.xi_buf || !A.soar_buf) return 0;
     return A.from_philox ? 3 : 2;
 }
 
 cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cudaStream_t st)
 {
-    if (C.tab > qhalf::TAB_MAX) return cudaErrorInvalidValue;
-    dim3 grid((G.nx + TW - 1) / TW, (G.ny + TH - 1) / TH, G.ne);
-    if (!A.xi_buf || !A.soar_buf) {
-        if (A.with_pull) qhalf_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
-        else qhalf_kernel<false><<<grid, NTHREADS, 0, st>>>(A, G, C);
-        return cudaGetLastError();
-    }
+    if (C.tab > qhalf::TAB_MAX || !A.xi_buf || !A.soar_buf) return cudaErrorInvalidValue;
     const long long NR = (long long)C.nRx * C.nRy;
     const float* src = A.x;
     if (A.from_philox) {
@@ -76,12 +62,9 @@ cudaError_t launch_qhalf(const QhalfArgs& A, const Grid& G, const Coarse& C, cud
         src = A.xi_buf;
     }
     coarse_soar_kernel<<<dim3((unsigned)((NR + 255) / 256), G.ne), 256, 0, st>>>(src, A.wtab, G, C, A.soar_buf);
-    if (A.with_pull) {
-        qhalf_fine_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
-    } else {
-        dim3 g2((G.nx + FINE_TX - 1) / FINE_TX, (G.ny + FINE_TY - 1) / FINE_TY, G.ne);
-        qhalf_fine_kernel<false><<<g2, NTHREADS, 0, st>>>(A, G, C);
-    }
+    const dim3 grid((G.nx + FINE_TX - 1) / FINE_TX, (G.ny + FINE_TY - 1) / FINE_TY, G.ne);
+    if (A.with_pull) qhalf_fine_kernel<true><<<grid, NTHREADS, 0, st>>>(A, G, C);
+    else qhalf_fine_kernel<false><<<grid, NTHREADS, 0, st>>>(A, G, C);
     return cudaGetLastError();
 }
 

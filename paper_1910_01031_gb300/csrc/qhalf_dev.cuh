@@ -1,12 +1,13 @@
 // Device code of the model-error operator Q^{1/2} = Q_GB^{1/2} I_Omega Q_SOAR^{1/2}
 // (Sec. 3.2 of arXiv 1910.01031, eqs. local_soar_on_eta,
-// geostrophic_balance_disc, covarianceOperatorsDef) applied and added to the
-// state in one pass per fine tile:
-//   coarse field (Philox normals in registers, or a given coarse array)
-//   -> 5x5 SOAR on the coarse tile -> bicubic to the fine tile + 1-cell ring
-//   -> central-difference geostrophic momentum -> read-modify-write.
-// The analysis update reuses it with the posterior coarse field and adds the
-// optimal-proposal pull (eq. detailedOPDUpdate) in the same read-modify-write.
+// geostrophic_balance_disc, covarianceOperatorsDef) in three stages:
+//   Philox normals once per coarse point (normals_block)
+//   -> 5x5 SOAR once per coarse point (soar_point)
+//   -> per fine tile: bicubic to the tile + 1-cell ring, central-difference
+//      geostrophic momentum, read-modify-write of the state (fine_tile).
+// The analysis update reuses the fine stage with the posterior coarse field
+// and adds the optimal-proposal pull (eq. detailedOPDUpdate) in the same
+// read-modify-write.
 #pragma once
 #include "common.cuh"
 #include "kernels.h"
@@ -14,129 +15,32 @@
 namespace iewpf {
 namespace qhalf {
 
-constexpr int FW = TW + 2, FH = TH + 2;       // fine eta with a 1-cell ring
-// coarse extents bounded by the densest case c = 1 (one point per cell)
-constexpr int XIW = FW + 7, XIH = FH + 7;     // normals (SOAR input)
-constexpr int SXW = FW + 3, SXH = FH + 3;     // SOAR output (bicubic taps)
 constexpr int TAB_MAX = 45;                   // 3 c for c <= 15
-constexpr int FINE_TX = 64, FINE_TY = 32;     // model-error tiles of the staged form
+// fine tiles of the model error and of the analysis update (the tiles the
+// observation lists are binned by)
+constexpr int FINE_TX = OBS_TX, FINE_TY = OBS_TY;
 
-// One fine tile (x0, y0) of particle p; `tile` indexes the per-tile
-// observation lists.  Called by whole CTAs of NTHREADS threads; a CTA may
-// call it for several tiles in turn.
-template <bool PULL>
-__device__ __forceinline__ void qhalf_tile(const QhalfArgs& A, const Grid& G, const Coarse& C, int x0, int y0, int p,
-                                           int tile, uint32_t t)
+// Per observation of a tile's list, once per tile: the minimum-image offset
+// of the tile origin (x0, y0) from the observed cell, in (-n/2, n/2], and the
+// particle's S d as float; the cells of the tile then add their own offset
+// (at most one period above).  Returns the list length.  Ends with a barrier.
+__device__ __forceinline__ int tile_obs_prep(const QhalfArgs& A, const Grid& G, int x0, int y0, int p, int tile,
+                                             int* ox0, int* oy0, float* su, float* sv)
 {
-    __shared__ float xi[XIH][XIW];
-    __shared__ float so[SXH][SXW];
-    __shared__ float deta[FH][FW];
-    __shared__ int px[XIW], py[XIH];
-    __shared__ int colA[FW], rowB[FH];
-    __shared__ float colW[FW][4], rowW[FH][4];
-    __shared__ float wt[TAB_MAX * TAB_MAX];
-
-    const int tid = threadIdx.x;
-    __syncthreads();   // the shared arrays may still be in use by the previous tile
-    float tdum;
-    const int a_lo = coarse_interval(x0 - 1, C.nRx, C.c, C.o, G.nx, tdum);
-    const int a_hi = coarse_interval(x0 + TW, C.nRx, C.c, C.o, G.nx, tdum);
-    const int b_lo = coarse_interval(y0 - 1, C.nRy, C.c, C.o, G.ny, tdum);
-    const int b_hi = coarse_interval(y0 + TH, C.nRy, C.c, C.o, G.ny, tdum);
-    const int nxi = a_hi - a_lo + 8, nyi = b_hi - b_lo + 8;     // normals, first at a_lo - 3
-    const int nsx = a_hi - a_lo + 4, nsy = b_hi - b_lo + 4;     // SOAR, first at a_lo - 1
-
-    for (int i = tid; i < nxi; i += NTHREADS) px[i] = coarse_pos(a_lo - 3 + i, C.nRx, C.c, C.o, G.nx);
-    for (int i = tid; i < nyi; i += NTHREADS) py[i] = coarse_pos(b_lo - 3 + i, C.nRy, C.c, C.o, G.ny);
-    for (int i = tid; i < C.tab * C.tab; i += NTHREADS) wt[i] = A.wtab[i];
-    for (int i = tid; i < FW; i += NTHREADS) {
-        float t;
-        const int a = coarse_interval(x0 - 1 + i, C.nRx, C.c, C.o, G.nx, t);
-        colA[i] = a - a_lo;
-        cubic_weights(t, colW[i]);
-    }
-    for (int i = tid; i < FH; i += NTHREADS) {
-        float t;
-        const int b = coarse_interval(y0 - 1 + i, C.nRy, C.c, C.o, G.ny, t);
-        rowB[i] = b - b_lo;
-        cubic_weights(t, rowW[i]);
-    }
-    const long long NR = (long long)C.nRx * C.nRy;
-    const uint2 key = seed_key(A.seed);
-    for (int i = tid; i < nxi * nyi; i += NTHREADS) {
-        const int ix = i % nxi, iy = i / nxi;
-        const int am = pmod(a_lo - 3 + ix, C.nRx), bm = pmod(b_lo - 3 + iy, C.nRy);
-        const uint32_t m = (uint32_t)(bm * C.nRx + am);
-        xi[iy][ix] = A.from_philox ? normal32(key, (uint32_t)p, t, A.stream, m)
-                                   : A.x[(long long)p * NR + m];
+    const int n = min(A.tile_cnt[tile], MAX_TILE_OBS);
+    for (int q = threadIdx.x; q < n; q += NTHREADS) {
+        const int l = A.tile_obs[tile * A.tile_cap + q];
+        int ox = pmod(x0 - A.obs_cell[2 * l], G.nx);
+        int oy = pmod(y0 - A.obs_cell[2 * l + 1], G.ny);
+        if (ox > G.nx / 2) ox -= G.nx;
+        if (oy > G.ny / 2) oy -= G.ny;
+        ox0[q] = ox;
+        oy0[q] = oy;
+        su[q] = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l];
+        sv[q] = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l + 1];
     }
     __syncthreads();
-    // Q_SOAR^{1/2}: 5x5 neighbours, weights by the fine-cell offsets
-    for (int i = tid; i < nsx * nsy; i += NTHREADS) {
-        const int sx = i % nsx, sy = i / nsx;
-        const int cx = sx + 2, cy = sy + 2;
-        float acc = 0.0f;
-#pragma unroll
-        for (int db = -2; db <= 2; ++db) {
-            const int dyf = abs(py[cy + db] - py[cy]);
-#pragma unroll
-            for (int da = -2; da <= 2; ++da) {
-                const int dxf = abs(px[cx + da] - px[cx]);
-                acc = fmaf(wt[dyf * C.tab + dxf], xi[cy + db][cx + da], acc);
-            }
-        }
-        so[sy][sx] = acc;
-    }
-    __syncthreads();
-    // I_Omega: Catmull-Rom tensor product at the fine cell centres
-    for (int i = tid; i < FW * FH; i += NTHREADS) {
-        const int fx = i % FW, fy = i / FW;
-        const int a = colA[fx], b = rowB[fy];
-        float acc = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float row = 0.0f;
-#pragma unroll
-            for (int pp = 0; pp < 4; ++pp) row = fmaf(colW[fx][pp], so[b + q][a + pp], row);
-            acc = fmaf(rowW[fy][q], row, acc);
-        }
-        deta[fy][fx] = acc;
-    }
-    __syncthreads();
-    // Q_GB^{1/2} and the read-modify-write of (eta, hu, hv)
-    float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
-    const int W = 2 * A.R + 1;
-    for (int i = tid; i < TW * TH; i += NTHREADS) {
-        const int tx = i % TW, ty = i / TW;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx >= G.nx || gy >= G.ny) continue;
-        const int fx = tx + 1, fy = ty + 1;
-        float de = deta[fy][fx];
-        float dhu = -G.sgh * (deta[fy + 1][fx] - deta[fy - 1][fx]) * G.inv_2dy;
-        float dhv = G.sgh * (deta[fy][fx + 1] - deta[fy][fx - 1]) * G.inv_2dx;
-        if (PULL) {
-            const int n = A.tile_cnt[tile];
-            for (int q = 0; q < n; ++q) {
-                const int l = A.tile_obs[tile * A.tile_cap + q];
-                int ox = pmod(gx - A.obs_cell[2 * l], G.nx);
-                int oy = pmod(gy - A.obs_cell[2 * l + 1], G.ny);
-                if (ox > G.nx / 2) ox -= G.nx;
-                if (oy > G.ny / 2) oy -= G.ny;
-                if (ox < -A.R || ox > A.R || oy < -A.R || oy > A.R) continue;
-                const float su = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l];
-                const float sv = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l + 1];
-                const int o = (oy + A.R) * W + (ox + A.R);
-                const int fs = W * W;
-                de = fmaf(sv, A.K[3 * fs + o], fmaf(su, A.K[0 * fs + o], de));
-                dhu = fmaf(sv, A.K[4 * fs + o], fmaf(su, A.K[1 * fs + o], dhu));
-                dhv = fmaf(sv, A.K[5 * fs + o], fmaf(su, A.K[2 * fs + o], dhv));
-            }
-        }
-        const long long g = (long long)gy * G.nx + gx;
-        U[g] += de;
-        U[G.plane + g] += dhu;
-        U[2 * G.plane + g] += dhv;
-    }
+    return n;
 }
 
 // Coarse stages once per coarse point.  Normals of block q (counter q) of a
@@ -154,8 +58,8 @@ __device__ __forceinline__ void normals_block(uint2 key, uint32_t p, uint32_t t,
         if (4LL * q + j < NR) out[4LL * q + j] = z[j];
 }
 
-// Q_SOAR^{1/2} at coarse point (am, bm) of field src [N_R]: the same 5 x 5 sum,
-// in the same order, as the fused tile
+// Q_SOAR^{1/2} at coarse point (am, bm) of field src [N_R]: the 5 x 5 sum of
+// eq. local_soar_on_eta over the coarse neighbours, rows outer
 __device__ __forceinline__ float soar_point(const float* __restrict__ src, const float* __restrict__ wtab,
                                             const Coarse& C, const Grid& G, int am, int bm)
 {
@@ -179,15 +83,16 @@ __device__ __forceinline__ float soar_point(const float* __restrict__ src, const
 
 // One fine tile (TX x TY cells) from the SOAR field so_g [N_R] of particle
 // p: bicubic to the tile and its 1-cell ring, geostrophic momentum, optional
-// pull (tiles of TW x TH, which the observation lists index), and the
-// read-modify-write of the state.  The interpolation runs separably (rows
-// first, the same multiply-adds in the same order as qhalf_tile).
+// pull (`tile` indexes the observation lists, binned by the same tiles), and
+// the read-modify-write of the state.  The interpolation runs separably (rows
+// first).  Called by whole CTAs of NTHREADS threads; a CTA may call it for
+// several tiles in turn.
 template <bool PULL, int TX, int TY>
 __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, const Coarse& C, int x0, int y0, int p,
                                           int tile, const float* __restrict__ so_g)
 {
     constexpr int FW = TX + 2, FH = TY + 2, SXW = FW + 3, SXH = FH + 3;
-    static_assert(!PULL || (TX == TW && TY == TH), "pull tiles follow the observation lists");
+    static_assert(!PULL || (TX == OBS_TX && TY == OBS_TY), "pull tiles follow the observation lists");
     __shared__ float so[SXH][SXW];
     __shared__ float rows[SXH][FW];
     __shared__ float deta[FH][FW];
@@ -238,6 +143,9 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
         deta[fy][fx] = acc;
     }
     __syncthreads();
+    __shared__ int obs_ox[PULL ? MAX_TILE_OBS : 1], obs_oy[PULL ? MAX_TILE_OBS : 1];
+    __shared__ float obs_su[PULL ? MAX_TILE_OBS : 1], obs_sv[PULL ? MAX_TILE_OBS : 1];
+    const int n_obs_tile = PULL ? tile_obs_prep(A, G, x0, y0, p, tile, obs_ox, obs_oy, obs_su, obs_sv) : 0;
     float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
     float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
@@ -250,16 +158,14 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
         float dhu = -G.sgh * (deta[fy + 1][fx] - deta[fy - 1][fx]) * G.inv_2dy;
         float dhv = G.sgh * (deta[fy][fx + 1] - deta[fy][fx - 1]) * G.inv_2dx;
         if (PULL) {
-            const int n = A.tile_cnt[tile];
-            for (int q = 0; q < n; ++q) {
-                const int l = A.tile_obs[tile * A.tile_cap + q];
-                int ox = pmod(gx - A.obs_cell[2 * l], G.nx);
-                int oy = pmod(gy - A.obs_cell[2 * l + 1], G.ny);
+            for (int q = 0; q < n_obs_tile; ++q) {
+                // the tile origin's offset is in (-n/2, n/2] and the cell's
+                // is at most one period above it
+                int ox = obs_ox[q] + tx, oy = obs_oy[q] + ty;
                 if (ox > G.nx / 2) ox -= G.nx;
                 if (oy > G.ny / 2) oy -= G.ny;
                 if (ox < -A.R || ox > A.R || oy < -A.R || oy > A.R) continue;
-                const float su = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l];
-                const float sv = (float)A.Sd[(long long)p * 2 * A.nobs + 2 * l + 1];
+                const float su = obs_su[q], sv = obs_sv[q];
                 const int o = (oy + A.R) * W + (ox + A.R);
                 const int fs = W * W;
                 de = fmaf(sv, A.K[3 * fs + o], fmaf(su, A.K[0 * fs + o], de));
