@@ -18,7 +18,9 @@ observations of (hu, hv) with sigma = 0.01 m/s * H every 5 minutes.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 from dataclasses import dataclass, field, asdict
 
 import numpy as np
@@ -217,3 +219,37 @@ def observation_subsets(n_obs: int, size: int, n_subsets: int, seed: int = 13):
     the standard particle filter (Sec. 5.3: 50 subsets per size)."""
     rng = np.random.Generator(np.random.Philox(seed + 7919 * size))
     return np.stack([np.sort(rng.choice(n_obs, size, replace=False)) for _ in range(n_subsets)]).astype(np.int32)
+
+
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+
+
+def workloads():
+    """The named workloads of this library: name -> Config or list of Config."""
+    return {"plain_64x64": config1(), "plain_512x512": config2(), "batched_32": config3(),
+            "moorings_1024x1024": config4(), "surrogate_256x256": config5(), "rank_500x300": config_rank()}
+
+
+def config_to_json(cfg):
+    """A Config (or a list of them) as JSON text."""
+    obj = [c.as_dict() for c in cfg] if isinstance(cfg, list) else cfg.as_dict()
+    return json.dumps(obj, indent=1, sort_keys=True) + "\n"
+
+
+def load_config(path_or_name):
+    """A Config (or a list of them, for batched workloads) from a JSON file,
+    or from the name of one of configs/*.json."""
+    path = path_or_name
+    if not os.path.exists(path):
+        path = os.path.join(CONFIG_DIR, path_or_name + ".json")
+    with open(path) as f:
+        obj = json.load(f)
+    return [Config(**o) for o in obj] if isinstance(obj, list) else Config(**obj)
+
+
+def write_configs(directory=CONFIG_DIR):
+    """Writes configs/<workload>.json for every named workload."""
+    os.makedirs(directory, exist_ok=True)
+    for name, cfg in workloads().items():
+        with open(os.path.join(directory, name + ".json"), "w") as f:
+            f.write(config_to_json(cfg))
