@@ -164,3 +164,44 @@ def test_largest_ensemble_sampled():
         assert math.isclose(dg["phi"][i], do["phi"][0], rel_tol=1e-4)
         assert math.isclose(dg["alpha"][i], o["alpha"][i], rel_tol=1e-10)
         assert rel_l2(out[i].cpu().numpy(), post[0]) < 1e-5, i
+
+
+def test_config2_one_stage_analysis_full_size():
+    """512 x 512, 100 particles, 64 drifters, the one-stage scheme (App. A):
+    one analysis of the initial ensemble.  phi, gamma, zeta and alpha of every
+    particle against the oracle's own, w_target = max c, and the updated
+    state of two sampled particles."""
+    cfg = synth.config2()
+    ne = cfg.n_particles
+    P = oracle_problem(cfg)
+    sample = (0, 77)
+    xy = synth.drifter_positions(cfg)
+    cells = np.array([O.obs_cell(P, *p) for p in xy])
+    U, kept, at = _device_ensemble(cfg, ne, keep=sample, cells=cells)
+    truth = synth.initial_particle(cfg, 4242, seed=5)
+    y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), 0))
+    ens = iewpf.Ensemble(iewpf.params_from_config(cfg, scheme=iewpf.ONE_STAGE))
+    ens.set_state(U)
+    dg = ens.assimilate(xy, y)
+    s = (cfg.H + at[:, :, 0]) / cfg.H
+    d = np.stack([y[None, :, 0] * s - at[:, :, 1], y[None, :, 1] * s - at[:, :, 2]], axis=2).reshape(ne, -1)
+    cl = [tuple(c) for c in cells]
+    K = O.pull_stencil(P)
+    Sd = O.cholesky_solve(O.s_matrix(P, K, cl, dense=True), d.T).T
+    phi = np.einsum("ij,ij->i", d, Sd)
+    assert np.allclose(dg["phi"], phi, rtol=1e-9, atol=0)
+    rv = O.rand_vectors(P, ne, t=0)
+    assert np.allclose(dg["gamma"], rv["gamma"], rtol=1e-10, atol=0)
+    sc = O.iewpf_scalars_one_stage(phi + math.log(ne), rv["gamma"], P.N_psi)
+    assert dg["beta"] == 0.0 and dg["w_target"] == dg["c"].max()
+    assert math.isclose(dg["w_target"], sc["w_target"], rel_tol=1e-9)
+    assert np.allclose(dg["alpha"], sc["alpha"], rtol=1e-9, atol=0)
+    assert np.allclose(dg["neglogw"], dg["w_target"], rtol=1e-10, atol=0)
+    out = torch.empty_like(U)
+    ens.get_state(out)
+    torch.cuda.synchronize()
+    Msq = O.local_block_sqrt(P)
+    for i in sample:
+        post, _ = O.assimilate(P, kept[i][None], cl, y, t=0, K=K, Msq=Msq, p0=i,
+                               scalars={"beta": 0.0, "alpha": [sc["alpha"][i]]})
+        assert rel_l2(out[i].cpu().numpy(), post[0]) < 1e-5, i
