@@ -317,3 +317,50 @@ def test_forecast_errors_equal_rmse_for_mean_truth():
     assert np.allclose(E, R, rtol=1e-14)
     E2, _ = O.forecast_errors(traj, truth + 100.0)
     assert np.all(E2 > E)
+
+
+def _phis(c_omega, cells, n=400):
+    """phi = d^T (HQH^T + R)^{-1} d for innovations drawn as H Q^{1/2} xi + eps
+    (the forward model-error chain at the observed cells plus observation
+    noise), with HQH^T assembled from the pull stencils."""
+    P = p64(obs_sigma=2.0, c_omega=c_omega)
+    K = O.pull_stencil(P)
+    A = O.s_matrix(P, K, cells, dense=True)
+    rng = np.random.default_rng(17)
+    zero = np.zeros((3, 64, 64))
+    phis = []
+    for k in range(n):
+        xi = O.normals(P.seed, k, 3, O.STREAM_MODEL_ERROR, P.N_R)
+        dpsi = O.add_qhalf(P, xi, zero)
+        y = np.array([[dpsi[1, b, a], dpsi[2, b, a]] for a, b in cells])
+        y = y + P.obs_sigma * rng.standard_normal(y.shape)
+        d = O.innovations(P, zero[None], cells, y).reshape(-1)
+        phis.append(float(d @ O.cholesky_solve(A, d)))
+    return np.array(phis)
+
+
+CHI2_CELLS = [(10, 12), (40, 15), (20, 45), (50, 50)]
+
+
+def test_phi_is_chi_square_with_n_y_degrees_of_freedom():
+    # with c_Omega = 1 the stencil HQH^T is the covariance of the forward
+    # chain's output exactly, so phi follows chi^2(N_y) (Sec. 4, App. A:
+    # c_bar - c_i about N_y +- sqrt(2 N_y)); the assembly from the stencils is
+    # independent of the forward chain
+    n_y = 2 * len(CHI2_CELLS)
+    phis = _phis(1, CHI2_CELLS)
+    se = math.sqrt(2 * n_y / len(phis))
+    assert abs(phis.mean() - n_y) < 4 * se, (phis.mean(), n_y)
+    assert 0.7 * 2 * n_y < phis.var() < 1.4 * 2 * n_y
+    # a 20% error in the scale of HQH^T + R would be seen
+    assert abs(0.8 * phis.mean() - n_y) > 4 * se
+
+
+def test_observation_centred_lattice_bias_with_coarse_model_error():
+    # with c_Omega = 3 the pull puts the coarse lattice on the observation
+    # (Sec. 4.2, Fig. optimalproposalpull) while the model error lives on the
+    # fixed lattice: for observations between coarse nodes HQH^T is the
+    # at-node covariance and phi averages about 10% above N_y
+    n_y = 2 * len(CHI2_CELLS)
+    phis = _phis(3, CHI2_CELLS)
+    assert 1.03 * n_y < phis.mean() < 1.2 * n_y, phis.mean()
