@@ -112,3 +112,45 @@ def test_batch_rejects_short_observation_sets():
     batch = iewpf.Batch(params[:1], None)
     with pytest.raises(iewpf.IewpfError):
         batch.cycle(5, [(np.zeros((2, 2)), np.zeros((2, 2)))])
+
+
+def test_full_size_batched_workload_sampled():
+    """The 32-problem batched workload (grids 128^2..1024^2, 20-500
+    particles, 4-128 drifters, 73 GB of state) through one CUDA-graph cycle,
+    as the bench runs it; the two smallest problems run one by one as well
+    and must agree bitwise."""
+    torch = pytest.importorskip("torch")
+    cfgs = synth.config3()
+    params = []
+    for i, c in enumerate(cfgs):
+        p = iewpf.params_from_config(c)
+        p.instance_id = i
+        params.append(p)
+    batch = iewpf.Batch(params)
+    starts = {}
+    for i, c in enumerate(cfgs):
+        x = synth.initial_particle(c, 0, seed=100 + i, dtype=np.float32)
+        U = torch.from_numpy(x).cuda().unsqueeze(0).expand(c.n_particles, -1, -1, -1).contiguous()
+        batch.instances[i].set_state(U)
+        starts[i] = x
+        del U
+    obs = []
+    for c in cfgs:
+        xy = synth.drifter_positions(c)
+        cells = np.stack([np.floor(xy[:, 0] / c.dx) % c.nx, np.floor(xy[:, 1] / c.dy) % c.ny], 1).astype(int)
+        obs.append((xy, synth.obs_from_state(c, synth.initial_particle(c, 1, seed=300), cells,
+                                             synth.obs_noise(c, len(cells), 0))))
+    diag = batch.cycle(5, obs)
+    assert np.all(diag[:, 2] == 0)
+    small = sorted(range(len(cfgs)), key=lambda i: cfgs[i].n_particles * cfgs[i].nx * cfgs[i].ny)[:2]
+    for i in small:
+        c = cfgs[i]
+        s = iewpf.Ensemble(params[i])
+        s.set_state(np.broadcast_to(starts[i], (c.n_particles,) + starts[i].shape).copy())
+        s.forecast(4, True)
+        s.forecast(1, False)
+        d = s.assimilate(*obs[i])
+        assert diag[i, 0] == d["w_target"] and diag[i, 1] == d["beta"], i
+        assert np.array_equal(batch.instances[i].get_state(), s.get_state()), i
+        s.close()
+    batch.close()

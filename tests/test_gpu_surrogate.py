@@ -265,3 +265,27 @@ def test_tcgen05_many_tiles_per_cta_match_mma_sync():
     d_mma = out_mma.astype(np.float64) - U
     assert np.linalg.norm(d_mma) > 0
     assert _rel(d_tc, d_mma) < 1e-2
+
+
+def test_full_size_network_call_sampled_against_oracle():
+    # the surrogate workload's network call: 1000 fields of 256 x 256 in one
+    # call on the tcgen05 path, as the drift forecast and the bench make it;
+    # two sampled fields against the FP64 oracle
+    torch = pytest.importorskip("torch")
+    sur, p = _net(nx=256, ny=256, seed=21)
+    assert sur.uses_tcgen05()
+    n = 1000
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    U = torch.randn(n, 3, 256, 256, device="cuda", generator=gen)
+    for _ in range(2):       # smooth periodic fields of the state's magnitudes
+        U = (U + U.roll(1, 2) + U.roll(-1, 2) + U.roll(1, 3) + U.roll(-1, 3)) / 5.0
+    U *= (torch.tensor([0.05, 5.0, 5.0], device="cuda") / U.std(dim=(0, 2, 3))).view(1, 3, 1, 1)
+    U = U.contiguous()
+    out = torch.empty_like(U)
+    sur.apply_device(U, out=out)
+    torch.cuda.synchronize()
+    for i in (0, n - 1):
+        x = U[i:i + 1].double().cpu().numpy()
+        ref = S.apply(p, x, SI, SO, W, D)
+        got = out[i:i + 1].double().cpu().numpy()
+        assert _rel(got - x, ref - x) < FWD_TOL, i
