@@ -68,26 +68,80 @@ __device__ __forceinline__ float gmm2(float a, float b, float th2)
     return gmm2s(th2 * a, a + b, th2 * b);   // no contraction here
 }
 
+// A pair of floats in one 64-bit register pair, for the packed f32x2
+// instructions of sm_100+ (one issue slot for two IEEE-rounded operations,
+// the same results as the scalar forms).
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 x, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
 // central-upwind flux, normal momentum qn, tangential qt carried by the mass
-// flux with the upwind tangential velocity
+// flux with the upwind tangential velocity.  The left and right states go
+// through the same operations, paired in f32x2 instructions.
 __device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, float qnR, float qtR, const Grid& G,
                                      float& F0, float& F1, float& F2)
 {
-    const float hL = G.H + eL, hR = G.H + eR;
+    const f2 e = pk(eL, eR), qn = pk(qnL, qnR);
+    const f2 h = add2(pk(G.H, G.H), e);
+    float hL, hR;
+    upk(h, hL, hR);
     const float rL = frcp(hL), rR = frcp(hR);
-    const float unL = qnL * rL, unR = qnR * rR;
-    const float cL = fsqrt(G.g * hL), cR = fsqrt(G.g * hR);
-    const float ap = fmax3(unL + cL, unR + cR, 0.0f);
-    const float am = fmin3(unL - cL, unR - cR, 0.0f);
+    const f2 r = pk(rL, rR);
+    const f2 un = mul2(qn, r);
+    const f2 gh = mul2(pk(G.g, G.g), h);
+    float ghL, ghR;
+    upk(gh, ghL, ghR);
+    const f2 c = mul2(gh, pk(frsqrt(ghL), frsqrt(ghR)));      // sqrt(g h)
+    float sL, sR, dL, dR;
+    upk(add2(un, c), sL, sR);
+    upk(sub2(un, c), dL, dR);
+    const float ap = fmax3(sL, sR, 0.0f);
+    const float am = fmin3(dL, dR, 0.0f);
     const float inv = frcp(ap - am);
     const float apam = ap * am;
     F0 = fmaf(apam, eR - eL, fmaf(ap, qnL, -(am * qnR))) * inv;
     // p(eta) = g eta (H + eta/2) = eta (g/2 eta + g H)
-    const float pL = eL * fmaf(G.g_half, eL, G.gH);
-    const float pR = eR * fmaf(G.g_half, eR, G.gH);
-    const float mL = fmaf(qnL, unL, pL), mR = fmaf(qnR, unR, pR);
+    const f2 pr = mul2(e, fma2(pk(G.g_half, G.g_half), e, pk(G.gH, G.gH)));
+    float mL, mR;
+    upk(fma2(qn, un, pr), mL, mR);
     F1 = fmaf(apam, qnR - qnL, fmaf(ap, mL, -(am * mR))) * inv;
-    F2 = F0 * ((F0 >= 0.0f) ? qtL * rL : qtR * rR);
+    float tL, tR;
+    upk(mul2(pk(qtL, qtR), r), tL, tR);
+    F2 = F0 * ((F0 >= 0.0f) ? tL : tR);
 }
 
 template <int NC>
