@@ -111,11 +111,13 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 
 // central-upwind flux, normal momentum qn, tangential qt carried by the mass
 // flux with the upwind tangential velocity.  The left and right states go
-// through the same operations, paired in f32x2 instructions.
-__device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, float qnR, float qtR, const Grid& G,
-                                     float& F0, float& F1, float& F2)
+// through the same operations, paired in f32x2 instructions: e, qn, qt hold
+// (left, right).
+__device__ __forceinline__ void flux2(f2 e, f2 qn, f2 qt, const Grid& G, float& F0, float& F1, float& F2)
 {
-    const f2 e = pk(eL, eR), qn = pk(qnL, qnR);
+    float eL, eR, qnL, qnR;
+    upk(e, eL, eR);
+    upk(qn, qnL, qnR);
     const f2 h = add2(pk(G.H, G.H), e);
     float hL, hR;
     upk(h, hL, hR);
@@ -140,8 +142,14 @@ __device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, f
     upk(fma2(qn, un, pr), mL, mR);
     F1 = fmaf(apam, qnR - qnL, fmaf(ap, mL, -(am * mR))) * inv;
     float tL, tR;
-    upk(mul2(pk(qtL, qtR), r), tL, tR);
+    upk(mul2(qt, r), tL, tR);
     F2 = F0 * ((F0 >= 0.0f) ? tL : tR);
+}
+
+__device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, float qnR, float qtR, const Grid& G,
+                                     float& F0, float& F1, float& F2)
+{
+    flux2(pk(eL, eR), pk(qnL, qnR), pk(qtL, qtR), G, F0, F1, F2);
 }
 
 template <int NC>
@@ -186,11 +194,15 @@ struct Marcher {
             const float s1u = gmm2s(tup[k], (qu[1][k] - qu[0][k]) + dun, tun);
             const float s1v = gmm2s(tvp[k], (qv[1][k] - qv[0][k]) + dvn, tvn);
             tLp[k] = tLn; tup[k] = tun; tvp[k] = tvn;
-            const float eB = fmaf(fmaf(-G.fdy2, u[0][k], sL[k]), G.inv_4g, e[0][k]);
-            const float eT = fmaf(fmaf(-G.fdy2, u[1][k], s1L), -G.inv_4g, e[1][k]);
+            // face values below (B, from row 0) and above (T, from row 1) the
+            // face, paired: eta, hv (normal), hu (tangential)
+            const f2 eBT = fma2(fma2(pk(-G.fdy2, -G.fdy2), pk(u[0][k], u[1][k]), pk(sL[k], s1L)),
+                                pk(G.inv_4g, -G.inv_4g), pk(e[0][k], e[1][k]));
+            const f2 q4 = pk(0.25f, -0.25f);
+            const f2 vBT = fma2(q4, pk(sv[k], s1v), pk(qv[0][k], qv[1][k]));
+            const f2 uBT = fma2(q4, pk(su[k], s1u), pk(qu[0][k], qu[1][k]));
             float g0, gv, gu;
-            flux(eB, fmaf(0.25f, sv[k], qv[0][k]), fmaf(0.25f, su[k], qu[0][k]), eT, fmaf(-0.25f, s1v, qv[1][k]),
-                 fmaf(-0.25f, s1u, qu[1][k]), G, g0, gv, gu);
+            flux2(eBT, vBT, uBT, G, g0, gv, gu);
             L0[k] = (G0[k] - g0) * G.inv_dy;
             L1[k] = (Gu[k] - gu) * G.inv_dy;
             L2[k] = (Gv[k] - gv) * G.inv_dy;
