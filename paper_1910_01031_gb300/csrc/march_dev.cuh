@@ -68,88 +68,26 @@ __device__ __forceinline__ float gmm2(float a, float b, float th2)
     return gmm2s(th2 * a, a + b, th2 * b);   // no contraction here
 }
 
-// A pair of floats in one 64-bit register pair, for the packed f32x2
-// instructions of sm_100+ (one issue slot for two IEEE-rounded operations,
-// the same results as the scalar forms).
-struct f2 {
-    unsigned long long v;
-};
-__device__ __forceinline__ f2 pk(float a, float b)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 x, float& a, float& b)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return r;
-}
-
 // central-upwind flux, normal momentum qn, tangential qt carried by the mass
-// flux with the upwind tangential velocity.  The left and right states go
-// through the same operations, paired in f32x2 instructions: e, qn, qt hold
-// (left, right).
-__device__ __forceinline__ void flux2(f2 e, f2 qn, f2 qt, const Grid& G, float& F0, float& F1, float& F2)
+// flux with the upwind tangential velocity
+__device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, float qnR, float qtR, const Grid& G,
+                                     float& F0, float& F1, float& F2)
 {
-    float eL, eR, qnL, qnR;
-    upk(e, eL, eR);
-    upk(qn, qnL, qnR);
-    const f2 h = add2(pk(G.H, G.H), e);
-    float hL, hR;
-    upk(h, hL, hR);
+    const float hL = G.H + eL, hR = G.H + eR;
     const float rL = frcp(hL), rR = frcp(hR);
-    const f2 r = pk(rL, rR);
-    const f2 un = mul2(qn, r);
-    const f2 gh = mul2(pk(G.g, G.g), h);
-    float ghL, ghR;
-    upk(gh, ghL, ghR);
-    const f2 c = mul2(gh, pk(frsqrt(ghL), frsqrt(ghR)));      // sqrt(g h)
-    float sL, sR, dL, dR;
-    upk(add2(un, c), sL, sR);
-    upk(sub2(un, c), dL, dR);
-    const float ap = fmax3(sL, sR, 0.0f);
-    const float am = fmin3(dL, dR, 0.0f);
+    const float unL = qnL * rL, unR = qnR * rR;
+    const float cL = fsqrt(G.g * hL), cR = fsqrt(G.g * hR);
+    const float ap = fmax3(unL + cL, unR + cR, 0.0f);
+    const float am = fmin3(unL - cL, unR - cR, 0.0f);
     const float inv = frcp(ap - am);
     const float apam = ap * am;
     F0 = fmaf(apam, eR - eL, fmaf(ap, qnL, -(am * qnR))) * inv;
     // p(eta) = g eta (H + eta/2) = eta (g/2 eta + g H)
-    const f2 pr = mul2(e, fma2(pk(G.g_half, G.g_half), e, pk(G.gH, G.gH)));
-    float mL, mR;
-    upk(fma2(qn, un, pr), mL, mR);
+    const float pL = eL * fmaf(G.g_half, eL, G.gH);
+    const float pR = eR * fmaf(G.g_half, eR, G.gH);
+    const float mL = fmaf(qnL, unL, pL), mR = fmaf(qnR, unR, pR);
     F1 = fmaf(apam, qnR - qnL, fmaf(ap, mL, -(am * mR))) * inv;
-    float tL, tR;
-    upk(mul2(qt, r), tL, tR);
-    F2 = F0 * ((F0 >= 0.0f) ? tL : tR);
-}
-
-__device__ __forceinline__ void flux(float eL, float qnL, float qtL, float eR, float qnR, float qtR, const Grid& G,
-                                     float& F0, float& F1, float& F2)
-{
-    flux2(pk(eL, eR), pk(qnL, qnR), pk(qtL, qtR), G, F0, F1, F2);
+    F2 = F0 * ((F0 >= 0.0f) ? qtL * rL : qtR * rR);
 }
 
 template <int NC>
@@ -194,15 +132,11 @@ struct Marcher {
             const float s1u = gmm2s(tup[k], (qu[1][k] - qu[0][k]) + dun, tun);
             const float s1v = gmm2s(tvp[k], (qv[1][k] - qv[0][k]) + dvn, tvn);
             tLp[k] = tLn; tup[k] = tun; tvp[k] = tvn;
-            // face values below (B, from row 0) and above (T, from row 1) the
-            // face, paired: eta, hv (normal), hu (tangential)
-            const f2 eBT = fma2(fma2(pk(-G.fdy2, -G.fdy2), pk(u[0][k], u[1][k]), pk(sL[k], s1L)),
-                                pk(G.inv_4g, -G.inv_4g), pk(e[0][k], e[1][k]));
-            const f2 q4 = pk(0.25f, -0.25f);
-            const f2 vBT = fma2(q4, pk(sv[k], s1v), pk(qv[0][k], qv[1][k]));
-            const f2 uBT = fma2(q4, pk(su[k], s1u), pk(qu[0][k], qu[1][k]));
+            const float eB = fmaf(fmaf(-G.fdy2, u[0][k], sL[k]), G.inv_4g, e[0][k]);
+            const float eT = fmaf(fmaf(-G.fdy2, u[1][k], s1L), -G.inv_4g, e[1][k]);
             float g0, gv, gu;
-            flux2(eBT, vBT, uBT, G, g0, gv, gu);
+            flux(eB, fmaf(0.25f, sv[k], qv[0][k]), fmaf(0.25f, su[k], qu[0][k]), eT, fmaf(-0.25f, s1v, qv[1][k]),
+                 fmaf(-0.25f, s1u, qu[1][k]), G, g0, gv, gu);
             L0[k] = (G0[k] - g0) * G.inv_dy;
             L1[k] = (Gu[k] - gu) * G.inv_dy;
             L2[k] = (Gv[k] - gv) * G.inv_dy;
