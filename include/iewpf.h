@@ -97,11 +97,17 @@ typedef struct {
 /* One observation time (Sec. 3.3).  xy: [n_obs][2] observed positions;
  * value: [n_obs][2] observed (hu, hv) in m^2/s, i.e. eq. drifterObservation
  * or eq. buoyObservation including the observation error.  For moorings the
- * positions must be the ones given to iewpf_create (xy may be NULL). */
+ * positions must be the ones given to iewpf_create (xy may be NULL).
+ * Drifters may instead give value = NULL with their previous fixes xy_prev
+ * ([n_obs][2]) taken dt seconds earlier: the library then forms
+ * eq. drifterObservation itself, as iewpf_drifter_obs does.  xy_prev and dt
+ * are ignored when value is given. */
 typedef struct {
     int n_obs;
     const double* xy;
     const double* value;
+    const double* xy_prev;
+    double dt;
 } iewpf_obs_t;
 
 /* Per-cycle diagnostics of iewpf_assimilate (App. A).  Each array has
@@ -167,6 +173,16 @@ IEWPF_API int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_
  * value or position: refused before any device work, the state unchanged),
  * EBETA, EDOMAIN, ENONFINITE, ENOTPD, ECUDA. */
 IEWPF_API int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* diag);
+
+/* Drifter observations from two GPS fixes (Sec. 3.3, eq. drifterObservation):
+ * value[d] = ((x_d - x_prev_d) / dt * H_eq, (y_d - y_prev_d) / dt * H_eq),
+ * each displacement taken by the minimum image on the periodic domain of
+ * params (nx dx by ny dy metres), so a drifter that crossed the boundary
+ * moves by its short way round.  Host arithmetic in FP64, no device work.
+ * xy, xy_prev: host [n][2] metres; value: host [n][2] m^2/s.
+ * Errors: EINVAL (NULL pointers, n < 0, dt not positive, non-finite input). */
+IEWPF_API int iewpf_drifter_obs(const iewpf_params_t* params, int n, const double* xy, const double* xy_prev,
+                                double dt, double* value);
 
 /* Weights of the standard particle filter (Sec. 2.1, eqs.
  * standardParticleFilter and standardParticleFilterWeight) for the current

@@ -706,6 +706,24 @@ def assimilate(P: Problem, ens, cells, y, t, dense=True, K=None, Msq=None, p0=0,
     return ens, diag
 
 
+def drifter_observation(P: Problem, xy, xy_prev, dt):
+    """eq. drifterObservation without its observation error: the drifter
+    velocity estimated from two fixes dt seconds apart times H_eq, the
+    displacement taken by the minimum image on the periodic domain."""
+    xy = np.asarray(xy, np.float64).reshape(-1, 2)
+    xy_prev = np.asarray(xy_prev, np.float64).reshape(-1, 2)
+    out = np.empty_like(xy)
+    for d in range(len(xy)):
+        for k, L in enumerate((P.nx * P.dx, P.ny * P.dy)):
+            disp = math.fmod(xy[d, k] - xy_prev[d, k], L)
+            if disp > 0.5 * L:
+                disp -= L
+            if disp < -0.5 * L:
+                disp += L
+            out[d, k] = disp / dt * P.H
+    return out
+
+
 def sir_weights(d, sets, sigma2, r_scale=1.0):
     """Normalised weights of the standard particle filter (Sec. 2.1, eqs.
     standardParticleFilter, standardParticleFilterWeight) for each subset of

@@ -160,12 +160,42 @@ int dalloc(iewpf_ctx* ctx, T** p, size_t n)
 
 int coarse_count(int n, int c) { return (n - 1 - c / 2) / c + 1; }
 
+// eq. drifterObservation: displacement over dt (minimum image on the
+// periodic domain of size Lx by Ly) times H_eq
+int drifter_obs_values(double Lx, double Ly, double H, int n, const double* xy, const double* xy_prev, double dt,
+                       double* value)
+{
+    if (n < 0 || (n > 0 && (!xy || !xy_prev || !value)) || !(dt > 0) || !std::isfinite(dt)) return IEWPF_EINVAL;
+    const double L[2] = {Lx, Ly};
+    for (int k = 0; k < 2 * n; ++k) {
+        if (!std::isfinite(xy[k]) || !std::isfinite(xy_prev[k])) return IEWPF_EINVAL;
+        const double Lk = L[k & 1];
+        double d = std::fmod(xy[k] - xy_prev[k], Lk);
+        if (d > 0.5 * Lk) d -= Lk;
+        if (d < -0.5 * Lk) d += Lk;
+        value[k] = d / dt * H;
+    }
+    return IEWPF_OK;
+}
+
+// the observed values of obs: as given, or formed from the drifters' two
+// fixes into tmp; NULL when neither is usable
+const double* obs_values(const iewpf_params_t& P, const iewpf_obs_t& o, std::vector<double>& tmp)
+{
+    if (o.value) return o.value;
+    if (P.obs_kind != IEWPF_OBS_DRIFTER || !o.xy || !o.xy_prev) return nullptr;
+    tmp.resize(2 * (size_t)std::max(o.n_obs, 0));
+    if (drifter_obs_values(P.nx * P.dx, P.ny * P.dy, P.H_eq, o.n_obs, o.xy, o.xy_prev, o.dt, tmp.data()) != IEWPF_OK)
+        return nullptr;
+    return tmp.data();
+}
+
 // every observed value (and position, where given) finite: corrupted
 // observations are refused before any device work
-bool obs_finite(const iewpf_obs_t& o)
+bool obs_finite(const iewpf_obs_t& o, const double* value)
 {
     for (int k = 0; k < 2 * o.n_obs; ++k)
-        if (!std::isfinite(o.value[k]) || (o.xy && !std::isfinite(o.xy[k]))) return false;
+        if (!std::isfinite(value[k]) || (o.xy && !std::isfinite(o.xy[k]))) return false;
     return true;
 }
 
@@ -806,20 +836,22 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
 {
     Phase phase_("assimilate");
     if (!ctx) return IEWPF_EINVAL;
-    if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max || !obs->value)
-        return fail(ctx, IEWPF_EINVAL, "bad observation set");
+    if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max) return fail(ctx, IEWPF_EINVAL, "bad observation set");
     const bool mooring = ctx->P.obs_kind == IEWPF_OBS_MOORING;
     if (!mooring && !obs->xy) return fail(ctx, IEWPF_EINVAL, "drifter observations need positions");
     if (mooring && obs->n_obs != ctx->nobs_max)
         return fail(ctx, IEWPF_EINVAL, "mooring observations must cover every mooring");
-    if (!obs_finite(*obs)) return fail(ctx, IEWPF_EINVAL, "non-finite observation value or position");
+    std::vector<double> derived;
+    const double* value = obs_values(ctx->P, *obs, derived);
+    if (!value) return fail(ctx, IEWPF_EINVAL, "no observed values (and no usable previous drifter fixes)");
+    if (!obs_finite(*obs, value)) return fail(ctx, IEWPF_EINVAL, "non-finite observation value or position");
     CK(cudaSetDevice(ctx->dev));
     const int nobs = obs->n_obs, n = 2 * nobs, ne = ctx->G.ne;
     int rc;
     if (!mooring) {
         if ((rc = upload_obs_layout(ctx, obs->xy, nobs))) return rc;
     }
-    CK(cudaMemcpyAsync(ctx->d_obs_y, obs->value, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_obs_y, value, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
     // 1-2: innovations, S d, phi
     {
         Phase sub_("innovations");
@@ -887,13 +919,15 @@ int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, 
 {
     Phase phase_("sir_weights");
     if (!ctx) return IEWPF_EINVAL;
-    if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max || !obs->value)
-        return fail(ctx, IEWPF_EINVAL, "bad observation set");
+    if (!obs || obs->n_obs < 1 || obs->n_obs > ctx->nobs_max) return fail(ctx, IEWPF_EINVAL, "bad observation set");
     const bool mooring = ctx->P.obs_kind == IEWPF_OBS_MOORING;
     if (!mooring && !obs->xy) return fail(ctx, IEWPF_EINVAL, "drifter observations need positions");
     if (mooring && obs->n_obs != ctx->nobs_max)
         return fail(ctx, IEWPF_EINVAL, "mooring observations must cover every mooring");
-    if (!obs_finite(*obs)) return fail(ctx, IEWPF_EINVAL, "non-finite observation value or position");
+    std::vector<double> derived;
+    const double* value = obs_values(ctx->P, *obs, derived);
+    if (!value) return fail(ctx, IEWPF_EINVAL, "no observed values (and no usable previous drifter fixes)");
+    if (!obs_finite(*obs, value)) return fail(ctx, IEWPF_EINVAL, "non-finite observation value or position");
     const int nobs = obs->n_obs, ne = ctx->G.ne;
     if (!(r_scale > 0) || !std::isfinite(r_scale) || n_sets < 0 || set_size < 1 || set_size > nobs ||
         (n_sets > 0 && (!sets || !n_kept)))
@@ -904,7 +938,7 @@ int iewpf_sir_weights(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, double r_scale, 
     CK(cudaSetDevice(ctx->dev));
     int rc;
     if (!mooring && (rc = upload_obs_layout(ctx, obs->xy, nobs))) return rc;
-    CK(cudaMemcpyAsync(ctx->d_obs_y, obs->value, sizeof(double) * 2 * nobs, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_obs_y, value, sizeof(double) * 2 * nobs, cudaMemcpyHostToDevice, ctx->st));
     KL(1, launch_innovate(ctx->buf[0], ctx->buf[1], ctx->par, ctx->d_cell, ctx->d_obs_y, nobs, ctx->G,
                        ctx->P.H_eq, ctx->d_d, ctx->st));
     const size_t nidx = (size_t)n_sets * set_size, nw = (size_t)n_sets * ne;
@@ -1258,6 +1292,13 @@ int iewpf_weights(int ne, double N_psi, const double* c, const double* gamma, co
     return weights_host(IEWPF_TWO_STAGE, ne, N_psi, c, gamma, zeta, out2, alpha, cstar, neglogw);
 }
 
+int iewpf_drifter_obs(const iewpf_params_t* params, int n, const double* xy, const double* xy_prev, double dt,
+                      double* value)
+{
+    if (!params || !(params->dx > 0) || !(params->dy > 0) || params->nx < 1 || params->ny < 1) return IEWPF_EINVAL;
+    return drifter_obs_values(params->nx * params->dx, params->ny * params->dy, params->H_eq, n, xy, xy_prev, dt, value);
+}
+
 int iewpf_alpha_gamma(int ne, double N_psi, const double* gamma, const double* cstar, double* alpha)
 {
     Phase phase_("alpha_gamma");
@@ -1580,9 +1621,15 @@ int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* ob
     for (int i = 0; i < n; ++i) {
         const iewpf_ctx* c = b->inst[i];
         const bool mooring = c->P.obs_kind == IEWPF_OBS_MOORING;
-        if (obs[i].n_obs != c->nobs_max || !obs[i].value || (!mooring && !obs[i].xy))
+        if (obs[i].n_obs != c->nobs_max || (!mooring && !obs[i].xy))
             return bfail(b, IEWPF_EINVAL, "problem " + std::to_string(i) + ": observations must fill n_obs_max");
-        if (!obs_finite(obs[i]))
+    }
+    std::vector<std::vector<double>> derived(n);
+    std::vector<const double*> values(n);
+    for (int i = 0; i < n; ++i) {
+        values[i] = obs_values(b->inst[i]->P, obs[i], derived[i]);
+        if (!values[i]) return bfail(b, IEWPF_EINVAL, "problem " + std::to_string(i) + ": no observed values");
+        if (!obs_finite(obs[i], values[i]))
             return bfail(b, IEWPF_EINVAL, "problem " + std::to_string(i) + ": non-finite observation");
     }
     BCK(cudaSetDevice(b->dev));
@@ -1593,7 +1640,7 @@ int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* ob
         const int m = obs[i].n_obs;
         if (obs[i].xy) std::memcpy(dst, obs[i].xy, sizeof(double) * 2 * m);
         else std::memset(dst, 0, sizeof(double) * 2 * m);
-        std::memcpy(dst + 2 * m, obs[i].value, sizeof(double) * 2 * m);
+        std::memcpy(dst + 2 * m, values[i], sizeof(double) * 2 * m);
         uint32_t* ctr = batch_counter_staging(*b->impl);
         ctr[2 * i] = b->inst[i]->step;
         ctr[2 * i + 1] = b->inst[i]->cycle;

@@ -25,7 +25,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "drifter_forecast", "iewpf_save", "iewpf_load", "iewpf_get_counters", "iewpf_set_counters",
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma", "iewpf_rank",
-           "iewpf_batch_forecast",
+           "iewpf_batch_forecast", "iewpf_drifter_obs",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
@@ -60,7 +60,8 @@ ONE_STAGE = 1
 
 class Obs(ctypes.Structure):
     _fields_ = [("n_obs", ctypes.c_int), ("xy", ctypes.POINTER(ctypes.c_double)),
-                ("value", ctypes.POINTER(ctypes.c_double))]
+                ("value", ctypes.POINTER(ctypes.c_double)), ("xy_prev", ctypes.POINTER(ctypes.c_double)),
+                ("dt", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -118,6 +119,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_weights_noalloc.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_weights_one_stage.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
     L.iewpf_alpha_gamma.argtypes = [c.c_int, c.c_double, _dp, _dp, _dp]
+    L.iewpf_drifter_obs.argtypes = [c.POINTER(Params), c.c_int, _dp, _dp, c.c_double, _dp]
     L.iewpf_pull_stencil.argtypes = [_vp, _dp]
     L.iewpf_local_block.argtypes = [_vp, _dp]
     L.iewpf_add_qhalf.argtypes = [_vp, _fp]
@@ -249,11 +251,18 @@ class Ensemble:
         self._chk(self.L.iewpf_forecast_fixed(self.h, int(n_steps), int(bool(add_model_error)), int(n_sub)),
                   "forecast_fixed")
 
-    def assimilate(self, xy, values, diag=True):
-        values = _f64(values, (-1, 2))
-        n = values.shape[0]
+    def assimilate(self, xy, values, diag=True, xy_prev=None, dt=0.0):
+        """values None: drifter observations formed by the library from the
+        fixes xy and xy_prev taken dt seconds apart (eq. drifterObservation)."""
         xy = None if xy is None else _f64(xy, (-1, 2))
-        obs = Obs(n, _ptr(xy), _ptr(values))
+        if values is None:
+            xy_prev = _f64(xy_prev, (-1, 2))
+            n = xy.shape[0]
+        else:
+            values = _f64(values, (-1, 2))
+            n = values.shape[0]
+            xy_prev = None
+        obs = Obs(n, _ptr(xy), _ptr(values), _ptr(xy_prev), float(dt))
         out = None
         dptr = None
         if diag:
@@ -621,6 +630,18 @@ def weights(c, gamma, zeta, N_psi, noalloc=False):
     if rc != IEWPF_OK:
         raise IewpfError(rc, "weights")
     return {"cbar": out2[0], "beta": out2[1], "alpha": alpha, "cstar": cstar, "neglogw": nlw}
+
+
+def drifter_obs(params, xy, xy_prev, dt):
+    """eq. drifterObservation on the host through the C ABI: (hu, hv) from two
+    drifter fixes dt seconds apart, minimum image on the periodic domain."""
+    L = load()
+    xy, xy_prev = _f64(xy, (-1, 2)), _f64(xy_prev, (-1, 2))
+    out = np.zeros_like(xy)
+    rc = L.iewpf_drifter_obs(ctypes.byref(params), xy.shape[0], _ptr(xy), _ptr(xy_prev), float(dt), _ptr(out))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "drifter_obs")
+    return out
 
 
 def alpha_gamma(gamma, cstar, N_psi):

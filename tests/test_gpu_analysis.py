@@ -293,3 +293,22 @@ def test_single_particle_analysis_matches_oracle(scheme):
     assert dg["w_target"] == dg["c"][0] == dg["cbar"]
     assert math.isclose(dg["alpha"][0], do["alpha"][0], rel_tol=1e-6)
     assert rel_l2(ens.get_state(), ref) < 1e-5
+
+
+def test_drifter_values_formed_from_two_fixes():
+    # value = NULL with the previous fixes: the library forms eq.
+    # drifterObservation itself; the analysis equals one given those values
+    cfg = synth.config1(n_particles=5, n_obs=2)
+    U = synth.initial_state(cfg, 5, seed=6).astype(np.float32)
+    xy = synth.drifter_positions(cfg)
+    xy_prev = xy - np.array([[120.0, -40.0], [-30.0, 85.0]])
+    a, b = ensemble(cfg), ensemble(cfg)
+    a.set_state(U)
+    b.set_state(U)
+    da = a.assimilate(xy, None, xy_prev=xy_prev, dt=300.0)
+    db = b.assimilate(xy, iewpf.drifter_obs(iewpf.params_from_config(cfg), xy, xy_prev, 300.0))
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(da["phi"], db["phi"])
+    with pytest.raises(iewpf.IewpfError) as e:      # neither values nor usable fixes
+        a.assimilate(xy, None, xy_prev=xy_prev, dt=0.0)
+    assert e.value.name == "EINVAL"
