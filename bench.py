@@ -506,7 +506,9 @@ def run_surrogate(rank, n_pairs=20000, epochs=8, batch=32, lr=1e-3, hours=12.0, 
     same ensemble and counters: with the plain stepper and with the
     surrogate (model error from the same Philox draws in both).  Reports the
     time of both, the RMS and largest drifter distance between the two
-    forecasts at every hour, and the tensor-core rate of a network call."""
+    forecasts at every hour, the forecast error E(t) of both against a truth
+    run and its difference at 12 h, and the tensor-core rate of a network
+    call."""
     import torch
     from paper_1910_01031_gb300 import iewpf, synth
     out = {"workload": "surrogate_256x256_ne%d_64drifters, %g h drift forecast, network 6 x conv3x3 (64 ch), "
@@ -540,8 +542,16 @@ def run_surrogate(rank, n_pairs=20000, epochs=8, batch=32, lr=1e-3, hours=12.0, 
     sur.set_scales(si, so)
     ens.set_surrogate(sur, k)
     xy0 = synth.drifter_positions(cfg)
+    # the truth: one more draw of the initial state with its own model error,
+    # its drifters advected by the plain stepper
+    Pt = iewpf.params_from_config(synth.Config(**{**cfg.as_dict(), "n_particles": 1}), n_drifters_max=cfg.n_obs)
+    Pt.instance_id = 9000 + rank
+    truth_ens = iewpf.Ensemble(Pt)
+    truth_ens.set_state(synth.initial_particle(cfg, ne + 17, seed=31 + rank, dtype=np.float32)[None])
+    truth = truth_ens.drifter_forecast(xy0, hours, 3600.0)[:, 0]
+    truth_ens.close()
     stream = torch.cuda.ExternalStream(ens.stream())
-    res = {}
+    res, errs = {}, {}
     for mode in ("plain", "surrogate"):
         ens.set_state(U0)
         ens.set_counters(0, 0)
@@ -550,10 +560,12 @@ def run_surrogate(rank, n_pairs=20000, epochs=8, batch=32, lr=1e-3, hours=12.0, 
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         h0 = time.perf_counter()
-        traj = ens.drifter_forecast(xy0, hours, 3600.0, use_surrogate=(mode == "surrogate"))
+        E, R, traj = ens.drifter_forecast_errors(xy0, hours, 3600.0, truth, want_traj=True,
+                                                 use_surrogate=(mode == "surrogate"))
         e1.record(stream)
         e1.synchronize()
         res[mode] = (traj, time.perf_counter() - h0, e0.elapsed_time(e1) / 1e3, ens.work() - w0)
+        errs[mode] = (E, R)
     calls, fallbacks = ens.surrogate_stats()
     d = np.sqrt(np.sum((res["surrogate"][0] - res["plain"][0]) ** 2, axis=-1)) / 1e3     # km, [hour][p][drifter]
     rms = np.sqrt(np.mean(d ** 2, axis=(1, 2)))
@@ -570,6 +582,17 @@ def run_surrogate(rank, n_pairs=20000, epochs=8, batch=32, lr=1e-3, hours=12.0, 
                                 "max_at_end": round(float(d[-1].max()), 4),
                                 "median_at_end": round(float(np.median(d[-1])), 4)}
     out["within_1km"] = bool(rms[-1] <= 1.0)
+    # forecast error against the truth (eqs. errorPerEnsembleDrifter, errorNorm), computed on the GPU
+    e_p, e_s = float(errs["plain"][0][-1]) / 1e3, float(errs["surrogate"][0][-1]) / 1e3
+    out["forecast_error_km"] = {"E_plain_by_hour": [round(float(v) / 1e3, 3) for v in errs["plain"][0]],
+                                "E_surrogate_by_hour": [round(float(v) / 1e3, 3) for v in errs["surrogate"][0]],
+                                "RMSE_plain_end": round(float(errs["plain"][1][-1]) / 1e3, 3),
+                                "RMSE_surrogate_end": round(float(errs["surrogate"][1][-1]) / 1e3, 3),
+                                "abs_E_difference_end": round(abs(e_s - e_p), 4)}
+    out["within_1km_E"] = bool(abs(e_s - e_p) <= 1.0)
+    pdh = ne * len(xy0) * hours
+    out["particle_drifter_hours_per_s"] = {"plain": round(pdh / res["plain"][1], 1),
+                                           "surrogate": round(pdh / res["surrogate"][1], 1)}
     # one network call over the whole ensemble, CUDA events on the surrogate stream
     s_stream = torch.cuda.ExternalStream(sur.stream())
     V = U0.clone()
