@@ -364,3 +364,54 @@ def test_observation_centred_lattice_bias_with_coarse_model_error():
     n_y = 2 * len(CHI2_CELLS)
     phis = _phis(3, CHI2_CELLS)
     assert 1.03 * n_y < phis.mean() < 1.2 * n_y, phis.mean()
+
+
+def test_innovation_of_a_particle_equal_to_the_truth_is_zero():
+    # eq. buoyObservation observes hu H/(H + eta) of the truth and eq.
+    # etaCompensatedInnovation scales the observation back by (H + eta_i)/H
+    # (the paper states the two are consistent): a particle equal to the
+    # truth has zero innovation even where eta is far from 0, and a particle
+    # with the truth's momentum but another eta does not
+    P = p64()
+    rng = np.random.default_rng(31)
+    truth = np.stack([rng.normal(0, 1, (64, 64)) * 3.0,        # eta of metres
+                      rng.normal(0, 1, (64, 64)) * 20.0,
+                      rng.normal(0, 1, (64, 64)) * 20.0])
+    cells = [(3, 5), (40, 22), (63, 63)]
+    s = np.array([P.H / (P.H + truth[0, b, a]) for a, b in cells])
+    y = np.array([[truth[1, b, a], truth[2, b, a]] for a, b in cells]) * s[:, None]
+    d = O.innovations(P, truth[None], cells, y)
+    assert np.max(np.abs(d)) <= 1e-12 * np.max(np.abs(y))
+    other = truth.copy()
+    other[0] += 1.0
+    assert np.min(np.abs(O.innovations(P, other[None], cells, y))) > 1e-3
+
+
+def test_observed_cell_contains_the_position():
+    # the cell (j, k) covers [j dx, (j+1) dx) x [k dy, (k+1) dy) (cell centres
+    # at ((j + 1/2) dx, (k + 1/2) dy)); positions outside the domain wrap
+    P = O.Problem(nx=64, ny=48, dx=2000.0, dy=2500.0)
+    for j, k in ((0, 0), (63, 47), (17, 30)):
+        for fx, fy in ((0.5, 0.5), (0.0, 0.0), (0.999, 0.001)):
+            assert O.obs_cell(P, (j + fx) * 2000.0, (k + fy) * 2500.0) == (j, k)
+    assert O.obs_cell(P, -1.0, 48 * 2500.0 + 1.0) == (63, 0)
+
+
+def test_nearest_coarse_point_and_its_7x7_block():
+    # coarse points at o + c a (o = c // 2); the nearest one to a fine index,
+    # across the seam of the short last gap; the block is 7 x 7 coarse points
+    # around it, ordered (dy + 3) * 7 + (dx + 3), wrapping periodically
+    n, c = 64, 3                          # points 1, 4, ..., 61; the gap 61 -> 65 = 1
+    nR = O.Problem(nx=n, ny=n, dx=1.0, dy=1.0).nRx
+    pos = [c // 2 + c * a for a in range(nR)]
+    for j in range(n):
+        dist = [min(abs(j - p), n - abs(j - p)) for p in pos]
+        best = min(dist)
+        a = O.nearest_coarse(n, nR, c, j)
+        assert dist[a] == best, j
+    P = p64()
+    idx = O.block_indices(P, (4, 61))     # x at coarse 1, y at coarse 20 (the last)
+    ax, by = O.nearest_coarse(64, P.nRx, 3, 4), O.nearest_coarse(64, P.nRy, 3, 61)
+    assert (ax, by) == (1, 20)
+    expect = [((by + dy) % P.nRy) * P.nRx + (ax + dx) % P.nRx for dy in range(-3, 4) for dx in range(-3, 4)]
+    assert list(idx) == expect and len(set(expect)) == 49
