@@ -36,8 +36,8 @@ __global__ void hqht_kernel(const double* __restrict__ K, int R, const int* __re
 }
 
 __global__ void __launch_bounds__(1024)
-cholesky_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, int* __restrict__ rowidx,
-                int* __restrict__ flag, int* __restrict__ nzlist)
+cholesky_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, int* rowidx, int* __restrict__ flag,
+                int* nzlist)
 {
     ana::cholesky_cta(A, n, colptr, rowidx, flag, nzlist);
 }

@@ -194,9 +194,10 @@ __device__ __forceinline__ void csc_cta(const double* __restrict__ L, int n, int
 
 // Factor in global memory and list the factor's columns; rowidx doubles as
 // the work list during the factorisation.
-__device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int* __restrict__ colptr,
-                                             int* __restrict__ rowidx, int* __restrict__ flag,
-                                             int* __restrict__ nzlist)
+// rowidx and nzlist may be the same array (the work list of the
+// factorisation, then the row indices of the factor), so neither is restrict
+__device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int* __restrict__ colptr, int* rowidx,
+                                             int* __restrict__ flag, int* nzlist)
 {
     __shared__ int bad;
     __syncthreads();

@@ -580,7 +580,8 @@ static cudaError_t capture_model_step(BatchImpl& b, cudaStream_t st, cudaStream_
     if ((e = cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
     cudaGraphConditionalHandle h;
     if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
-    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
     prm.conditional.handle = h;
     prm.conditional.type = cudaGraphCondTypeWhile;
     prm.conditional.size = 1;
