@@ -136,14 +136,20 @@ typedef struct iewpf_ctx iewpf_ctx_t;
  * The state is zero until iewpf_set_state. */
 IEWPF_API int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_ctx_t** out);
 
-/* Free every resource of the context.  NULL is accepted. */
+/* Free every resource of the context (a service of the library, not a step
+ * of the method).  NULL is accepted and returns IEWPF_OK. */
 IEWPF_API int iewpf_destroy(iewpf_ctx_t* ctx);
 
-/* Copy the ensemble in ([N_e][3][ny][nx] float32).  on_device: src is a
- * device pointer (copied on the context stream, after `stream` if given). */
+/* Copy the ensemble in ([N_e][3][ny][nx] float32; the state psi of Sec. 2,
+ * fields (eta, hu, hv) of Sec. 3.1).  on_device: src is a device pointer
+ * (copied on the context stream, after `stream` if given), else host
+ * memory.  Clears the CFL rates kept from the last update.
+ * Errors: EINVAL (NULL pointer), ECUDA. */
 IEWPF_API int iewpf_set_state(iewpf_ctx_t* ctx, const float* src, int on_device, void* stream);
 
-/* Copy the ensemble out ([N_e][3][ny][nx] float32). */
+/* Copy the ensemble out ([N_e][3][ny][nx] float32), to device memory when
+ * on_device (ordered after the context's work and before `stream`), else to
+ * host memory.  Errors: EINVAL (NULL pointer), ECUDA. */
 IEWPF_API int iewpf_get_state(iewpf_ctx_t* ctx, float* dst, int on_device, void* stream);
 
 /* Ensemble forecast (eq. model_equation): n_model_steps model steps of
@@ -156,8 +162,10 @@ IEWPF_API int iewpf_get_state(iewpf_ctx_t* ctx, float* dst, int on_device, void*
  * ENONFINITE (checked once per call). */
 IEWPF_API int iewpf_forecast(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error);
 
-/* As iewpf_forecast but with a fixed number of scheme steps per model step
- * (n_sub > 0) for every particle, skipping the CFL evaluation. */
+/* As iewpf_forecast (eq. model_equation) but with a fixed number of scheme
+ * steps per model step (n_sub > 0) for every particle, skipping the CFL
+ * evaluation of eq. swecfl.  Errors: EINVAL (n_sub < 1, n_model_steps < 0),
+ * ECUDA, ENONFINITE. */
 IEWPF_API int iewpf_forecast_fixed(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error, int n_sub);
 
 /* One two-stage IEWPF analysis of the current ensemble against `obs`
@@ -219,8 +227,9 @@ IEWPF_API int iewpf_rank(iewpf_ctx_t* ctx, int n_pts, const int* cells, const do
 
 /* Drifters carried by every particle (Sec. 3.3, forward Euler with the
  * velocity hu/(H+eta) of the containing cell after each scheme step).
- * xy: [N_e][n][2] float64 unwrapped positions; n <= n_drifters_max.
- * n = 0 removes them. */
+ * xy: [N_e][n][2] float64 unwrapped positions (host); n <= n_drifters_max.
+ * n = 0 removes them.  get: the current positions into xy ([N_e][n][2]).
+ * Errors: EINVAL (n out of range, NULL xy with n > 0), ECUDA. */
 IEWPF_API int iewpf_set_drifters(iewpf_ctx_t* ctx, const double* xy, int n);
 IEWPF_API int iewpf_get_drifters(iewpf_ctx_t* ctx, double* xy);
 
@@ -246,16 +255,22 @@ IEWPF_API int drifter_forecast(iewpf_ctx_t* ctx, const double* xy0, int n, doubl
 IEWPF_API int drifter_forecast_errors(iewpf_ctx_t* ctx, const double* xy0, int n, double hours, double out_every_s,
                                       const double* truth, double* E, double* RMSE, double* traj, int use_surrogate);
 
-/* Checkpoint: raw state, drifters and the two draw counters; because the
- * random numbers are counter-based, a resumed run is bit-identical. */
+/* Checkpoint (a service of the library): raw state, drifters and the two
+ * draw counters written to / read from a host file; because the random
+ * numbers are counter-based (Philox), a resumed run is bit-identical.  load
+ * needs a context of the same sizes.  Errors: EINVAL (NULL path, file not
+ * readable or writable, a checkpoint of other sizes or truncated), ECUDA. */
 IEWPF_API int iewpf_save(const iewpf_ctx_t* ctx, const char* path);
 IEWPF_API int iewpf_load(iewpf_ctx_t* ctx, const char* path);
 
-/* Draw counters: model steps taken (model error) and cycles assimilated. */
+/* Draw counters: model steps taken (the draw index of the model error,
+ * eq. model_error) and cycles assimilated (the draw index of xi and nu,
+ * App. A).  Either output pointer may be NULL.  Errors: EINVAL (NULL ctx). */
 IEWPF_API int iewpf_get_counters(const iewpf_ctx_t* ctx, uint32_t* model_step, uint32_t* cycle);
 IEWPF_API int iewpf_set_counters(iewpf_ctx_t* ctx, uint32_t model_step, uint32_t cycle);
 
-/* Scheme steps each particle took in the last model step ([N_e] ints). */
+/* Scheme steps each particle took in the last model step ([N_e] ints,
+ * host), n_sub of eq. swecfl.  Errors: EINVAL (NULL), ECUDA. */
 IEWPF_API int iewpf_last_nsub(const iewpf_ctx_t* ctx, int* n_sub);
 
 /* Message of the last error of ctx ("" if none); static text for NULL. */
@@ -271,8 +286,10 @@ IEWPF_API const char* iewpf_last_error(const iewpf_ctx_t* ctx);
 IEWPF_API int iewpf_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream,
                         int64_t n_blocks, uint32_t* out);
 
-/* Standard normals from those blocks by the Box-Muller pairing, computed
- * on the GPU in FP64 (out64) and FP32 (out32); either may be NULL. */
+/* Standard normals from those blocks by the Box-Muller pairing (the xi of
+ * eq. model_error and App. A), computed on the GPU in FP64 (out64) and
+ * FP32 (out32), host arrays of n; either may be NULL, not both.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 IEWPF_API int iewpf_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, int64_t n,
                   double* out64, float* out32);
 
@@ -335,20 +352,24 @@ IEWPF_API int iewpf_weights_noalloc(int ne, double N_psi, const double* c, const
                                     const double* zeta, double* out2, double* alpha, double* cstar,
                                     double* neglogw);
 
-/* The context's precomputed pull stencils: K[2][3][2R+1][2R+1] float64,
- * R = 7 c_omega (unit hu, unit hv observation; fields eta, hu, hv). */
+/* The context's precomputed pull stencils (eq. detailedOPDUpdate for a
+ * unit observation): K[2][3][2R+1][2R+1] float64 (host), R = 7 c_omega
+ * (unit hu, unit hv observation; fields eta, hu, hv).  Errors: EINVAL. */
 IEWPF_API int iewpf_pull_stencil(const iewpf_ctx_t* ctx, double* K);
 
-/* The context's 49x49 local block root (row-major float64, block entries
- * ordered (dy+3)*7 + (dx+3)). */
+/* The context's 49x49 local block root U Sigma^{1/2} (eq. Psquareroot,
+ * Sec. 4.6; row-major float64, host; block entries ordered
+ * (dy+3)*7 + (dx+3)).  Errors: EINVAL. */
 IEWPF_API int iewpf_local_block(const iewpf_ctx_t* ctx, double* M);
 
 /* Add Q^{1/2} x to every particle for coarse fields x ([N_e][N_R] float32,
- * host), the operator of eq. covarianceOperatorsDef (testing aid). */
+ * host), the operator of eq. covarianceOperatorsDef (testing aid).
+ * Errors: EINVAL (NULL x), ECUDA. */
 IEWPF_API int iewpf_add_qhalf(iewpf_ctx_t* ctx, const float* x);
 
 /* The CUDA stream (cudaStream_t) on which all work of ctx runs, so that a
- * caller can order its own work or record timing events on it. */
+ * caller can order its own work or record timing events on it (a service of
+ * the library).  Errors: EINVAL. */
 IEWPF_API int iewpf_stream(const iewpf_ctx_t* ctx, void** stream);
 
 /* n scheme steps (eq. swecfl's subdivision of the model step) of length dt
@@ -358,7 +379,8 @@ IEWPF_API int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt);
 
 /* Particle scheme steps (sum over particles of the scheme steps each took)
  * executed by the context so far; one unit of work is a particle scheme
- * step over nx*ny cells. */
+ * step over nx*ny cells (the unit of the throughput metric).
+ * Errors: EINVAL, ECUDA. */
 IEWPF_API int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps);
 
 /* Scheme-step kernel of the context (Sec. 3.1; all kinds compute the same
@@ -366,17 +388,20 @@ IEWPF_API int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps);
  * root; kind 1: register-marching kernel with nc (2, 3 or 4) columns per
  * lane, `rows` rows per chunk and `warps` (1..8) warps per CTA, using the
  * hardware reciprocal and reciprocal square root.  Marching shapes give
- * bit-identical results to one another. */
+ * bit-identical results to one another.  Errors: EINVAL (an unknown kind
+ * or shape). */
 IEWPF_API int iewpf_set_stepper(iewpf_ctx_t* ctx, int kind, int nc, int rows, int warps);
 
 /* Autotuner: times every marching shape on the context's own problem (the
  * state is left unchanged) and keeps the fastest; shape[4] (may be NULL)
  * receives (kind, nc, rows, warps).  Runs by itself before the first
- * forecast unless iewpf_set_stepper was called. */
+ * forecast unless iewpf_set_stepper was called.  get_stepper reads the
+ * current shape.  Errors: EINVAL, ECUDA. */
 IEWPF_API int iewpf_tune(iewpf_ctx_t* ctx, int* shape);
 IEWPF_API int iewpf_get_stepper(const iewpf_ctx_t* ctx, int* shape);
 
-/* Number of kernels the context has launched so far. */
+/* Number of kernels the context has launched so far (a service of the
+ * library).  Errors: EINVAL. */
 IEWPF_API int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count);
 
 /* ---- batched problems -------------------------------------------- */
@@ -505,7 +530,9 @@ IEWPF_API int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_
 IEWPF_API int iewpf_surrogate_stats(const iewpf_ctx_t* ctx, int64_t* calls, int64_t* fallbacks);
 IEWPF_API const char* iewpf_surrogate_last_error(const iewpf_surrogate_t* s);
 
-/* Sizes derived from the parameters. */
+/* Sizes derived from the parameters: the coarse grid Omega^R of Sec. 3.2
+ * (nRx x nRy points every c_omega cells) and the pull-stencil radius R;
+ * any output pointer may be NULL.  Errors: EINVAL (NULL ctx). */
 IEWPF_API int iewpf_sizes(const iewpf_ctx_t* ctx, int* nRx, int* nRy, int* stencil_R);
 
 #ifdef __cplusplus
