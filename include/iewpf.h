@@ -416,28 +416,36 @@ IEWPF_API int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count);
  * problems run one by one through iewpf_forecast / iewpf_assimilate. */
 typedef struct iewpf_batch iewpf_batch_t;
 
-/* n problems; params[i] as for iewpf_create (n_obs_max >= 1, a distinct
- * instance_id gives independent draws); mooring_xy may be NULL or hold one
- * pointer per problem (NULL for drifter problems). */
+/* Batched problems (not in the paper, whose experiments run one problem per
+ * GPU): n independent IEWPF problems advanced together by persistent
+ * kernels, each cycle one CUDA graph.  params[i] as for iewpf_create
+ * (n_obs_max >= 1, a distinct instance_id gives independent draws);
+ * mooring_xy may be NULL or hold one pointer per problem (NULL for drifter
+ * problems).  destroy frees the batch and its contexts (NULL accepted).
+ * Errors: EINVAL (n < 1, a problem's parameters), ENOMEM, ECUDA, ENOTPD. */
 IEWPF_API int iewpf_batch_create(const iewpf_params_t* params, const double* const* mooring_xy, int n,
                                  iewpf_batch_t** out);
 IEWPF_API int iewpf_batch_destroy(iewpf_batch_t* b);
 
 /* The context of problem i (owned by the batch): set or read its state,
- * counters and per-particle diagnostics with the one-problem calls. */
+ * counters and per-particle diagnostics with the one-problem calls.
+ * Errors: EINVAL (i out of range, NULL out). */
 IEWPF_API int iewpf_batch_instance(iewpf_batch_t* b, int i, iewpf_ctx_t** ctx);
 
 /* Autotuner of the batched scheme step (columns per lane, rows per chunk,
  * warps per CTA); shape[3] may be NULL.  Runs by itself before the first
- * cycle. */
+ * cycle.  Errors: EINVAL, ECUDA. */
 IEWPF_API int iewpf_batch_tune(iewpf_batch_t* b, int* shape);
 
 /* One cycle of every problem: n_model_steps model steps (model error after
  * all but the last, Sec. 4.1) and one IEWPF analysis against obs[i]
  * (obs[i].n_obs must equal problem i's n_obs_max).  diag (may be NULL)
  * receives [n][3] = (w_target, beta, error flags) per problem, w_target
- * being c_bar for the two-stage scheme.  Returns the
- * first problem's error, if any. */
+ * being c_bar for the two-stage scheme.  Drifter problems may give their
+ * observations as two fixes (value = NULL, see iewpf_obs_t).  Returns the
+ * first problem's error, if any: EINVAL (observations that do not fill
+ * n_obs_max, non-finite values; refused before any device work), EBETA,
+ * EDOMAIN, ENONFINITE, ENOTPD, ECUDA. */
 IEWPF_API int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf_obs_t* obs, double* diag);
 
 /* A free forecast of every problem (eq. model_equation without
@@ -449,8 +457,10 @@ IEWPF_API int iewpf_batch_cycle(iewpf_batch_t* b, int n_model_steps, const iewpf
 IEWPF_API int iewpf_batch_forecast(iewpf_batch_t* b, int n_model_steps, int add_model_error);
 IEWPF_API int iewpf_batch_stream(const iewpf_batch_t* b, void** stream);
 
-/* Particle scheme steps executed by the batch and kernel launches it
- * enqueued (a graph replay counts the launches of one capture). */
+/* The batch's CUDA stream; the particle scheme steps executed by the batch
+ * and the kernel launches it enqueued (a graph replay counts the launches
+ * of one capture; either pointer may be NULL); the message of the last
+ * error.  Errors: EINVAL, ECUDA. */
 IEWPF_API int iewpf_batch_work(iewpf_batch_t* b, int64_t* particle_substeps, int64_t* launches);
 IEWPF_API const char* iewpf_batch_last_error(const iewpf_batch_t* b);
 
@@ -475,24 +485,32 @@ IEWPF_API const char* iewpf_batch_last_error(const iewpf_batch_t* b);
  * ------------------------------------------------------------------------ */
 typedef struct iewpf_surrogate iewpf_surrogate_t;
 
-/* width 64 (or 16), depth >= 2; He-normal weights from `seed`, zero biases,
- * output layer scaled by 0.1. */
+/* A network for nx x ny fields: width 64 (or 16), depth >= 2; He-normal
+ * weights from `seed`, zero biases, output layer scaled by 0.1 (not in the
+ * paper: the learned surrogate described above).  destroy frees it (NULL
+ * accepted); param_count gives the length of the flat parameter array.
+ * Errors: EINVAL (sizes), ENOMEM, ECUDA. */
 IEWPF_API int iewpf_surrogate_create(int nx, int ny, int width, int depth, uint64_t seed, iewpf_surrogate_t** out);
 IEWPF_API int iewpf_surrogate_destroy(iewpf_surrogate_t* s);
 IEWPF_API int iewpf_surrogate_param_count(const iewpf_surrogate_t* s, int64_t* n);
-/* FP32 parameters in the flat layout above (host arrays, copied). */
+/* FP32 parameters in the flat layout above (host arrays, copied).
+ * Errors: EINVAL (NULL), ECUDA. */
 IEWPF_API int iewpf_surrogate_set_params(iewpf_surrogate_t* s, const float* params);
 IEWPF_API int iewpf_surrogate_get_params(const iewpf_surrogate_t* s, float* params);
-/* in_scale[3], out_scale[3] (> 0) */
+/* Input and output scales per field, in_scale[3], out_scale[3] (> 0, host).
+ * Errors: EINVAL (NULL or not positive). */
 IEWPF_API int iewpf_surrogate_set_scales(iewpf_surrogate_t* s, const double* in_scale, const double* out_scale);
 IEWPF_API int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, double* out_scale);
 /* Convolution path: 0 (default) = tcgen05 tensor-core kernels where nx is a
  * multiple of 128 and ny even, else mma.sync kernels; 1 = always mma.sync.
  * The backward pass always uses the mma.sync kernels.  get_path tells
- * whether the forward pass runs on tcgen05. */
+ * whether the forward pass runs on tcgen05.  Errors: EINVAL (path not 0 or 1,
+ * NULL). */
 IEWPF_API int iewpf_surrogate_set_path(iewpf_surrogate_t* s, int path);
 IEWPF_API int iewpf_surrogate_get_path(const iewpf_surrogate_t* s, int* uses_tcgen05);
-/* U ([n][3][ny][nx] host FP32) -> Unext (same layout), one network call. */
+/* U ([n][3][ny][nx] host FP32) -> Unext (same layout), one network call.
+ * Errors: EINVAL (n < 1, NULL), ENOMEM, ECUDA, ETIMEOUT (a bounded wait of
+ * the tensor-core kernel gave up). */
 IEWPF_API int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n, float* Unext);
 /* The same on device memory: U and Unext (may be equal: in place) are
  * device pointers [n][3][ny][nx], borrowed; the work is ordered after the
@@ -501,10 +519,11 @@ IEWPF_API int iewpf_surrogate_apply(iewpf_surrogate_t* s, const float* U, int n,
  * stream, a timeout of a bounded wait inside the tensor-core kernel
  * (IEWPF_ETIMEOUT) is reported by the next synchronous call. */
 IEWPF_API int iewpf_surrogate_apply_device(iewpf_surrogate_t* s, const float* U, int n, float* Unext, void* stream);
-/* The surrogate's own CUDA stream. */
+/* The surrogate's own CUDA stream.  Errors: EINVAL. */
 IEWPF_API int iewpf_surrogate_stream(const iewpf_surrogate_t* s, void** stream);
 /* Loss and its gradient w.r.t. the FP32 parameters (grad[n_params], may be
- * NULL) for the pairs X -> Y ([n][3][ny][nx] host FP32). */
+ * NULL) for the pairs X -> Y ([n][3][ny][nx] host FP32).
+ * Errors: EINVAL (n < 1, NULL), ENOMEM, ECUDA. */
 IEWPF_API int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, const float* Y, int n, double* loss,
                                         float* grad);
 /* Training on n_pairs pairs (psi, M^k psi), M^k = k_steps model steps of the
@@ -515,7 +534,10 @@ IEWPF_API int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, co
  * the input and of the change; one scale for eta, one shared by hu and hv).
  * Then `epochs` shuffled passes of Adam (beta 0.9, 0.999, eps 1e-8, step lr)
  * in mini-batches of `batch` (a last partial batch is skipped);
- * epoch_loss[epochs] (may be NULL) receives the mean batch loss. */
+ * epoch_loss[epochs] (may be NULL) receives the mean batch loss.
+ * Errors: EINVAL (sizes that differ from ctx's grid, non-positive counts or
+ * rate), ENOMEM, ECUDA, ENONFINITE (a non-finite state while generating
+ * the pairs). */
 IEWPF_API int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs,
                                     int batch, double lr, double* epoch_loss);
 /* Attach (s != NULL, k_steps >= 1) or detach (s = NULL) a surrogate to ctx
@@ -524,9 +546,11 @@ IEWPF_API int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int 
  * and those steps are run by the plain stepper when the network's state is
  * not finite or, for some particle, max|eta| exceeds 1.5 x its value before
  * plus 0.01 m, or the largest |hu/h|, |hv/h| exceeds 1.5 x its value before
- * plus 0.05 m/s. */
+ * plus 0.05 m/s.  Errors: EINVAL (k_steps < 1, a network of another grid
+ * size). */
 IEWPF_API int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_steps);
-/* Surrogate calls made for ctx and how many fell back to the plain stepper. */
+/* Surrogate calls made for ctx and how many fell back to the plain stepper;
+ * the message of a surrogate's last error.  Errors: EINVAL. */
 IEWPF_API int iewpf_surrogate_stats(const iewpf_ctx_t* ctx, int64_t* calls, int64_t* fallbacks);
 IEWPF_API const char* iewpf_surrogate_last_error(const iewpf_surrogate_t* s);
 
