@@ -57,3 +57,11 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.replace("the oracle", ""), f
+
+
+def test_every_export_has_its_argument_types_declared():
+    # a C function called through ctypes without argtypes would have its
+    # arguments converted by guesswork (doubles and 64-bit ints lost)
+    from paper_1910_01031_gb300 import iewpf
+    L = iewpf.load()
+    assert [n for n in iewpf.EXPORTS if getattr(L, n).argtypes is None] == []
