@@ -174,6 +174,24 @@ def _f64(a, shape=None):
     return a
 
 
+def make_obs(xy, values, xy_prev=None, dt=0.0):
+    """An iewpf_obs_t for one observation time and the arrays it points to
+    (kept alive by the caller).  values None: drifter observations given as
+    the fixes xy and xy_prev taken dt seconds apart, formed by the library
+    (eq. drifterObservation)."""
+    xy = None if xy is None else _f64(xy, (-1, 2))
+    if values is None:
+        if xy is None or xy_prev is None:
+            raise ValueError("without values, both fixes xy and xy_prev are needed")
+        xy_prev = _f64(xy_prev, (-1, 2))
+        n = xy.shape[0]
+    else:
+        values = _f64(values, (-1, 2))
+        n = values.shape[0]
+        xy_prev = None
+    return Obs(n, _ptr(xy), _ptr(values), _ptr(xy_prev), float(dt)), (xy, values, xy_prev)
+
+
 def params_from_config(cfg, n_drifters_max=0, n_obs_max=None, scheme=TWO_STAGE):
     """iewpf_params_t from a synth.Config."""
     return Params(cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.g, cfg.f, cfg.H, cfg.theta, cfg.courant, cfg.dt_model,
@@ -254,15 +272,7 @@ class Ensemble:
     def assimilate(self, xy, values, diag=True, xy_prev=None, dt=0.0):
         """values None: drifter observations formed by the library from the
         fixes xy and xy_prev taken dt seconds apart (eq. drifterObservation)."""
-        xy = None if xy is None else _f64(xy, (-1, 2))
-        if values is None:
-            xy_prev = _f64(xy_prev, (-1, 2))
-            n = xy.shape[0]
-        else:
-            values = _f64(values, (-1, 2))
-            n = values.shape[0]
-            xy_prev = None
-        obs = Obs(n, _ptr(xy), _ptr(values), _ptr(xy_prev), float(dt))
+        obs, keep = make_obs(xy, values, xy_prev, dt)
         out = None
         dptr = None
         if diag:
@@ -276,15 +286,14 @@ class Ensemble:
             out["w_target"] = d.w_target
         return out
 
-    def sir_weights(self, xy, values, sets, r_scale=1.0, weights=True):
+    def sir_weights(self, xy, values, sets, r_scale=1.0, weights=True, xy_prev=None, dt=0.0):
         """Standard particle filter weights against each row of sets (observation
-        indices): returns (w [n_sets][N_e] or None, n_kept [n_sets])."""
-        values = _f64(values, (-1, 2))
-        xy = None if xy is None else _f64(xy, (-1, 2))
+        indices): returns (w [n_sets][N_e] or None, n_kept [n_sets]).  values
+        None: drifter observations from the fixes xy, xy_prev (see make_obs)."""
         sets = np.ascontiguousarray(sets, np.int32)
         if sets.ndim != 2:
             raise ValueError("sets must be [n_sets][set_size]")
-        obs = Obs(values.shape[0], _ptr(xy), _ptr(values))
+        obs, keep = make_obs(xy, values, xy_prev, dt)
         w = np.zeros((sets.shape[0], self.ne)) if weights else None
         kept = np.zeros(sets.shape[0], np.int32)
         self._chk(self.L.iewpf_sir_weights(self.h, ctypes.byref(obs), float(r_scale), sets.shape[0], sets.shape[1],
@@ -466,14 +475,13 @@ class Batch:
         return tuple(int(v) for v in out)
 
     def cycle(self, n_steps, obs):
-        """obs: list of (xy or None, values) per problem; returns diag [n][3]."""
+        """obs: list per problem of (xy or None, values) or, for drifters,
+        (xy, None, xy_prev, dt) (see make_obs); returns diag [n][3]."""
         keep = []
         arr = (Obs * self.n)()
-        for i, (xy, val) in enumerate(obs):
-            val = _f64(val, (-1, 2))
-            xy = None if xy is None else _f64(xy, (-1, 2))
-            keep += [val, xy]
-            arr[i] = Obs(val.shape[0], _ptr(xy), _ptr(val))
+        for i, o in enumerate(obs):
+            arr[i], k = make_obs(*o)
+            keep.append(k)
         diag = np.zeros((self.n, 3))
         self._chk(self.L.iewpf_batch_cycle(self.h, int(n_steps), arr, _ptr(diag)), "batch_cycle")
         return diag

@@ -38,3 +38,17 @@ def test_library_form_rejects_bad_arguments():
         iewpf.drifter_obs(p, np.zeros((2, 2)), np.zeros((2, 2)), 0.0)
     with pytest.raises(iewpf.IewpfError):
         iewpf.drifter_obs(p, np.array([[np.nan, 0.0]]), np.zeros((1, 2)), 60.0)
+
+
+def test_observation_structure_of_the_binding():
+    # values given: xy_prev is not passed; values None: both fixes and dt
+    xy = np.array([[1.0, 2.0], [3.0, 4.0]])
+    vals = np.array([[0.5, -0.5], [1.5, 2.5]])
+    obs, keep = iewpf.make_obs(xy, vals)
+    assert obs.n_obs == 2 and obs.xy[3] == 4.0 and obs.value[2] == 1.5 and not obs.xy_prev
+    obs, keep = iewpf.make_obs(xy, None, xy_prev=xy - 1.0, dt=60.0)
+    assert obs.n_obs == 2 and not obs.value and obs.xy_prev[0] == 0.0 and obs.dt == 60.0
+    obs, keep = iewpf.make_obs(None, vals)                      # moorings: positions fixed at creation
+    assert not obs.xy and obs.value[1] == -0.5
+    with pytest.raises(ValueError):
+        iewpf.make_obs(xy, None)
