@@ -65,3 +65,24 @@ def test_every_export_has_its_argument_types_declared():
     from paper_1910_01031_gb300 import iewpf
     L = iewpf.load()
     assert [n for n in iewpf.EXPORTS if getattr(L, n).argtypes is None] == []
+
+
+def test_building_blocks_refuse_bad_arguments_before_device_work():
+    # these checks run on the host, so they hold without a GPU
+    import ctypes
+    import numpy as np
+    from paper_1910_01031_gb300 import iewpf
+    L = iewpf.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    one = np.ones(3)
+    p = one.ctypes.data_as(dp)
+    out = np.zeros(3)
+    q = out.ctypes.data_as(dp)
+    assert L.iewpf_weights(0, 10.0, p, p, p, q, q, q, q) == -1                 # no particles
+    assert L.iewpf_weights(3, 0.0, p, p, p, q, q, q, q) == -1                  # N_psi not positive
+    assert L.iewpf_weights(3, 10.0, None, p, p, q, q, q, q) == -1
+    assert L.iewpf_weights_one_stage(3, -1.0, p, p, q, q, q, q) == -1
+    neg = np.array([1.0, -0.5, 2.0])
+    assert L.iewpf_alpha_gamma(3, 10.0, p, neg.ctypes.data_as(dp), q) == -1   # c* < 0
+    assert L.iewpf_alpha_gamma(3, 10.0, neg.ctypes.data_as(dp), p, q) == -1   # gamma <= 0
+    assert L.iewpf_normals(0, 0, 0, 0, 4, None, None) == -1                   # no output
