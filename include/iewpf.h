@@ -340,9 +340,12 @@ IEWPF_API int iewpf_alpha_gamma(int ne, double N_psi, const double* gamma, const
  * library holds until the process exits.
  *   - ne must not exceed IEWPF_WEIGHTS_NOALLOC_MAX_NE (4096); larger ensembles
  *     get IEWPF_EINVAL before any GPU work.
- *   - The first call on a device looks up the scratch's device address with
- *     cudaGetSymbolAddress (with that device current) and keeps it; make that
- *     first call before any stream capture on the device.
+ *   - Every call looks up the scratch's device address with
+ *     cudaGetSymbolAddress on the current device; no address is cached, so a
+ *     context that was reset and created again is handled.
+ *   - It must not be called while any stream capture is active on the
+ *     device: its synchronous copies on the legacy default stream are not
+ *     allowed during a capture.
  *   - Every call shares the one array, which keeps the last call's contents;
  *     the call clears its error flag itself.  Calls whose GPU work overlaps
  *     (from several host threads) race on the array: serialise them.

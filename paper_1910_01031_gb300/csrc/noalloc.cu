@@ -3,11 +3,11 @@
 //
 // The scratch is one file-scope __device__ array that every GPU loading the
 // library holds until the process exits.  Host code must not use its name as
-// a device address (in host code it is only a stand-in symbol), so the first
-// call on each device looks the address up with cudaGetSymbolAddress while
-// that device is current and keeps it for later calls.
-#include <mutex>
-
+// a device address (in host code it is only a stand-in symbol), so every call
+// looks the address up with cudaGetSymbolAddress while the caller's device is
+// current.  Nothing is cached: a context torn down and created again (after
+// cudaDeviceReset, say) loads the module at a new address, and the next call
+// sees it.
 #include "../../include/iewpf.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -23,25 +23,15 @@ constexpr int kDoubles = 6 * kMax + 8;
 
 static __device__ __align__(256) double g_weights_scratch[kDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch on the current device (looked up once).
+// Device address of the scratch in the current device's context.
 int scratch_address(double** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IEWPF_ECUDA;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_weights_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return IEWPF_ECUDA;
-        }
-        g_addr[dev] = static_cast<double*>(p);
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_weights_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return IEWPF_ECUDA;
     }
-    *out = g_addr[dev];
+    *out = static_cast<double*>(p);
     return IEWPF_OK;
 }
 

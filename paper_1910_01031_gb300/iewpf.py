@@ -184,10 +184,14 @@ def make_obs(xy, values, xy_prev=None, dt=0.0):
         if xy is None or xy_prev is None:
             raise ValueError("without values, both fixes xy and xy_prev are needed")
         xy_prev = _f64(xy_prev, (-1, 2))
+        if xy_prev.shape != xy.shape:
+            raise ValueError("xy_prev must have the shape of xy")
         n = xy.shape[0]
     else:
         values = _f64(values, (-1, 2))
         n = values.shape[0]
+        if xy is not None and xy.shape != values.shape:
+            raise ValueError("xy and values must have the same shape")
         xy_prev = None
     return Obs(n, _ptr(xy), _ptr(values), _ptr(xy_prev), float(dt)), (xy, values, xy_prev)
 
@@ -645,6 +649,8 @@ def drifter_obs(params, xy, xy_prev, dt):
     drifter fixes dt seconds apart, minimum image on the periodic domain."""
     L = load()
     xy, xy_prev = _f64(xy, (-1, 2)), _f64(xy_prev, (-1, 2))
+    if xy_prev.shape != xy.shape:
+        raise ValueError("xy_prev must have the shape of xy")
     out = np.zeros_like(xy)
     rc = L.iewpf_drifter_obs(ctypes.byref(params), xy.shape[0], _ptr(xy), _ptr(xy_prev), float(dt), _ptr(out))
     if rc != IEWPF_OK:

@@ -52,3 +52,16 @@ def test_observation_structure_of_the_binding():
     assert not obs.xy and obs.value[1] == -0.5
     with pytest.raises(ValueError):
         iewpf.make_obs(xy, None)
+
+
+def test_binding_refuses_mismatched_observation_arrays():
+    # the C side reads 2 n doubles from every pointer it is given, so a short
+    # array must be refused in the binding before any call
+    xy = np.array([[1.0, 2.0], [3.0, 4.0]])
+    with pytest.raises(ValueError):
+        iewpf.make_obs(xy, None, xy_prev=xy[:1], dt=60.0)
+    with pytest.raises(ValueError):
+        iewpf.make_obs(xy, np.zeros((3, 2)))
+    cfg = synth.config1()
+    with pytest.raises(ValueError):
+        iewpf.drifter_obs(iewpf.params_from_config(cfg), xy, xy[:1], 60.0)

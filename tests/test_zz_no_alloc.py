@@ -51,3 +51,22 @@ def test_noalloc_weights_reject_ensembles_above_the_maximum():
     with pytest.raises(iewpf.IewpfError) as e:
         iewpf.weights(c, gamma, zeta, 12288.0, noalloc=True)
     assert e.value.name == "EINVAL"
+
+
+def test_noalloc_weights_at_the_largest_accepted_ensemble_then_a_smaller_call():
+    # ne = maximum fills the -log w slice up to the c_bar/beta slot and the
+    # flag that follow it; a smaller call afterwards must be unaffected
+    ne = iewpf.WEIGHTS_NOALLOC_MAX_NE
+    c, gamma, zeta = _inputs(5, ne, 3145728.0, 3042)
+    ref = iewpf.weights(c, gamma, zeta, 3145728.0)
+    got = iewpf.weights(c, gamma, zeta, 3145728.0, noalloc=True)
+    assert math.isclose(got["cbar"], ref["cbar"], rel_tol=1e-10)
+    assert math.isclose(got["beta"], ref["beta"], rel_tol=1e-10)
+    for k in ("alpha", "cstar", "neglogw"):
+        assert np.allclose(got[k], ref[k], rtol=1e-10, atol=1e-12), k
+    c, gamma, zeta = _inputs(6, 10, 12288.0, 2)
+    ref = iewpf.weights(c, gamma, zeta, 12288.0)
+    got = iewpf.weights(c, gamma, zeta, 12288.0, noalloc=True)
+    assert math.isclose(got["beta"], ref["beta"], rel_tol=1e-10)
+    for k in ("alpha", "cstar", "neglogw"):
+        assert np.allclose(got[k], ref[k], rtol=1e-10, atol=1e-12), k
