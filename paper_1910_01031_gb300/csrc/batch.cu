@@ -119,7 +119,7 @@ __global__ void b_nsub(BatchDev B)
     }
 }
 
-template <int NC>
+template <int NC, bool PAIRED>
 __global__ void __launch_bounds__(256) b_step(BatchDev B)
 {
     const long long* pre = space(B, SP_STEP);
@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(256) b_step(BatchDev B)
         const long long per_p = (long long)a.n_strips * a.n_chunks;
         const int p = (int)(r / per_p);
         const int rem = (int)(r % per_p);
-        march::march_warp<NC>(a, p, rem / a.n_strips, rem % a.n_strips, s);
+        if (PAIRED) march::march_warp_paired<NC>(a, p, rem / a.n_strips, rem % a.n_strips, s);
+        else march::march_warp<NC>(a, p, rem / a.n_strips, rem % a.n_strips, s);
     }
 }
 
@@ -407,6 +408,7 @@ struct BatchImpl {
     bool fgraph_err = false;
     int nc = 2;
     int warps = 4;
+    int paired = 0;     // scheme step with the two stages in f32x2 pairs (nc 2 or 3)
     int fixed = 0;
     bool tuned = false;
     long long launches = 0;
@@ -426,22 +428,17 @@ cudaError_t launch_step_nc(BatchImpl& b, cudaStream_t st)
     const BatchDev B = dev_view(b);
     const int thr = 32 * b.warps;
     const long long need = (items(b, SP_STEP) + b.warps - 1) / b.warps;
-    switch (b.nc) {
-    case 2: {
-        const int g = (int)std::min<long long>(need, resident_blocks((const void*)b_step<2>, thr));
-        b_step<2><<<g, thr, 0, st>>>(B);
-        break;
-    }
-    case 3: {
-        const int g = (int)std::min<long long>(need, resident_blocks((const void*)b_step<3>, thr));
-        b_step<3><<<g, thr, 0, st>>>(B);
-        break;
-    }
-    default: {
-        const int g = (int)std::min<long long>(need, resident_blocks((const void*)b_step<4>, thr));
-        b_step<4><<<g, thr, 0, st>>>(B);
-        break;
-    }
+    auto run = [&](auto kern) {
+        const int g = (int)std::min<long long>(need, resident_blocks((const void*)kern, thr));
+        kern<<<g, thr, 0, st>>>(B);
+    };
+    if (b.paired) {
+        if (b.nc == 2) run(b_step<2, true>);
+        else run(b_step<3, true>);
+    } else {
+        if (b.nc == 2) run(b_step<2, false>);
+        else if (b.nc == 3) run(b_step<3, false>);
+        else run(b_step<4, false>);
     }
     return cudaGetLastError();
 }
@@ -455,10 +452,12 @@ int grid_for(K kern, int threads, long long work_items_per_block_units)
 
 }  // namespace
 
-cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps)
+cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps, int paired)
 {
+    if (paired && nc == 4) return cudaErrorInvalidValue;
     b.nc = nc;
     b.warps = warps;
+    b.paired = paired;
     long long acc = 0;
     for (int i = 0; i < b.n; ++i) {
         BInst& I = b.h_inst[i];
@@ -523,7 +522,7 @@ cudaError_t batch_init(BatchImpl& b, const std::vector<BInst>& insts)
         b.h_inst[i].step_ctr = b.d_ctr + 2 * i;
         b.h_inst[i].cycle = b.d_ctr + 2 * i + 1;
     }
-    return batch_set_step_shape(b, b.nc, 64, b.warps);
+    return batch_set_step_shape(b, b.nc, 64, b.warps, b.paired);
 }
 
 BatchImpl* batch_new() { return new (std::nothrow) BatchImpl(); }
@@ -745,11 +744,13 @@ cudaError_t batch_tune(BatchImpl& b, cudaStream_t st)
     cudaEventCreate(&a);
     cudaEventCreate(&z);
     float best = 1e30f;
-    int bnc = 2, bth = 64, bw = 4;
+    int bnc = 2, bth = 64, bw = 4, bp = 0;
+    for (int paired = 0; paired < 2; ++paired)
     for (int nc : ncs)
         for (int th : ths)
             for (int w : wps) {
-                if ((e = batch_set_step_shape(b, nc, th, w)) != cudaSuccess) return e;
+                if (paired && nc == 4) continue;
+                if ((e = batch_set_step_shape(b, nc, th, w, paired)) != cudaSuccess) return e;
                 if ((e = launch_step_nc(b, st)) != cudaSuccess) return e;
                 cudaEventRecord(a, st);
                 if ((e = launch_step_nc(b, st)) != cudaSuccess) return e;
@@ -763,21 +764,23 @@ cudaError_t batch_tune(BatchImpl& b, cudaStream_t st)
                     bnc = nc;
                     bth = th;
                     bw = w;
+                    bp = paired;
                 }
             }
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     b.tuned = true;
-    return batch_set_step_shape(b, bnc, bth, bw);
+    return batch_set_step_shape(b, bnc, bth, bw, bp);
 }
 
 bool batch_tuned(const BatchImpl& b) { return b.tuned; }
 
 void batch_shape(const BatchImpl& b, int* shape)
 {
-    shape[0] = b.nc;
-    shape[1] = b.n ? b.h_inst[0].step.TH : 0;
-    shape[2] = b.warps;
+    shape[0] = 1 + b.paired;
+    shape[1] = b.nc;
+    shape[2] = b.n ? b.h_inst[0].step.TH : 0;
+    shape[3] = b.warps;
 }
 
 }  // namespace iewpf

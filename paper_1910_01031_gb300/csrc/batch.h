@@ -70,7 +70,7 @@ struct BatchImpl;
 BatchImpl* batch_new();
 void batch_delete(BatchImpl* b);
 cudaError_t batch_init(BatchImpl& b, const std::vector<BInst>& insts);
-cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps);
+cudaError_t batch_set_step_shape(BatchImpl& b, int nc, int th, int warps, int paired);
 cudaError_t batch_tune(BatchImpl& b, cudaStream_t st);
 cudaError_t batch_cycle(BatchImpl& b, int n_steps, cudaStream_t st, cudaStream_t st2);
 cudaError_t batch_forecast(BatchImpl& b, int n_steps, bool err, cudaStream_t st, cudaStream_t st2);

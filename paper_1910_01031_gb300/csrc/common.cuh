@@ -7,9 +7,6 @@
 
 namespace iewpf {
 
-// Tile of fine cells handled by one CTA of the shared-memory scheme step.
-constexpr int TW = 32;
-constexpr int TH = 16;
 // Tile of the fine model-error and analysis-update kernels, and of the
 // observation lists of the pull.
 constexpr int OBS_TX = 64;

@@ -9,9 +9,6 @@
 namespace iewpf {
 
 // ---- stepper.cu -----------------------------------------------------------
-size_t rk2_smem_bytes();
-cudaError_t launch_rk2(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
-                       const Grid& G, cudaStream_t st);
 // have_amax: amax already holds the CFL rates of the current state (left by
 // the model-error or analysis update); only n_sub is derived then
 cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* amax, int* nsub, float* dtp,
@@ -57,9 +54,12 @@ struct StepArgs {
 }  // namespace march
 
 // tile shape of the register-marching scheme step: NC columns per lane, TH
-// rows per chunk, warps per CTA
+// rows per chunk, warps per CTA, and whether the two Runge-Kutta stages run
+// paired in packed f32x2 registers (march_warp_paired) or one after the other
+// in scalar registers (march_warp)
 struct MarchShape {
     int nc, TH, warps;
+    int paired = 0;
 };
 cudaError_t launch_rk2_march(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
                              const Grid& G, const MarchShape& shape, cudaStream_t st);

@@ -1,194 +1,13 @@
-// Shallow-water ensemble stepper (Sec. 3.1 of arXiv 1910.01031): one scheme
-// step of the second-order SSP Runge-Kutta method with central-upwind fluxes
-// and the Coriolis-adjusted (well-balanced) reconstruction of eta, both
-// Runge-Kutta stages fused in one kernel on a shared-memory tile with a
-// 4-cell halo; plus the per-particle CFL reduction (eq. swecfl), drifter
-// advection and the state scan for non-finite values.
+// Per-particle services of the shallow-water ensemble stepper (Sec. 3.1 of
+// arXiv 1910.01031; the scheme step itself is in march.cu): the CFL
+// reduction (eq. swecfl), drifter advection, the drift-forecast errors and
+// the state scan for non-finite values.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace iewpf {
 
 namespace {
-
-constexpr int HALO = 4;
-constexpr int IW = TW + 2 * HALO;   // loaded tile width  (40)
-constexpr int IH = TH + 2 * HALO;   // loaded tile height (24)
-constexpr int S1W = TW + 4, S1H = TH + 4;   // stage-1 output region (36 x 20)
-
-// shared-memory scratch sized for the larger (first) stage
-constexpr int VEL_N = IW * IH;                    // u, v on the stage input
-constexpr int SLP_N = (IW - 2) * (IH - 2);        // slopes on the inner ring
-constexpr int FX_N = (S1W + 1) * S1H;             // x-face fluxes
-constexpr int GY_N = S1W * (S1H + 1);             // y-face fluxes
-
-struct Smem {
-    float U0[3][IH][IW];
-    float U1[3][S1H][S1W];
-    float vel[2][VEL_N];
-    float slp[6][SLP_N];
-    float fx[3][FX_N];
-    float gy[3][GY_N];
-};
-
-__device__ __forceinline__ float gminmod(float a, float b, float th)
-{
-    const float x = th * a, y = 0.5f * (a + b), z = th * b;
-    const float mn = fminf(x, fminf(y, z));
-    const float mx = fmaxf(x, fmaxf(y, z));
-    return mn > 0.0f ? mn : (mx < 0.0f ? mx : 0.0f);
-}
-
-// Central-upwind flux across a face with left state L and right state R;
-// qn is the momentum normal to the face, qt the tangential one.  Returns
-// (mass, normal momentum, tangential momentum) fluxes.  The tangential
-// momentum is carried by the mass flux with the upwind tangential velocity.
-__device__ __forceinline__ void cu_flux(float etaL, float qnL, float qtL, float etaR, float qnR,
-                                        float qtR, const Grid& G, float& F0, float& F1, float& F2)
-{
-    const float hL = G.H + etaL, hR = G.H + etaR;
-    const float unL = qnL / hL, unR = qnR / hR;
-    const float cL = sqrtf(G.g * hL), cR = sqrtf(G.g * hR);
-    const float ap = fmaxf(fmaxf(unL + cL, unR + cR), 0.0f);
-    const float am = fminf(fminf(unL - cL, unR - cR), 0.0f);
-    const float inv = 1.0f / (ap - am);
-    const float apam = ap * am;
-    F0 = (ap * qnL - am * qnR + apam * (etaR - etaL)) * inv;
-    const float pL = G.g * etaL * (G.H + 0.5f * etaL);
-    const float pR = G.g * etaR * (G.H + 0.5f * etaR);
-    F1 = (ap * (qnL * unL + pL) - am * (qnR * unR + pR) + apam * (qnR - qnL)) * inv;
-    const float ut = (F0 >= 0.0f) ? qtL / hL : qtR / hR;
-    F2 = F0 * ut;
-}
-
-// One evaluation of L(U) on an output region of RW x RH cells from an input
-// array in[3][RH+4][RW+4] (2-cell halo); writes out(c, r, L0, L1, L2) for
-// input-coordinates (c, r) in [2, RW+2) x [2, RH+2).
-template <int RW, int RH, typename Out>
-__device__ __forceinline__ void stage(const float* __restrict__ in, Smem& sm, const Grid& G, Out out)
-{
-    constexpr int W = RW + 4, Hh = RH + 4;
-    constexpr int N = W * Hh;
-    const int tid = threadIdx.x;
-    const float* eta = in;
-    const float* hu = in + N;
-    const float* hv = in + 2 * N;
-    float* u = sm.vel[0];
-    float* v = sm.vel[1];
-    // pass 0: velocities
-    for (int i = tid; i < N; i += NTHREADS) {
-        const float h = G.H + eta[i];
-        u[i] = hu[i] / h;
-        v[i] = hv[i] / h;
-    }
-    __syncthreads();
-    // pass 1: limited slopes of K, hu, hv in x and of L, hu, hv in y
-    constexpr int SW = W - 2, SH = Hh - 2;
-    for (int i = tid; i < SW * SH; i += NTHREADS) {
-        const int c = 1 + i % SW, r = 1 + i / SW;
-        const int k = r * W + c;
-        const int kw = k - 1, ke = k + 1, ks = k - W, kn = k + W;
-        const float dKw = G.g * (eta[k] - eta[kw]) - G.fdx_half * (v[kw] + v[k]);
-        const float dKe = G.g * (eta[ke] - eta[k]) - G.fdx_half * (v[k] + v[ke]);
-        const float dLs = G.g * (eta[k] - eta[ks]) + G.fdy_half * (u[ks] + u[k]);
-        const float dLn = G.g * (eta[kn] - eta[k]) + G.fdy_half * (u[k] + u[kn]);
-        sm.slp[0][i] = gminmod(dKw, dKe, G.theta);
-        sm.slp[1][i] = gminmod(hu[k] - hu[kw], hu[ke] - hu[k], G.theta);
-        sm.slp[2][i] = gminmod(hv[k] - hv[kw], hv[ke] - hv[k], G.theta);
-        sm.slp[3][i] = gminmod(dLs, dLn, G.theta);
-        sm.slp[4][i] = gminmod(hu[k] - hu[ks], hu[kn] - hu[k], G.theta);
-        sm.slp[5][i] = gminmod(hv[k] - hv[ks], hv[kn] - hv[k], G.theta);
-    }
-    __syncthreads();
-    // pass 2a: x-faces between input columns c and c+1, c in [1, RW+2), rows [2, RH+2)
-    constexpr int FXW = RW + 1;
-    for (int i = tid; i < FXW * RH; i += NTHREADS) {
-        const int c = 1 + i % FXW, r = 2 + i / FXW;
-        const int kL = r * W + c, kR = kL + 1;
-        const int sL = (r - 1) * SW + (c - 1), sR = sL + 1;
-        const float eL = eta[kL] + (sm.slp[0][sL] + G.fdx * v[kL]) * G.inv_2g;
-        const float eR = eta[kR] - (sm.slp[0][sR] + G.fdx * v[kR]) * G.inv_2g;
-        const float quL = hu[kL] + 0.5f * sm.slp[1][sL], quR = hu[kR] - 0.5f * sm.slp[1][sR];
-        const float qvL = hv[kL] + 0.5f * sm.slp[2][sL], qvR = hv[kR] - 0.5f * sm.slp[2][sR];
-        float F0, F1, F2;
-        cu_flux(eL, quL, qvL, eR, quR, qvR, G, F0, F1, F2);
-        sm.fx[0][i] = F0;
-        sm.fx[1][i] = F1;
-        sm.fx[2][i] = F2;
-    }
-    // pass 2b: y-faces between input rows r and r+1, r in [1, RH+2), columns [2, RW+2)
-    for (int i = tid; i < RW * (RH + 1); i += NTHREADS) {
-        const int c = 2 + i % RW, r = 1 + i / RW;
-        const int kB = r * W + c, kT = kB + W;
-        const int sB = (r - 1) * SW + (c - 1), sT = sB + SW;
-        const float eB = eta[kB] + (sm.slp[3][sB] - G.fdy * u[kB]) * G.inv_2g;
-        const float eT = eta[kT] - (sm.slp[3][sT] - G.fdy * u[kT]) * G.inv_2g;
-        const float quB = hu[kB] + 0.5f * sm.slp[4][sB], quT = hu[kT] - 0.5f * sm.slp[4][sT];
-        const float qvB = hv[kB] + 0.5f * sm.slp[5][sB], qvT = hv[kT] - 0.5f * sm.slp[5][sT];
-        float G0, Gv, Gu;
-        cu_flux(eB, qvB, quB, eT, qvT, quT, G, G0, Gv, Gu);
-        sm.gy[0][i] = G0;
-        sm.gy[1][i] = Gu;
-        sm.gy[2][i] = Gv;
-    }
-    __syncthreads();
-    // pass 3: flux differences plus the Coriolis source (f hv, -f hu)
-    for (int i = tid; i < RW * RH; i += NTHREADS) {
-        const int c = 2 + i % RW, r = 2 + i / RW;
-        const int k = r * W + c;
-        const int fr = (r - 2) * FXW + (c - 1);      // right x-face; left is fr - 1
-        const int gt = (r - 1) * RW + (c - 2);       // top y-face; bottom is gt - RW
-        float L[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            L[q] = -(sm.fx[q][fr] - sm.fx[q][fr - 1]) * G.inv_dx - (sm.gy[q][gt] - sm.gy[q][gt - RW]) * G.inv_dy;
-        L[1] += G.f * hv[k];
-        L[2] -= G.f * hu[k];
-        out(c, r, L[0], L[1], L[2]);
-    }
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(NTHREADS)
-rk2_kernel(float* __restrict__ buf0, float* __restrict__ buf1, const int* __restrict__ par,
-           const int* __restrict__ nsub, const float* __restrict__ dtp, int s, Grid G)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-    const int p = blockIdx.z;
-    if (s >= nsub[p]) return;
-    const int src = par[p] ^ (s & 1);
-    const float* __restrict__ in = (src ? buf1 : buf0) + (long long)p * 3 * G.plane;
-    float* __restrict__ outp = (src ? buf0 : buf1) + (long long)p * 3 * G.plane;
-    const float dt = dtp[p];
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    // load the tile with a 4-cell periodic halo
-    for (int i = threadIdx.x; i < IW * IH; i += NTHREADS) {
-        const int c = i % IW, r = i / IW;
-        const int gx = pmod(x0 - HALO + c, G.nx), gy = pmod(y0 - HALO + r, G.ny);
-        const long long g = (long long)gy * G.nx + gx;
-        sm.U0[0][r][c] = in[g];
-        sm.U0[1][r][c] = in[G.plane + g];
-        sm.U0[2][r][c] = in[2 * G.plane + g];
-    }
-    __syncthreads();
-    // stage 1: U1 = U0 + dt L(U0) on the 36 x 20 region at offset 2
-    stage<S1W, S1H>(&sm.U0[0][0][0], sm, G, [&](int c, int r, float L0, float L1, float L2) {
-        sm.U1[0][r - 2][c - 2] = sm.U0[0][r][c] + dt * L0;
-        sm.U1[1][r - 2][c - 2] = sm.U0[1][r][c] + dt * L1;
-        sm.U1[2][r - 2][c - 2] = sm.U0[2][r][c] + dt * L2;
-    });
-    // stage 2: U = (U0 + U1 + dt L(U1)) / 2 on the 32 x 16 tile
-    stage<TW, TH>(&sm.U1[0][0][0], sm, G, [&](int c, int r, float L0, float L1, float L2) {
-        const int gx = x0 + c - 2, gy = y0 + r - 2;
-        if (gx < G.nx && gy < G.ny) {
-            const long long g = (long long)gy * G.nx + gx;
-            outp[g] = 0.5f * (sm.U0[0][r + 2][c + 2] + (sm.U1[0][r][c] + dt * L0));
-            outp[G.plane + g] = 0.5f * (sm.U0[1][r + 2][c + 2] + (sm.U1[1][r][c] + dt * L1));
-            outp[2 * G.plane + g] = 0.5f * (sm.U0[2][r + 2][c + 2] + (sm.U1[2][r][c] + dt * L2));
-        }
-    });
-}
 
 // max over the particle's cells of max((|u| + c)/dx, (|v| + c)/dy)
 __global__ void __launch_bounds__(NTHREADS)
@@ -322,23 +141,6 @@ cudaError_t launch_drift_errors(const double* xy, const double* truth, int ne, i
                                 cudaStream_t st)
 {
     drift_errors_kernel<<<1, 256, 0, st>>>(xy, truth, ne, nd, E, RMSE);
-    return cudaGetLastError();
-}
-
-size_t rk2_smem_bytes() { return sizeof(Smem); }
-
-cudaError_t launch_rk2(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
-                       const Grid& G, cudaStream_t st)
-{
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(rk2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(Smem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid((G.nx + TW - 1) / TW, (G.ny + TH - 1) / TH, G.ne);
-    rk2_kernel<<<grid, NTHREADS, sizeof(Smem), st>>>(b0, b1, par, nsub, dtp, s, G);
     return cudaGetLastError();
 }
 
