@@ -386,13 +386,12 @@ IEWPF_API int iewpf_substeps(iewpf_ctx_t* ctx, int n, double dt);
  * Errors: EINVAL, ECUDA. */
 IEWPF_API int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps);
 
-/* Scheme-step kernel of the context (Sec. 3.1; all kinds compute the same
- * scheme).  kind 0: shared-memory tile kernel with IEEE division and square
- * root; kind 1: register-marching kernel with nc (2, 3 or 4) columns per
- * lane, `rows` rows per chunk and `warps` (1..8) warps per CTA, using the
- * hardware reciprocal and reciprocal square root.  Marching shapes give
- * bit-identical results to one another.  Errors: EINVAL (an unknown kind
- * or shape). */
+/* Scheme-step kernel of the context (Sec. 3.1; both kinds compute the same
+ * scheme, bit for bit).  kind 1: register-marching kernel with nc (2, 3 or
+ * 4) columns per lane, `rows` rows per chunk and `warps` (1..8) warps per
+ * CTA, using the hardware reciprocal and reciprocal square root; kind 2: the
+ * same march with its two Runge-Kutta stages paired in packed f32x2
+ * instructions.  Errors: EINVAL (an unknown kind or shape). */
 IEWPF_API int iewpf_set_stepper(iewpf_ctx_t* ctx, int kind, int nc, int rows, int warps);
 
 /* Autotuner: times every marching shape on the context's own problem (the
@@ -435,9 +434,10 @@ IEWPF_API int iewpf_batch_destroy(iewpf_batch_t* b);
  * Errors: EINVAL (i out of range, NULL out). */
 IEWPF_API int iewpf_batch_instance(iewpf_batch_t* b, int i, iewpf_ctx_t** ctx);
 
-/* Autotuner of the batched scheme step (columns per lane, rows per chunk,
- * warps per CTA); shape[3] may be NULL.  Runs by itself before the first
- * cycle.  Errors: EINVAL, ECUDA. */
+/* Autotuner of the batched scheme step: shape[4] (may be NULL) receives
+ * (kind, columns per lane, rows per chunk, warps per CTA), kind as in
+ * iewpf_set_stepper.  Runs by itself before the first cycle.
+ * Errors: EINVAL, ECUDA. */
 IEWPF_API int iewpf_batch_tune(iewpf_batch_t* b, int* shape);
 
 /* One cycle of every problem: n_model_steps model steps (model error after
@@ -511,6 +511,16 @@ IEWPF_API int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_
  * NULL). */
 IEWPF_API int iewpf_surrogate_set_path(iewpf_surrogate_t* s, int path);
 IEWPF_API int iewpf_surrogate_get_path(const iewpf_surrogate_t* s, int* uses_tcgen05);
+/* Failure injection for tests of the timeout path (the failure detection
+ * of a bounded device wait; no counterpart in the paper).  The next n_evals
+ * evaluations of the network on the tcgen05 path (one per chunk of at most
+ * 64 fields) run kernels whose CTAs first wait, at most 2^16 polls, on an
+ * mbarrier that nothing can complete, before issuing any copy or product;
+ * the wait runs out, each CTA records the timeout, frees its tensor memory
+ * and exits, so the call returns IEWPF_ETIMEOUT and leaves the context
+ * usable.  0 cancels.  The mma.sync path ignores it.
+ * Errors: EINVAL (NULL, n_evals < 0). */
+IEWPF_API int iewpf_surrogate_inject_timeout(iewpf_surrogate_t* s, int n_evals);
 /* U ([n][3][ny][nx] host FP32) -> Unext (same layout), one network call.
  * Errors: EINVAL (n < 1, NULL), ENOMEM, ECUDA, ETIMEOUT (a bounded wait of
  * the tensor-core kernel gave up). */

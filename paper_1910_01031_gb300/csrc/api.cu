@@ -359,8 +359,6 @@ void build_block_root(const iewpf_params_t& P, std::vector<double>& M)
 
 cudaError_t launch_step(iewpf_ctx* ctx, int s)
 {
-    if (ctx->stepper == 0)
-        return launch_rk2(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->st);
     return launch_rk2_march(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, s, ctx->G, ctx->shape, ctx->st);
 }
 
@@ -382,11 +380,12 @@ int tune_stepper(iewpf_ctx* ctx)
     CK(cudaEventCreate(&b));
     float best = 1e30f;
     MarchShape best_shape = ctx->shape;
+    for (int paired = 0; paired < 2; ++paired)
     for (int nc : ncs)
         for (int th : ths) {
-            if (th > 2 * ctx->G.ny) continue;
+            if (th > 2 * ctx->G.ny || (paired && nc == 4)) continue;
             for (int w : wps) {
-                MarchShape sh{nc, th, w};
+                MarchShape sh{nc, th, w, paired};
                 CK(launch_rk2_march(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, 0, ctx->G, sh, ctx->st));
                 CK(cudaEventRecord(a, ctx->st));
                 for (int r = 0; r < 3; ++r)
@@ -406,7 +405,7 @@ int tune_stepper(iewpf_ctx* ctx)
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->shape = best_shape;
-    ctx->stepper = 1;
+    ctx->stepper = 1 + best_shape.paired;
     ctx->tuned = true;
     return IEWPF_OK;
 }
@@ -1410,15 +1409,10 @@ int iewpf_work(iewpf_ctx_t* ctx, int64_t* particle_substeps)
 int iewpf_set_stepper(iewpf_ctx_t* ctx, int kind, int nc, int rows, int warps)
 {
     if (!ctx) return IEWPF_EINVAL;
-    if (kind == 0) {
-        ctx->stepper = 0;
-        ctx->tuned = true;
-        return IEWPF_OK;
-    }
-    if (kind != 1 || (nc != 2 && nc != 3 && nc != 4) || rows < 1 || warps < 1 || warps > 8)
+    if ((kind != 1 && kind != 2) || (nc != 2 && nc != 3 && nc != 4) || rows < 1 || warps < 1 || warps > 8)
         return fail(ctx, IEWPF_EINVAL, "bad stepper shape");
-    ctx->stepper = 1;
-    ctx->shape = MarchShape{nc, rows, warps};
+    ctx->stepper = kind;
+    ctx->shape = MarchShape{nc, rows, warps, kind == 2};
     ctx->tuned = true;
     return IEWPF_OK;
 }
@@ -1842,6 +1836,13 @@ int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, dou
         in_scale[c] = s->net.in_scale[c];
         out_scale[c] = s->net.out_scale[c];
     }
+    return IEWPF_OK;
+}
+
+int iewpf_surrogate_inject_timeout(iewpf_surrogate_t* s, int n_evals)
+{
+    if (!s || n_evals < 0) return IEWPF_EINVAL;
+    s->net.inject_timeouts = n_evals;
     return IEWPF_OK;
 }
 

@@ -70,9 +70,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 }
 
 // bounded wait for the phase of `parity`; gives up when the CTA aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          long long limit = TC_WAIT_LIMIT)
 {
-    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -148,7 +149,7 @@ template <int CIN, int COUT, bool OUT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16* __restrict__ W,
                const float* __restrict__ bias, int nb, int ny, int nx, __nv_bfloat16* __restrict__ aout,
-               float* __restrict__ fout, int* __restrict__ flag)
+               float* __restrict__ fout, int* __restrict__ flag, int probe_polls)
 {
     using L = TcLayout<CIN, COUT>;
     extern __shared__ unsigned char smem_raw[];
@@ -197,10 +198,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[2]), tfull0 = su32(&bars[4]), tempty0 = su32(&bars[6]);
+    // injected failure (probe_polls > 0): before any copy or product is
+    // issued, thread 0 waits on stage 0's full barrier, which nothing can
+    // complete yet, for at most probe_polls polls; the wait runs out through
+    // the same bounded-wait path as the pipeline's, the CTA aborts and runs
+    // no tile, and FLAG_TIMEOUT is recorded below
+    if (probe_polls > 0) {
+        if (tid == 0) mbar_wait(full0, 0, abort, probe_polls);
+        __syncthreads();
+    }
+
     const int tiles_x = nx / TC_PX, tiles_y = ny / TC_ROWS;
     const long long ntiles = (long long)nb * tiles_x * tiles_y;
     const long long first = blockIdx.x, stride = gridDim.x;
-    const int nloc = first < ntiles ? (int)((ntiles - 1 - first) / stride + 1) : 0;
+    const int nloc = (first < ntiles && !*abort) ? (int)((ntiles - 1 - first) / stride + 1) : 0;
     auto tile_coords = [&](int i, int& b, int& y0, int& x0) {
         const long long t = first + (long long)i * stride;
         b = (int)(t / ((long long)tiles_x * tiles_y));
@@ -208,7 +220,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
         y0 = (rem / tiles_x) * TC_ROWS;
         x0 = (rem % tiles_x) * TC_PX;
     };
-    const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[2]), tfull0 = su32(&bars[4]), tempty0 = su32(&bars[6]);
 
     if (warp == 0) {
         // ---- TMA producer ----
@@ -362,7 +373,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
 
 template <int CIN, int COUT, bool OUT>
 cudaError_t conv_tc(const CUtensorMap& map, const __nv_bfloat16* W, const float* bias, int nb, int ny, int nx,
-                    __nv_bfloat16* a, float* f, int* flag, cudaStream_t st)
+                    __nv_bfloat16* a, float* f, int* flag, int probe_polls, cudaStream_t st)
 {
     using L = TcLayout<CIN, COUT>;
     static_assert(L::REQUEST <= 227 * 1024, "shared memory");
@@ -376,7 +387,8 @@ cudaError_t conv_tc(const CUtensorMap& map, const __nv_bfloat16* W, const float*
     const long long tiles = (long long)nb * (nx / TC_PX) * (ny / TC_ROWS);
     const int grid = (int)std::min<long long>(tiles, sms);
     if (grid < 1) return cudaSuccess;
-    conv_tc_kernel<CIN, COUT, OUT><<<grid, TC_THREADS, L::REQUEST, st>>>(map, W, bias, nb, ny, nx, a, f, flag);
+    conv_tc_kernel<CIN, COUT, OUT><<<grid, TC_THREADS, L::REQUEST, st>>>(map, W, bias, nb, ny, nx, a, f, flag,
+                                                                         probe_polls);
     return cudaGetLastError();
 }
 
@@ -388,13 +400,14 @@ bool conv_tc_supported(int nx, int ny)
 }
 
 cudaError_t launch_conv_tc(int layer_kind, const CUtensorMap& in_map, const __nv_bfloat16* W, const float* bias,
-                           int nb, int ny, int nx, __nv_bfloat16* a, float* f, int* flag, cudaStream_t st)
+                           int nb, int ny, int nx, __nv_bfloat16* a, float* f, int* flag, int probe_polls,
+                           cudaStream_t st)
 {
-    if (!conv_tc_supported(nx, ny)) return cudaErrorInvalidValue;
+    if (!conv_tc_supported(nx, ny) || probe_polls < 0) return cudaErrorInvalidValue;
     switch (layer_kind) {
-    case 0: return conv_tc<16, 64, false>(in_map, W, bias, nb, ny, nx, a, f, flag, st);
-    case 1: return conv_tc<64, 64, false>(in_map, W, bias, nb, ny, nx, a, f, flag, st);
-    case 2: return conv_tc<64, 16, true>(in_map, W, bias, nb, ny, nx, a, f, flag, st);
+    case 0: return conv_tc<16, 64, false>(in_map, W, bias, nb, ny, nx, a, f, flag, probe_polls, st);
+    case 1: return conv_tc<64, 64, false>(in_map, W, bias, nb, ny, nx, a, f, flag, probe_polls, st);
+    case 2: return conv_tc<64, 16, true>(in_map, W, bias, nb, ny, nx, a, f, flag, probe_polls, st);
     default: return cudaErrorInvalidValue;
     }
 }

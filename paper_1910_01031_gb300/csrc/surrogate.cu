@@ -29,6 +29,9 @@ namespace iewpf {
 namespace {
 
 constexpr int TROWS = 8, TCOLS = 16;      // pixel tile of the convolution kernels (128 pixels)
+// polls of the injected bounded wait (iewpf_surrogate_inject_timeout): a
+// few milliseconds, against 2^24 for the pipeline's own waits
+constexpr int kInjectedWaitPolls = 1 << 16;
 constexpr int CONV_THREADS = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -702,12 +705,14 @@ int Surrogate::infer(const float* U, int nb, cudaStream_t st)
     const long long n = (long long)nb * (nx + 2) * (ny + 2);
     pack_input_padded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, nb, ny, nx, in_scale[0], in_scale[1],
                                                                          in_scale[2], xp);
+    const int probe = inject_timeouts > 0 ? kInjectedWaitPolls : 0;
+    if (inject_timeouts > 0) --inject_timeouts;
     for (int l = 0; l < depth; ++l) {
         const float* bias = master + b_off[l];
         const int kind = l == 0 ? 0 : (l + 1 < depth ? 1 : 2);
         const CUtensorMap& in_map = l == 0 ? map_x : map_a[(l - 1) & 1];
         e = launch_conv_tc(kind, in_map, wf[l], bias, nb, ny, nx, kind < 2 ? ap[l & 1] : nullptr,
-                           kind == 2 ? out_i : nullptr, dflag, st);
+                           kind == 2 ? out_i : nullptr, dflag, probe, st);
         if (e != cudaSuccess) return IEWPF_ECUDA;
     }
     return cudaGetLastError() == cudaSuccess ? IEWPF_OK : IEWPF_ECUDA;

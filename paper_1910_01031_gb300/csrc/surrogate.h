@@ -64,6 +64,7 @@ struct Surrogate {
     float* y_out = nullptr;                 // output of the last infer(): out or out_i
     int path = 0;                           // inference convolutions: 0 tcgen05 where the grid allows, 1 mma.sync
     int* dflag = nullptr;                   // FLAG_TIMEOUT of the tensor-core kernel
+    int inject_timeouts = 0;                // network calls left whose tensor-core kernels time out on purpose
     float in_scale[3] = {1.0f, 1.0f, 1.0f};     // network input = state * in_scale
     float out_scale[3] = {1.0f, 1.0f, 1.0f};    // state change = output * out_scale
     std::vector<void*> owned;
@@ -96,10 +97,14 @@ struct Surrogate {
 // into f as FP32 [b][ny][nx][3]).  in_map: 16 channels as a 5-D map
 // (8 ch, nx+2, ny+2, 2, b) without swizzle, box (8, 130, 4, 2, 1); 64
 // channels as a 4-D map (64 ch, nx+2, ny+2, b) with the 128-byte swizzle, box
-// (64, 130, 4, 1).  Needs nx % 128 == 0 and ny % 2 == 0.
+// (64, 130, 4, 1).  Needs nx % 128 == 0 and ny % 2 == 0.  probe_polls > 0
+// injects a timeout: every CTA first waits at most that many polls on a
+// barrier nothing completes, then aborts without issuing a copy or product
+// and records FLAG_TIMEOUT (tests of the timeout path); 0 runs normally.
 bool conv_tc_supported(int nx, int ny);
 cudaError_t launch_conv_tc(int layer_kind, const CUtensorMap& in_map, const __nv_bfloat16* W, const float* bias,
-                           int nb, int ny, int nx, __nv_bfloat16* a, float* f, int* flag, cudaStream_t st);
+                           int nb, int ny, int nx, __nv_bfloat16* a, float* f, int* flag, int probe_polls,
+                           cudaStream_t st);
 
 // drifters advected over T seconds with the mean of the cell velocities of the
 // states before (S0) and after (S1), both [ne][3][ny][nx]

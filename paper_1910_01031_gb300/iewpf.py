@@ -32,7 +32,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
            "iewpf_batch_work", "iewpf_batch_last_error", "iewpf_surrogate_create", "iewpf_surrogate_destroy",
            "iewpf_surrogate_param_count", "iewpf_surrogate_set_params", "iewpf_surrogate_get_params",
-           "iewpf_surrogate_set_scales", "iewpf_surrogate_set_path", "iewpf_surrogate_get_path", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_apply_device", "iewpf_surrogate_stream", "iewpf_surrogate_loss_grad",
+           "iewpf_surrogate_set_scales", "iewpf_surrogate_set_path", "iewpf_surrogate_get_path", "iewpf_surrogate_inject_timeout", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_apply_device", "iewpf_surrogate_stream", "iewpf_surrogate_loss_grad",
            "iewpf_surrogate_train", "iewpf_set_surrogate", "iewpf_surrogate_stats", "iewpf_surrogate_last_error"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
@@ -150,6 +150,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_surrogate_get_scales.argtypes = [_vp, _dp, _dp]
     L.iewpf_surrogate_set_path.argtypes = [_vp, c.c_int]
     L.iewpf_surrogate_get_path.argtypes = [_vp, _ip]
+    L.iewpf_surrogate_inject_timeout.argtypes = [_vp, c.c_int]
     L.iewpf_surrogate_apply.argtypes = [_vp, _fp, c.c_int, _fp]
     L.iewpf_surrogate_apply_device.argtypes = [_vp, _vp, c.c_int, _vp, _vp]
     L.iewpf_surrogate_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
@@ -474,7 +475,7 @@ class Batch:
             pass
 
     def tune(self):
-        out = np.zeros(3, np.int32)
+        out = np.zeros(4, np.int32)
         self._chk(self.L.iewpf_batch_tune(self.h, _ptr(out, _ip)), "batch_tune")
         return tuple(int(v) for v in out)
 
@@ -557,6 +558,11 @@ class Surrogate:
     def set_path(self, path):
         """0: tcgen05 forward convolutions where the grid allows; 1: mma.sync only."""
         self._chk(self.L.iewpf_surrogate_set_path(self.h, int(path)), "set_path")
+
+    def inject_timeout(self, n_evals=1):
+        """Failure injection: the next n_evals tcgen05 network evaluations time
+        out on a bounded device wait and the call raises ETIMEOUT."""
+        self._chk(self.L.iewpf_surrogate_inject_timeout(self.h, int(n_evals)), "inject_timeout")
 
     def uses_tcgen05(self):
         v = ctypes.c_int()

@@ -228,6 +228,24 @@ def test_tcgen05_forward_matches_oracle_and_mma_sync():
     assert _rel(out_tc.astype(np.float64) - U, out_mma.astype(np.float64) - U) < 1e-2
 
 
+def test_bounded_device_wait_times_out_and_the_context_stays_usable():
+    """Failure detection of the tensor-core pipeline: the injected kernels
+    wait on a barrier that nothing completes, give up after their poll limit
+    and report FLAG_TIMEOUT, so the call raises ETIMEOUT; the next call on the
+    same device runs normally and matches the oracle, twice."""
+    sur, p = _net(nx=128, ny=16, seed=21)
+    assert sur.uses_tcgen05()
+    U = _fields(3, 16, 128, 22)
+    sur.inject_timeout(1)
+    with pytest.raises(iewpf.IewpfError) as e:
+        sur.apply(U)
+    assert e.value.name == "ETIMEOUT"
+    ref = S.apply(p, U.astype(np.float64), SI, SO, W, D)
+    for _ in range(2):
+        out = sur.apply(U)
+        assert _rel(out.astype(np.float64) - U, ref - U) < FWD_TOL
+
+
 def test_tcgen05_forward_small_grid_and_gradients():
     # one tile row pair per field, fewer tiles than SMs; training forward keeps z
     sur, p = _net(nx=128, ny=16, seed=8)
