@@ -199,6 +199,43 @@ def test_full_cycle_matches_oracle():
         assert e < 1e-5, (cycle, e)
 
 
+def test_fifty_model_steps_match_oracle_every_step():
+    """Ten assimilation cycles, 50 model steps, on the 64 x 64 ten-particle
+    one-drifter problem: model error after the first four model steps of a
+    cycle, none on the fifth, then the analysis (Sec. 4).  The state is
+    compared with the oracle after every model step and every analysis at the
+    1e-5 relative bound; each particle's scheme-step count is the oracle's."""
+    cfg = synth.config1()
+    ne = cfg.n_particles
+    U32, U64 = start_state(cfg, ne)
+    P = oracle_problem(cfg)
+    ens = ensemble(cfg)
+    ens.set_state(U32)
+    ref = U64
+    truth = synth.initial_state(cfg, 1, seed=3)[0]
+    xy = synth.drifter_positions(cfg)
+    cells = [O.obs_cell(P, *p) for p in xy]
+    step = 0
+    worst = 0.0
+    for cycle in range(10):
+        for k in range(cfg.obs_every_steps):
+            err = k < cfg.obs_every_steps - 1
+            ens.forecast(1, err)
+            ref, ns, _ = O.forecast(P, ref, 1, [int(err)], t0=step)
+            assert np.array_equal(ens.last_nsub(), ns[:, 0]), (cycle, k)
+            step += 1
+            e = rel_l2(ens.get_state(), ref)
+            worst = max(worst, e)
+            assert e < 1e-5, (cycle, k, e)
+        y = _obs_for(cfg, truth, np.array(cells), cycle)
+        ens.assimilate(xy, y)
+        ref, _ = O.assimilate(P, ref, cells, y, t=cycle)
+        e = rel_l2(ens.get_state(), ref)
+        worst = max(worst, e)
+        assert e < 1e-5, (cycle, e)
+    assert step == 50
+
+
 def test_assimilate_rejects_bad_observations():
     cfg = synth.config1()
     ens = ensemble(cfg)

@@ -5,6 +5,9 @@ FP64 weights.
 
 * 512 x 512, 100 particles: one model step with model error, two sampled
   particles against the oracle.
+* 512 x 512, 100 particles, 64 drifters: one two-stage and one one-stage
+  analysis of the initial ensemble, every particle's FP64 scalars and two
+  sampled states.
 * 1024 x 1024, 1000 particles, 1521 moorings every 26 cells: one analysis
   from the initial ensemble.  phi_i of every particle, gamma_i and zeta_i,
   beta and alpha_i from the oracle's own inputs, and the updated state of two
@@ -204,4 +207,46 @@ def test_config2_one_stage_analysis_full_size():
     for i in sample:
         post, _ = O.assimilate(P, kept[i][None], cl, y, t=0, K=K, Msq=Msq, p0=i,
                                scalars={"beta": 0.0, "alpha": [sc["alpha"][i]]})
+        assert rel_l2(out[i].cpu().numpy(), post[0]) < 1e-5, i
+
+
+def test_config2_two_stage_analysis_full_size():
+    """512 x 512, 100 particles, 64 drifters, the two-stage scheme (Sec. 4):
+    one analysis of the initial ensemble.  phi, gamma, zeta, beta and alpha
+    of every particle against the oracle's own, every particle at the common
+    target weight, and the updated state of two sampled particles."""
+    cfg = synth.config2()
+    ne = cfg.n_particles
+    P = oracle_problem(cfg)
+    sample = (5, 96)
+    xy = synth.drifter_positions(cfg)
+    cells = np.array([O.obs_cell(P, *p) for p in xy])
+    U, kept, at = _device_ensemble(cfg, ne, keep=sample, cells=cells)
+    truth = synth.initial_particle(cfg, 31337, seed=6)
+    y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), 0))
+    ens = ensemble(cfg)
+    ens.set_state(U)
+    dg = ens.assimilate(xy, y)
+    s = (cfg.H + at[:, :, 0]) / cfg.H
+    d = np.stack([y[None, :, 0] * s - at[:, :, 1], y[None, :, 1] * s - at[:, :, 2]], axis=2).reshape(ne, -1)
+    cl = [tuple(c) for c in cells]
+    K = O.pull_stencil(P)
+    Sd = O.cholesky_solve(O.s_matrix(P, K, cl, dense=True), d.T).T
+    phi = np.einsum("ij,ij->i", d, Sd)
+    assert np.allclose(dg["phi"], phi, rtol=1e-9, atol=0)
+    rv = O.rand_vectors(P, ne, t=0)
+    assert np.allclose(dg["gamma"], rv["gamma"], rtol=1e-10, atol=0)
+    assert np.allclose(dg["zeta"], rv["zeta"], rtol=1e-10, atol=0)
+    sc = O.iewpf_scalars(phi + math.log(ne), rv["gamma"], rv["zeta"], P.N_psi)
+    assert math.isclose(dg["cbar"], sc["cbar"], rel_tol=1e-9)
+    assert math.isclose(dg["beta"], sc["beta"], rel_tol=1e-9)
+    assert np.allclose(dg["alpha"], sc["alpha"], rtol=1e-9, atol=0)
+    assert np.allclose(dg["neglogw"], dg["cbar"], rtol=1e-10, atol=0)
+    out = torch.empty_like(U)
+    ens.get_state(out)
+    torch.cuda.synchronize()
+    Msq = O.local_block_sqrt(P)
+    for i in sample:
+        post, _ = O.assimilate(P, kept[i][None], cl, y, t=0, K=K, Msq=Msq, p0=i,
+                               scalars={"beta": sc["beta"], "alpha": [sc["alpha"][i]]})
         assert rel_l2(out[i].cpu().numpy(), post[0]) < 1e-5, i
