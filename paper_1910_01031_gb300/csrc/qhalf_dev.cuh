@@ -101,23 +101,6 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
 
     const int tid = threadIdx.x;
     __syncthreads();   // the shared arrays may still be in use by the previous tile
-    // the tile's state, read first so that the loads are in flight while the
-    // coarse field is interpolated (the read-modify-write is at the end)
-    static_assert((TX * TY) % NTHREADS == 0, "whole tiles per thread");
-    constexpr int PER = TX * TY / NTHREADS;
-    float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
-    float s0[PER], s1[PER], s2[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = tid + k * NTHREADS;
-        const int gx = x0 + i % TX, gy = y0 + i / TX;
-        if (gx < G.nx && gy < G.ny) {
-            const long long g = (long long)gy * G.nx + gx;
-            s0[k] = __ldcs(U + g);
-            s1[k] = __ldcs(U + G.plane + g);
-            s2[k] = __ldcs(U + 2 * G.plane + g);
-        }
-    }
     float tdum;
     const int a_lo = coarse_interval(x0 - 1, C.nRx, C.c, C.o, G.nx, tdum);
     const int a_hi = coarse_interval(x0 + TX, C.nRx, C.c, C.o, G.nx, tdum);
@@ -163,11 +146,10 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     __shared__ int obs_ox[PULL ? MAX_TILE_OBS : 1], obs_oy[PULL ? MAX_TILE_OBS : 1];
     __shared__ float obs_su[PULL ? MAX_TILE_OBS : 1], obs_sv[PULL ? MAX_TILE_OBS : 1];
     const int n_obs_tile = PULL ? tile_obs_prep(A, G, x0, y0, p, tile, obs_ox, obs_oy, obs_su, obs_sv) : 0;
+    float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
     float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = tid + k * NTHREADS;
+    for (int i = tid; i < TX * TY; i += NTHREADS) {
         const int tx = i % TX, ty = i / TX;
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= G.nx || gy >= G.ny) continue;
@@ -192,10 +174,10 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
             }
         }
         const long long g = (long long)gy * G.nx + gx;
-        const float e1 = s0[k] + de, u1 = s1[k] + dhu, v1 = s2[k] + dhv;
-        __stcs(U + g, e1);
-        __stcs(U + G.plane + g, u1);
-        __stcs(U + 2 * G.plane + g, v1);
+        const float e1 = U[g] + de, u1 = U[G.plane + g] + dhu, v1 = U[2 * G.plane + g] + dhv;
+        U[g] = e1;
+        U[G.plane + g] = u1;
+        U[2 * G.plane + g] = v1;
         if (A.amax) m = fmaxf(m, cfl_of(e1, u1, v1, G));
     }
     if (A.amax) {
