@@ -144,13 +144,17 @@ __device__ __forceinline__ void cubic_weights(float t, float w[4])
     w[3] = 0.5f * (t3 - t2);
 }
 
-// max((|u| + c)/dx, (|v| + c)/dy) of one cell, c = sqrt(g h) (eq. swecfl)
+// max((|u| + c)/dx, (|v| + c)/dy) of one cell, c = sqrt(g h) (eq. swecfl),
+// with the hardware reciprocal and square root (a few ulp: only the ceiling
+// of dt_model over the CFL step is used, which such errors move only at
+// exact ties)
 __device__ __forceinline__ float cfl_of(float eta, float hu, float hv, const Grid& G)
 {
     const float h = G.H + eta;
-    const float c = sqrtf(G.g * h);
-    const float u = hu / h, v = hv / h;
-    return fmaxf((fabsf(u) + c) * G.inv_dx, (fabsf(v) + c) * G.inv_dy);
+    float r, c;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(h));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(G.g * h));
+    return fmaxf(fmaf(fabsf(hu), r, c) * G.inv_dx, fmaf(fabsf(hv), r, c) * G.inv_dy);
 }
 
 __device__ __forceinline__ float cfl_cell(const float* __restrict__ U, long long i, const Grid& G)
