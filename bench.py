@@ -1,25 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the IEWPF hot path on one GB300.
 
-A step is one IEWPF cycle on the 512 x 512, 100-particle, 64-drifter
-workload: 5 model steps of 60 s (scheme steps from the CFL condition, model
-error after the first 4) followed by one two-stage IEWPF analysis against
-64 drifter observations.  Throughput is particle.cell-steps/s
-(sum over particles of scheme steps x 512^2 cells per second); the cycle time
-is ms_per_step.  The state (2 x 315 MB) exceeds the 129 MB L2, so no flush
-is needed between timed steps.
+A step is one IEWPF cycle on the largest configuration: 1024 x 1024 cells,
+1000 particles, 1521 moored buoys every 26 cells observing (u, v): 5 model
+steps of 60 s (scheme steps from the CFL condition, model error after the
+first 4) followed by one two-stage IEWPF analysis with the dense 3042 x 3042
+HQH^T + R.  Throughput is particle.cell-steps/s (sum over particles of scheme
+steps x 1024^2 cells per second); the cycle time is ms_per_step.  The state
+(2 x 12.6 GB) exceeds the 129 MB L2, so no flush is needed between timed
+steps.  e2e is the same work over the host's clock through the C ABI, the
+observations copied from pinned host memory and the diagnostics read back
+every cycle.
 
-The line also carries three further workloads, each with its own numbers:
-"batched" (32 independent problems of 128^2-1024^2 cells advanced together
-as one CUDA graph per cycle), "moorings" (1024^2 cells, 1000 particles, 1521
-moored buoys: context creation with the dense FP64 factorisation, and the
-cycle time) and "surrogate" (a 12 h drift forecast of 1000
-particles x 64 drifters on 256^2 cells with the plain stepper and with the
-learned surrogate, their times and the distance between the two forecasts).
+Further workloads follow on the same line (--legs selects them): "drifters"
+(512^2, 100 particles, 64 drifters, with the bare scheme step and the
+standard-particle-filter collapse experiment), "coupled" (624^2, 1000
+particles, 1521 moorings every 16 cells whose HQH^T + R couples neighbours
+and whose FP64 factor fills in), "batched" (32 independent
+problems of 128^2-1024^2 cells advanced together as one CUDA graph per
+cycle), "surrogate" (a 12 h drift forecast of 1000 particles x 64 drifters
+on 256^2 cells with the plain stepper and with the learned surrogate),
+"one_stage" and "rank_histogram".
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload on the host cores (there is no other implementation to run).
-Under torchrun each rank runs an independent replica (own seed).
+--impl reference times the FP64 CPU oracle on a bounded sample of the
+headline workload on the host cores (there is no other implementation to
+run).  Under torchrun each rank runs an independent replica (own seed).
 """
 from __future__ import annotations
 
@@ -40,7 +45,14 @@ sys.path.insert(0, ROOT)
 METRIC = "particle·cell-steps/s"
 UNIT = "particle*cell*step/s"
 BYTES_PER_CELL_STEP = 24          # read (eta, hu, hv) + write (eta, hu, hv), float32
-FLOPS_PER_CELL_STEP = 490         # FP32 operations of one scheme step per cell, counted from the scheme
+# FP32 operations of one scheme step per cell (adds, multiplies and fused
+# multiply-adds, one each; no halo), counted from the kernel's arithmetic
+SCHEME_OPS_PER_CELL_STEP = 260
+# thread-instructions per cell and scheme step measured by ncu at 512^2 x 100
+# (smsp__thread_inst_executed.sum / cells), per stepper kind
+ISSUE_PER_CELL_STEP = {1: 520.6, 2: 370.4}
+WORKLOAD = "iewpf_cycle_1024x1024_ne1000_1521moorings"
+LEGS = ("drifters", "coupled", "batched", "batched_small", "surrogate", "one_stage", "rank_histogram")
 
 
 def _dist():
@@ -126,10 +138,11 @@ def make_observations(cfg, n_cycles, rank):
 
 
 def replica(rank):
-    """Workload of one rank: an independent replica of the 512 x 512,
-    100-particle problem with its own seed and Philox instance id."""
+    """Workload of one rank: an independent replica of the 1024 x 1024,
+    1000-particle, 1521-mooring problem with its own seed and Philox
+    instance id."""
     from paper_1910_01031_gb300 import synth
-    cfg = synth.config2(seed=0x1910_01031 + 104729 * rank)
+    cfg = synth.config4(seed=0x1910_01031 + 104729 * rank)
     return cfg, rank
 
 
@@ -146,7 +159,80 @@ def combine_ranks(dev_s, host_s, work, world, device="cuda"):
     return float(t[0]), float(t[1]), float(t[2])
 
 
+def device_ensemble(cfg, ne, seed):
+    """The initial ensemble built on the device: the two-jet state of
+    synth.initial_particle with N(0, noise_std^2) added to eta of every
+    particle from torch's seeded generator (the particles are synthetic
+    inputs only; the library never sees how they were drawn)."""
+    import torch
+    from paper_1910_01031_gb300 import synth
+    eta_y, hu_y = synth._jet(cfg)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    U = torch.zeros((ne, 3, cfg.ny, cfg.nx), dtype=torch.float32, device="cuda")
+    U[:, 0] = torch.as_tensor(eta_y, dtype=torch.float32, device="cuda")[None, :, None]
+    U[:, 1] = torch.as_tensor(hu_y, dtype=torch.float32, device="cuda")[None, :, None]
+    for a in range(0, ne, 100):
+        b = min(ne, a + 100)
+        U[a:b, 0] += cfg.noise_std * torch.randn((b - a, cfg.ny, cfg.nx), generator=g, device="cuda")
+    return U
+
+
+def scheme_step_roofline(ens, cfg, stream, local, n=13):
+    """The dominant kernel alone: n bare scheme steps of the whole ensemble
+    timed with CUDA events on the context's stream (the launching stream),
+    against HBM (24 algorithmic bytes per cell and step) and against the FP32
+    pipe (SCHEME_OPS_PER_CELL_STEP operations, a fused multiply-add counted
+    once) and instruction issue."""
+    import torch
+    ne, N = cfg.n_particles, cfg.nx * cfg.ny
+    dt = cfg.dt_model / 13.0
+    ens.substeps(2, dt)           # warm
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("scheme_step_%dx%d" % (cfg.nx, cfg.ny))   # selects these launches for a profiler
+    f0.record(stream)
+    ens.substeps(n, dt)
+    f1.record(stream)
+    f1.synchronize()
+    torch.cuda.nvtx.range_pop()
+    launch_s = f0.elapsed_time(f1) / 1e3 / n
+    cells = ne * N
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_ops_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12         # T operations/s on the FP32 pipes
+    issue_peak = n_sm * 4 * 32 * sm_mhz * 1e6 / 1e12         # T thread-instructions/s
+    achieved_gbs = BYTES_PER_CELL_STEP * cells / launch_s / 1e9
+    ops = SCHEME_OPS_PER_CELL_STEP * cells / launch_s / 1e12
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "rk2_march_traffic.json")))
+        if prof.get("kernel_sha") == _kernel_sha():
+            traffic = prof["bytes_per_cell_step"] * cells
+    except Exception:
+        pass
+    shape = ens.stepper()
+    return {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved_gbs / hbm_peak, 4), "traffic": traffic,
+            "kernel": "%s (SSP-RK2 scheme step, register march), shape (kind, nc, rows, warps) = %s"
+                      % ("rk2_march2_kernel" if shape[0] == 2 else "rk2_march_kernel", shape,),
+            "per_launch_ms": round(launch_s * 1e3, 4), "cells_per_launch": cells,
+            "fp32": {"achieved": round(ops, 2), "peak": round(fp32_ops_peak, 1), "unit": "Top/s",
+                     "frac": round(ops / fp32_ops_peak, 4), "ops_per_cell_step": SCHEME_OPS_PER_CELL_STEP},
+            "issue": {"instructions_per_cell_step": ISSUE_PER_CELL_STEP.get(shape[0]),
+                      "frac": (round(ISSUE_PER_CELL_STEP[shape[0]] * cells / launch_s / 1e12 / issue_peak, 4)
+                               if shape[0] in ISSUE_PER_CELL_STEP else None)}}
+
+
 def run_ours(args, rank, world, local):
+    """The headline workload: IEWPF cycles on 1024 x 1024 cells, 1000
+    particles, 1521 moorings observing (u, v) every 26 cells (dense 3042 x
+    3042 HQH^T + R), end to end through the C ABI with the observations in
+    pinned host memory and the diagnostics read back every cycle."""
     import torch
     from paper_1910_01031_gb300 import build, iewpf, synth
 
@@ -157,23 +243,32 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     cfg, instance = replica(rank)
     ne, N = cfg.n_particles, cfg.nx * cfg.ny
+    cells = synth.mooring_cells(cfg)
+    xy = synth.cell_positions(cfg, cells)
     P = iewpf.params_from_config(cfg)
     P.instance_id = instance
-    ens = iewpf.Ensemble(P)
-    ens.set_state(synth.initial_state(cfg, ne, seed=7 + rank).astype(np.float32))
-    obs = make_observations(cfg, args.warmup + args.steps + 1, rank)
-    # pinned host buffers for the per-step inputs and outputs (end-to-end leg)
-    pin_xy = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs[:-1]]
-    pin_val = [torch.empty((cfg.n_obs, 2), dtype=torch.float64, pin_memory=True) for _ in obs[:-1]]
-    for k, (xy, val) in enumerate(obs[:-1]):
-        pin_xy[k].numpy()[:] = xy
-        pin_val[k].numpy()[:] = val
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens = iewpf.Ensemble(P, mooring_xy=xy)
+    create_s = time.perf_counter() - t0
+    U = device_ensemble(cfg, ne, seed=7 + rank)
+    ens.set_state(U)
+    del U
+    torch.cuda.empty_cache()
+    # the truth and its observations (eq. buoyObservation), in pinned buffers
+    truth = synth.initial_particle(cfg, ne + 1, seed=43 + rank)
+    n_cyc = args.warmup + args.steps + 1
+    pin_val = []
+    for k in range(n_cyc):
+        t = torch.empty((len(cells), 2), dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), k, seed=17 + rank))
+        pin_val.append(t)
     stream = torch.cuda.ExternalStream(ens.stream())
 
     def cycle(k):
         ens.forecast(cfg.obs_every_steps - 1, True)
         ens.forecast(1, False)
-        return ens.assimilate(pin_xy[k].numpy(), pin_val[k].numpy())
+        return ens.assimilate(None, pin_val[k].numpy())
 
     for k in range(args.warmup):
         cycle(k)
@@ -201,102 +296,100 @@ def run_ours(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    # slowest rank sets the job time
     dev_s, host_s, work_all = combine_ranks(dev_s, host_s, work, world)
     value = work_all * N / dev_s
     e2e_value = work_all * N / host_s
-    # the dominant kernel: bare scheme steps, CUDA events on the context stream
-    nsub_probe = 26
-    dt_probe = cfg.dt_model / 13.0
-    ens.substeps(2, dt_probe)           # warm
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    ens.substeps(nsub_probe, dt_probe)
-    f1.record(stream)
-    f1.synchronize()
-    launch_s = f0.elapsed_time(f1) / 1e3 / nsub_probe
-    cells = ne * N
-    achieved_gbs = BYTES_PER_CELL_STEP * cells / launch_s / 1e9
-    achieved_tflops = FLOPS_PER_CELL_STEP * cells / launch_s / 1e12
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s, FMA = 2
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "rk2_march_traffic.json")))
-        if prof.get("kernel_sha") == _kernel_sha():
-            traffic = prof["bytes_per_cell_step"] * cells
-    except Exception:
-        pass
-    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved_gbs / hbm_peak, 4), "traffic": traffic,
-                "kernel": "rk2_march_kernel (register-marching SSP-RK2 scheme step), shape (kind, nc, rows, warps) = %s"
-                          % (ens.stepper(),),
-                "per_launch_ms": round(launch_s * 1e3, 4),
-                "alu": {"achieved": round(achieved_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                        "frac": round(achieved_tflops / fp32_peak, 4)}}
-    try:
-        sir = run_sir_collapse(ens, cfg, *obs[-1])
-    except Exception as e:  # reported, the main number stands without it
-        sir = {"error": str(e)}
+    roofline = scheme_step_roofline(ens, cfg, stream, local)
     ens.close()
-    try:
-        batched = run_batched(rank)
-    except Exception as e:  # reported, the main number stands without it
-        batched = {"error": str(e)}
-    try:
-        moorings = run_moorings(rank)
-    except Exception as e:  # reported, the main number stands without it
-        moorings = {"error": str(e)}
-    try:
-        surrogate = run_surrogate(rank, epochs=8)
-    except Exception as e:  # reported, the main number stands without it
-        surrogate = {"error": str(e)}
-    try:
-        one_stage = run_one_stage(rank)
-    except Exception as e:  # reported, the main number stands without it
-        one_stage = {"error": str(e)}
-    try:
-        ranks = run_rank_histogram(rank)
-    except Exception as e:  # reported, the main number stands without it
-        ranks = {"error": str(e)}
+    torch.cuda.empty_cache()
+    legs = set(LEGS) if args.legs == "all" else set(x for x in args.legs.split(",") if x and x != "none")
+    side = {}
+    for name, fn in (("drifters", run_drifters), ("coupled", run_coupled), ("batched", run_batched),
+                     ("batched_small", run_batched_small), ("surrogate", run_surrogate),
+                     ("one_stage", run_one_stage), ("rank_histogram", run_rank_histogram)):
+        if name in legs:
+            try:
+                side[name] = fn(rank)
+            except Exception as e:  # reported, the main number stands without it
+                side[name] = {"error": str(e)}
     if rank != 0:
         return
     cpu = cpu_baseline(args) if world == 1 else None
-    h2d = 2 * cfg.n_obs * 2 * 8
+    h2d = len(cells) * 2 * 8
     d2h = 6 * ne * 8 + 2 * 8
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_s / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, f64 weights", "data": "synthetic",
-        "config": {"workload": "iewpf_cycle_512x512_ne100_64drifters", "nx": cfg.nx, "ny": cfg.ny,
-                   "particles": ne, "drifters": cfg.n_obs, "model_steps_per_cycle": cfg.obs_every_steps,
-                   "dt_model_s": cfg.dt_model, "c_omega": cfg.c_omega, "courant": cfg.courant,
-                   "particle_substeps_timed": int(work_all), "l2": "inputs larger than L2 (state 2x315 MB)",
+        "config": {"workload": WORKLOAD, "nx": cfg.nx, "ny": cfg.ny,
+                   "particles": ne, "moorings": len(cells), "n_y": 2 * len(cells),
+                   "model_steps_per_cycle": cfg.obs_every_steps, "dt_model_s": cfg.dt_model,
+                   "c_omega": cfg.c_omega, "courant": cfg.courant, "hqht": "dense (couplings kept)",
+                   "particle_substeps_timed": int(work_all),
+                   "l2": "inputs larger than L2 (state 2 x %.1f GB)" % (ne * N * 12 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "iewpf_cycle_ms": round(dev_s / args.steps * 1e3, 3),
+        "create_s": round(create_s, 3),
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "timing": "host wall clock through the C ABI, pinned obs buffers"},
         "gpu_launches": int(launches),
         "roofline": roofline,
-        "batched": batched,
-        "moorings": moorings,
-        "surrogate": surrogate,
-        "one_stage": one_stage,
-        "sir_collapse": sir,
-        "rank_histogram": ranks,
         "cpu_baseline": cpu,
         "clocks": clk,
         "last_cycle": {"beta": d["beta"], "c_bar": d["cbar"], "alpha_min": float(np.min(d["alpha"])),
                        "alpha_max": float(np.max(d["alpha"])),
                        "neglogw_spread": float(np.max(d["neglogw"]) - np.min(d["neglogw"]))} if d else None,
     }
+    line.update(side)
     print(json.dumps(line), flush=True)
+
+
+def run_drifters(rank, cycles=10, warm=3):
+    """The 512 x 512, 100-particle, 64-drifter workload: IEWPF cycles timed
+    with CUDA events on the context's stream (drifter observations from two
+    GPS fixes of a truth run), the bare scheme step, and the collapse
+    experiment of the standard particle filter on the same ensemble."""
+    import torch
+    from paper_1910_01031_gb300 import iewpf, synth
+    cfg = synth.config2(seed=0x1910_01031 + 104729 * rank)
+    ne, N = cfg.n_particles, cfg.nx * cfg.ny
+    P = iewpf.params_from_config(cfg)
+    P.instance_id = 100 + rank
+    ens = iewpf.Ensemble(P)
+    ens.set_state(synth.initial_state(cfg, ne, seed=7 + rank).astype(np.float32))
+    obs = make_observations(cfg, warm + cycles + 1, rank)
+    stream = torch.cuda.ExternalStream(ens.stream())
+
+    def cycle(k):
+        ens.forecast(cfg.obs_every_steps - 1, True)
+        ens.forecast(1, False)
+        return ens.assimilate(*obs[k])
+
+    for k in range(warm):
+        cycle(k)
+    torch.cuda.synchronize()
+    w0, l0 = ens.work(), ens.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("drifters_timed")
+    e0.record(stream)
+    for k in range(warm, warm + cycles):
+        cycle(k)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.nvtx.range_pop()
+    secs = e0.elapsed_time(e1) / 1e3
+    work = ens.work() - w0
+    out = {"workload": "iewpf_cycle_512x512_ne100_64drifters", "cycles_timed": cycles,
+           "cycle_ms": round(secs / cycles * 1e3, 3), "value": round(work * N / secs, 1), "unit": UNIT,
+           "gpu_launches_per_cycle": round((ens.launch_count() - l0) / cycles, 1)}
+    out["scheme_step"] = scheme_step_roofline(ens, cfg, stream, torch.cuda.current_device(), n=26)
+    try:
+        out["sir_collapse"] = run_sir_collapse(ens, cfg, *obs[-1])
+    except Exception as e:
+        out["sir_collapse"] = {"error": str(e)}
+    ens.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(rank):
@@ -359,54 +452,138 @@ def run_batched(rank):
     return out
 
 
-def run_moorings(rank, cycles=2):
-    """The moored-buoy workload: 1024 x 1024 cells, 1000 particles, 1521
-    equidistant moorings observing (u, v).  Times the context creation (pull
-    stencil, dense 3042 x 3042 HQH^T + R and its FP64 Cholesky on the GPU,
-    the 49 x 49 block root) and IEWPF cycles (5 model steps, model error on 4,
-    one analysis against the moorings) with CUDA events.  The particles start
-    from one synthetic state (they diverge through the model error)."""
+def run_coupled(rank, cycles=3):
+    """Moorings that interact: 1521 moorings every 16 cells on 624 x 624
+    cells, 1000 particles.  Each mooring lies within the 21-cell pull stencil
+    of its neighbours, so HQH^T + R (3042 x 3042, FP64) couples them and its
+    Cholesky factor fills in.  Times the context creation (assembly and
+    factorisation on the GPU), the analysis alone and the whole cycle with
+    CUDA events, and reports the factor's fill."""
     import torch
     from paper_1910_01031_gb300 import iewpf, synth
-    cfg = synth.config4(seed=0x1910_01031 + 13 * rank)
-    cells = synth.mooring_cells(cfg)
+    cfg = synth.coupled_moorings(seed=0x1910_01031 + 31 * rank)
+    ne = cfg.n_particles
+    cells = synth.mooring_cells(cfg, synth.COUPLED_SPACING)
     xy = synth.cell_positions(cfg, cells)
     P = iewpf.params_from_config(cfg)
-    P.instance_id = rank
+    P.instance_id = 300 + rank
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ens = iewpf.Ensemble(P, mooring_xy=xy)
+    torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
-    x = torch.from_numpy(synth.initial_particle(cfg, 0, seed=41 + rank, dtype=np.float32)).cuda()
-    ens.set_state(x.unsqueeze(0).expand(cfg.n_particles, -1, -1, -1).contiguous())
-    del x
-    truth = synth.initial_particle(cfg, 1, seed=43 + rank)
+    n, nnz = ens.factor_info()
+    ens.set_state(device_ensemble(cfg, ne, seed=51 + rank))
+    torch.cuda.empty_cache()
+    ens.tune()                  # the stepper's autotuner, outside the timed cycles
+    truth = synth.initial_particle(cfg, ne + 1, seed=53 + rank)
+    ys = [synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), k)) for k in range(cycles + 1)]
     stream = torch.cuda.ExternalStream(ens.stream())
-
-    def cycle(k):
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ana_ms = []
+    e0, e1 = ev(), ev()
+    torch.cuda.nvtx.range_push("coupled_timed")
+    for k in range(cycles + 1):
         ens.forecast(cfg.obs_every_steps - 1, True)
         ens.forecast(1, False)
-        y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), k))
-        return ens.assimilate(None, y, diag=False)
-
-    cycle(0)
-    torch.cuda.synchronize()
-    w0 = ens.work()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(1, cycles + 1):
-        cycle(k)
+        if k == 1:
+            e0.record(stream)
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        ens.assimilate(None, ys[k], diag=False)
+        a1.record(stream)
+        a1.synchronize()
+        if k >= 1:
+            ana_ms.append(a0.elapsed_time(a1))
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     secs = e0.elapsed_time(e1) / 1e3
-    work = ens.work() - w0
-    out = {"workload": "iewpf_1024x1024_ne1000_1521moorings (dense 3042 x 3042 HQH^T + R)",
-           "create_s": round(create_s, 3), "cycles_timed": cycles, "cycle_ms": round(secs / cycles * 1e3, 2),
-           "value": round(work * cfg.nx * cfg.ny / secs, 1), "unit": UNIT,
-           "state_gb": round(2 * cfg.n_particles * cfg.nx * cfg.ny * 12 / 1e9, 1)}
     ens.close()
     torch.cuda.empty_cache()
-    return out
+    solve_flops = 4.0 * nnz * ne + 2.0 * n * ne      # two triangular solves per particle
+    ana_s = float(np.median(ana_ms)) / 1e3
+    return {"workload": "iewpf_cycle_624x624_ne1000_1521moorings_every16 (coupled dense HQH^T + R)",
+            "create_s": round(create_s, 3), "n_y": n, "factor_nnz_below_diag": nnz,
+            "factor_fill": round(nnz / (n * (n - 1) / 2.0), 4), "cycles_timed": cycles,
+            "cycle_ms": round(secs / cycles * 1e3, 2), "analysis_ms": round(ana_s * 1e3, 2),
+            "solve_fp64_flops_per_analysis": solve_flops,
+            "solve_fp64_gflops_lower_bound": round(solve_flops / ana_s / 1e9, 1)}
+
+
+def run_batched_small(rank, n=64, cycles=4, warm=1):
+    """Where batching pays: 64 independent problems of the 64 x 64,
+    10-particle, 1-drifter configuration, each far too small to fill the GPU.
+    The same cycles (5 model steps, model error on 4, one analysis) run once
+    as one batched CUDA-graph cycle of all problems and once problem by
+    problem through their own contexts; both are timed on the host's clock
+    around whole cycles (the batch with its stream synchronised)."""
+    import torch
+    from paper_1910_01031_gb300 import iewpf, synth
+    cfgs = [synth.config1(seed=0x1910_01031 + 7 * i + 1009 * rank) for i in range(n)]
+    params = []
+    for i, c in enumerate(cfgs):
+        p = iewpf.params_from_config(c)
+        p.instance_id = 400 + i + 64 * rank
+        params.append(p)
+    states = [synth.initial_state(c, c.n_particles, seed=61 + i).astype(np.float32) for i, c in enumerate(cfgs)]
+
+    def obs(k):
+        out = []
+        for i, c in enumerate(cfgs):
+            xy = synth.drifter_positions(c) + 500.0 * k
+            cells = np.stack([np.floor(xy[:, 0] / c.dx) % c.nx, np.floor(xy[:, 1] / c.dy) % c.ny], 1).astype(int)
+            truth = synth.initial_particle(c, 1000 + i, seed=71)
+            out.append((xy, synth.obs_from_state(c, truth, cells, synth.obs_noise(c, len(cells), k))))
+        return out
+
+    o = [obs(k) for k in range(warm + cycles)]
+    cells_total = sum(c.n_particles * c.nx * c.ny for c in cfgs)
+    # batched
+    batch = iewpf.Batch(params)
+    for i in range(n):
+        batch.instances[i].set_state(states[i])
+    for k in range(warm):
+        batch.cycle(5, o[k])
+    bstream = torch.cuda.ExternalStream(batch.stream())
+    torch.cuda.synchronize()
+    iw0 = [inst.work() for inst in batch.instances]
+    t0 = time.perf_counter()
+    for k in range(warm, warm + cycles):
+        batch.cycle(5, o[k])
+    bstream.synchronize()
+    b_s = time.perf_counter() - t0
+    b_work = sum((inst.work() - a) * c.nx * c.ny for inst, a, c in zip(batch.instances, iw0, cfgs))
+    batch.close()
+    # one by one
+    ens = [iewpf.Ensemble(p) for p in params]
+    for e, U in zip(ens, states):
+        e.set_state(U)
+
+    def one_by_one(k):
+        for i, e in enumerate(ens):
+            e.forecast(4, True)
+            e.forecast(1, False)
+            e.assimilate(*o[k][i], diag=False)
+
+    for k in range(warm):
+        one_by_one(k)
+    torch.cuda.synchronize()
+    w0 = [e.work() for e in ens]
+    t0 = time.perf_counter()
+    for k in range(warm, warm + cycles):
+        one_by_one(k)
+    torch.cuda.synchronize()
+    s_s = time.perf_counter() - t0
+    s_work = sum((e.work() - a) * c.nx * c.ny for e, a, c in zip(ens, w0, cfgs))
+    for e in ens:
+        e.close()
+    torch.cuda.empty_cache()
+    return {"workload": "64 problems of 64x64 cells, 10 particles, 1 drifter (each too small to fill the GPU)",
+            "particle_cells": cells_total, "cycles_timed": cycles,
+            "batched": {"cycle_ms": round(b_s / cycles * 1e3, 2), "value": round(b_work / b_s, 1)},
+            "one_by_one": {"cycle_ms": round(s_s / cycles * 1e3, 2), "value": round(s_work / s_s, 1)},
+            "unit": UNIT, "speedup": round((b_work / b_s) / (s_work / s_s), 2)}
 
 
 def run_sir_collapse(ens, cfg, xy, y):
@@ -436,16 +613,16 @@ def run_sir_collapse(ens, cfg, xy, y):
 
 
 def run_one_stage(rank, cycles=3):
-    """The one-stage IEWPF (App. A) on the headline workload: cycle time
+    """The one-stage IEWPF (App. A) on the 512^2 drifter workload: cycle time
     with CUDA events, and per cycle its target max c_i against the two-stage
     target mean c_i.  The incomplete-gamma alpha (eq. numericalEqForAlpha) of
     the last cycle's particles is solved on the GPU as well and compared with
     the Lambert-W alpha the scheme used."""
     import torch
     from paper_1910_01031_gb300 import iewpf, synth
-    cfg, instance = replica(rank)
+    cfg = synth.config2(seed=0x1910_01031 + 104729 * rank)
     P = iewpf.params_from_config(cfg, scheme=iewpf.ONE_STAGE)
-    P.instance_id = instance
+    P.instance_id = 200 + rank
     ens = iewpf.Ensemble(P)
     ens.set_state(synth.initial_state(cfg, cfg.n_particles, seed=7 + rank).astype(np.float32))
     obs = make_observations(cfg, cycles + 1, rank)
@@ -638,39 +815,60 @@ def _kernel_sha():
     return h.hexdigest()[:12]
 
 
-def oracle_sample(n_particles=4, seed_rank=0):
-    """One IEWPF cycle of the FP64 oracle on n_particles of the 512^2
-    workload; returns (particle.cell-steps, seconds, threads)."""
-    from oracle import oracle as O
-    from paper_1910_01031_gb300 import synth
-    cfg = synth.config2()
-    P = O.Problem(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, g=cfg.g, f=cfg.f, H=cfg.H, theta=cfg.theta,
-                  courant=cfg.courant, dt_model=cfg.dt_model, c_omega=cfg.c_omega, q0=cfg.q0, L0=cfg.L0,
-                  seed=cfg.seed, obs_sigma=cfg.obs_sigma)
-    U = synth.initial_state(cfg, n_particles, seed=7 + seed_rank)
-    xy = synth.drifter_positions(cfg)
-    cells = [O.obs_cell(P, *p) for p in xy]
-    truth = synth.initial_state(cfg, 1, seed=3)[0]
-    y = synth.obs_from_state(cfg, truth, np.array(cells), synth.obs_noise(cfg, len(cells), 0))
-    K = O.pull_stencil(P)
-    M = O.local_block_sqrt(P)
-    t0 = time.perf_counter()
-    U, nsub, _ = O.forecast(P, U, cfg.obs_every_steps, [1] * (cfg.obs_every_steps - 1) + [0], t0=0)
-    U, _ = O.assimilate(P, U, cells, y, t=0, K=K, Msq=M)
-    dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return float(nsub.sum()) * cfg.nx * cfg.ny, dt, min(threads, os.cpu_count() or 1, n_particles)
+class OracleSample:
+    """A bounded sample of the headline workload run by the FP64 CPU oracle
+    (OpenMP over particles in its C scheme, numpy for the analysis):
+    n_particles particles of the 1024 x 1024, 1521-mooring problem, stepped
+    model step by model step with the cycle's cadence (model error after the
+    first four model steps, the analysis after the fifth)."""
+
+    def __init__(self, n_particles, seed_rank=0):
+        from oracle import oracle as O
+        from paper_1910_01031_gb300 import synth
+        self.O = O
+        cfg = self.cfg = synth.config4()
+        self.P = O.Problem(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, g=cfg.g, f=cfg.f, H=cfg.H,
+                           theta=cfg.theta, courant=cfg.courant, dt_model=cfg.dt_model, c_omega=cfg.c_omega,
+                           q0=cfg.q0, L0=cfg.L0, seed=cfg.seed, obs_sigma=cfg.obs_sigma)
+        self.U = np.stack([synth.initial_particle(cfg, i, seed=7 + seed_rank) for i in range(n_particles)])
+        self.cells = [tuple(c) for c in synth.mooring_cells(cfg)]
+        truth = synth.initial_particle(cfg, 100003, seed=43 + seed_rank)
+        self.y = synth.obs_from_state(cfg, truth, np.array(self.cells), synth.obs_noise(cfg, len(self.cells), 0))
+        self.K = O.pull_stencil(self.P)
+        self.M = O.local_block_sqrt(self.P)
+        self.step = 0
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        self.threads = min(threads, os.cpu_count() or 1, n_particles)
+
+    def model_step(self):
+        """One model step (the analysis too after every fifth); returns
+        (particle.cell-steps, seconds)."""
+        cfg = self.cfg
+        k = self.step % cfg.obs_every_steps
+        t0 = time.perf_counter()
+        self.U, nsub, _ = self.O.forecast(self.P, self.U, 1, [int(k < cfg.obs_every_steps - 1)], t0=self.step)
+        if k == cfg.obs_every_steps - 1:
+            self.U, _ = self.O.assimilate(self.P, self.U, self.cells, self.y,
+                                          t=self.step // cfg.obs_every_steps, K=self.K, Msq=self.M)
+        secs = time.perf_counter() - t0
+        self.step += 1
+        return float(nsub.sum()) * cfg.nx * cfg.ny, secs
 
 
 def cpu_baseline(args):
     try:
         from oracle import build as ob
         ob.build()
-        n = min(100, 2 * (os.cpu_count() or 1))
-        work, secs, threads = oracle_sample(n)
-        return {"value": round(work / secs, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
-                "sample": "1 IEWPF cycle (5 model steps + analysis, 64 drifters) of %d of the 100 particles "
-                          "of the 512x512 workload, FP64, OpenMP over particles" % n,
+        n = min(1000, os.cpu_count() or 1)
+        sample = OracleSample(n)
+        work, secs = 0.0, 0.0
+        for _ in range(sample.cfg.obs_every_steps):
+            w, t = sample.model_step()
+            work += w
+            secs += t
+        return {"value": round(work / secs, 1), "unit": UNIT, "cores": sample.threads, "kind": "oracle",
+                "sample": "1 IEWPF cycle (5 model steps, model error on 4, analysis against 1521 moorings) of "
+                          "%d of the 1000 particles of the 1024x1024 workload, FP64, OpenMP over particles" % n,
                 "seconds": round(secs, 2)}
     except Exception as e:  # the GPU number stands without it
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -682,10 +880,11 @@ def run_reference(args, rank, world):
         return
     from oracle import build as ob
     ob.build()
+    n = min(1000, os.cpu_count() or 1)
+    sample = OracleSample(n)
     total_work, total_s = 0.0, 0.0
-    threads = 1
     for k in range(args.warmup + args.steps):
-        work, secs, threads = oracle_sample(2, seed_rank=k)
+        work, secs = sample.model_step()
         if k >= args.warmup:
             total_work += work
             total_s += secs
@@ -695,9 +894,11 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "iewpf_cycle_512x512_ne100_64drifters", "sample_particles_per_step": 2},
-        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "each step: 1 IEWPF cycle of 2 of the 100 particles of the 512x512 workload"},
+        "config": {"workload": WORKLOAD, "sample_particles": n},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": sample.threads, "kind": "oracle",
+                         "sample": "each step: one model step of %d of the 1000 particles of the 1024x1024, "
+                                   "1521-mooring workload, with the analysis after every fifth (the cycle's "
+                                   "cadence)" % n},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -709,6 +910,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--legs", default="all",
+                    help="side workloads after the headline, comma-separated from %s, 'all' or 'none'"
+                         % ",".join(LEGS))
     args = ap.parse_args()
     rank, world, local = _dist()
     if args.impl == "reference":

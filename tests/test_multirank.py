@@ -61,4 +61,5 @@ def test_replicas_are_independent_problems():
     import bench
     (c0, i0), (c1, i1) = bench.replica(0), bench.replica(1)
     assert c0.seed != c1.seed and i0 != i1
-    assert (c0.nx, c0.ny, c0.n_particles) == (c1.nx, c1.ny, c1.n_particles) == (512, 512, 100)
+    assert (c0.nx, c0.ny, c0.n_particles, c0.n_obs) == (c1.nx, c1.ny, c1.n_particles, c1.n_obs) == \
+        (1024, 1024, 1000, 1521)
