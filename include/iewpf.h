@@ -567,6 +567,14 @@ IEWPF_API int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_
 IEWPF_API int iewpf_surrogate_stats(const iewpf_ctx_t* ctx, int64_t* calls, int64_t* fallbacks);
 IEWPF_API const char* iewpf_surrogate_last_error(const iewpf_surrogate_t* s);
 
+/* The last factored system (HQH^T + R of Sec. 4.2, eq. S_extended): its
+ * order N_y (0 before any factorisation) and the nonzeros of its FP64
+ * Cholesky factor strictly below the diagonal (the fill: N_y (N_y - 1) / 2
+ * for a dense factor, N_y / 2 for observations that do not interact, whose
+ * factor is 2 x 2 blocks).  Synchronises the context's stream.
+ * Errors: EINVAL, ECUDA. */
+IEWPF_API int iewpf_factor_info(iewpf_ctx_t* ctx, int* n_y, int64_t* nnz_L);
+
 /* Sizes derived from the parameters: the coarse grid Omega^R of Sec. 3.2
  * (nRx x nRy points every c_omega cells) and the pull-stencil radius R;
  * any output pointer may be NULL.  Errors: EINVAL (NULL ctx). */

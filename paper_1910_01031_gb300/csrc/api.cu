@@ -107,6 +107,7 @@ struct iewpf_ctx {
     // model-error or analysis update); any other change of the state clears it
     bool cfl_ready = false;
     bool factored = false;      // mooring factor ready
+    int n_fact = 0;             // order of the last factored HQH^T + R
     // pinned staging
     int* h_flag = nullptr;
     int* h_maxsub = nullptr;
@@ -428,6 +429,7 @@ int factor(iewpf_ctx* ctx, int nobs)
     KL(1, launch_hqht(ctx->d_K64, ctx->R, ctx->d_cell, nobs, ctx->G, ctx->P.dense_S,
                    ctx->P.obs_sigma * ctx->P.obs_sigma, ctx->d_L, ctx->st));
     KL(1, launch_cholesky(ctx->d_L, n, ctx->d_colptr, ctx->d_rowidx, ctx->flag, ctx->st));
+    ctx->n_fact = n;
     return IEWPF_OK;
 }
 
@@ -1446,6 +1448,20 @@ int iewpf_launch_count(const iewpf_ctx_t* ctx, int64_t* count)
 {
     if (!ctx || !count) return IEWPF_EINVAL;
     *count = ctx->launches;
+    return IEWPF_OK;
+}
+
+int iewpf_factor_info(iewpf_ctx_t* ctx, int* n_y, int64_t* nnz_L)
+{
+    if (!ctx) return IEWPF_EINVAL;
+    CK(cudaSetDevice(ctx->dev));
+    int nnz = 0;
+    if (ctx->n_fact > 0) {
+        CK(cudaMemcpyAsync(&nnz, ctx->d_colptr + ctx->n_fact, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    if (n_y) *n_y = ctx->n_fact;
+    if (nnz_L) *nnz_L = nnz;
     return IEWPF_OK;
 }
 

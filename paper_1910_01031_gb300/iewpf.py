@@ -27,7 +27,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma", "iewpf_rank",
            "iewpf_batch_forecast", "iewpf_drifter_obs",
            "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
-           "iewpf_substeps", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
+           "iewpf_substeps", "iewpf_factor_info", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
            "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
            "iewpf_batch_work", "iewpf_batch_last_error", "iewpf_surrogate_create", "iewpf_surrogate_destroy",
@@ -123,6 +123,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_pull_stencil.argtypes = [_vp, _dp]
     L.iewpf_local_block.argtypes = [_vp, _dp]
     L.iewpf_add_qhalf.argtypes = [_vp, _fp]
+    L.iewpf_factor_info.argtypes = [_vp, _ip, c.POINTER(c.c_int64)]
     L.iewpf_sizes.argtypes = [_vp, _ip, _ip, _ip]
     L.iewpf_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
     L.iewpf_substeps.argtypes = [_vp, c.c_int, c.c_double]
@@ -390,6 +391,13 @@ class Ensemble:
 
     def substeps(self, n, dt):
         self._chk(self.L.iewpf_substeps(self.h, int(n), float(dt)), "substeps")
+
+    def factor_info(self):
+        """(N_y, nonzeros of the FP64 Cholesky factor) of the last factored HQH^T + R."""
+        n = ctypes.c_int()
+        z = ctypes.c_int64()
+        self._chk(self.L.iewpf_factor_info(self.h, ctypes.byref(n), ctypes.byref(z)), "factor_info")
+        return n.value, z.value
 
     def launch_count(self):
         c = ctypes.c_int64()

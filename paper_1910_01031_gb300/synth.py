@@ -87,6 +87,19 @@ def config4(**kw):
                 {"n_particles": 1000, "obs_kind": OBS_MOORING, "n_obs": 1521}, kw)
 
 
+def coupled_moorings(**kw):
+    """1521 moorings every 16 cells on 624 x 624 cells, 1000 particles: the
+    moorings sit closer than the 21-cell radius of the pull stencil, so the
+    dense 3042 x 3042 HQH^T + R couples neighbouring moorings and its
+    Cholesky factor fills in (the moorings of config4, 26 cells apart, do not
+    interact).  Use mooring_cells(cfg, COUPLED_SPACING)."""
+    return _cfg("iewpf_624x624_ne1000_1521moorings_every16", 624,
+                {"n_particles": 1000, "obs_kind": OBS_MOORING, "n_obs": 1521}, kw)
+
+
+COUPLED_SPACING = 16
+
+
 def config5(**kw):
     return _cfg("surrogate_256x256_ne1000_64drifters", 256, {"n_particles": 1000, "n_obs": 64}, kw)
 

@@ -8,10 +8,11 @@ FP64 weights.
 * 512 x 512, 100 particles, 64 drifters: one two-stage and one one-stage
   analysis of the initial ensemble, every particle's FP64 scalars and two
   sampled states.
-* 1024 x 1024, 1000 particles, 1521 moorings every 26 cells: one analysis
-  from the initial ensemble.  phi_i of every particle, gamma_i and zeta_i,
-  beta and alpha_i from the oracle's own inputs, and the updated state of two
-  sampled particles."""
+* 1024 x 1024, 1000 particles, 1521 moorings every 26 cells, and 624 x 624,
+  1000 particles, 1521 moorings every 16 cells (coupled through HQH^T): one
+  analysis from the initial ensemble.  phi_i of every particle, gamma_i and
+  zeta_i, beta and alpha_i from the oracle's own inputs, the fill of the
+  factor, and the updated state of two sampled particles."""
 import math
 
 import numpy as np
@@ -75,18 +76,20 @@ def _forecast_as_particle(P, U, i):
     return V[None], np.array([[n]]), None
 
 
-def test_config4_analysis_full_size():
-    cfg = synth.config4()
+def _mooring_analysis_full_size(cfg, cells, sample, coupled):
     ne = cfg.n_particles
     P = oracle_problem(cfg)
-    cells = synth.mooring_cells(cfg)
-    assert len(cells) == 1521
     xy = synth.cell_positions(cfg, cells)
-    sample = (3, 998)
     U, kept, at = _device_ensemble(cfg, ne, keep=sample, cells=cells)
     truth = synth.initial_particle(cfg, 123456, seed=99)
     y = synth.obs_from_state(cfg, truth, cells, synth.obs_noise(cfg, len(cells), 0))
     ens = ensemble(cfg, mooring_xy=xy)
+    n, nnz = ens.factor_info()
+    assert n == 2 * len(cells)
+    if coupled:
+        assert nnz > 100 * n        # the factor fills in between neighbouring moorings
+    else:
+        assert nnz == n // 2        # 2 x 2 blocks: the moorings do not interact
     ens.set_state(U)
     dg = ens.assimilate(None, y)
     # the oracle's own innovations, S d and phi for every particle
@@ -118,6 +121,24 @@ def test_config4_analysis_full_size():
         ref = O.add_pull(P, K, cells, Sd[i].reshape(-1, 2), kept[i])
         ref = O.add_qhalf(P, r, ref)
         assert rel_l2(out[i].cpu().numpy(), ref) < 1e-5
+
+
+def test_config4_analysis_full_size():
+    cfg = synth.config4()
+    cells = synth.mooring_cells(cfg)
+    assert len(cells) == 1521
+    _mooring_analysis_full_size(cfg, cells, (3, 998), coupled=False)
+
+
+def test_coupled_moorings_analysis_full_size():
+    """1521 moorings every 16 cells on 624 x 624, 1000 particles: each
+    mooring lies within the 21-cell pull stencil of its neighbours, so the
+    3042 x 3042 HQH^T + R couples them and its FP64 Cholesky factor fills in
+    (Sec. 4.2, eq. S_extended, with the cross-covariances kept)."""
+    cfg = synth.coupled_moorings()
+    cells = synth.mooring_cells(cfg, synth.COUPLED_SPACING)
+    assert len(cells) == 1521
+    _mooring_analysis_full_size(cfg, cells, (1, 999), coupled=True)
 
 
 def test_largest_ensemble_sampled():
