@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local):
                 side[name] = {"error": str(e)}
     if rank != 0:
         return
-    cpu = cpu_baseline(args) if world == 1 else None
+    cpu = cpu_baseline(args) if world == 1 and not args.no_cpu_baseline else None
     h2d = len(cells) * 2 * 8
     d2h = 6 * ne * 8 + 2 * 8
     line = {
@@ -910,6 +910,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="leave out the oracle's CPU timing (profiling runs)")
     ap.add_argument("--legs", default="all",
                     help="side workloads after the headline, comma-separated from %s, 'all' or 'none'"
                          % ",".join(LEGS))

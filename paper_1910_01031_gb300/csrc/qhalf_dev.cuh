@@ -63,6 +63,20 @@ __device__ __forceinline__ void normals_block(uint2 key, uint32_t p, uint32_t t,
 __device__ __forceinline__ float soar_point(const float* __restrict__ src, const float* __restrict__ wtab,
                                             const Coarse& C, const Grid& G, int am, int bm)
 {
+    if (am >= 2 && am + 2 < C.nRx && bm >= 2 && bm + 2 < C.nRy) {
+        // away from the periodic seam the neighbours are c fine cells apart:
+        // the same weights and sums as below without the periodic index
+        // arithmetic
+        float acc = 0.0f;
+#pragma unroll
+        for (int db = -2; db <= 2; ++db) {
+            const float* __restrict__ row = src + (bm + db) * C.nRx + am;
+            const float* __restrict__ wr = wtab + C.c * (db < 0 ? -db : db) * C.tab;
+#pragma unroll
+            for (int da = -2; da <= 2; ++da) acc = fmaf(wr[C.c * (da < 0 ? -da : da)], row[da], acc);
+        }
+        return acc;
+    }
     const int x0 = coarse_pos(am, C.nRx, C.c, C.o, G.nx), y0 = coarse_pos(bm, C.nRy, C.c, C.o, G.ny);
     int dxf[5], col[5];
 #pragma unroll
@@ -93,9 +107,15 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
 {
     constexpr int FW = TX + 2, FH = TY + 2, SXW = FW + 3, SXH = FH + 3;
     static_assert(!PULL || (TX == OBS_TX && TY == OBS_TY), "pull tiles follow the observation lists");
-    __shared__ float so[SXH][SXW];
-    __shared__ float rows[SXH][FW];
-    __shared__ float deta[FH][FW];
+    // the coarse patch, its rows interpolated and the interpolated field share
+    // one pool; with the pull, the tile's per-cell sums take its start once
+    // the interpolated field has been read
+    constexpr int SO_N = SXH * SXW, ROWS_N = SXH * FW, DETA_N = FH * FW;
+    static_assert(SO_N + ROWS_N + DETA_N >= 3 * TX * TY, "pull sums fit the pool");
+    __shared__ float pool[SO_N + ROWS_N + DETA_N];
+    float(*so)[SXW] = reinterpret_cast<float(*)[SXW]>(pool);
+    float(*rows)[FW] = reinterpret_cast<float(*)[FW]>(pool + SO_N);
+    float(*deta)[FW] = reinterpret_cast<float(*)[FW]>(pool + SO_N + ROWS_N);
     __shared__ int colA[FW], rowB[FH];
     __shared__ float colW[FW][4], rowW[FH][4];
 
@@ -149,6 +169,86 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
     float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
+    if (PULL && 2 * A.R < G.nx && 2 * A.R < G.ny) {
+        // Pull by observation: each observation of the list, in list order,
+        // adds its stencil to the cells it reaches (up to two column and two
+        // row intervals of the tile, split where the minimum image wraps),
+        // with a barrier between observations.  Every cell thus receives the
+        // same operations in the same order as in the per-cell loop below,
+        // without testing the observations that do not reach it.  Needs the
+        // stencil's reach 2R + 1 within the grid on both axes.
+        static_assert(TX * TY % NTHREADS == 0, "whole tiles per thread");
+        constexpr int PER = TX * TY / NTHREADS, N = TX * TY;
+        float v0[PER], v1[PER], v2[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * NTHREADS;
+            const int fx = i % TX + 1, fy = i / TX + 1;
+            v0[k] = deta[fy][fx];
+            v1[k] = -G.sgh * (deta[fy + 1][fx] - deta[fy - 1][fx]) * G.inv_2dy;
+            v2[k] = G.sgh * (deta[fy][fx + 1] - deta[fy][fx - 1]) * G.inv_2dx;
+        }
+        __syncthreads();
+        float* __restrict__ acc = pool;     // [3][TY][TX]
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * NTHREADS;
+            acc[i] = v0[k];
+            acc[N + i] = v1[k];
+            acc[2 * N + i] = v2[k];
+        }
+        __syncthreads();
+        const int txv = min(TX, G.nx - x0), tyv = min(TY, G.ny - y0);
+        const int fs = W * W;
+        for (int q = 0; q < n_obs_tile; ++q) {
+            const int ox0 = obs_ox[q], oy0 = obs_oy[q];
+            const float su = obs_su[q], sv = obs_sv[q];
+            // cells tx with the offset ox0 + tx in [-R, R], or ox0 + tx - n
+            // in [-R, R] past the wrap (offset at the interval's start)
+            const int xa[2] = {max(0, -A.R - ox0), max(0, G.nx - A.R - ox0)};
+            const int xb[2] = {min(txv, A.R - ox0 + 1), min(txv, G.nx + A.R - ox0 + 1)};
+            const int ya[2] = {max(0, -A.R - oy0), max(0, G.ny - A.R - oy0)};
+            const int yb[2] = {min(tyv, A.R - oy0 + 1), min(tyv, G.ny + A.R - oy0 + 1)};
+#pragma unroll
+            for (int ix = 0; ix < 2; ++ix) {
+                const int w = xb[ix] - xa[ix];
+                if (w <= 0) continue;
+                const int oxa = ox0 + xa[ix] - (ix ? G.nx : 0) + A.R;
+#pragma unroll
+                for (int iy = 0; iy < 2; ++iy) {
+                    const int h = yb[iy] - ya[iy];
+                    if (h <= 0) continue;
+                    const int oya = oy0 + ya[iy] - (iy ? G.ny : 0) + A.R;
+                    // the rectangle's w x h cells, linearised over the CTA;
+                    // row = floor((i + 1/2) / w) in float is exact here
+                    // (w, h <= 2R + 1, far below float's integer range)
+                    const float rw = 1.0f / (float)w;
+                    for (int i = tid; i < w * h; i += NTHREADS) {
+                        const int ry = __float2int_rz(((float)i + 0.5f) * rw);
+                        const int rx = i - ry * w;
+                        const int o = (oya + ry) * W + oxa + rx;
+                        const int c = (ya[iy] + ry) * TX + xa[ix] + rx;
+                        acc[c] = fmaf(sv, A.K[3 * fs + o], fmaf(su, A.K[0 * fs + o], acc[c]));
+                        acc[N + c] = fmaf(sv, A.K[4 * fs + o], fmaf(su, A.K[1 * fs + o], acc[N + c]));
+                        acc[2 * N + c] = fmaf(sv, A.K[5 * fs + o], fmaf(su, A.K[2 * fs + o], acc[2 * N + c]));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * NTHREADS;
+            const int gx = x0 + i % TX, gy = y0 + i / TX;
+            if (gx >= G.nx || gy >= G.ny) continue;
+            const long long g = (long long)gy * G.nx + gx;
+            const float e1 = U[g] + acc[i], u1 = U[G.plane + g] + acc[N + i], v1 = U[2 * G.plane + g] + acc[2 * N + i];
+            U[g] = e1;
+            U[G.plane + g] = u1;
+            U[2 * G.plane + g] = v1;
+            if (A.amax) m = fmaxf(m, cfl_of(e1, u1, v1, G));
+        }
+    } else
     for (int i = tid; i < TX * TY; i += NTHREADS) {
         const int tx = i % TX, ty = i / TX;
         const int gx = x0 + tx, gy = y0 + ty;
