@@ -37,15 +37,16 @@ __global__ void hqht_kernel(const double* __restrict__ K, int R, const int* __re
 
 __global__ void __launch_bounds__(1024)
 cholesky_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, int* rowidx, int* __restrict__ flag,
-                int* nzlist)
+                int* nzlist, double* __restrict__ rdiag, int* plan)
 {
     ana::cholesky_cta(A, n, colptr, rowidx, flag, nzlist);
+    ana::solve_plan_cta(A, n, colptr, rowidx, rdiag, plan);
 }
 
 // the same factorisation on a copy in shared memory (n * n doubles + n ints)
 __global__ void __launch_bounds__(1024)
 cholesky_small_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, int* __restrict__ rowidx,
-                      int* __restrict__ flag)
+                      int* __restrict__ flag, double* __restrict__ rdiag, int* plan)
 {
     extern __shared__ double sA[];
     int* work = reinterpret_cast<int*>(sA + (long long)n * n);
@@ -56,15 +57,17 @@ cholesky_small_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, i
     ana::cholesky_factor_cta(sA, n, work, &bad);
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) A[q] = sA[q];
     ana::csc_cta(sA, n, colptr, rowidx);
+    ana::solve_plan_cta(sA, n, colptr, rowidx, rdiag, plan);
     if (threadIdx.x == 0 && bad) atomicOr(flag, FLAG_NOTPD);
 }
 
 __global__ void solve_kernel(const double* __restrict__ L, const int* __restrict__ colptr,
-                             const int* __restrict__ rowidx, int n, const double* __restrict__ d,
+                             const int* __restrict__ rowidx, const double* __restrict__ rdiag,
+                             const int* __restrict__ plan, int n, const double* __restrict__ d,
                              double* __restrict__ x, double* __restrict__ phi, int ne)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp < ne) ana::solve_warp(L, colptr, rowidx, n, d, x, phi, warp);
+    if (warp < ne) ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, warp);
 }
 
 __global__ void __launch_bounds__(ana::DOT_THREADS)
@@ -157,7 +160,8 @@ cudaError_t launch_hqht(const double* K64, int R, const int* obs_cell, int nobs,
     return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, cudaStream_t st)
+cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, double* rdiag, int* plan,
+                            cudaStream_t st)
 {
     // small systems (drifter layouts change every cycle) factor in shared memory
     const size_t smem = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(int);
@@ -165,20 +169,20 @@ cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* fla
         cudaError_t e = cudaFuncSetAttribute(cholesky_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        cholesky_small_kernel<<<1, 1024, smem, st>>>(M, n, colptr, rowidx, flag);
+        cholesky_small_kernel<<<1, 1024, smem, st>>>(M, n, colptr, rowidx, flag, rdiag, plan);
         return cudaGetLastError();
     }
     // rowidx doubles as the per-column work list during the factorisation
-    cholesky_kernel<<<1, 1024, 0, st>>>(M, n, colptr, rowidx, flag, rowidx);
+    cholesky_kernel<<<1, 1024, 0, st>>>(M, n, colptr, rowidx, flag, rowidx, rdiag, plan);
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, int n, const double* d,
-                         double* Sd, double* phi, int ne, cudaStream_t st)
+cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, const double* rdiag, const int* plan,
+                         int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st)
 {
     const int threads = 128;
     const int blocks = (ne * 32 + threads - 1) / threads;
-    solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, n, d, Sd, phi, ne);
+    solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi, ne);
     return cudaGetLastError();
 }
 

@@ -246,6 +246,184 @@ __device__ __forceinline__ void solve_warp(const double* __restrict__ L, const i
     if (lane == 0) phi[w] = acc;
 }
 
+// Level schedule of the triangular solves with the factor L (CSC below the
+// diagonal in colptr/rowidx).  Rows of one level of the forward sweep
+// L y = d depend only on rows of lower levels, and likewise columns of one
+// level of the backward sweep L^T x = y; 2 x 2 blocks (observations that do
+// not interact) give two levels each.  Int layout of `plan`, n = order:
+// rowptr[n+1] | forder[n] | fptr[n+1] | border[n] | bptr[n+1] | nlev[2] |
+// lev[n] | colidx[n(n-1)/2] (CSR below the diagonal, column order in a row).
+struct SolvePlan {
+    int *rowptr, *forder, *fptr, *border, *bptr, *nlev, *lev, *colidx;
+};
+
+__host__ __device__ inline SolvePlan solve_plan_view(int* base, int n)
+{
+    SolvePlan P;
+    P.rowptr = base;
+    P.forder = P.rowptr + n + 1;
+    P.fptr = P.forder + n;
+    P.border = P.fptr + n + 1;
+    P.bptr = P.border + n;
+    P.nlev = P.bptr + n + 1;
+    P.lev = P.nlev + 2;
+    P.colidx = P.lev + n;
+    return P;
+}
+
+// rows in increasing index within each level (deterministic); ptr gets the
+// level boundaries; one thread
+__device__ __forceinline__ int level_sort(const int* __restrict__ lev, int n, int* __restrict__ order,
+                                          int* __restrict__ ptr)
+{
+    int nl = 0;
+    for (int i = 0; i < n; ++i) nl = max(nl, lev[i] + 1);
+    for (int l = 0; l <= nl; ++l) ptr[l] = 0;
+    for (int i = 0; i < n; ++i) ptr[lev[i] + 1]++;
+    for (int l = 0; l < nl; ++l) ptr[l + 1] += ptr[l];
+    for (int i = 0; i < n; ++i) order[ptr[lev[i]]++] = i;
+    for (int l = nl; l > 0; --l) ptr[l] = ptr[l - 1];
+    ptr[0] = 0;
+    return nl;
+}
+
+// CTA: reciprocal diagonal, CSR of L below the diagonal and both level
+// schedules; after csc_cta (colptr/rowidx complete)
+__device__ __forceinline__ void solve_plan_cta(const double* __restrict__ L, int n, const int* __restrict__ colptr,
+                                               const int* __restrict__ rowidx, double* __restrict__ rdiag,
+                                               int* plan_base)
+{
+    const SolvePlan P = solve_plan_view(plan_base, n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rdiag[i] = 1.0 / L[(long long)i * n + i];
+    for (int i = warp; i < n; i += nw) {
+        int cnt = 0;
+        for (int j0 = 0; j0 < i; j0 += 32) {
+            const int j = j0 + lane;
+            cnt += __popc(__ballot_sync(0xffffffffu, j < i && L[(long long)i * n + j] != 0.0));
+        }
+        if (lane == 0) P.rowptr[i + 1] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P.rowptr[0] = 0;
+        for (int i = 0; i < n; ++i) P.rowptr[i + 1] += P.rowptr[i];
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += nw) {
+        int pos = P.rowptr[i];
+        for (int j0 = 0; j0 < i; j0 += 32) {
+            const int j = j0 + lane;
+            const bool nz = j < i && L[(long long)i * n + j] != 0.0;
+            const unsigned bal = __ballot_sync(0xffffffffu, nz);
+            if (nz) P.colidx[pos + __popc(bal & ((1u << lane) - 1u))] = j;
+            pos += __popc(bal);
+        }
+    }
+    __syncthreads();
+    // forward levels: 1 + the largest level among the row's columns
+    if (warp == 0) {
+        for (int i = 0; i < n; ++i) {
+            int m = -1;
+            for (int q = P.rowptr[i] + lane; q < P.rowptr[i + 1]; q += 32) m = max(m, P.lev[P.colidx[q]]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) P.lev[i] = m + 1;
+            __syncwarp();
+        }
+        if (lane == 0) P.nlev[0] = level_sort(P.lev, n, P.forder, P.fptr);
+        __syncwarp();
+        // backward levels: 1 + the largest level among the column's rows
+        for (int i = n - 1; i >= 0; --i) {
+            int m = -1;
+            for (int q = colptr[i] + lane; q < colptr[i + 1]; q += 32) m = max(m, P.lev[rowidx[q]]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) P.lev[i] = m + 1;
+            __syncwarp();
+        }
+        if (lane == 0) P.nlev[1] = level_sort(P.lev, n, P.border, P.bptr);
+    }
+    __syncthreads();
+}
+
+// warp: S d = (L L^T)^{-1} d for particle w and phi_w = d^T S d along the
+// level schedule: a level of at least 8 rows gives one row per lane (the
+// row's sum in column order), a smaller one the whole warp to each row
+// (lane-strided partial sums, then the warp sum)
+__device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, const int* __restrict__ colptr,
+                                                  const int* __restrict__ rowidx, const double* __restrict__ rdiag,
+                                                  const int* plan_base, int n, const double* __restrict__ d,
+                                                  double* __restrict__ x, double* __restrict__ phi, int w)
+{
+    const SolvePlan P = solve_plan_view(const_cast<int*>(plan_base), n);
+    const int lane = threadIdx.x & 31;
+    double* xp = x + (long long)w * n;
+    const double* dp = d + (long long)w * n;
+    // forward: y_i = (d_i - sum_j L_ij y_j) / L_ii
+    const int nf = P.nlev[0];
+    for (int l = 0; l < nf; ++l) {
+        const int a = P.fptr[l], b = P.fptr[l + 1];
+        if (b - a >= 8) {
+            for (int t = a + lane; t < b; t += 32) {
+                const int i = P.forder[t];
+                double acc = 0.0;
+                for (int q = P.rowptr[i]; q < P.rowptr[i + 1]; ++q) {
+                    const int j = P.colidx[q];
+                    acc = fma(L[(long long)i * n + j], xp[j], acc);
+                }
+                xp[i] = (dp[i] - acc) * rdiag[i];
+            }
+        } else {
+            for (int t = a; t < b; ++t) {
+                const int i = P.forder[t];
+                double acc = 0.0;
+                for (int q = P.rowptr[i] + lane; q < P.rowptr[i + 1]; q += 32) {
+                    const int j = P.colidx[q];
+                    acc = fma(L[(long long)i * n + j], xp[j], acc);
+                }
+                acc = warp_sum(acc);
+                if (lane == 0) xp[i] = (dp[i] - acc) * rdiag[i];
+            }
+        }
+        __syncwarp();
+    }
+    // backward: x_i = (y_i - sum_k L_ki x_k) / L_ii over k > i
+    const int nb = P.nlev[1];
+    for (int l = 0; l < nb; ++l) {
+        const int a = P.bptr[l], b = P.bptr[l + 1];
+        if (b - a >= 8) {
+            for (int t = a + lane; t < b; t += 32) {
+                const int i = P.border[t];
+                double acc = 0.0;
+                for (int q = colptr[i]; q < colptr[i + 1]; ++q) {
+                    const int k = rowidx[q];
+                    acc = fma(L[(long long)k * n + i], xp[k], acc);
+                }
+                xp[i] = (xp[i] - acc) * rdiag[i];
+            }
+        } else {
+            for (int t = a; t < b; ++t) {
+                const int i = P.border[t];
+                double acc = 0.0;
+                for (int q = colptr[i] + lane; q < colptr[i + 1]; q += 32) {
+                    const int k = rowidx[q];
+                    acc = fma(L[(long long)k * n + i], xp[k], acc);
+                }
+                acc = warp_sum(acc);
+                __syncwarp();
+                if (lane == 0) xp[i] = (xp[i] - acc) * rdiag[i];
+            }
+        }
+        __syncwarp();
+    }
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) acc = fma(dp[i], xp[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) phi[w] = acc;
+}
+
 constexpr int DOT_THREADS = 256;
 constexpr int DOT_BLOCKS_PER_CTA = 8;
 

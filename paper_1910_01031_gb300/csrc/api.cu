@@ -87,6 +87,8 @@ struct iewpf_ctx {
     double* d_L = nullptr;      // (HQH^T + R) and its factor [Ny][Ny]
     int* d_colptr = nullptr;
     int* d_rowidx = nullptr;
+    double* d_rdiag = nullptr;  // 1 / diagonal of the factor [Ny]
+    int* d_plan = nullptr;      // level schedule of the triangular sweeps (ana::SolvePlan)
     double* d_d = nullptr;      // innovations [ne][Ny]
     double* d_Sd = nullptr;     // [ne][Ny]
     double* d_phi = nullptr;
@@ -428,7 +430,7 @@ int factor(iewpf_ctx* ctx, int nobs)
     const int n = 2 * nobs;
     KL(1, launch_hqht(ctx->d_K64, ctx->R, ctx->d_cell, nobs, ctx->G, ctx->P.dense_S,
                    ctx->P.obs_sigma * ctx->P.obs_sigma, ctx->d_L, ctx->st));
-    KL(1, launch_cholesky(ctx->d_L, n, ctx->d_colptr, ctx->d_rowidx, ctx->flag, ctx->st));
+    KL(1, launch_cholesky(ctx->d_L, n, ctx->d_colptr, ctx->d_rowidx, ctx->flag, ctx->d_rdiag, ctx->d_plan, ctx->st));
     ctx->n_fact = n;
     return IEWPF_OK;
 }
@@ -727,6 +729,7 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
         (rc = dalloc(ctx, &ctx->d_tile_obs, (size_t)ctx->ntiles * ctx->tile_cap)) ||
         (rc = dalloc(ctx, &ctx->d_L, ny * ny)) || (rc = dalloc(ctx, &ctx->d_colptr, ny + 1)) ||
         (rc = dalloc(ctx, &ctx->d_rowidx, ny * (ny - 1) / 2 + ny)) || (rc = dalloc(ctx, &ctx->d_d, ne * ny)) ||
+        (rc = dalloc(ctx, &ctx->d_rdiag, ny)) || (rc = dalloc(ctx, &ctx->d_plan, solve_plan_ints((int)ny))) ||
         (rc = dalloc(ctx, &ctx->d_Sd, ne * ny)) || (rc = dalloc(ctx, &ctx->d_phi, ne)) ||
         (rc = dalloc(ctx, &ctx->d_c, ne)) || (rc = dalloc(ctx, &ctx->d_gamma, ne)) ||
         (rc = dalloc(ctx, &ctx->d_zeta, ne)) || (rc = dalloc(ctx, &ctx->d_alpha, ne)) ||
@@ -756,7 +759,7 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
     void* ptrs[] = {ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->amax, ctx->maxsub, ctx->flag, ctx->work,
                     ctx->d_wtab, ctx->d_K32, ctx->d_K64, ctx->d_M49, ctx->d_xy, ctx->d_obs_xy, ctx->d_obs_y,
                     ctx->d_cell, ctx->d_block0, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
-                    ctx->d_rowidx, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
+                    ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
                     ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
                     ctx->d_r, ctx->d_xi, ctx->d_soar};
     for (void* p : ptrs)
@@ -859,7 +862,8 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
         KL(1, launch_innovate(ctx->buf[0], ctx->buf[1], ctx->par, ctx->d_cell, ctx->d_obs_y, nobs, ctx->G,
                            ctx->P.H_eq, ctx->d_d, ctx->st));
         if (!mooring && (rc = factor(ctx, nobs))) return rc;
-        KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, n, ctx->d_d, ctx->d_Sd, ctx->d_phi, ne, ctx->st));
+        KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, n, ctx->d_d, ctx->d_Sd,
+                           ctx->d_phi, ne, ctx->st));
     }
     // 3: random vectors
     Phase sub_("weights_and_update");
@@ -1567,6 +1571,8 @@ int iewpf_batch_create(const iewpf_params_t* params, const double* const* moorin
         I.K32 = ctx->d_K32;
         I.M49 = ctx->d_M49;
         I.L = ctx->d_L;
+        I.rdiag = ctx->d_rdiag;
+        I.plan = ctx->d_plan;
         I.colptr = ctx->d_colptr;
         I.rowidx = ctx->d_rowidx;
         I.d = ctx->d_d;

@@ -297,7 +297,10 @@ __global__ void __launch_bounds__(1024) b_cholesky(BatchDev B)
 {
     for (int i = blockIdx.x; i < B.n; i += gridDim.x) {
         const BInst& I = B.inst[i];
-        if (I.moving_obs) ana::cholesky_cta(I.L, 2 * I.nobs, I.colptr, I.rowidx, I.flag, I.rowidx);
+        if (I.moving_obs) {
+            ana::cholesky_cta(I.L, 2 * I.nobs, I.colptr, I.rowidx, I.flag, I.rowidx);
+            ana::solve_plan_cta(I.L, 2 * I.nobs, I.colptr, I.rowidx, I.rdiag, I.plan);
+        }
     }
 }
 
@@ -308,7 +311,8 @@ __global__ void b_solve(BatchDev B)
     for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < pre[B.n]; w += wpg) {
         const int i = find_inst(pre, B.n, w);
         const BInst& I = B.inst[i];
-        ana::solve_warp(I.L, I.colptr, I.rowidx, 2 * I.nobs, I.d, I.Sd, I.phi, (int)(w - pre[i]));
+        ana::solve_levels_warp(I.L, I.colptr, I.rowidx, I.rdiag, I.plan, 2 * I.nobs, I.d, I.Sd, I.phi,
+                               (int)(w - pre[i]));
     }
 }
 

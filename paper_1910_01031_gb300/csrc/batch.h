@@ -46,6 +46,8 @@ struct BInst {
     double* L;
     int* colptr;
     int* rowidx;
+    double* rdiag;              // level-scheduled solves (ana::solve_plan_cta)
+    int* plan;
     double* d;
     double* Sd;
     double* phi;

@@ -111,9 +111,18 @@ cudaError_t launch_innovate(const float* b0, const float* b1, const int* par, co
                             const double* y, int nobs, const Grid& G, double H, double* d, cudaStream_t st);
 cudaError_t launch_hqht(const double* K64, int R, const int* obs_cell, int nobs, const Grid& G, int dense,
                         double sigma2, double* M, cudaStream_t st);
-cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, cudaStream_t st);
-cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, int n, const double* d,
-                         double* Sd, double* phi, int ne, cudaStream_t st);
+// ints of the level schedule of the triangular sweeps of an n x n factor
+__host__ __device__ inline size_t solve_plan_ints(int n)
+{
+    return 6 * (size_t)n + 5 + (size_t)n * (n - 1) / 2;
+}
+// FP64 Cholesky of M (n x n) in place, the CSC of the factor below the
+// diagonal, its reciprocal diagonal and the level schedule of the two
+// triangular sweeps (plan: ana::solve_plan_ints(n) ints)
+cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, double* rdiag, int* plan,
+                            cudaStream_t st);
+cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, const double* rdiag, const int* plan,
+                         int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st);
 cudaError_t launch_rand_dots(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
                              double* partial, int nblk, cudaStream_t st);
 int rand_dots_blocks(int NR);
