@@ -372,7 +372,7 @@ cudaError_t launch_step(iewpf_ctx* ctx, int s)
 int tune_stepper(iewpf_ctx* ctx)
 {
     static const int ncs[] = {2, 3, 4};
-    static const int ths[] = {16, 32, 64, 128, 256};
+    static const int ths[] = {16, 32, 64, 128, 256, 512};
     static const int wps[] = {2, 4, 8};
     std::vector<int> ones(ctx->G.ne, 1);
     std::vector<float> dts(ctx->G.ne, (float)(ctx->P.dt_model / 16.0));

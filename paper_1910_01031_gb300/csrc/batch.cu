@@ -733,7 +733,7 @@ cudaError_t batch_forecast(BatchImpl& b, int n_steps, bool err, cudaStream_t st,
 cudaError_t batch_tune(BatchImpl& b, cudaStream_t st)
 {
     static const int ncs[] = {2, 3, 4};
-    static const int ths[] = {32, 64, 128, 256};
+    static const int ths[] = {32, 64, 128, 256, 512};
     static const int wps[] = {2, 4, 8};
     cudaError_t e;
     // every particle one probe step of dt_model / 16

@@ -12,7 +12,7 @@
 // shared memory and no block barriers.  The 4 outermost columns on each side
 // of a strip are halo (recomputed by the neighbouring strip) and 8 extra rows
 // fill the pipeline of each chunk.  Divisions and square roots use the
-// hardware approximations (rcp, rsqrt; a few ulp).  The file is compiled
+// hardware approximations (rcp, sqrt; a few ulp).  The file is compiled
 // without automatic multiply-add contraction and every fused multiply-add is
 // written out, so each cell's arithmetic is the same whatever the tile shape.
 #pragma once
@@ -32,13 +32,12 @@ __device__ __forceinline__ float frcp(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float frsqrt(float x)
+__device__ __forceinline__ float fsqrt(float x)
 {
     float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float fsqrt(float x) { return x * frsqrt(x); }
 
 // three-input minimum and maximum (one instruction each on sm_100 and later)
 __device__ __forceinline__ float fmin3(float a, float b, float c)
@@ -325,7 +324,7 @@ __device__ __forceinline__ f2 sub(f2 a, f2 b) { return __fadd2_rn(a, neg(b)); }
 __device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 rcp(f2 a) { return make_float2(frcp(a.x), frcp(a.y)); }
-__device__ __forceinline__ f2 rsq(f2 a) { return make_float2(frsqrt(a.x), frsqrt(a.y)); }
+__device__ __forceinline__ f2 sqr(f2 a) { return make_float2(fsqrt(a.x), fsqrt(a.y)); }
 __device__ __forceinline__ f2 max3z(f2 a, f2 b) { return make_float2(fmax3(a.x, b.x, 0.0f), fmax3(a.y, b.y, 0.0f)); }
 __device__ __forceinline__ f2 min3z(f2 a, f2 b) { return make_float2(fmin3(a.x, b.x, 0.0f), fmin3(a.y, b.y, 0.0f)); }
 __device__ __forceinline__ f2 gmm(f2 x, f2 y, f2 z) { return make_float2(gmm2s(x.x, y.x, z.x), gmm2s(x.y, y.y, z.y)); }
@@ -355,7 +354,7 @@ __device__ __forceinline__ void flux(f2 eL, f2 qnL, f2 qtL, f2 eR, f2 qnR, f2 qt
     const f2 rL = rcp(hL), rR = rcp(hR);
     const f2 unL = mul(qnL, rL), unR = mul(qnR, rR);
     const f2 xL = mul(K.g, hL), xR = mul(K.g, hR);
-    const f2 cL = mul(xL, rsq(xL)), cR = mul(xR, rsq(xR));
+    const f2 cL = sqr(xL), cR = sqr(xR);
     const f2 ap = max3z(add(unL, cL), add(unR, cR));
     const f2 am = min3z(sub(unL, cL), sub(unR, cR));
     const f2 inv = rcp(sub(ap, am));
