@@ -253,11 +253,12 @@ __device__ __forceinline__ void march_warp(const StepArgs& a, int p, int chunk, 
             nqv[k] = __ldg(in + 2 * G.plane + r0 + gx[k]);
         }
     }
+    int yn = pmod(y0 - 3, G.ny);     // row of the next prefetch, wrapped as it advances
     for (int it = 0; it < n_it; ++it) {
         // prefetch the next input row
         float pe[NC], pqu[NC], pqv[NC];
         if (it + 1 < n_it) {
-            const long long rn = (long long)pmod(y0 - 3 + it, G.ny) * G.nx;
+            const long long rn = (long long)yn * G.nx;
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
                 pe[k] = __ldg(in + rn + gx[k]);
@@ -265,6 +266,7 @@ __device__ __forceinline__ void march_warp(const StepArgs& a, int p, int chunk, 
                 pqv[k] = __ldg(in + 2 * G.plane + rn + gx[k]);
             }
         }
+        yn = yn + 1 == G.ny ? 0 : yn + 1;
         // stage 1 on U0, then stage 2 on U1 = U0 + dt L(U0)
         float L0[NC], L1[NC], L2[NC], ue[NC], uu[NC], uv[NC];
         S1.push(ne, nqu, nqv, G, L0, L1, L2, ue, uu, uv);
@@ -507,10 +509,11 @@ __device__ __forceinline__ void march_warp_paired(const StepArgs& a, int p, int 
         }
     }
     const int n_it = rows + 9;
+    int yn = pmod(y0 - 3, G.ny);     // row of the next prefetch, wrapped as it advances
     for (int it = 0; it < n_it; ++it) {
         float pe[NC], pqu[NC], pqv[NC];
         if (it + 1 < n_it) {
-            const long long rn = (long long)pmod(y0 - 3 + it, G.ny) * G.nx;
+            const long long rn = (long long)yn * G.nx;
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
                 pe[k] = __ldg(in + rn + gx[k]);
@@ -518,6 +521,7 @@ __device__ __forceinline__ void march_warp_paired(const StepArgs& a, int p, int 
                 pqv[k] = __ldg(in + 2 * G.plane + rn + gx[k]);
             }
         }
+        yn = yn + 1 == G.ny ? 0 : yn + 1;
         // the original state of this iteration's output row, read again
         // (issued here so that the loads complete during the push)
         const bool emit = it >= 9;
