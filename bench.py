@@ -48,9 +48,9 @@ BYTES_PER_CELL_STEP = 24          # read (eta, hu, hv) + write (eta, hu, hv), fl
 # FP32 operations of one scheme step per cell (adds, multiplies and fused
 # multiply-adds, one each; no halo), counted from the kernel's arithmetic
 SCHEME_OPS_PER_CELL_STEP = 260
-# thread-instructions per cell and scheme step measured by ncu at 512^2 x 100
-# (smsp__thread_inst_executed.sum / cells), per stepper kind
-ISSUE_PER_CELL_STEP = {1: 520.6, 2: 370.4}
+# issue slots per cell and scheme step measured by ncu at 512^2 x 100
+# (smsp__inst_executed.sum x 32 / cells), per stepper kind
+ISSUE_PER_CELL_STEP = {1: 524.3, 2: 363.3}
 WORKLOAD = "iewpf_cycle_1024x1024_ne1000_1521moorings"
 LEGS = ("drifters", "coupled", "batched", "batched_small", "surrogate", "one_stage", "rank_histogram")
 
