@@ -139,9 +139,18 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
         rowB[i] = b - b_lo;
         cubic_weights(t, rowW[i]);
     }
-    for (int i = tid; i < nsx * nsy; i += NTHREADS) {
-        const int sx = i % nsx, sy = i / nsx;
-        so[sy][sx] = so_g[pmod(b_lo - 1 + sy, C.nRy) * C.nRx + pmod(a_lo - 1 + sx, C.nRx)];
+    // the coarse patch, a row per warp (the indices lie within a period or
+    // two of the grid: wrapped by steps, not by an integer modulo)
+    for (int sy = tid >> 5; sy < nsy; sy += NTHREADS / 32) {
+        int r = b_lo - 1 + sy;
+        while (r < 0) r += C.nRy;
+        while (r >= C.nRy) r -= C.nRy;
+        for (int sx = tid & 31; sx < nsx; sx += 32) {
+            int c = a_lo - 1 + sx;
+            while (c < 0) c += C.nRx;
+            while (c >= C.nRx) c -= C.nRx;
+            so[sy][sx] = so_g[r * C.nRx + c];
+        }
     }
     __syncthreads();
     // rows: the x-interpolation of every SOAR row at every fine column
@@ -169,7 +178,7 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
     float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
-    if (PULL && 2 * A.R < G.nx && 2 * A.R < G.ny) {
+    if (PULL && n_obs_tile > 0 && 2 * A.R < G.nx && 2 * A.R < G.ny) {
         // Pull by observation: each observation of the list, in list order,
         // adds its stencil to the cells it reaches (up to two column and two
         // row intervals of the tile, split where the minimum image wraps),

@@ -82,8 +82,19 @@ __global__ void nonfinite_kernel(const float* __restrict__ buf0, const float* __
     const int p = blockIdx.y;
     const float* __restrict__ U = (par[p] ? buf1 : buf0) + (long long)p * 3 * G.plane;
     bool bad = false;
-    for (long long i = (long long)blockIdx.x * NTHREADS + threadIdx.x; i < 3 * G.plane;
-         i += (long long)gridDim.x * NTHREADS)
+    const long long n = 3 * G.plane;
+    long long i0 = 0;
+    if ((G.plane & 3) == 0) {
+        // four values per load (the particle's state starts 16-byte aligned)
+        const float4* __restrict__ U4 = reinterpret_cast<const float4*>(U);
+        for (long long i = (long long)blockIdx.x * NTHREADS + threadIdx.x; i < n / 4;
+             i += (long long)gridDim.x * NTHREADS) {
+            const float4 v = __ldcs(U4 + i);
+            bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+        }
+        i0 = n;
+    }
+    for (long long i = i0 + (long long)blockIdx.x * NTHREADS + threadIdx.x; i < n; i += (long long)gridDim.x * NTHREADS)
         bad |= !isfinite(U[i]);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, (int)FLAG_NONFINITE);
 }
@@ -176,7 +187,7 @@ cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const
 cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, const Grid& G, int* flag,
                              cudaStream_t st)
 {
-    const long long blocks = (3 * G.plane + NTHREADS * 16 - 1) / (NTHREADS * 16);
+    const long long blocks = (3 * G.plane + NTHREADS * 32 - 1) / (NTHREADS * 32);
     dim3 grid((unsigned)(blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks)), G.ne);
     nonfinite_kernel<<<grid, NTHREADS, 0, st>>>(b0, b1, par, G, flag);
     return cudaGetLastError();
