@@ -438,17 +438,34 @@ __device__ __forceinline__ void rand_dots_cta(uint64_t seed, uint32_t t, uint32_
     for (int b = bx * DOT_THREADS + threadIdx.x; b < nq; b += nblk * DOT_THREADS) {
         const uint4 wx = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)p, t, s_xi), key);
         const uint4 wn = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)p, t, s_nu), key);
-        double x[4], v[4];
-        box_muller64(wx.x, wx.y, x[0], x[1]);
-        box_muller64(wx.z, wx.w, x[2], x[3]);
-        box_muller64(wn.x, wn.y, v[0], v[1]);
-        box_muller64(wn.z, wn.w, v[2], v[3]);
+        if (4 * b + 3 < NR) {
+            // whole Box-Muller pairs: with z = r (cos, sin)(pi 2u_b) the pair
+            // contributes r^2 = -2 log u_a to the squared norm, and to the cross
+            // product r_nu r_xi cos(pi (2u_b,nu - 2u_b,xi)); one logarithm per
+            // pair, one square root and one cosine per pair of pairs
+            const uint32_t xa[2] = {wx.x, wx.z}, xb[2] = {wx.y, wx.w}, na[2] = {wn.x, wn.z}, nb[2] = {wn.y, wn.w};
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            if (4 * b + l < NR) {
-                xx = fma(x[l], x[l], xx);
-                nn = fma(v[l], v[l], nn);
-                nx = fma(v[l], x[l], nx);
+            for (int l = 0; l < 2; ++l) {
+                const double rx2 = -2.0 * log(((double)xa[l] + 0.5) * 0x1p-32);
+                const double rn2 = -2.0 * log(((double)na[l] + 0.5) * 0x1p-32);
+                const double d = ((double)nb[l] - (double)xb[l]) * 0x1p-31;   // 2u_b,nu - 2u_b,xi, exact
+                xx += rx2;
+                nn += rn2;
+                nx = fma(sqrt(rx2 * rn2), cospi(d), nx);
+            }
+        } else {
+            double x[4], v[4];
+            box_muller64(wx.x, wx.y, x[0], x[1]);
+            box_muller64(wx.z, wx.w, x[2], x[3]);
+            box_muller64(wn.x, wn.y, v[0], v[1]);
+            box_muller64(wn.z, wn.w, v[2], v[3]);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                if (4 * b + l < NR) {
+                    xx = fma(x[l], x[l], xx);
+                    nn = fma(v[l], v[l], nn);
+                    nx = fma(v[l], x[l], nx);
+                }
             }
         }
     }

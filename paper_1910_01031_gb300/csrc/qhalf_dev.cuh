@@ -178,14 +178,15 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
     float* __restrict__ U = (A.par[p] ? A.b1 : A.b0) + (long long)p * 3 * G.plane;
     const int W = 2 * A.R + 1;
     float m = 0.0f;    // CFL rate max of the updated cells (with A.amax)
-    if (PULL && n_obs_tile > 0 && 2 * A.R < G.nx && 2 * A.R < G.ny) {
+    if (PULL && n_obs_tile > 0) {
         // Pull by observation: each observation of the list, in list order,
         // adds its stencil to the cells it reaches (up to two column and two
         // row intervals of the tile, split where the minimum image wraps),
         // with a barrier between observations.  Every cell thus receives the
         // same operations in the same order as in the per-cell loop below,
-        // without testing the observations that do not reach it.  Needs the
-        // stencil's reach 2R + 1 within the grid on both axes.
+        // without testing the observations that do not reach it.  The
+        // stencil's reach 2R + 1 lies within the grid on both axes (iewpf_create
+        // refuses smaller grids), so each cell sees one image of each stencil.
         static_assert(TX * TY % NTHREADS == 0, "whole tiles per thread");
         constexpr int PER = TX * TY / NTHREADS, N = TX * TY;
         float v0[PER], v1[PER], v2[PER];
@@ -266,22 +267,6 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
         float de = deta[fy][fx];
         float dhu = -G.sgh * (deta[fy + 1][fx] - deta[fy - 1][fx]) * G.inv_2dy;
         float dhv = G.sgh * (deta[fy][fx + 1] - deta[fy][fx - 1]) * G.inv_2dx;
-        if (PULL) {
-            for (int q = 0; q < n_obs_tile; ++q) {
-                // the tile origin's offset is in (-n/2, n/2] and the cell's
-                // is at most one period above it
-                int ox = obs_ox[q] + tx, oy = obs_oy[q] + ty;
-                if (ox > G.nx / 2) ox -= G.nx;
-                if (oy > G.ny / 2) oy -= G.ny;
-                if (ox < -A.R || ox > A.R || oy < -A.R || oy > A.R) continue;
-                const float su = obs_su[q], sv = obs_sv[q];
-                const int o = (oy + A.R) * W + (ox + A.R);
-                const int fs = W * W;
-                de = fmaf(sv, A.K[3 * fs + o], fmaf(su, A.K[0 * fs + o], de));
-                dhu = fmaf(sv, A.K[4 * fs + o], fmaf(su, A.K[1 * fs + o], dhu));
-                dhv = fmaf(sv, A.K[5 * fs + o], fmaf(su, A.K[2 * fs + o], dhv));
-            }
-        }
         const long long g = (long long)gy * G.nx + gx;
         const float e1 = U[g] + de, u1 = U[G.plane + g] + dhu, v1 = U[2 * G.plane + g] + dhv;
         U[g] = e1;
