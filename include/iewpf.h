@@ -158,8 +158,13 @@ IEWPF_API int iewpf_get_state(iewpf_ctx_t* ctx, float* dst, int on_device, void*
  * particle's drifters after each, if any are set), then adds the model
  * error Q^{1/2} xi (eq. model_error) when add_model_error != 0.  The model
  * error of step k uses draw counter = the context's model-step counter,
- * which advances by one per model step.  Errors: EINVAL, ECUDA,
- * ENONFINITE (checked once per call). */
+ * which advances by one per model step.  The call runs as one CUDA graph
+ * (captured at the first call with its pattern of steps, model error and
+ * drifters, then replayed): the scheme steps of a model step loop on the
+ * device while the index is below the largest n_sub, so no host
+ * synchronisation sits between model steps; the call returns after one at
+ * the end.  Errors: EINVAL, ECUDA, ENONFINITE (checked once per call; also
+ * when a CFL count exceeds 100 000 scheme steps, which caps the loop). */
 IEWPF_API int iewpf_forecast(iewpf_ctx_t* ctx, int n_model_steps, int add_model_error);
 
 /* As iewpf_forecast (eq. model_equation) but with a fixed number of scheme

@@ -120,8 +120,23 @@ struct iewpf_ctx {
     struct iewpf_surrogate* sur = nullptr;   // learned surrogate for drift forecasts (not owned)
     int sur_k = 0;
     int64_t sur_calls = 0, sur_fallbacks = 0;
-    // scheme-step kernel: 0 = shared-memory tile kernel, 1 = register march
+    // scheme-step kernel: 1 = register march, 2 = the same with the two stages paired
     int stepper = 1;
+    // captured forecasts: device copies of the scheme-step index, the
+    // model-step counter and the count of loop iterations, and the graphs
+    // by their launch pattern
+    int* d_s = nullptr;
+    uint32_t* d_step = nullptr;
+    unsigned int* d_iters = nullptr;
+    uint32_t* h_step = nullptr;
+    unsigned int* h_iters = nullptr;
+    cudaStream_t st2 = nullptr;
+    struct FcGraph {
+        int n, err, fixed, have, nd, stepper, nc, TH, warps, paired;
+        cudaGraphExec_t exec;
+        int64_t launches_fixed, launches_per_iter;
+    };
+    std::vector<FcGraph> fgraphs;
     MarchShape shape{2, 64, 4};
     bool tuned = false;
     std::string err;
@@ -455,6 +470,98 @@ int read_flags(iewpf_ctx* ctx)
     return check_flags(ctx, f);
 }
 
+// Captures n_steps model steps into one executable graph: per model step the
+// CFL pass, a conditional WHILE node whose body is one scheme step (with the
+// drifters) and the loop control reading the largest n_sub on the device, the
+// parity flip, and the model error.  The scheme-step index and the model-step
+// counter come from device memory, so the graph serves every call with the
+// same pattern and needs no host synchronisation between model steps.
+static cudaError_t capture_forecast(iewpf_ctx* ctx, int n_steps, int add_err, int fixed, bool have0,
+                                    iewpf_ctx::FcGraph& fg)
+{
+    cudaStream_t st = ctx->st, st2 = ctx->st2;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int64_t fixed_launches = 0;
+    const int64_t per_iter = 2 + (ctx->nd > 0 ? 1 : 0);
+    bool have = have0;
+    auto body = [&]() -> cudaError_t {
+        cudaError_t r;
+        for (int k = 0; k < n_steps; ++k) {
+            if ((r = launch_cfl(ctx->buf[0], ctx->buf[1], ctx->par, ctx->amax, ctx->nsub, ctx->dtp, ctx->maxsub,
+                                ctx->G, ctx->P.courant, ctx->P.dt_model, fixed, st, have, ctx->flag)) != cudaSuccess)
+                return r;
+            fixed_launches += (fixed > 0 || have) ? 1 : 2;
+            if ((r = launch_step_reset(ctx->d_s, st)) != cudaSuccess) return r;
+            fixed_launches += 1;
+            cudaStreamCaptureStatus status;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndeps = 0;
+            if ((r = cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &ndeps)) != cudaSuccess)
+                return r;
+            cudaGraphConditionalHandle h;
+            if ((r = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return r;
+            cudaGraphNodeParams prm = {};
+            prm.type = cudaGraphNodeTypeConditional;
+            prm.conditional.handle = h;
+            prm.conditional.type = cudaGraphCondTypeWhile;
+            prm.conditional.size = 1;
+            cudaGraphNode_t node;
+            if ((r = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &prm)) != cudaSuccess) return r;
+            cudaGraph_t loop = prm.conditional.phGraph_out[0];
+            if ((r = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+                cudaSuccess)
+                return r;
+            if ((r = cudaStreamBeginCaptureToGraph(st2, loop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+                cudaSuccess)
+                return r;
+            cudaError_t rb = launch_rk2_march(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, 0, ctx->G,
+                                              ctx->shape, st2, ctx->d_s);
+            if (rb == cudaSuccess && ctx->nd > 0)
+                rb = launch_drift(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->d_xy, ctx->nd, 0,
+                                  ctx->G, ctx->P.dx, ctx->P.dy, st2, ctx->d_s);
+            if (rb == cudaSuccess) rb = launch_step_ctl(ctx->d_s, ctx->maxsub, h, ctx->d_iters, st2);
+            r = cudaStreamEndCapture(st2, &loop);
+            if (rb != cudaSuccess) return rb;
+            if (r != cudaSuccess) return r;
+            if ((r = launch_par_update(ctx->par, ctx->nsub, ctx->G.ne, ctx->work, st)) != cudaSuccess) return r;
+            fixed_launches += 1;
+            if (add_err) {
+                QhalfArgs A{};
+                A.b0 = ctx->buf[0];
+                A.b1 = ctx->buf[1];
+                A.par = ctx->par;
+                A.wtab = ctx->d_wtab;
+                A.from_philox = 1;
+                A.seed = ctx->P.seed;
+                A.t = 0;
+                A.t_dev = ctx->d_step;
+                A.stream = 0u + 16u * (uint32_t)ctx->P.instance_id;
+                A.xi_buf = ctx->d_xi;
+                A.soar_buf = ctx->d_soar;
+                A.amax = ctx->amax;
+                if ((r = cudaMemsetAsync(ctx->amax, 0, sizeof(float) * ctx->G.ne, st)) != cudaSuccess) return r;
+                if ((r = launch_qhalf(A, ctx->G, ctx->C, st)) != cudaSuccess) return r;
+                fixed_launches += qhalf_launches(A);
+            }
+            have = add_err && fixed <= 0;
+            if ((r = launch_counter_inc(ctx->d_step, st)) != cudaSuccess) return r;
+            fixed_launches += 1;
+        }
+        return cudaSuccess;
+    };
+    cudaError_t eb = body();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (eb == cudaSuccess) eb = e;
+    if (eb == cudaSuccess) eb = cudaGraphInstantiate(&fg.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    fg.launches_fixed = fixed_launches;
+    fg.launches_per_iter = per_iter;
+    return eb;
+}
+
 int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
 {
     if (!ctx) return IEWPF_EINVAL;
@@ -462,45 +569,38 @@ int forecast_impl(iewpf_ctx* ctx, int n_steps, int add_err, int fixed)
     CK(cudaSetDevice(ctx->dev));
     int rc;
     if (!ctx->tuned && (rc = tune_stepper(ctx))) return rc;
-    for (int k = 0; k < n_steps; ++k) {
-        const bool have = ctx->cfl_ready && fixed <= 0;
-        KL(fixed > 0 || have ? 1 : 2, launch_cfl(ctx->buf[0], ctx->buf[1], ctx->par, ctx->amax, ctx->nsub, ctx->dtp,
-                                                 ctx->maxsub, ctx->G, ctx->P.courant, ctx->P.dt_model, fixed, ctx->st,
-                                                 have));
-        ctx->cfl_ready = false;
-        CK(cudaMemcpyAsync(ctx->h_maxsub, ctx->maxsub, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
-        const int ms = *ctx->h_maxsub;
-        if (ms < 1 || ms > 100000) return fail(ctx, IEWPF_ENONFINITE, "invalid CFL substep count");
-        for (int s = 0; s < ms; ++s) {
-            KL(1, launch_step(ctx, s));
-            if (ctx->nd > 0)
-                KL(1, launch_drift(ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->d_xy, ctx->nd, s,
-                                ctx->G, ctx->P.dx, ctx->P.dy, ctx->st));
+    if (n_steps > 0) {
+        const int have = ctx->cfl_ready && fixed <= 0;
+        iewpf_ctx::FcGraph key{n_steps, add_err ? 1 : 0, fixed, have, ctx->nd, ctx->stepper, ctx->shape.nc,
+                               ctx->shape.TH, ctx->shape.warps, ctx->shape.paired, nullptr, 0, 0};
+        iewpf_ctx::FcGraph* fg = nullptr;
+        for (auto& g : ctx->fgraphs)
+            if (g.n == key.n && g.err == key.err && g.fixed == key.fixed && g.have == key.have && g.nd == key.nd &&
+                g.stepper == key.stepper && g.nc == key.nc && g.TH == key.TH && g.warps == key.warps &&
+                g.paired == key.paired)
+                fg = &g;
+        if (!fg) {
+            if (ctx->fgraphs.size() >= 8) {
+                cudaGraphExecDestroy(ctx->fgraphs.front().exec);
+                ctx->fgraphs.erase(ctx->fgraphs.begin());
+            }
+            CK(capture_forecast(ctx, n_steps, add_err, fixed, have != 0, key));
+            ctx->fgraphs.push_back(key);
+            fg = &ctx->fgraphs.back();
         }
-        KL(1, launch_par_update(ctx->par, ctx->nsub, ctx->G.ne, ctx->work, ctx->st));
-        if (add_err) {
-            QhalfArgs A{};
-            A.b0 = ctx->buf[0];
-            A.b1 = ctx->buf[1];
-            A.par = ctx->par;
-            A.wtab = ctx->d_wtab;
-            A.from_philox = 1;
-            A.seed = ctx->P.seed;
-            A.t = ctx->step;
-            A.t_dev = nullptr;
-            A.stream = 0u + 16u * (uint32_t)ctx->P.instance_id;
-            A.xi_buf = ctx->d_xi;
-            A.soar_buf = ctx->d_soar;
-            A.amax = ctx->amax;
-            CK(cudaMemsetAsync(ctx->amax, 0, sizeof(float) * ctx->G.ne, ctx->st));
-            KL(qhalf_launches(A), launch_qhalf(A, ctx->G, ctx->C, ctx->st));
-            ctx->cfl_ready = true;
-        }
-        ctx->step++;
+        *ctx->h_step = ctx->step;
+        CK(cudaMemcpyAsync(ctx->d_step, ctx->h_step, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemsetAsync(ctx->d_iters, 0, sizeof(unsigned int), ctx->st));
+        CK(cudaGraphLaunch(fg->exec, ctx->st));
+        CK(cudaMemcpyAsync(ctx->h_iters, ctx->d_iters, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+        ctx->launches += fg->launches_fixed;
+        ctx->step += (uint32_t)n_steps;
+        ctx->cfl_ready = add_err && fixed <= 0;
     }
     KL(1, launch_nonfinite(ctx->buf[0], ctx->buf[1], ctx->par, ctx->G, ctx->flag, ctx->st));
-    return read_flags(ctx);
+    rc = read_flags(ctx);
+    if (n_steps > 0) ctx->launches += (int64_t)*ctx->h_iters * (2 + (ctx->nd > 0 ? 1 : 0));
+    return rc;
 }
 
 }  // namespace
@@ -702,8 +802,13 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
         return bail(rc);
     if (cudaMallocHost((void**)&ctx->h_flag, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&ctx->h_maxsub, sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&ctx->h_scal, 4 * sizeof(double)) != cudaSuccess)
+        cudaMallocHost((void**)&ctx->h_scal, 4 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_step, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_iters, sizeof(unsigned int)) != cudaSuccess)
         return bail(IEWPF_ENOMEM);
+    if ((rc = dalloc(ctx, &ctx->d_s, 1)) || (rc = dalloc(ctx, &ctx->d_step, 1)) || (rc = dalloc(ctx, &ctx->d_iters, 1)))
+        return bail(rc);
+    if (cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking) != cudaSuccess) return bail(IEWPF_ECUDA);
     std::vector<float> K32(ctx->K64.begin(), ctx->K64.end());
     std::vector<float> M32(ctx->M49.begin(), ctx->M49.end());
     if (cudaMemsetAsync(ctx->buf[0], 0, state * sizeof(float), ctx->st) != cudaSuccess ||
@@ -767,6 +872,12 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
     if (ctx->h_maxsub) cudaFreeHost(ctx->h_maxsub);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->h_step) cudaFreeHost(ctx->h_step);
+    if (ctx->h_iters) cudaFreeHost(ctx->h_iters);
+    for (auto& fg : ctx->fgraphs) cudaGraphExecDestroy(fg.exec);
+    for (void* p : {(void*)ctx->d_s, (void*)ctx->d_step, (void*)ctx->d_iters})
+        if (p) cudaFree(p);
+    if (ctx->st2) cudaStreamDestroy(ctx->st2);
     if (ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
     return IEWPF_OK;

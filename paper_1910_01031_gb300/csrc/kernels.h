@@ -13,10 +13,21 @@ namespace iewpf {
 // the model-error or analysis update); only n_sub is derived then
 cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* amax, int* nsub, float* dtp,
                        int* maxsub, const Grid& G, double courant, double dt_model, int fixed,
-                       cudaStream_t st, bool have_amax = false);
+                       cudaStream_t st, bool have_amax = false,
+                       int* flag = nullptr);
 cudaError_t launch_par_update(int* par, const int* nsub, int ne, unsigned long long* work, cudaStream_t st);
+// the scheme-step loop of a captured model step: reset the index, then after
+// every step advance it and keep looping while it is below the largest n_sub
+// (and below kMaxSubSingle); the model-step counter of the model error
+constexpr int kMaxSubSingle = 100000;
+cudaError_t launch_step_reset(int* s_dev, cudaStream_t st);
+cudaError_t launch_step_ctl(int* s_dev, const int* maxsub, cudaGraphConditionalHandle h, unsigned int* iters,
+                            cudaStream_t st);
+cudaError_t launch_counter_inc(uint32_t* t_dev, cudaStream_t st);
+// s_dev (may be null): the scheme-step index read from device memory instead of s
 cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const int* nsub, const float* dtp,
-                         double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st);
+                         double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st,
+                         const int* s_dev = nullptr);
 cudaError_t launch_drift_errors(const double* xy, const double* truth, int ne, int nd, double* E, double* RMSE,
                                 cudaStream_t st);
 cudaError_t launch_nonfinite(const float* b0, const float* b1, const int* par, const Grid& G, int* flag,
@@ -50,6 +61,7 @@ struct StepArgs {
     const float* dtp;
     Grid G;
     int TH, n_strips, n_chunks;
+    const int* s_dev = nullptr;   // scheme-step index in device memory (graph loops), else the kernel argument
 };
 }  // namespace march
 
@@ -62,7 +74,8 @@ struct MarchShape {
     int paired = 0;
 };
 cudaError_t launch_rk2_march(float* b0, float* b1, const int* par, const int* nsub, const float* dtp, int s,
-                             const Grid& G, const MarchShape& shape, cudaStream_t st);
+                             const Grid& G, const MarchShape& shape, cudaStream_t st,
+                             const int* s_dev = nullptr);
 
 // ---- qhalf.cu -------------------------------------------------------------
 // psi += Q^{1/2} x (+ the optimal-proposal pull) for every particle.

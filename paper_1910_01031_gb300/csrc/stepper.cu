@@ -34,11 +34,18 @@ cfl_kernel(const float* __restrict__ buf0, const float* __restrict__ buf1, const
 
 // n_sub = ceil(dt_model / dt_cfl), dt_cfl = courant / 4 / amax; dt = dt_model / n_sub
 __global__ void nsub_kernel(const float* __restrict__ amax, int* __restrict__ nsub, float* __restrict__ dtp,
-                            int* __restrict__ maxsub, int ne, double courant, double dt_model, int fixed)
+                            int* __restrict__ maxsub, int ne, double courant, double dt_model, int fixed,
+                            int* __restrict__ flag)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ne) return;
-    const int n = nsub_of(amax[p], courant, dt_model, fixed);
+    int n = nsub_of(amax[p], courant, dt_model, fixed);
+    if (flag && n > kMaxSubSingle) {
+        // a non-finite or runaway state: cap the count so that a device-side
+        // loop over the scheme steps ends, and report it
+        n = kMaxSubSingle;
+        atomicOr(flag, (int)FLAG_NONFINITE);
+    }
     nsub[p] = n;
     dtp[p] = (float)(dt_model / (double)n);
     atomicMax(maxsub, n);
@@ -58,10 +65,11 @@ __global__ void par_update_kernel(int* __restrict__ par, const int* __restrict__
 __global__ void drift_kernel(const float* __restrict__ buf0, const float* __restrict__ buf1,
                              const int* __restrict__ par, const int* __restrict__ nsub,
                              const float* __restrict__ dtp, double* __restrict__ xy, int nd, int s, Grid G,
-                             double dx, double dy)
+                             double dx, double dy, const int* __restrict__ s_dev)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G.ne * nd) return;
+    if (s_dev) s = *s_dev;
     const int p = i / nd;
     if (s >= nsub[p]) return;
     const int cur = par[p] ^ ((s + 1) & 1);     // buffer written by scheme step s
@@ -157,7 +165,7 @@ cudaError_t launch_drift_errors(const double* xy, const double* truth, int ne, i
 
 cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* amax, int* nsub, float* dtp,
                        int* maxsub, const Grid& G, double courant, double dt_model, int fixed,
-                       cudaStream_t st, bool have_amax)
+                       cudaStream_t st, bool have_amax, int* flag)
 {
     if (!have_amax) cudaMemsetAsync(amax, 0, sizeof(float) * G.ne, st);
     cudaMemsetAsync(maxsub, 0, sizeof(int), st);
@@ -166,7 +174,7 @@ cudaError_t launch_cfl(const float* b0, const float* b1, const int* par, float* 
         dim3 grid((unsigned)(blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks)), G.ne);
         cfl_kernel<<<grid, NTHREADS, 0, st>>>(b0, b1, par, amax, G);
     }
-    nsub_kernel<<<(G.ne + 127) / 128, 128, 0, st>>>(amax, nsub, dtp, maxsub, G.ne, courant, dt_model, fixed);
+    nsub_kernel<<<(G.ne + 127) / 128, 128, 0, st>>>(amax, nsub, dtp, maxsub, G.ne, courant, dt_model, fixed, flag);
     return cudaGetLastError();
 }
 
@@ -177,10 +185,46 @@ cudaError_t launch_par_update(int* par, const int* nsub, int ne, unsigned long l
 }
 
 cudaError_t launch_drift(const float* b0, const float* b1, const int* par, const int* nsub, const float* dtp,
-                         double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st)
+                         double* xy, int nd, int s, const Grid& G, double dx, double dy, cudaStream_t st,
+                         const int* s_dev)
 {
     const int n = G.ne * nd;
-    drift_kernel<<<(n + 127) / 128, 128, 0, st>>>(b0, b1, par, nsub, dtp, xy, nd, s, G, dx, dy);
+    drift_kernel<<<(n + 127) / 128, 128, 0, st>>>(b0, b1, par, nsub, dtp, xy, nd, s, G, dx, dy, s_dev);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void step_reset_kernel(int* s_dev) { *s_dev = 0; }
+
+// advances the scheme-step index and sets the loop's condition; the cap keeps
+// the loop finite whatever the largest n_sub holds
+__global__ void step_ctl_kernel(int* s_dev, const int* maxsub, cudaGraphConditionalHandle h, unsigned int* iters)
+{
+    const int s = *s_dev + 1;
+    *s_dev = s;
+    if (iters) *iters += 1u;
+    cudaGraphSetConditional(h, (s < *maxsub && s < kMaxSubSingle) ? 1u : 0u);
+}
+
+__global__ void counter_inc_kernel(uint32_t* t) { *t += 1u; }
+}  // namespace
+
+cudaError_t launch_step_reset(int* s_dev, cudaStream_t st)
+{
+    step_reset_kernel<<<1, 1, 0, st>>>(s_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_ctl(int* s_dev, const int* maxsub, cudaGraphConditionalHandle h, unsigned int* iters,
+                            cudaStream_t st)
+{
+    step_ctl_kernel<<<1, 1, 0, st>>>(s_dev, maxsub, h, iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counter_inc(uint32_t* t_dev, cudaStream_t st)
+{
+    counter_inc_kernel<<<1, 1, 0, st>>>(t_dev);
     return cudaGetLastError();
 }
 
