@@ -665,7 +665,9 @@ __device__ __forceinline__ void form_r_one(uint64_t seed, uint32_t t, uint32_t s
     const float xi = normal32(key, (uint32_t)p, t, s_xi, (uint32_t)m);
     const float nut = normal32(key, (uint32_t)p, t, s_nu, (uint32_t)m);
     const float a = (float)coef[2 * p], sc = (float)coef[2 * p + 1];
-    const float sb = (float)sqrt(fmax(scal[1], 0.0)), sa = (float)sqrt(alpha[p]);
+    // square roots in FP32 (the factors enter an FP32 field; an FP64 square
+    // root per coarse point would cost more than the rest of the kernel)
+    const float sb = sqrtf((float)fmax(scal[1], 0.0)), sa = sqrtf((float)alpha[p]);
     r[(long long)p * NR + m] = fmaf(sb, sc * fmaf(-a, xi, nut), sa * xi);
 }
 

@@ -153,23 +153,40 @@ __device__ __forceinline__ void fine_tile(const QhalfArgs& A, const Grid& G, con
         }
     }
     __syncthreads();
-    // rows: the x-interpolation of every SOAR row at every fine column
-    for (int i = tid; i < nsy * FW; i += NTHREADS) {
-        const int fx = i % FW, sy = i / FW;
-        const int a = colA[fx];
-        float row = 0.0f;
+    // rows: the x-interpolation of every SOAR row at every fine column; a
+    // lane keeps its columns' taps and weights, the warps take the rows
+    {
+        const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) row = fmaf(colW[fx][pp], so[sy][a + pp], row);
-        rows[sy][fx] = row;
+        for (int j = 0; j < (FW + 31) / 32; ++j) {
+            const int fx = lane + 32 * j;
+            if (fx < FW) {
+                const int a = colA[fx];
+                const float w0 = colW[fx][0], w1 = colW[fx][1], w2 = colW[fx][2], w3 = colW[fx][3];
+                for (int sy = warp; sy < nsy; sy += NTHREADS / 32) {
+                    float row = 0.0f;
+                    row = fmaf(w0, so[sy][a], row);
+                    row = fmaf(w1, so[sy][a + 1], row);
+                    row = fmaf(w2, so[sy][a + 2], row);
+                    row = fmaf(w3, so[sy][a + 3], row);
+                    rows[sy][fx] = row;
+                }
+            }
+        }
     }
     __syncthreads();
-    for (int i = tid; i < FW * FH; i += NTHREADS) {
-        const int fx = i % FW, fy = i / FW;
+    // the y-interpolation: a row of the tile per warp, the lanes along it
+    for (int fy = tid >> 5; fy < FH; fy += NTHREADS / 32) {
         const int b = rowB[fy];
-        float acc = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc = fmaf(rowW[fy][q], rows[b + q][fx], acc);
-        deta[fy][fx] = acc;
+        const float w0 = rowW[fy][0], w1 = rowW[fy][1], w2 = rowW[fy][2], w3 = rowW[fy][3];
+        for (int fx = tid & 31; fx < FW; fx += 32) {
+            float acc = 0.0f;
+            acc = fmaf(w0, rows[b][fx], acc);
+            acc = fmaf(w1, rows[b + 1][fx], acc);
+            acc = fmaf(w2, rows[b + 2][fx], acc);
+            acc = fmaf(w3, rows[b + 3][fx], acc);
+            deta[fy][fx] = acc;
+        }
     }
     __syncthreads();
     __shared__ int obs_ox[PULL ? MAX_TILE_OBS : 1], obs_oy[PULL ? MAX_TILE_OBS : 1];
