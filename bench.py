@@ -55,6 +55,15 @@ WORKLOAD = "iewpf_cycle_1024x1024_ne1000_1521moorings"
 LEGS = ("drifters", "coupled", "batched", "batched_small", "surrogate", "one_stage", "rank_histogram")
 
 
+def measured_peak(key, default):
+    """A peak from MEASURED_PEAKS.json (HBM copy, cuBLAS BF16 burst and
+    sustained), else the stated fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get(key, default))
+    except Exception:
+        return float(default)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -700,11 +709,27 @@ def run_surrogate(rank, n_pairs=20000, epochs=8, batch=32, lr=1e-3, hours=12.0, 
     t0 = time.perf_counter()
     losses = net.train(ens1, n_pairs=n_pairs, k_steps=k, epochs=epochs, batch=batch, lr=lr)
     train_s = time.perf_counter() - t0
+    epochs_s = net.train_time()
+    tc_train = net.uses_tcgen05_training()
     params, (si, so) = net.params(), net.scales()
     net.close()
     ens1.close()
+    # tensor-core work of one optimizer step per pixel: forward, data passes
+    # of layers 1..5 and weight gradients of all six layers (the 3 used
+    # channels of the network's input and output)
+    fwd = 2 * 9 * (3 * 64 + 4 * 64 * 64 + 64 * 3)
+    flop_px = fwd + (fwd - 2 * 9 * 3 * 64) + fwd
+    steps = epochs * (n_pairs // batch)
+    flops = float(flop_px) * batch * cfg1.nx * cfg1.ny * steps
     out["train"] = {"pairs": n_pairs, "grid": "64x64", "epochs": epochs, "batch": batch, "lr": lr,
-                    "seconds": round(train_s, 2), "epoch_loss": [round(float(v), 5) for v in losses]}
+                    "seconds": round(train_s, 2), "epochs_device_s": round(epochs_s, 3),
+                    "path": "tcgen05" if tc_train else "mma.sync", "optimizer_steps": steps,
+                    "flops_per_pixel_step": flop_px,
+                    "tflops": round(flops / epochs_s / 1e12, 1) if epochs_s > 0 else None,
+                    "peak": measured_peak("bf16_tflops_sustained", 1700.0),
+                    "frac": round(flops / epochs_s / 1e12 / measured_peak("bf16_tflops_sustained", 1700.0), 4)
+                    if epochs_s > 0 else None,
+                    "epoch_loss": [round(float(v), 5) for v in losses]}
     cfg = synth.config5(n_particles=ne, seed=0x1910_01031 + 11 * rank)
     P = iewpf.params_from_config(cfg, n_drifters_max=cfg.n_obs)
     P.instance_id = rank

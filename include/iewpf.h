@@ -509,11 +509,16 @@ IEWPF_API int iewpf_surrogate_get_params(const iewpf_surrogate_t* s, float* para
  * Errors: EINVAL (NULL or not positive). */
 IEWPF_API int iewpf_surrogate_set_scales(iewpf_surrogate_t* s, const double* in_scale, const double* out_scale);
 IEWPF_API int iewpf_surrogate_get_scales(const iewpf_surrogate_t* s, double* in_scale, double* out_scale);
-/* Convolution path: 0 (default) = tcgen05 tensor-core kernels where nx is a
- * multiple of 128 and ny even, else mma.sync kernels; 1 = always mma.sync.
- * The backward pass always uses the mma.sync kernels.  get_path tells
- * whether the forward pass runs on tcgen05.  Errors: EINVAL (path not 0 or 1,
- * NULL). */
+/* Convolution path: 0 (default) = tcgen05 tensor-core kernels where the
+ * grid allows, else mma.sync kernels; 1 = always mma.sync.  Inference
+ * (apply, the drift forecast) runs on tcgen05 where nx is a multiple of 128
+ * and ny even; training (loss_grad, train: the forward pass that keeps the
+ * pre-activations, the backward data passes and the weight gradients of
+ * layers 1..depth-1) where nx is a multiple of 64 and ny of 4, and an
+ * inference on such a grid that the first rule excludes uses the training
+ * forward.  The weight gradient of layer 0 (16 input channels) always runs
+ * on mma.sync.  get_path writes a bit mask: bit 0 = inference on tcgen05,
+ * bit 1 = training on tcgen05.  Errors: EINVAL (path not 0 or 1, NULL). */
 IEWPF_API int iewpf_surrogate_set_path(iewpf_surrogate_t* s, int path);
 IEWPF_API int iewpf_surrogate_get_path(const iewpf_surrogate_t* s, int* uses_tcgen05);
 /* Failure injection for tests of the timeout path (the failure detection
@@ -558,6 +563,10 @@ IEWPF_API int iewpf_surrogate_loss_grad(iewpf_surrogate_t* s, const float* X, co
  * the pairs). */
 IEWPF_API int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, int k_steps, int epochs,
                                     int batch, double lr, double* epoch_loss);
+/* Device time in seconds of the epochs (the optimizer steps, without the
+ * generation of the pairs) of the last successful train call, from CUDA
+ * events on the surrogate's stream; 0 before the first.  Errors: EINVAL. */
+IEWPF_API int iewpf_surrogate_train_time(const iewpf_surrogate_t* s, double* seconds);
 /* Attach (s != NULL, k_steps >= 1) or detach (s = NULL) a surrogate to ctx
  * for drifter_forecast(..., use_surrogate = 1).  Not owned by ctx.  Each
  * surrogate call covers k_steps model steps of all particles; it is rejected

@@ -616,6 +616,7 @@ struct iewpf_surrogate {
     float* stats = nullptr;
     size_t cap_state = 0;
     int chunk = 64;
+    double train_s = 0.0;       // device time of the epochs of the last train call
 };
 
 // the timeout flag of the network's tensor-core kernels (read and cleared)
@@ -1870,7 +1871,7 @@ int iewpf_surrogate_set_path(iewpf_surrogate_t* s, int path)
 int iewpf_surrogate_get_path(const iewpf_surrogate_t* s, int* uses_tcgen05)
 {
     if (!s || !uses_tcgen05) return IEWPF_EINVAL;
-    *uses_tcgen05 = s->net.uses_tc() ? 1 : 0;
+    *uses_tcgen05 = (s->net.uses_tc() ? 1 : 0) | (s->net.uses_tc_train() ? 2 : 0);
     return IEWPF_OK;
 }
 
@@ -2071,13 +2072,27 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
     SCK(cudaSetDevice(s->dev));
     const int ne = ctx->G.ne;
     const size_t per = 3ull * s->net.nx * s->net.ny;
-    float *X = nullptr, *Y = nullptr, *bx = nullptr, *by = nullptr;
+    const int nbat = n_pairs / batch;       // batches per epoch (a last partial batch is skipped)
+    const long long total = (long long)epochs * nbat;
+    float *X = nullptr, *Y = nullptr, *d_bc = nullptr;
+    int* d_order = nullptr;                 // the epoch's order of the pairs; a batch reads its slice
+    int* d_ctr = nullptr;                   // batch cursor, optimizer step of this call
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     auto cleanup = [&]() {
-        for (float* p : {X, Y, bx, by})
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        for (void* p : {(void*)X, (void*)Y, (void*)d_order, (void*)d_ctr, (void*)d_bc})
             if (p) cudaFree(p);
+        X = Y = d_bc = nullptr;
+        d_order = d_ctr = nullptr;
     };
     if (cudaMalloc((void**)&X, per * n_pairs * 4) != cudaSuccess || cudaMalloc((void**)&Y, per * n_pairs * 4) != cudaSuccess ||
-        cudaMalloc((void**)&bx, per * batch * 4) != cudaSuccess || cudaMalloc((void**)&by, per * batch * 4) != cudaSuccess) {
+        cudaMalloc((void**)&d_order, sizeof(int) * n_pairs) != cudaSuccess ||
+        cudaMalloc((void**)&d_ctr, sizeof(int) * 2) != cudaSuccess ||
+        cudaMalloc((void**)&d_bc, sizeof(float) * 2 * std::max<long long>(total, 1)) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return sfail(s, IEWPF_ENOMEM, "training pairs");
@@ -2158,30 +2173,63 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
     std::mt19937_64 gen(12345);
     std::vector<int> order(n_pairs);
     for (int i = 0; i < n_pairs; ++i) order[i] = i;
+    // Adam's bias corrections of this call's steps (host arithmetic, as adam_step)
+    {
+        std::vector<float> bc(2 * std::max<long long>(total, 1), 1.0f);
+        for (long long k = 0; k < total; ++k) {
+            const float t = (float)(s->net.t_adam + 1 + k);
+            bc[2 * k] = 1.0f - std::pow(Surrogate::kAdamB1, t);
+            bc[2 * k + 1] = 1.0f - std::pow(Surrogate::kAdamB2, t);
+        }
+        SCK(cudaMemcpyAsync(d_bc, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice, s->st));
+        SCK(cudaMemsetAsync(d_ctr, 0, sizeof(int) * 2, s->st));
+        SCK(cudaStreamSynchronize(s->st));
+    }
+    // one optimizer step captured as a CUDA graph and replayed per batch: the
+    // step reads its batch through the cursor and its bias corrections
+    // through the step counter, both in device memory
+    if (total > 0) {
+        SCK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ce = s->net.train_step(X, Y, d_order, d_ctr, d_bc, batch, (float)lr, s->st);
+        const cudaError_t ee = cudaStreamEndCapture(s->st, &graph);
+        SCK(ce);
+        SCK(ee);
+        SCK(cudaGraphInstantiate(&gexec, graph, 0));
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    SCK(cudaEventCreate(&ev0));
+    SCK(cudaEventCreate(&ev1));
+    SCK(cudaEventRecord(ev0, s->st));
+    // the batches of an epoch are queued without a host synchronisation; the
+    // batch losses add up on the device and are read once per epoch
     for (int ep = 0; ep < epochs; ++ep) {
         for (int i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[gen() % (uint64_t)(i + 1)]);
+        SCK(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n_pairs, cudaMemcpyHostToDevice, s->st));
+        SCK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s->st));
+        SCK(cudaMemsetAsync(s->net.eloss, 0, sizeof(double), s->st));
+        for (int k = 0; k < nbat; ++k) SCK(cudaGraphLaunch(gexec, s->st));
         double acc = 0.0;
-        int nbat = 0;
-        for (int b0 = 0; b0 + batch <= n_pairs; b0 += batch) {
-            for (int j = 0; j < batch; ++j) {
-                SCK(cudaMemcpyAsync(bx + per * j, X + per * order[b0 + j], per * 4, cudaMemcpyDeviceToDevice, s->st));
-                SCK(cudaMemcpyAsync(by + per * j, Y + per * order[b0 + j], per * 4, cudaMemcpyDeviceToDevice, s->st));
-            }
-            SCK(s->net.pack_input(bx, batch, s->st));
-            SCK(s->net.pack_target(bx, by, batch, s->st));
-            SCK(s->net.forward(batch, s->st));
-            SCK(s->net.backward(batch, s->st));
-            SCK(s->net.adam_step((float)lr, s->st));
-            double l = 0.0;
-            SCK(cudaMemcpyAsync(&l, s->net.dloss, 8, cudaMemcpyDeviceToHost, s->st));
-            SCK(cudaStreamSynchronize(s->st));
-            acc += l;
-            ++nbat;
-        }
+        SCK(cudaMemcpyAsync(&acc, s->net.eloss, 8, cudaMemcpyDeviceToHost, s->st));
+        SCK(cudaStreamSynchronize(s->st));
         if (epoch_loss) epoch_loss[ep] = nbat ? acc / nbat : 0.0;
     }
+    s->net.t_adam += (int)total;
+    SCK(cudaEventRecord(ev1, s->st));
+    SCK(cudaEventSynchronize(ev1));
+    float ms = 0.0f;
+    SCK(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    s->train_s = ms * 1e-3;
     cleanup();
     return sur_flag(s, s->st);
+}
+
+int iewpf_surrogate_train_time(const iewpf_surrogate_t* s, double* seconds)
+{
+    if (!s || !seconds) return IEWPF_EINVAL;
+    *seconds = s->train_s;
+    return IEWPF_OK;
 }
 
 int iewpf_set_surrogate(iewpf_ctx_t* ctx, iewpf_surrogate_t* s, int k_steps)

@@ -33,6 +33,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "surrogate.h"
+#include "tc_dev.cuh"
 
 #include <cuda_bf16.h>
 
@@ -47,87 +48,13 @@ constexpr int TC_PCOLS = TC_PX + 2;        // patch columns
 constexpr int TC_EPI_WARPS = 16;           // 4 lane quarters x 2 rows x 2 column halves
 constexpr int TC_WARPS = 2 + TC_EPI_WARPS;
 constexpr int TC_THREADS = 32 * TC_WARPS;
-constexpr long long TC_WAIT_LIMIT = 1LL << 24;
-
-__device__ __forceinline__ uint32_t su32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor (K-major): layout 0 = no swizzle
-// (lbo = bytes between core matrices along K, sbo = along M/N), 2 = 128-byte
-// swizzle (sbo = bytes between 8-row atoms)
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7) << 61);
-}
-
-// instruction descriptor: BF16 A and B (K-major), FP32 D, M x N
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// bounded wait for the phase of `parity`; gives up when the CTA aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
-                                          long long limit = TC_WAIT_LIMIT)
-{
-    for (long long it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (done) return true;
-        if ((it & 255) == 255 && *abort) return false;
-    }
-    *abort = 1;
-    return false;
-}
-
-// the same without the abort check (draining after an abort)
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
-{
-    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (done) return;
-    }
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v)
-{
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                 "[%16];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15])
-                 : "r"(ta));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// 32 consecutive accumulator columns of the warp's 32 lanes (one register each)
-__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t* r)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(ta));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
+using tc::idesc_bf16;
+using tc::mbar_drain;
+using tc::mbar_wait;
+using tc::sdesc;
+using tc::su32;
+using tc::tmem_ld16;
+using tc::tmem_ld32;
 
 template <int CIN, int COUT>
 struct TcLayout {
@@ -378,12 +305,9 @@ cudaError_t conv_tc(const CUtensorMap& map, const __nv_bfloat16* W, const float*
     using L = TcLayout<CIN, COUT>;
     static_assert(L::REQUEST <= 227 * 1024, "shared memory");
     static_assert(L::TMEM_COLS >= 32 && (L::TMEM_COLS & (L::TMEM_COLS - 1)) == 0, "tensor memory columns");
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         L::REQUEST);
+    cudaError_t e = tc::smem_attr_once<conv_tc_kernel<CIN, COUT, OUT>>(L::REQUEST);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = tc::sm_count();
     const long long tiles = (long long)nb * (nx / TC_PX) * (ny / TC_ROWS);
     const int grid = (int)std::min<long long>(tiles, sms);
     if (grid < 1) return cudaSuccess;

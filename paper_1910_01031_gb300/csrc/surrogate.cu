@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "surrogate.h"
+#include "tc_dev.cuh"
 
 #include <cuda_bf16.h>
 
@@ -160,7 +161,8 @@ conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
 
 // Weight gradients of one tap: dW[tap][co][ci] = sum_p dZ[p][co] X[p + off(tap)][ci]
 // over the pixel tiles [t0, t1) of CTA (tap, group); partial sums per group.
-template <int CIN, int COUT>
+// PAD: dZ and X in the halo-padded layout [b][ny + 2][nx + 2][C].
+template <int CIN, int COUT, bool PAD>
 __global__ void __launch_bounds__(CONV_THREADS)
 wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ X, int nb, int ny, int nx,
              int tiles_per_group, float* __restrict__ partial)
@@ -188,14 +190,20 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
         for (int i = tid; i < TROWS * TCOLS * (COUT / 8); i += CONV_THREADS) {
             const int c8 = i % (COUT / 8), pix = i / (COUT / 8);
             const int gy = y0 + pix / TCOLS, gx = x0 + pix % TCOLS;
+            const long long src = PAD ? ((long long)b * (ny + 2) + gy + 1) * (nx + 2) + gx + 1
+                                      : ((long long)b * ny + gy) * nx + gx;
             *reinterpret_cast<uint4*>(Ds + pix * CPO + c8 * 8) =
-                *reinterpret_cast<const uint4*>(dz + (((long long)b * ny + gy) * nx + gx) * COUT + c8 * 8);
+                *reinterpret_cast<const uint4*>(dz + src * COUT + c8 * 8);
         }
         for (int i = tid; i < TROWS * TCOLS * (CIN / 8); i += CONV_THREADS) {
             const int c8 = i % (CIN / 8), pix = i / (CIN / 8);
-            const int gy = pmod(y0 + pix / TCOLS + ky - 1, ny), gx = pmod(x0 + pix % TCOLS + kx - 1, nx);
+            long long src;
+            if (PAD)
+                src = ((long long)b * (ny + 2) + y0 + pix / TCOLS + ky) * (nx + 2) + x0 + pix % TCOLS + kx;
+            else
+                src = ((long long)b * ny + pmod(y0 + pix / TCOLS + ky - 1, ny)) * nx + pmod(x0 + pix % TCOLS + kx - 1, nx);
             *reinterpret_cast<uint4*>(Xs + pix * CPI + c8 * 8) =
-                *reinterpret_cast<const uint4*>(X + (((long long)b * ny + gy) * nx + gx) * CIN + c8 * 8);
+                *reinterpret_cast<const uint4*>(X + src * CIN + c8 * 8);
         }
         __syncthreads();
         // K = 128 pixels in 8 steps of 16
@@ -249,26 +257,78 @@ __global__ void reduce_groups_kernel(const float* __restrict__ partial, int grou
     grad[i] = s;
 }
 
-// bias gradients: db[co] = sum_p dZ[p][co]; one CTA per channel, fixed order
-__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dz, long long npix, int C, float* __restrict__ db)
+// bias gradients db[co] = sum_p dZ[p][co] in two fixed-order levels: block k
+// sums the pixel rows [k R, (k + 1) R) of the batch (thread: 8 channels of
+// one pixel lane, 16-byte loads), then bias_reduce_kernel adds the blocks
+constexpr int BIAS_BLOCKS = 256;
+__global__ void __launch_bounds__(256) bias_partial_kernel(const __nv_bfloat16* __restrict__ dz, int nb, int ny, int nx,
+                                                           int C, int pad, float* __restrict__ partial)
 {
-    const int co = blockIdx.x;
-    float s = 0.0f;
-    for (long long p = threadIdx.x; p < npix; p += blockDim.x) s += __bfloat162float(dz[p * C + co]);
-    __shared__ float red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    const int groups = C / 8, lanes = 256 / groups;
+    const int cg = threadIdx.x % groups, pl = threadIdx.x / groups;
+    const long long rows = (long long)nb * ny;
+    const long long per = (rows + gridDim.x - 1) / gridDim.x;
+    const long long r0 = (long long)blockIdx.x * per, r1 = min(rows, r0 + per);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long row = r0; row < r1; ++row) {
+        const long long b = row / ny;
+        const int y = (int)(row % ny);
+        const long long base = pad ? (b * (ny + 2) + y + 1) * (nx + 2) + 1 : row * nx;
+        for (int x = pl; x < nx; x += lanes) {
+            const uint4 u = *reinterpret_cast<const uint4*>(dz + (base + x) * C + cg * 8);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s[2 * k] += __bfloat162float(h[k].x);
+                s[2 * k + 1] += __bfloat162float(h[k].y);
+            }
+        }
     }
-    if (threadIdx.x == 0) db[co] = red[0];
+    __shared__ float red[256 * 8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x * 8 + k] = s[k];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const int c = threadIdx.x, g = c / 8, k = c % 8;
+        float t = 0.0f;
+        for (int l = 0; l < lanes; ++l) t += red[(l * groups + g) * 8 + k];
+        partial[blockIdx.x * C + c] = t;
+    }
+}
+
+__global__ void bias_reduce_kernel(const float* __restrict__ partial, int blocks, int C, float* __restrict__ db)
+{
+    const int c = threadIdx.x;
+    if (c >= C) return;
+    float s = 0.0f;
+    for (int k = 0; k < blocks; ++k) s += partial[k * C + c];
+    db[c] = s;
+}
+
+// 16 BF16 channels of one pixel into the padded [b][ny + 2][nx + 2][16]
+// array at the pixel and at its periodic halo images
+__device__ __forceinline__ void store_padded16(__nv_bfloat16* __restrict__ out, const uint4* src, long long b, int y,
+                                               int x, int ny, int nx)
+{
+    const long long pw = nx + 2, plane = (long long)(ny + 2) * pw;
+    const int ys[2] = {y + 1, y == 0 ? ny + 1 : (y == ny - 1 ? 0 : -1)};
+    const int xs[2] = {x + 1, x == 0 ? nx + 1 : (x == nx - 1 ? 0 : -1)};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (ys[a] >= 0 && xs[c] >= 0) {
+                uint4* d = reinterpret_cast<uint4*>(out + (b * plane + (long long)ys[a] * pw + xs[c]) * 16);
+                d[0] = src[0];
+                d[1] = src[1];
+            }
 }
 
 // fp32 last-layer output (3 ch) vs target (3 ch): loss partials (per block)
 // and dZ_out = 2 (out - target) / count into the 16-channel bf16 buffer
 __global__ void loss_kernel(const float* __restrict__ out, const float* __restrict__ target, long long npix,
-                            double inv_count, __nv_bfloat16* __restrict__ dz, double* __restrict__ partial)
+                            int ny, int nx, int pad, double inv_count, __nv_bfloat16* __restrict__ dz,
+                            double* __restrict__ partial)
 {
     double s = 0.0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
@@ -281,9 +341,15 @@ __global__ void loss_kernel(const float* __restrict__ out, const float* __restri
             s += (double)r * r;
             g[c] = __float2bfloat16((float)(2.0 * inv_count) * r);
         }
-        uint4* d = reinterpret_cast<uint4*>(dz + p * 16);
-        d[0] = *reinterpret_cast<uint4*>(&g[0]);
-        d[1] = *reinterpret_cast<uint4*>(&g[8]);
+        if (pad) {
+            const long long b = p / ((long long)ny * nx);
+            const int r = (int)(p % ((long long)ny * nx));
+            store_padded16(dz, reinterpret_cast<const uint4*>(g), b, r / nx, r % nx, ny, nx);
+        } else {
+            uint4* d = reinterpret_cast<uint4*>(dz + p * 16);
+            d[0] = *reinterpret_cast<uint4*>(&g[0]);
+            d[1] = *reinterpret_cast<uint4*>(&g[8]);
+        }
     }
     __shared__ double red[256];
     red[threadIdx.x] = s;
@@ -295,12 +361,23 @@ __global__ void loss_kernel(const float* __restrict__ out, const float* __restri
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-__global__ void sum_kernel(const double* __restrict__ partial, int n, double scale, double* __restrict__ out)
+// the loss of the batch; added to *acc as well when acc is given
+// (one block of 256 threads; a fixed-order tree)
+__global__ void sum_kernel(const double* __restrict__ partial, int n, double scale, double* __restrict__ out,
+                           double* __restrict__ acc)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += partial[i];
-        *out = s * scale;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out = red[0] * scale;
+        if (acc) *acc += red[0] * scale;
     }
 }
 
@@ -320,6 +397,33 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// the same with the bias corrections c1, c2 of optimizer step *step from
+// the table bc[2 t], bc[2 t + 1] (a captured training step), then the step
+// counter and the batch cursor advance
+__global__ void adam_dev_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                                const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                                const float* __restrict__ bc, const int* __restrict__ step)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int t = *step;
+    const float c1 = bc[2 * t], c2 = bc[2 * t + 1];
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void advance_kernel(int* __restrict__ cursor, int* __restrict__ step, int batch)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *cursor += batch;
+        *step += 1;
+    }
+}
+
 __global__ void cast_weights_kernel(const float* __restrict__ w, int cin, int cout, __nv_bfloat16* __restrict__ wf,
                                     __nv_bfloat16* __restrict__ wd)
 {
@@ -331,14 +435,16 @@ __global__ void cast_weights_kernel(const float* __restrict__ w, int cin, int co
     wd[((8 - tap) * cin + ci) * cout + co] = b;
 }
 
-// state [n][3][ny][nx] fp32 -> network input [n][ny][nx][16] bf16 (normalised)
-__global__ void pack_input_kernel(const float* __restrict__ U, int n, int ny, int nx, float s0, float s1, float s2,
+// state [n][3][ny][nx] fp32 -> network input [n][ny][nx][16] bf16
+// (normalised); field b of the input is field idx[b] of U (b without idx)
+__global__ void pack_input_kernel(const float* __restrict__ U, const int* __restrict__ idx,
+                                  const int* __restrict__ cursor, int n, int ny, int nx, float s0, float s1, float s2,
                                   __nv_bfloat16* __restrict__ x)
 {
     const long long plane = (long long)ny * nx;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n * plane) return;
-    const long long b = p / plane, c = p % plane;
+    const long long b0 = p / plane, c = p % plane, b = idx ? idx[(cursor ? *cursor : 0) + b0] : b0;
     __align__(16) __nv_bfloat16 g[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) g[k] = __float2bfloat16(0.0f);
@@ -352,13 +458,14 @@ __global__ void pack_input_kernel(const float* __restrict__ U, int n, int ny, in
 
 // the same into the halo-padded layout [n][ny + 2][nx + 2][16]: padded
 // position (yp, xp) holds interior cell ((yp - 1) mod ny, (xp - 1) mod nx)
-__global__ void pack_input_padded_kernel(const float* __restrict__ U, int n, int ny, int nx, float s0, float s1,
+__global__ void pack_input_padded_kernel(const float* __restrict__ U, const int* __restrict__ idx,
+                                         const int* __restrict__ cursor, int n, int ny, int nx, float s0, float s1,
                                          float s2, __nv_bfloat16* __restrict__ x)
 {
     const long long pw = nx + 2, pplane = (long long)(ny + 2) * pw, plane = (long long)ny * nx;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n * pplane) return;
-    const long long b = p / pplane, r = p % pplane;
+    const long long b0 = p / pplane, r = p % pplane, b = idx ? idx[(cursor ? *cursor : 0) + b0] : b0;
     const int yp = (int)(r / pw), xq = (int)(r % pw);
     const long long c = (long long)pmod(yp - 1, ny) * nx + pmod(xq - 1, nx);
     __align__(16) __nv_bfloat16 g[16];
@@ -373,13 +480,14 @@ __global__ void pack_input_padded_kernel(const float* __restrict__ U, int n, int
 }
 
 // target of a pair: normalised change (Y - X) / scale, [n][ny][nx][3] fp32
-__global__ void pack_target_kernel(const float* __restrict__ X, const float* __restrict__ Y, int n, int ny, int nx,
+__global__ void pack_target_kernel(const float* __restrict__ X, const float* __restrict__ Y,
+                                   const int* __restrict__ idx, const int* __restrict__ cursor, int n, int ny, int nx,
                                    float d0, float d1, float d2, float* __restrict__ t)
 {
     const long long plane = (long long)ny * nx;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n * plane) return;
-    const long long b = p / plane, c = p % plane;
+    const long long b0 = p / plane, c = p % plane, b = idx ? idx[(cursor ? *cursor : 0) + b0] : b0;
     t[p * 3 + 0] = (Y[(b * 3 + 0) * plane + c] - X[(b * 3 + 0) * plane + c]) * d0;
     t[p * 3 + 1] = (Y[(b * 3 + 1) * plane + c] - X[(b * 3 + 1) * plane + c]) * d1;
     t[p * 3 + 2] = (Y[(b * 3 + 2) * plane + c] - X[(b * 3 + 2) * plane + c]) * d2;
@@ -453,37 +561,59 @@ size_t conv_smem()
     return (size_t)(9 * COUT * (CIN + 8) + (TROWS + 2) * (TCOLS + 2) * (CIN + 8)) * sizeof(__nv_bfloat16);
 }
 
+// the shared-memory limit of conv_kernel<CIN, COUT, MODE> and its resident
+// CTAs per SM (set and queried once per device)
+template <int CIN, int COUT, int MODE>
+cudaError_t conv_setup(int* per_sm)
+{
+    const size_t sm = conv_smem<CIN, COUT, MODE>();
+    cudaError_t e = tc::smem_attr_once<conv_kernel<CIN, COUT, MODE>>((int)sm);
+    if (e != cudaSuccess) return e;
+    static int per_dev[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per = dev < 64 ? per_dev[dev] : 0;
+    if (per == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conv_kernel<CIN, COUT, MODE>, CONV_THREADS, sm);
+        per = std::max(per, 1);
+        if (dev < 64) per_dev[dev] = per;
+    }
+    if (per_sm) *per_sm = per;
+    return cudaSuccess;
+}
+
 template <int CIN, int COUT, int MODE>
 cudaError_t conv(const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias, int nb, int ny, int nx,
                  __nv_bfloat16* z, __nv_bfloat16* a, float* f, const __nv_bfloat16* zprev, cudaStream_t st)
 {
     const size_t sm = conv_smem<CIN, COUT, MODE>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conv_kernel<CIN, COUT, MODE>, CONV_THREADS, sm);
+    int per = 1;
+    cudaError_t e = conv_setup<CIN, COUT, MODE>(&per);
+    if (e != cudaSuccess) return e;
+    const int sms = tc::sm_count();
     const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
     const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per, 1));
     conv_kernel<CIN, COUT, MODE><<<grid, CONV_THREADS, sm, st>>>(in, W, bias, nb, ny, nx, z, a, f, zprev);
     return cudaGetLastError();
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool PAD>
 cudaError_t wgrad(const __nv_bfloat16* dz, const __nv_bfloat16* X, int nb, int ny, int nx, int groups, float* partial,
                   float* grad, cudaStream_t st)
 {
     const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
     const int tpg = (int)((tiles + groups - 1) / groups);
-    wgrad_kernel<CIN, COUT><<<dim3(groups, 9), CONV_THREADS, 0, st>>>(dz, X, nb, ny, nx, tpg, partial);
+    wgrad_kernel<CIN, COUT, PAD><<<dim3(groups, 9), CONV_THREADS, 0, st>>>(dz, X, nb, ny, nx, tpg, partial);
     const long long n = 9LL * CIN * COUT;
     reduce_groups_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, groups, n, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t bias_grad(const __nv_bfloat16* dz, int nb, int ny, int nx, int C, int pad, float* partial, float* db,
+                      cudaStream_t st)
+{
+    bias_partial_kernel<<<BIAS_BLOCKS, 256, 0, st>>>(dz, nb, ny, nx, C, pad, partial);
+    bias_reduce_kernel<<<1, 64, 0, st>>>(partial, BIAS_BLOCKS, C, db);
     return cudaGetLastError();
 }
 
@@ -576,36 +706,108 @@ int Surrogate::init(int nx_, int ny_, int width_, int depth_)
     return cudaDeviceSynchronize() == cudaSuccess ? IEWPF_OK : IEWPF_ECUDA;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+// 64-channel halo-padded activations [nb][ny + 2][nx + 2][64] as a 4-D map
+// (64 ch, nx + 2, ny + 2, nb) with the 128-byte swizzle, box (64, bw, bh, 1)
+static bool map64(CUtensorMap* m, void* p, int nb, int ny, int nx, uint32_t bw, uint32_t bh)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t W2 = (cuuint64_t)nx + 2, H2 = (cuuint64_t)ny + 2;
+    const cuuint64_t dims[4] = {64, W2, H2, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {128, W2 * 128, H2 * W2 * 128};
+    const cuuint32_t box[4] = {64, bw, bh, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 16-channel halo-padded arrays [nb][ny + 2][nx + 2][16] as a 5-D map (8 ch,
+// nx + 2, ny + 2, channel group, nb) without swizzle, box (8, bw, bh, 2, 1)
+static bool map16(CUtensorMap* m, void* p, int nb, int ny, int nx, uint32_t bw, uint32_t bh)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t W2 = (cuuint64_t)nx + 2, H2 = (cuuint64_t)ny + 2;
+    const cuuint64_t dims[5] = {8, W2, H2, 2, (cuuint64_t)nb};
+    const cuuint64_t strides[4] = {32, W2 * 32, 16, H2 * W2 * 32};
+    const cuuint32_t box[5] = {8, bw, bh, 2, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool Surrogate::uses_tc_train() const
+{
+    return path == 0 && conv_tr_supported(nx, ny);
+}
+
 int Surrogate::ensure_batch(int nb)
 {
-    if (nb <= cap_batch) return IEWPF_OK;
+    const int pad = uses_tc_train() ? 1 : 0;
+    if (nb <= cap_batch && pad == batch_pad) return IEWPF_OK;
     // activations per layer: input (16 ch), then z and a per hidden layer
-    const size_t pix = (size_t)nb * nx * ny;
     for (void* p : {(void*)x_in, (void*)out, (void*)target, (void*)dz_a, (void*)dz_b, (void*)dz_out, (void*)wpartial,
-                    (void*)lpartial, (void*)dloss})
+                    (void*)bpartial, (void*)lpartial, (void*)dloss, (void*)eloss})
         sfree(*this, p);
     for (auto* p : z) sfree(*this, p);
     for (auto* p : a) sfree(*this, p);
     cap_batch = 0;
-    x_in = salloc<__nv_bfloat16>(*this, pix * 16);
+    const size_t pix = (size_t)nb * nx * ny;
+    const size_t ppix = pad ? (size_t)nb * (nx + 2) * (ny + 2) : pix;
+    x_in = salloc<__nv_bfloat16>(*this, ppix * 16);
     z.assign(depth, nullptr);
     a.assign(depth, nullptr);
     for (int l = 0; l + 1 < depth; ++l) {
         z[l] = salloc<__nv_bfloat16>(*this, pix * width);
-        a[l] = salloc<__nv_bfloat16>(*this, pix * width);
+        a[l] = salloc<__nv_bfloat16>(*this, ppix * width);
     }
     out = salloc<float>(*this, pix * 3);
     target = salloc<float>(*this, pix * 3);
-    dz_a = salloc<__nv_bfloat16>(*this, pix * width);
-    dz_b = salloc<__nv_bfloat16>(*this, pix * width);
-    dz_out = salloc<__nv_bfloat16>(*this, pix * 16);
-    const int groups = wgrad_groups(nb);
-    wpartial = salloc<float>(*this, (size_t)groups * 9 * width * width);
+    dz_a = salloc<__nv_bfloat16>(*this, ppix * width);
+    dz_b = salloc<__nv_bfloat16>(*this, ppix * width);
+    dz_out = salloc<__nv_bfloat16>(*this, ppix * 16);
+    int groups = wgrad_groups(nb);
+    if (pad) {
+        int g = 0, tpg = 0;
+        wgrad_tc_split(nb, ny, nx, &g, &tpg);
+        groups = std::max(groups, g);
+    }
+    wpartial = salloc<float>(*this, (size_t)groups * std::max(9 * width * width, wgrad_tc_partial(width)));
+    bpartial = salloc<float>(*this, (size_t)BIAS_BLOCKS * width);
     lpartial = salloc<double>(*this, 1024);
     dloss = salloc<double>(*this, 1);
-    if (!x_in || !out || !target || !dz_a || !dz_b || !dz_out || !wpartial || !lpartial || !dloss) return IEWPF_ENOMEM;
+    eloss = salloc<double>(*this, 1);
+    if (!x_in || !out || !target || !dz_a || !dz_b || !dz_out || !wpartial || !bpartial || !lpartial || !dloss ||
+        !eloss)
+        return IEWPF_ENOMEM;
     for (int l = 0; l + 1 < depth; ++l)
         if (!z[l] || !a[l]) return IEWPF_ENOMEM;
+    if (pad) {
+        // tensor maps of the padded buffers (boxes: conv_tr.cu's stages and tiles)
+        tm_fwd.assign(depth, CUtensorMap{});
+        tm_wx.assign(depth, CUtensorMap{});
+        bool ok = map16(&tm_in, x_in, nb, ny, nx, 64, 6) && map16(&tm_dout_f, dz_out, nb, ny, nx, 64, 6) &&
+                  map16(&tm_dout_w, dz_out, nb, ny, nx, 64, 4);
+        for (int l = 0; l + 1 < depth && ok; ++l)
+            ok = map64(&tm_fwd[l], a[l], nb, ny, nx, 64, 6) && map64(&tm_wx[l], a[l], nb, ny, nx, 66, 6);
+        __nv_bfloat16* dzs[2] = {dz_a, dz_b};
+        for (int k = 0; k < 2 && ok; ++k)
+            ok = map64(&tm_dz_f[k], dzs[k], nb, ny, nx, 64, 6) && map64(&tm_dz_w[k], dzs[k], nb, ny, nx, 64, 4);
+        if (!ok) return IEWPF_ECUDA;
+    }
+    // launch attributes set now, outside any capture of a training step
+    cudaError_t e = pad ? conv_tr_prepare() : cudaSuccess;
+    if (e == cudaSuccess) e = conv_setup<16, 64, MODE_HIDDEN>(nullptr);
+    if (e == cudaSuccess) e = conv_setup<64, 64, MODE_HIDDEN>(nullptr);
+    if (e == cudaSuccess) e = conv_setup<64, 16, MODE_OUT>(nullptr);
+    if (e == cudaSuccess) e = conv_setup<16, 64, MODE_DGRAD>(nullptr);
+    if (e == cudaSuccess) e = conv_setup<64, 64, MODE_DGRAD>(nullptr);
+    if (e != cudaSuccess) return IEWPF_ECUDA;
+    batch_pad = pad;
     cap_batch = nb;
     return IEWPF_OK;
 }
@@ -703,7 +905,7 @@ int Surrogate::infer(const float* U, int nb, cudaStream_t st)
         return IEWPF_OK;
     }
     const long long n = (long long)nb * (nx + 2) * (ny + 2);
-    pack_input_padded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, nb, ny, nx, in_scale[0], in_scale[1],
+    pack_input_padded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, nullptr, nullptr, nb, ny, nx, in_scale[0], in_scale[1],
                                                                          in_scale[2], xp);
     const int probe = inject_timeouts > 0 ? kInjectedWaitPolls : 0;
     if (inject_timeouts > 0) --inject_timeouts;
@@ -721,6 +923,16 @@ int Surrogate::infer(const float* U, int nb, cudaStream_t st)
 cudaError_t Surrogate::forward(int nb, cudaStream_t st)
 {
     cudaError_t e;
+    if (batch_pad) {
+        for (int l = 0; l < depth; ++l) {
+            const int kind = l == 0 ? 0 : (l + 1 < depth ? 1 : 2);
+            e = launch_conv_tr(kind, l == 0 ? tm_in : tm_fwd[l - 1], wf[l], master + b_off[l], nb, ny, nx,
+                               kind < 2 ? z[l] : nullptr, kind < 2 ? a[l] : nullptr, kind == 2 ? out : nullptr,
+                               nullptr, dflag, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const __nv_bfloat16* in = x_in;
     for (int l = 0; l < depth; ++l) {
         const float* bias = master + b_off[l];
@@ -734,17 +946,54 @@ cudaError_t Surrogate::forward(int nb, cudaStream_t st)
 }
 
 // loss of the current forward pass against `target`, gradients into grad
-cudaError_t Surrogate::backward(int nb, cudaStream_t st)
+cudaError_t Surrogate::backward(int nb, cudaStream_t st, bool add_eloss)
 {
     const long long pix = (long long)nb * nx * ny;
-    loss_kernel<<<1024, 256, 0, st>>>(out, target, pix, 1.0 / (3.0 * pix), dz_out, lpartial);
-    sum_kernel<<<1, 32, 0, st>>>(lpartial, 1024, 1.0 / (3.0 * pix), dloss);
+    loss_kernel<<<1024, 256, 0, st>>>(out, target, pix, ny, nx, batch_pad, 1.0 / (3.0 * pix), dz_out, lpartial);
+    sum_kernel<<<1, 256, 0, st>>>(lpartial, 1024, 1.0 / (3.0 * pix), dloss, add_eloss ? eloss : nullptr);
     const int groups = wgrad_groups(nb);
     cudaError_t e;
-    // last layer (64 -> 16)
     const int L = depth - 1;
-    if ((e = wgrad<64, 16>(dz_out, a[L - 1], nb, ny, nx, groups, wpartial, grad + w_off[L], st)) != cudaSuccess) return e;
-    bias_grad_kernel<<<16, 256, 0, st>>>(dz_out, pix, 16, grad + b_off[L]);
+    if (batch_pad) {
+        // tcgen05: weight gradients of layers 1..L, data passes; layer 0's
+        // weight gradient (16 input channels) on mma.sync
+        int tg = 0, tpg = 0;
+        wgrad_tc_split(nb, ny, nx, &tg, &tpg);
+        // weights and bias of a layer (contiguous in the parameters)
+        auto wg = [&](int cout, const CUtensorMap& xm, const CUtensorMap& dm, float* g) {
+            cudaError_t r = launch_wgrad_tc(cout, xm, dm, nb, ny, nx, tg, tpg, wpartial, dflag, st);
+            if (r != cudaSuccess) return r;
+            const long long n = wgrad_tc_partial(cout);
+            reduce_groups_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(wpartial, tg, n, g);
+            return cudaGetLastError();
+        };
+        if ((e = wg(16, tm_wx[L - 1], tm_dout_w, grad + w_off[L])) != cudaSuccess) return e;
+        if ((e = launch_conv_tr(3, tm_dout_f, wd[L], nullptr, nb, ny, nx, nullptr, dz_a, nullptr, z[L - 1], dflag,
+                                st)) != cudaSuccess)
+            return e;
+        int cur = 0;
+        __nv_bfloat16* dzs[2] = {dz_a, dz_b};
+        for (int l = L - 1; l >= 0; --l) {
+            if (l > 0) {
+                e = wg(64, tm_wx[l - 1], tm_dz_w[cur], grad + w_off[l]);
+            } else {
+                e = wgrad<16, 64, true>(dzs[cur], x_in, nb, ny, nx, groups, wpartial, grad + w_off[0], st);
+                if (e == cudaSuccess) e = bias_grad(dzs[cur], nb, ny, nx, 64, 1, bpartial, grad + b_off[0], st);
+            }
+            if (e != cudaSuccess) return e;
+            if (l > 0) {
+                if ((e = launch_conv_tr(4, tm_dz_f[cur], wd[l], nullptr, nb, ny, nx, nullptr, dzs[cur ^ 1], nullptr,
+                                        z[l - 1], dflag, st)) != cudaSuccess)
+                    return e;
+                cur ^= 1;
+            }
+        }
+        return cudaGetLastError();
+    }
+    // last layer (64 -> 16)
+    if ((e = wgrad<64, 16, false>(dz_out, a[L - 1], nb, ny, nx, groups, wpartial, grad + w_off[L], st)) != cudaSuccess)
+        return e;
+    if ((e = bias_grad(dz_out, nb, ny, nx, 16, 0, bpartial, grad + b_off[L], st)) != cudaSuccess) return e;
     // dZ of layer L-1 = conv(dZ_out, Wd_L) * silu'(z[L-1])
     if ((e = conv<16, 64, MODE_DGRAD>(dz_out, wd[L], nullptr, nb, ny, nx, nullptr, dz_a, nullptr, z[L - 1], st)) !=
         cudaSuccess)
@@ -753,10 +1002,10 @@ cudaError_t Surrogate::backward(int nb, cudaStream_t st)
     __nv_bfloat16* nxt = dz_b;
     for (int l = L - 1; l >= 0; --l) {
         const __nv_bfloat16* X = l == 0 ? x_in : a[l - 1];
-        if (l == 0) e = wgrad<16, 64>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
-        else e = wgrad<64, 64>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
+        if (l == 0) e = wgrad<16, 64, false>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
+        else e = wgrad<64, 64, false>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
         if (e != cudaSuccess) return e;
-        bias_grad_kernel<<<64, 256, 0, st>>>(cur, pix, 64, grad + b_off[l]);
+        if ((e = bias_grad(cur, nb, ny, nx, 64, 0, bpartial, grad + b_off[l], st)) != cudaSuccess) return e;
         if (l > 0) {
             if ((e = conv<64, 64, MODE_DGRAD>(cur, wd[l], nullptr, nb, ny, nx, nullptr, nxt, nullptr, z[l - 1], st)) !=
                 cudaSuccess)
@@ -767,28 +1016,51 @@ cudaError_t Surrogate::backward(int nb, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t Surrogate::adam_step(float lr, cudaStream_t st)
+cudaError_t Surrogate::train_step(const float* X, const float* Y, const int* order, int* ctr, const float* bc,
+                                  int batch, float lr, cudaStream_t st)
 {
-    ++t_adam;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - std::pow(b1, (float)t_adam), c2 = 1.0f - std::pow(b2, (float)t_adam);
-    adam_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, adam_m, adam_v, grad, (long long)n_params,
-                                                                   lr, b1, b2, 1e-8f, c1, c2);
-    return cast(st);
-}
-
-cudaError_t Surrogate::pack_input(const float* U, int nb, cudaStream_t st)
-{
-    const long long n = (long long)nb * nx * ny;
-    pack_input_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, nb, ny, nx, in_scale[0], in_scale[1], in_scale[2],
-                                                                  x_in);
+    cudaError_t e;
+    if ((e = pack_input(X, batch, st, order, ctr)) != cudaSuccess ||
+        (e = pack_target(X, Y, batch, st, order, ctr)) != cudaSuccess || (e = forward(batch, st)) != cudaSuccess ||
+        (e = backward(batch, st, true)) != cudaSuccess)
+        return e;
+    adam_dev_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, adam_m, adam_v, grad,
+                                                                       (long long)n_params, lr, kAdamB1, kAdamB2,
+                                                                       kAdamEps, bc, ctr + 1);
+    if ((e = cast(st)) != cudaSuccess) return e;
+    advance_kernel<<<1, 32, 0, st>>>(ctr, ctr + 1, batch);
     return cudaGetLastError();
 }
 
-cudaError_t Surrogate::pack_target(const float* X, const float* Y, int nb, cudaStream_t st)
+cudaError_t Surrogate::adam_step(float lr, cudaStream_t st)
+{
+    ++t_adam;
+    const float b1 = kAdamB1, b2 = kAdamB2;
+    const float c1 = 1.0f - std::pow(b1, (float)t_adam), c2 = 1.0f - std::pow(b2, (float)t_adam);
+    adam_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, adam_m, adam_v, grad, (long long)n_params,
+                                                                   lr, b1, b2, kAdamEps, c1, c2);
+    return cast(st);
+}
+
+cudaError_t Surrogate::pack_input(const float* U, int nb, cudaStream_t st, const int* idx, const int* cursor)
+{
+    if (batch_pad) {
+        const long long n = (long long)nb * (nx + 2) * (ny + 2);
+        pack_input_padded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, idx, cursor, nb, ny, nx, in_scale[0],
+                                                                             in_scale[1], in_scale[2], x_in);
+        return cudaGetLastError();
+    }
+    const long long n = (long long)nb * nx * ny;
+    pack_input_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, idx, cursor, nb, ny, nx, in_scale[0],
+                                                                  in_scale[1], in_scale[2], x_in);
+    return cudaGetLastError();
+}
+
+cudaError_t Surrogate::pack_target(const float* X, const float* Y, int nb, cudaStream_t st, const int* idx,
+                                   const int* cursor)
 {
     const long long n = (long long)nb * nx * ny;
-    pack_target_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, Y, nb, ny, nx, 1.0f / out_scale[0],
+    pack_target_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, Y, idx, cursor, nb, ny, nx, 1.0f / out_scale[0],
                                                                    1.0f / out_scale[1], 1.0f / out_scale[2], target);
     return cudaGetLastError();
 }

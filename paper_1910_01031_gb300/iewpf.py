@@ -33,7 +33,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_batch_work", "iewpf_batch_last_error", "iewpf_surrogate_create", "iewpf_surrogate_destroy",
            "iewpf_surrogate_param_count", "iewpf_surrogate_set_params", "iewpf_surrogate_get_params",
            "iewpf_surrogate_set_scales", "iewpf_surrogate_set_path", "iewpf_surrogate_get_path", "iewpf_surrogate_inject_timeout", "iewpf_surrogate_get_scales", "iewpf_surrogate_apply", "iewpf_surrogate_apply_device", "iewpf_surrogate_stream", "iewpf_surrogate_loss_grad",
-           "iewpf_surrogate_train", "iewpf_set_surrogate", "iewpf_surrogate_stats", "iewpf_surrogate_last_error"]
+           "iewpf_surrogate_train", "iewpf_surrogate_train_time", "iewpf_set_surrogate", "iewpf_surrogate_stats", "iewpf_surrogate_last_error"]
 WEIGHTS_NOALLOC_MAX_NE = 4096
 
 
@@ -157,6 +157,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_surrogate_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
     L.iewpf_surrogate_loss_grad.argtypes = [_vp, _fp, _fp, c.c_int, _dp, _fp]
     L.iewpf_surrogate_train.argtypes = [_vp, _vp, c.c_int, c.c_int, c.c_int, c.c_int, c.c_double, _dp]
+    L.iewpf_surrogate_train_time.argtypes = [_vp, _dp]
     L.iewpf_set_surrogate.argtypes = [_vp, _vp, c.c_int]
     L.iewpf_surrogate_stats.argtypes = [_vp, c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
     L.iewpf_surrogate_last_error.argtypes = [_vp]
@@ -573,9 +574,16 @@ class Surrogate:
         self._chk(self.L.iewpf_surrogate_inject_timeout(self.h, int(n_evals)), "inject_timeout")
 
     def uses_tcgen05(self):
+        """Whether inference (apply, the drift forecast) runs on tcgen05."""
         v = ctypes.c_int()
         self._chk(self.L.iewpf_surrogate_get_path(self.h, ctypes.byref(v)), "get_path")
-        return bool(v.value)
+        return bool(v.value & 1)
+
+    def uses_tcgen05_training(self):
+        """Whether training (loss_grad, train) runs on tcgen05."""
+        v = ctypes.c_int()
+        self._chk(self.L.iewpf_surrogate_get_path(self.h, ctypes.byref(v)), "get_path")
+        return bool(v.value & 2)
 
     def scales(self):
         a, b = np.zeros(3), np.zeros(3)
@@ -616,6 +624,12 @@ class Surrogate:
         self._chk(self.L.iewpf_surrogate_train(self.h, ens.h, int(n_pairs), int(k_steps), int(epochs), int(batch),
                                                float(lr), _ptr(losses)), "train")
         return losses
+
+    def train_time(self):
+        """Device seconds of the epochs of the last train call."""
+        v = ctypes.c_double()
+        self._chk(self.L.iewpf_surrogate_train_time(self.h, ctypes.byref(v)), "train_time")
+        return v.value
 
 
 def _torch_stream():

@@ -307,3 +307,62 @@ def test_full_size_network_call_sampled_against_oracle():
         ref = S.apply(p, x, SI, SO, W, D)
         got = out[i:i + 1].double().cpu().numpy()
         assert _rel(got - x, ref - x) < FWD_TOL, i
+
+
+def _oracle_grads(sur, p, X, Y):
+    """loss_grad through the C ABI against the FP64 oracle, per layer."""
+    L, g = sur.loss_grad(X, Y)
+    Lr, gr = S.loss_grad(p, X.astype(np.float64), Y.astype(np.float64), SI, SO, W, D)
+    assert abs(L - Lr) < 1e-2 * Lr
+    lg, lr = S.unpack(g, W, D), S.unpack(gr, W, D)
+    for l in range(D):
+        assert _rel(lg[l][0], lr[l][0]) < GRAD_TOL, ("weights", l)
+        assert _rel(lg[l][1], lr[l][1]) < GRAD_TOL, ("bias", l)
+    pad = S.pack([(np.ones_like(Wl), np.ones_like(bl)) for Wl, bl in lr], W, D) == 0
+    assert np.all(g[pad] == 0.0)
+    return L, g
+
+
+@pytest.mark.parametrize("nx,ny,n", [(64, 64, 3), (128, 8, 2), (192, 16, 1)])
+def test_tcgen05_training_matches_oracle(nx, ny, n):
+    # training on tcgen05: tiles of 4 rows x 64 pixels (one, two or three
+    # across), three column-shift stages per tile, weight gradients with tap
+    # pairs on M/N-major operands; the forward output as well
+    sur, p = _net(nx=nx, ny=ny, seed=31)
+    assert sur.uses_tcgen05_training()
+    assert sur.uses_tcgen05() == (nx % 128 == 0)
+    X = _fields(n, ny, nx, 32)
+    Y = X + (_fields(n, ny, nx, 33) * np.array([0.05, 0.1, 0.1], np.float32)[None, :, None, None]).astype(np.float32)
+    _oracle_grads(sur, p, X, Y)
+    out = sur.apply(X)
+    ref = S.apply(p, X.astype(np.float64), SI, SO, W, D)
+    assert _rel(out.astype(np.float64) - X, ref - X) < FWD_TOL
+
+
+def test_tcgen05_training_many_tiles_per_cta_match_mma_sync():
+    # 24 fields of 64 x 64: 384 tiles, two or three per CTA of the data passes
+    # (every shared-memory stage and both accumulator sets reused) and of the
+    # weight gradients; the same gradients on the mma.sync path
+    sur, p = _net(nx=64, ny=64, seed=34)
+    X = _fields(24, 64, 64, 35)
+    Y = X + (_fields(24, 64, 64, 36) * np.array([0.05, 0.1, 0.1], np.float32)[None, :, None, None]).astype(np.float32)
+    L_tc, g_tc = sur.loss_grad(X, Y)
+    sur.set_path(1)
+    assert not sur.uses_tcgen05_training()
+    L_mma, g_mma = sur.loss_grad(X, Y)
+    assert abs(L_tc - L_mma) < 1e-3 * L_mma
+    lt, lm = S.unpack(g_tc, W, D), S.unpack(g_mma, W, D)
+    for l in range(D):
+        assert np.linalg.norm(lm[l][0]) > 0
+        assert _rel(lt[l][0], lm[l][0]) < 2e-2, ("weights", l)
+        assert _rel(lt[l][1], lm[l][1]) < 2e-2, ("bias", l)
+
+
+def test_tcgen05_training_forward_is_bitwise_translation_equivariant():
+    # a shift by whole tiles (4 rows, 64 columns) moves every tile's work unchanged
+    sur, _ = _net(nx=64, ny=64, seed=37)
+    assert not sur.uses_tcgen05() and sur.uses_tcgen05_training()
+    V = _fields(2, 64, 64, 39)
+    a = sur.apply(V)
+    b = sur.apply(np.ascontiguousarray(np.roll(V, 8, axis=2)))
+    assert np.array_equal(np.roll(a, 8, axis=2), b)
