@@ -90,21 +90,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
     const uint32_t sbase = su32(smem);
 
     // weights of every tap, once per CTA (B operand, K-major, rows = output channels)
-    if (L::SW) {
-        // 128-byte rows of 64 input channels; 16-byte chunk c of row co at chunk c ^ (co & 7)
-        for (int i = tid; i < 9 * COUT * 8; i += TC_THREADS) {
-            const int c = i & 7, co = (i >> 3) % COUT, tap = i / (8 * COUT);
-            *reinterpret_cast<uint4*>(smem + L::W_OFF + (tap * COUT + co) * 128 + ((c ^ (co & 7)) << 4)) =
-                *reinterpret_cast<const uint4*>(W + ((size_t)tap * COUT + co) * CIN + c * 8);
-        }
-    } else {
-        // core matrices of 8 output channels x 16 bytes: [tap][chunk][co][8 ch]
-        for (int i = tid; i < 9 * COUT * (CIN / 8); i += TC_THREADS) {
-            const int j = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
-            *reinterpret_cast<uint4*>(smem + L::W_OFF + ((tap * (CIN / 8) + j) * COUT + co) * 16) =
-                *reinterpret_cast<const uint4*>(W + ((size_t)tap * COUT + co) * CIN + j * 8);
-        }
-    }
+    tc::stage_weights<CIN, COUT, TC_THREADS>(smem + L::W_OFF, W, tid);
     for (int i = tid; i < COUT; i += TC_THREADS) sbias[i] = bias[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),

@@ -84,26 +84,7 @@ struct TrLayout {
     static constexpr int TMEM_COLS = 2 * TR_NACC * COUT;
 };
 
-// stage the weights of every tap once per CTA (B operand, K-major, rows =
-// output channels): 128-byte swizzled rows of 64 input channels, or core
-// matrices of 8 output channels x 16 bytes ([tap][chunk][co][8 ch])
-template <int CIN, int COUT, int NTHREADS>
-__device__ __forceinline__ void stage_weights(unsigned char* wsm, const __nv_bfloat16* __restrict__ W, int tid)
-{
-    if (CIN == 64) {
-        for (int i = tid; i < 9 * COUT * 8; i += NTHREADS) {
-            const int c = i & 7, co = (i >> 3) % COUT, tap = i / (8 * COUT);
-            *reinterpret_cast<uint4*>(wsm + (tap * COUT + co) * 128 + ((c ^ (co & 7)) << 4)) =
-                *reinterpret_cast<const uint4*>(W + ((size_t)tap * COUT + co) * CIN + c * 8);
-        }
-    } else {
-        for (int i = tid; i < 9 * COUT * (CIN / 8); i += NTHREADS) {
-            const int j = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
-            *reinterpret_cast<uint4*>(wsm + ((tap * (CIN / 8) + j) * COUT + co) * 16) =
-                *reinterpret_cast<const uint4*>(W + ((size_t)tap * COUT + co) * CIN + j * 8);
-        }
-    }
-}
+using tc::stage_weights;
 
 // 32 BF16 channels of one pixel into the padded [b][ny + 2][nx + 2][C]
 // array at the pixel and at its periodic halo images

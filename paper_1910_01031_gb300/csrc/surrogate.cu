@@ -381,39 +381,65 @@ __global__ void sum_kernel(const double* __restrict__ partial, int n, double sca
     }
 }
 
-// Adam on fp32 master parameters; then the bf16 copies of the weights in the
-// forward layout [tap][co][ci] and the backward-data layout [8 - tap][ci][co]
-__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                            float c1, float c2)
+// Adam on the FP32 master parameters and, in the same pass, the BF16 copies
+// of each updated weight in the forward layout [tap][co][ci] and the
+// backward-data layout [8 - tap][ci][co].  The bias corrections c1, c2 are
+// arguments, or (bc != nullptr) bc[2 t], bc[2 t + 1] of optimizer step t =
+// *step (a captured training step).
+struct AdamArgs {
+    float *w, *m, *v;
+    const float* g;
+    long long n;
+    float lr, b1, b2, eps, c1, c2;
+    const float* bc;
+    const int* step;
+};
+struct CastPlan {
+    int depth;
+    long long w_off[16], b_off[16];
+    int cin[16], cout[16];
+    __nv_bfloat16* wf[16];
+    __nv_bfloat16* wd[16];
+};
+
+__device__ __forceinline__ void cast_one(const CastPlan& P, long long i, float wi)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    for (int l = 0; l < P.depth; ++l)
+        if (i >= P.w_off[l] && i < P.b_off[l]) {
+            const int j = (int)(i - P.w_off[l]), cin = P.cin[l], cout = P.cout[l];
+            const int ci = j % cin, co = (j / cin) % cout, tap = j / (cin * cout);
+            const __nv_bfloat16 b = __float2bfloat16(wi);
+            P.wf[l][j] = b;
+            P.wd[l][((8 - tap) * cin + ci) * cout + co] = b;
+            return;
+        }
 }
 
-// the same with the bias corrections c1, c2 of optimizer step *step from
-// the table bc[2 t], bc[2 t + 1] (a captured training step), then the step
-// counter and the batch cursor advance
-__global__ void adam_dev_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                                const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                                const float* __restrict__ bc, const int* __restrict__ step)
+__global__ void adam_cast_kernel(AdamArgs A, CastPlan P)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int t = *step;
-    const float c1 = bc[2 * t], c2 = bc[2 * t + 1];
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    if (i >= A.n) return;
+    float c1 = A.c1, c2 = A.c2;
+    if (A.bc) {
+        const int t = *A.step;
+        c1 = A.bc[2 * t];
+        c2 = A.bc[2 * t + 1];
+    }
+    const float gi = A.g[i];
+    const float mi = A.b1 * A.m[i] + (1.0f - A.b1) * gi;
+    const float vi = A.b2 * A.v[i] + (1.0f - A.b2) * gi * gi;
+    A.m[i] = mi;
+    A.v[i] = vi;
+    const float wi = A.w[i] - A.lr * (mi / c1) / (sqrtf(vi / c2) + A.eps);
+    A.w[i] = wi;
+    cast_one(P, i, wi);
+}
+
+// the BF16 copies of every weight (after new parameters)
+__global__ void cast_all_kernel(const float* __restrict__ w, long long n, CastPlan P)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cast_one(P, i, w[i]);
 }
 
 __global__ void advance_kernel(int* __restrict__ cursor, int* __restrict__ step, int batch)
@@ -422,17 +448,6 @@ __global__ void advance_kernel(int* __restrict__ cursor, int* __restrict__ step,
         *cursor += batch;
         *step += 1;
     }
-}
-
-__global__ void cast_weights_kernel(const float* __restrict__ w, int cin, int cout, __nv_bfloat16* __restrict__ wf,
-                                    __nv_bfloat16* __restrict__ wd)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * cin * cout) return;
-    const int ci = i % cin, co = (i / cin) % cout, tap = i / (cin * cout);
-    const __nv_bfloat16 b = __float2bfloat16(w[i]);
-    wf[i] = b;
-    wd[((8 - tap) * cin + ci) * cout + co] = b;
 }
 
 // state [n][3][ny][nx] fp32 -> network input [n][ny][nx][16] bf16
@@ -818,12 +833,24 @@ int Surrogate::wgrad_groups(int nb) const
     return (int)std::max<long long>(1, std::min<long long>(256, tiles / 16));
 }
 
+static CastPlan cast_plan(const Surrogate& s)
+{
+    CastPlan P{};
+    P.depth = s.depth;
+    for (int l = 0; l < s.depth; ++l) {
+        P.w_off[l] = (long long)s.w_off[l];
+        P.b_off[l] = (long long)s.b_off[l];
+        P.cin[l] = s.layer_cin(l);
+        P.cout[l] = s.layer_cout(l);
+        P.wf[l] = s.wf[l];
+        P.wd[l] = s.wd[l];
+    }
+    return P;
+}
+
 cudaError_t Surrogate::cast(cudaStream_t st)
 {
-    for (int l = 0; l < depth; ++l) {
-        const int n = (int)layer_w(l);
-        cast_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(master + w_off[l], layer_cin(l), layer_cout(l), wf[l], wd[l]);
-    }
+    cast_all_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, (long long)n_params, cast_plan(*this));
     return cudaGetLastError();
 }
 
@@ -1024,10 +1051,9 @@ cudaError_t Surrogate::train_step(const float* X, const float* Y, const int* ord
         (e = pack_target(X, Y, batch, st, order, ctr)) != cudaSuccess || (e = forward(batch, st)) != cudaSuccess ||
         (e = backward(batch, st, true)) != cudaSuccess)
         return e;
-    adam_dev_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, adam_m, adam_v, grad,
-                                                                       (long long)n_params, lr, kAdamB1, kAdamB2,
-                                                                       kAdamEps, bc, ctr + 1);
-    if ((e = cast(st)) != cudaSuccess) return e;
+    const AdamArgs A{master, adam_m, adam_v, grad, (long long)n_params, lr, kAdamB1, kAdamB2, kAdamEps, 1.0f, 1.0f,
+                     bc, ctr + 1};
+    adam_cast_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(A, cast_plan(*this));
     advance_kernel<<<1, 32, 0, st>>>(ctr, ctr + 1, batch);
     return cudaGetLastError();
 }
@@ -1035,11 +1061,11 @@ cudaError_t Surrogate::train_step(const float* X, const float* Y, const int* ord
 cudaError_t Surrogate::adam_step(float lr, cudaStream_t st)
 {
     ++t_adam;
-    const float b1 = kAdamB1, b2 = kAdamB2;
-    const float c1 = 1.0f - std::pow(b1, (float)t_adam), c2 = 1.0f - std::pow(b2, (float)t_adam);
-    adam_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(master, adam_m, adam_v, grad, (long long)n_params,
-                                                                   lr, b1, b2, kAdamEps, c1, c2);
-    return cast(st);
+    const float c1 = 1.0f - std::pow(kAdamB1, (float)t_adam), c2 = 1.0f - std::pow(kAdamB2, (float)t_adam);
+    const AdamArgs A{master, adam_m, adam_v, grad, (long long)n_params, lr, kAdamB1, kAdamB2, kAdamEps, c1, c2,
+                     nullptr, nullptr};
+    adam_cast_kernel<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(A, cast_plan(*this));
+    return cudaGetLastError();
 }
 
 cudaError_t Surrogate::pack_input(const float* U, int nb, cudaStream_t st, const int* idx, const int* cursor)

@@ -135,6 +135,35 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t adesc, uint64_t
                      "r"(idesc));
 }
 
+// stage the weights of every tap once per CTA (B operand, K-major, rows =
+// output channels): 128-byte swizzled rows of 64 input channels, or core
+// matrices of 8 output channels x 16 bytes ([tap][chunk][co][8 ch]).  Every
+// thread issues all its loads before its first store, so the copy costs one
+// round trip to L2 rather than one per chunk.
+template <int CIN, int COUT, int NTHREADS>
+__device__ __forceinline__ void stage_weights(unsigned char* wsm, const void* __restrict__ W, int tid)
+{
+    constexpr int N = 9 * COUT * (CIN / 8);                 // 16-byte chunks
+    constexpr int PER = (N + NTHREADS - 1) / NTHREADS;
+    uint4 r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NTHREADS;
+        if (i < N) r[k] = __ldg(reinterpret_cast<const uint4*>(W) + i);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NTHREADS;
+        if (i < N) {
+            // chunk i of W: row (tap, co), channels 8 c .. 8 c + 7
+            const int c = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
+            const int off = CIN == 64 ? (tap * COUT + co) * 128 + ((c ^ (co & 7)) << 4)
+                                      : ((tap * (CIN / 8) + c) * COUT + co) * 16;
+            *reinterpret_cast<uint4*>(wsm + off) = r[k];
+        }
+    }
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
