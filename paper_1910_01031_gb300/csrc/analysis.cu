@@ -1,5 +1,8 @@
 // IEWPF analysis kernels for one problem per launch (Sec. 4 and App. A of
 // arXiv 1910.01031); the device code is in analysis_dev.cuh.
+#include <algorithm>
+#include <vector>
+
 #include "analysis_dev.cuh"
 
 namespace iewpf {
@@ -105,6 +108,63 @@ __global__ void block_seq_kernel(float* __restrict__ r, int NR, const float* __r
                                  const int* __restrict__ block0, int nobs, int nRx, int nRy)
 {
     ana::block_seq_cta(r, NR, M49, block0, nobs, nRx, nRy, blockIdx.x);
+}
+
+// one level of blocks: warp w of the grid takes tasks (block, chunk of
+// BL_CHUNK particles) w, w + warps, ...: the block's 49 indices once per task,
+// then per particle lane t computes outputs t and t + 32 (< 49) with the FMA
+// order of block_seq_cta, its two rows of the 49 x 49 root held in registers
+// for all the warp's tasks, and the next particle's values loaded before the
+// current product
+constexpr int BL_CHUNK = 32;
+__global__ void __launch_bounds__(256, 2) block_level_kernel(float* __restrict__ r, int NR, int ne,
+                                                             const float* __restrict__ M49,
+                                                             const int* __restrict__ block0,
+                                                             const int* __restrict__ order, int lo, int nblk, int nRx,
+                                                             int nRy)
+{
+    __shared__ float v[8][49];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const bool two = lane + 32 < 49;
+    float m0[49], m1[49];
+#pragma unroll
+    for (int j = 0; j < 49; ++j) {
+        m0[j] = __ldg(M49 + lane * 49 + j);
+        m1[j] = two ? __ldg(M49 + (lane + 32) * 49 + j) : 0.0f;
+    }
+    const int chunks = (ne + BL_CHUNK - 1) / BL_CHUNK;
+    const long long tasks = (long long)nblk * chunks;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long task = (long long)blockIdx.x * (blockDim.x >> 5) + wl; task < tasks; task += warps) {
+        const int ib = (int)(task / chunks), c = (int)(task - (long long)ib * chunks);
+        const int l = order[lo + ib];
+        const int cx = block0[2 * l], cy = block0[2 * l + 1];
+        const int i0 = pmod(cy + lane / 7 - 3, nRy) * nRx + pmod(cx + lane % 7 - 3, nRx);
+        const int t1 = two ? lane + 32 : 48;
+        const int i1 = pmod(cy + t1 / 7 - 3, nRy) * nRx + pmod(cx + t1 % 7 - 3, nRx);
+        const int p0 = c * BL_CHUNK, p1 = min(ne, p0 + BL_CHUNK);
+        float* rp = r + (long long)p0 * NR;
+        float x0 = rp[i0], x1 = two ? rp[i1] : 0.0f;
+        for (int p = p0; p < p1; ++p, rp += NR) {
+            v[wl][lane] = x0;
+            if (two) v[wl][lane + 32] = x1;
+            if (p + 1 < p1) {
+                x0 = rp[NR + i0];
+                if (two) x1 = rp[NR + i1];
+            }
+            __syncwarp();
+            float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 49; ++j) {
+                const float vj = v[wl][j];
+                a0 = fmaf(m0[j], vj, a0);
+                a1 = fmaf(m1[j], vj, a1);
+            }
+            __syncwarp();
+            rp[i0] = a0;
+            if (two) rp[i1] = a1;
+        }
+    }
 }
 
 __global__ void philox_blocks_kernel(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,
@@ -234,6 +294,49 @@ cudaError_t launch_block_seq(float* r, int NR, int ne, const float* M49, const i
     if (nobs <= 0) return cudaSuccess;
     block_seq_kernel<<<ne, 64, 0, st>>>(r, NR, M49, obs_block0, nobs, nRx, nRy);
     return cudaGetLastError();
+}
+
+cudaError_t launch_block_level(float* r, int NR, int ne, const float* M49, const int* obs_block0, const int* order,
+                               int lo, int hi, int nRx, int nRy, cudaStream_t st)
+{
+    const int nblk = hi - lo;
+    if (nblk <= 0 || ne <= 0) return cudaSuccess;
+    const long long warps = (long long)nblk * ((ne + BL_CHUNK - 1) / BL_CHUNK);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = std::min<long long>((warps + 7) / 8, (long long)std::max(sms, 1) * 8);
+    block_level_kernel<<<(unsigned)grid, 256, 0, st>>>(r, NR, ne, M49, obs_block0, order, lo, nblk, nRx, nRy);
+    return cudaGetLastError();
+}
+
+void block_levels(const int* block0, int nobs, int nRx, int nRy, std::vector<int>& order, std::vector<int>& level_off)
+{
+    // two 7-point windows on a circle of n points meet when their centres are
+    // at most 6 apart (circular distance)
+    auto near = [](int a, int b, int n) {
+        int d = a - b;
+        if (d < 0) d = -d;
+        d %= n;
+        return std::min(d, n - d) <= 6;
+    };
+    std::vector<int> level(nobs, 0);
+    int top = 0;
+    for (int l = 0; l < nobs; ++l) {
+        int lv = 0;
+        for (int k = 0; k < l; ++k)
+            if (level[k] + 1 > lv && near(block0[2 * k], block0[2 * l], nRx) &&
+                near(block0[2 * k + 1], block0[2 * l + 1], nRy))
+                lv = level[k] + 1;
+        level[l] = lv;
+        top = std::max(top, lv);
+    }
+    level_off.assign(top + 2, 0);
+    for (int l = 0; l < nobs; ++l) ++level_off[level[l] + 1];
+    for (int v = 0; v <= top; ++v) level_off[v + 1] += level_off[v];
+    order.assign(nobs, 0);
+    std::vector<int> fill(level_off.begin(), level_off.end() - 1);
+    for (int l = 0; l < nobs; ++l) order[fill[level[l]]++] = l;
 }
 
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace iewpf {
@@ -152,6 +154,19 @@ cudaError_t launch_form_r(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_n
                           cudaStream_t st);
 cudaError_t launch_block_seq(float* r, int NR, int ne, const float* M49, const int* obs_block0, int nobs, int nRx,
                              int nRy, cudaStream_t st);
+// the same product for blocks order[lo..hi) that pairwise share no coarse
+// point (one level of block_levels), all particles at once: a warp per
+// (particle, block), the same arithmetic as block_seq, so a sequence of
+// levels gives block_seq's result bit for bit
+cudaError_t launch_block_level(float* r, int NR, int ne, const float* M49, const int* obs_block0, const int* order,
+                               int lo, int hi, int nRx, int nRy, cudaStream_t st);
+// host: level of each block (0 when it shares no coarse point with an earlier
+// block, else one more than the highest level among the earlier blocks it
+// overlaps; blocks are 7 x 7 coarse points around block0 on the periodic
+// nRx x nRy grid).  order = the blocks sorted by level (observation order
+// within a level); level_off[v] .. level_off[v + 1] = the range of level v.
+void block_levels(const int* block0, int nobs, int nRx, int nRy, std::vector<int>& order,
+                  std::vector<int>& level_off);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,
                                  uint32_t* out, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n, double* o64,
