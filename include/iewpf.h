@@ -370,6 +370,18 @@ IEWPF_API int iewpf_pull_stencil(const iewpf_ctx_t* ctx, double* K);
  * (dy+3)*7 + (dx+3)).  Errors: EINVAL. */
 IEWPF_API int iewpf_local_block(const iewpf_ctx_t* ctx, double* M);
 
+/* Levels of the local blocks of Sec. 4.6: block l is the 7 x 7 coarse
+ * points around the centre block0[l] = (a, b) (host int[nobs][2], coarse
+ * indices on the periodic nRx x nRy grid).  level[l] (host int[nobs]) = 0
+ * when block l shares no coarse point with an earlier block, else one more
+ * than the highest level among the earlier blocks it shares a point with.
+ * Blocks of one level commute, so applying the levels in turn gives the
+ * result of applying the blocks in observation order; the analysis of a
+ * fixed (mooring) layout does so.  Host arithmetic only (no device).
+ * Errors: EINVAL (nobs < 0, NULL arrays with nobs > 0, nRx or nRy < 1, a
+ * centre outside the grid). */
+IEWPF_API int iewpf_block_levels(const int* block0, int nobs, int nRx, int nRy, int* level);
+
 /* Add Q^{1/2} x to every particle for coarse fields x ([N_e][N_R] float32,
  * host), the operator of eq. covarianceOperatorsDef (testing aid).
  * Errors: EINVAL (NULL x), ECUDA. */

@@ -1484,6 +1484,19 @@ int iewpf_local_block(const iewpf_ctx_t* ctx, double* M)
     return IEWPF_OK;
 }
 
+int iewpf_block_levels(const int* block0, int nobs, int nRx, int nRy, int* level)
+{
+    if (nobs < 0 || nRx < 1 || nRy < 1 || (nobs > 0 && (!block0 || !level))) return IEWPF_EINVAL;
+    for (int l = 0; l < nobs; ++l)
+        if (block0[2 * l] < 0 || block0[2 * l] >= nRx || block0[2 * l + 1] < 0 || block0[2 * l + 1] >= nRy)
+            return IEWPF_EINVAL;
+    std::vector<int> order, off;
+    block_levels(block0, nobs, nRx, nRy, order, off);
+    for (size_t v = 0; v + 1 < off.size(); ++v)
+        for (int i = off[v]; i < off[v + 1]; ++i) level[order[i]] = (int)v;
+    return IEWPF_OK;
+}
+
 int iewpf_add_qhalf(iewpf_ctx_t* ctx, const float* x)
 {
     if (ctx) ctx->cfl_ready = false;

@@ -26,7 +26,7 @@ EXPORTS = ["iewpf_create", "iewpf_destroy", "iewpf_set_state", "iewpf_get_state"
            "iewpf_last_nsub", "iewpf_last_error", "iewpf_philox_blocks", "iewpf_normals", "iewpf_weights",
            "iewpf_weights_one_stage", "iewpf_sir_weights", "iewpf_alpha_gamma", "iewpf_rank",
            "iewpf_batch_forecast", "iewpf_drifter_obs",
-           "iewpf_pull_stencil", "iewpf_local_block", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
+           "iewpf_pull_stencil", "iewpf_local_block", "iewpf_block_levels", "iewpf_add_qhalf", "iewpf_sizes", "iewpf_stream",
            "iewpf_substeps", "iewpf_factor_info", "iewpf_launch_count", "iewpf_work", "iewpf_weights_noalloc", "iewpf_set_stepper", "iewpf_tune",
            "iewpf_get_stepper", "drifter_forecast_errors", "iewpf_batch_create", "iewpf_batch_destroy",
            "iewpf_batch_instance", "iewpf_batch_tune", "iewpf_batch_cycle", "iewpf_batch_stream",
@@ -156,6 +156,7 @@ def load(build_if_needed: bool = True):
     L.iewpf_surrogate_apply_device.argtypes = [_vp, _vp, c.c_int, _vp, _vp]
     L.iewpf_surrogate_stream.argtypes = [_vp, c.POINTER(c.c_void_p)]
     L.iewpf_surrogate_loss_grad.argtypes = [_vp, _fp, _fp, c.c_int, _dp, _fp]
+    L.iewpf_block_levels.argtypes = [_ip, c.c_int, c.c_int, c.c_int, _ip]
     L.iewpf_surrogate_train.argtypes = [_vp, _vp, c.c_int, c.c_int, c.c_int, c.c_int, c.c_double, _dp]
     L.iewpf_surrogate_train_time.argtypes = [_vp, _dp]
     L.iewpf_set_surrogate.argtypes = [_vp, _vp, c.c_int]
@@ -683,6 +684,21 @@ def drifter_obs(params, xy, xy_prev, dt):
     rc = L.iewpf_drifter_obs(ctypes.byref(params), xy.shape[0], _ptr(xy), _ptr(xy_prev), float(dt), _ptr(out))
     if rc != IEWPF_OK:
         raise IewpfError(rc, "drifter_obs")
+    return out
+
+
+def block_levels(block0, nRx, nRy):
+    """Levels of the 7 x 7 local blocks centred at the coarse points block0
+    ([n][2] ints (a, b)) on the periodic nRx x nRy coarse grid (Sec. 4.6):
+    blocks of one level share no coarse point, and each block's level is one
+    more than the highest level among the earlier blocks it overlaps."""
+    L = load()
+    b = np.ascontiguousarray(np.asarray(block0, np.int32).reshape(-1, 2))
+    out = np.zeros(b.shape[0], np.int32)
+    rc = L.iewpf_block_levels(b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), b.shape[0], int(nRx), int(nRy),
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if rc != IEWPF_OK:
+        raise IewpfError(rc, "block_levels")
     return out
 
 
