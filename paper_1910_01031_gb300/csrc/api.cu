@@ -2110,16 +2110,30 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
     int* d_ctr = nullptr;                   // batch cursor, optimizer step of this call
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     auto cleanup = [&]() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t ev : {ev0, ev1})
+            if (ev) cudaEventDestroy(ev);
         gexec = nullptr;
         graph = nullptr;
+        ev0 = ev1 = nullptr;
         for (void* p : {(void*)X, (void*)Y, (void*)d_order, (void*)d_ctr, (void*)d_bc})
             if (p) cudaFree(p);
         X = Y = d_bc = nullptr;
         d_order = d_ctr = nullptr;
     };
+    // from here on a failed CUDA call frees the buffers, graph and events
+#undef SCK
+#define SCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) {                                                                     \
+            cleanup();                                                                               \
+            return sfail(s, IEWPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+        }                                                                                            \
+    } while (0)
     if (cudaMalloc((void**)&X, per * n_pairs * 4) != cudaSuccess || cudaMalloc((void**)&Y, per * n_pairs * 4) != cudaSuccess ||
         cudaMalloc((void**)&d_order, sizeof(int) * n_pairs) != cudaSuccess ||
         cudaMalloc((void**)&d_ctr, sizeof(int) * 2) != cudaSuccess ||
@@ -2227,7 +2241,6 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
         SCK(ee);
         SCK(cudaGraphInstantiate(&gexec, graph, 0));
     }
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     SCK(cudaEventCreate(&ev0));
     SCK(cudaEventCreate(&ev1));
     SCK(cudaEventRecord(ev0, s->st));
@@ -2249,12 +2262,17 @@ int iewpf_surrogate_train(iewpf_surrogate_t* s, iewpf_ctx_t* ctx, int n_pairs, i
     SCK(cudaEventSynchronize(ev1));
     float ms = 0.0f;
     SCK(cudaEventElapsedTime(&ms, ev0, ev1));
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     s->train_s = ms * 1e-3;
     cleanup();
     return sur_flag(s, s->st);
 }
+#undef SCK
+#define SCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return sfail(s, IEWPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
 
 int iewpf_surrogate_train_time(const iewpf_surrogate_t* s, double* seconds)
 {
