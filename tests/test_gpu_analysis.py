@@ -349,3 +349,31 @@ def test_drifter_values_formed_from_two_fixes():
     with pytest.raises(iewpf.IewpfError) as e:      # neither values nor usable fixes
         a.assimilate(xy, None, xy_prev=xy_prev, dt=0.0)
     assert e.value.name == "EINVAL"
+
+
+def test_mooring_block_levels_equal_the_in_order_walk_bitwise():
+    """A fixed mooring layout applies its overlapping 7 x 7 blocks level by
+    level (Sec. 4.6, blocks in observation order); a drifter context with the
+    same observation cells and values walks them in order.  Everything else
+    of the two analyses is the same arithmetic, so the posterior states and
+    diagnostics agree bit for bit."""
+    kw = dict(n_particles=16, n_obs=100)
+    cm = synth.Config("moorings_192_every16", 192, 192, obs_kind=synth.OBS_MOORING, **kw)
+    cd = synth.Config("drifters_192_every16", 192, 192, obs_kind=synth.OBS_DRIFTER, **kw)
+    cells = synth.mooring_cells(cm, synth.COUPLED_SPACING)
+    xy = synth.cell_positions(cm, cells)
+    c = cm.c_omega
+    nR = -(-cm.nx // c)
+    b0 = [[O.nearest_coarse(cm.nx, nR, c, int(x)), O.nearest_coarse(cm.ny, nR, c, int(y))] for x, y in cells]
+    assert iewpf.block_levels(b0, nR, nR).max() >= 1          # the blocks overlap: several levels
+    U32, _ = start_state(cm, cm.n_particles)
+    truth = synth.initial_particle(cm, 999, seed=5)
+    y = synth.obs_from_state(cm, truth, cells, synth.obs_noise(cm, len(cells), 0))
+    em, ed = ensemble(cm, mooring_xy=xy), ensemble(cd)
+    em.set_state(U32)
+    ed.set_state(U32)
+    dm = em.assimilate(None, y)
+    dd = ed.assimilate(xy, y)
+    for k in ("phi", "gamma", "zeta", "alpha", "neglogw"):
+        assert np.array_equal(dm[k], dd[k]), k
+    assert np.array_equal(em.get_state(), ed.get_state())
