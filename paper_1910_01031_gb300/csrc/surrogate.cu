@@ -247,6 +247,86 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
     }
 }
 
+// Weight gradients of all 9 taps of a 16 -> 64 layer per CTA: the CTA loads
+// each pixel tile's dZ once and X once with its one-pixel halo, and every
+// tap's B fragment is read at the tap's offset in that patch; warp w owns the
+// same 16 x 8 output tile for every tap.  Partial sums per group, taps and
+// tiles summed in the order of wgrad_kernel.
+template <bool PAD>
+__global__ void __launch_bounds__(CONV_THREADS)
+wgrad9_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ X, int nb, int ny, int nx,
+              int tiles_per_group, float* __restrict__ partial)
+{
+    constexpr int CIN = 16, COUT = 64;
+    constexpr int CPI = CIN + 8, CPO = COUT + 8;
+    constexpr int NT = CIN / 8;                           // n8 blocks (ci); COUT / 16 = 4 m16 blocks (co)
+    constexpr int PR = TROWS + 2, PC = TCOLS + 2;
+    __shared__ __align__(16) __nv_bfloat16 Ds[TROWS * TCOLS * CPO];
+    __shared__ __align__(16) __nv_bfloat16 Xs[PR * PC * CPI];
+    const int group = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mt = warp / NT, nt = warp % NT;
+    const int tiles_x = nx / TCOLS, tiles_y = ny / TROWS;
+    const long long ntiles = (long long)nb * tiles_x * tiles_y;
+    float acc[9][4];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
+    const long long t0 = (long long)group * tiles_per_group, t1 = min(ntiles, t0 + tiles_per_group);
+    for (long long tile = t0; tile < t1; ++tile) {
+        const int b = (int)(tile / (tiles_x * tiles_y));
+        const int rem = (int)(tile % (tiles_x * tiles_y));
+        const int y0 = (rem / tiles_x) * TROWS, x0 = (rem % tiles_x) * TCOLS;
+        __syncthreads();
+        for (int i = tid; i < TROWS * TCOLS * (COUT / 8); i += CONV_THREADS) {
+            const int c8 = i % (COUT / 8), pix = i / (COUT / 8);
+            const int gy = y0 + pix / TCOLS, gx = x0 + pix % TCOLS;
+            const long long src = PAD ? ((long long)b * (ny + 2) + gy + 1) * (nx + 2) + gx + 1
+                                      : ((long long)b * ny + gy) * nx + gx;
+            *reinterpret_cast<uint4*>(Ds + pix * CPO + c8 * 8) =
+                *reinterpret_cast<const uint4*>(dz + src * COUT + c8 * 8);
+        }
+        for (int i = tid; i < PR * PC * (CIN / 8); i += CONV_THREADS) {
+            const int c8 = i % (CIN / 8), q = i / (CIN / 8);
+            const int py = q / PC, px = q % PC;
+            const long long src = PAD ? ((long long)b * (ny + 2) + y0 + py) * (nx + 2) + x0 + px
+                                      : ((long long)b * ny + pmod(y0 - 1 + py, ny)) * nx + pmod(x0 - 1 + px, nx);
+            *reinterpret_cast<uint4*>(Xs + q * CPI + c8 * 8) = *reinterpret_cast<const uint4*>(X + src * CIN + c8 * 8);
+        }
+        __syncthreads();
+        // K = the tile's 128 pixels in 8 steps of 16 (one tile row each)
+#pragma unroll 1
+        for (int k0 = 0; k0 < TROWS * TCOLS; k0 += 16) {
+            const int mi = lane >> 3, r = lane & 7;
+            // A = dZ^T (co x p): stored [p][co], transposed load
+            const uint32_t aaddr = smem_u32(Ds + (k0 + (mi >> 1) * 8 + r) * CPO + mt * 16 + (mi & 1) * 8);
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4_t(aaddr, a0, a1, a2, a3);
+            const int bi = lane & 15, qy = k0 / TCOLS, qx = (bi >> 3) * 8 + (bi & 7);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap % 3;
+                // B = X at the tap's shift (p x ci): rows of the halo patch, transposed load
+                const uint32_t baddr = smem_u32(Xs + ((qy + ky) * PC + qx + kx) * CPI + nt * 8);
+                uint32_t b0, b1;
+                asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                             : "=r"(b0), "=r"(b1)
+                             : "r"(baddr));
+                mma_bf16(acc[tap], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // partial[group][tap][co][ci]
+    const int co = mt * 16 + (lane >> 2), ci = nt * 8 + (lane & 3) * 2;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        float* P = partial + (((long long)group * 9 + tap) * COUT) * CIN;
+        P[co * CIN + ci] = acc[tap][0];
+        P[co * CIN + ci + 1] = acc[tap][1];
+        P[(co + 8) * CIN + ci] = acc[tap][2];
+        P[(co + 8) * CIN + ci + 1] = acc[tap][3];
+    }
+}
+
 // grad[i] = sum over groups of partial (fixed order)
 __global__ void reduce_groups_kernel(const float* __restrict__ partial, int groups, long long n, float* __restrict__ grad)
 {
@@ -624,6 +704,19 @@ cudaError_t wgrad(const __nv_bfloat16* dz, const __nv_bfloat16* X, int nb, int n
     return cudaGetLastError();
 }
 
+// layer 0's weight gradients (16 -> 64) with all taps per CTA
+template <bool PAD>
+cudaError_t wgrad9(const __nv_bfloat16* dz, const __nv_bfloat16* X, int nb, int ny, int nx, int groups,
+                   float* partial, float* grad, cudaStream_t st)
+{
+    const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
+    const int tpg = (int)((tiles + groups - 1) / groups);
+    wgrad9_kernel<PAD><<<groups, CONV_THREADS, 0, st>>>(dz, X, nb, ny, nx, tpg, partial);
+    const long long n = 9LL * 16 * 64;
+    reduce_groups_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, groups, n, grad);
+    return cudaGetLastError();
+}
+
 cudaError_t bias_grad(const __nv_bfloat16* dz, int nb, int ny, int nx, int C, int pad, float* partial, float* db,
                       cudaStream_t st)
 {
@@ -791,7 +884,8 @@ int Surrogate::ensure_batch(int nb)
         wgrad_tc_split(nb, ny, nx, &g, &tpg);
         groups = std::max(groups, g);
     }
-    wpartial = salloc<float>(*this, (size_t)groups * std::max(9 * width * width, wgrad_tc_partial(width)));
+    wpartial = salloc<float>(*this, std::max((size_t)groups * std::max(9 * width * width, wgrad_tc_partial(width)),
+                                             (size_t)wgrad9_groups(nb) * 9 * 16 * width));
     bpartial = salloc<float>(*this, (size_t)BIAS_BLOCKS * width);
     lpartial = salloc<double>(*this, 1024);
     dloss = salloc<double>(*this, 1);
@@ -825,6 +919,12 @@ int Surrogate::ensure_batch(int nb)
     batch_pad = pad;
     cap_batch = nb;
     return IEWPF_OK;
+}
+
+int Surrogate::wgrad9_groups(int nb) const
+{
+    const long long tiles = (long long)nb * (nx / TCOLS) * (ny / TROWS);
+    return (int)std::max<long long>(1, std::min<long long>(256, tiles / 4));
 }
 
 int Surrogate::wgrad_groups(int nb) const
@@ -1004,7 +1104,7 @@ cudaError_t Surrogate::backward(int nb, cudaStream_t st, bool add_eloss)
             if (l > 0) {
                 e = wg(64, tm_wx[l - 1], tm_dz_w[cur], grad + w_off[l]);
             } else {
-                e = wgrad<16, 64, true>(dzs[cur], x_in, nb, ny, nx, groups, wpartial, grad + w_off[0], st);
+                e = wgrad9<true>(dzs[cur], x_in, nb, ny, nx, wgrad9_groups(nb), wpartial, grad + w_off[0], st);
                 if (e == cudaSuccess) e = bias_grad(dzs[cur], nb, ny, nx, 64, 1, bpartial, grad + b_off[0], st);
             }
             if (e != cudaSuccess) return e;
@@ -1029,7 +1129,7 @@ cudaError_t Surrogate::backward(int nb, cudaStream_t st, bool add_eloss)
     __nv_bfloat16* nxt = dz_b;
     for (int l = L - 1; l >= 0; --l) {
         const __nv_bfloat16* X = l == 0 ? x_in : a[l - 1];
-        if (l == 0) e = wgrad<16, 64, false>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
+        if (l == 0) e = wgrad9<false>(cur, X, nb, ny, nx, wgrad9_groups(nb), wpartial, grad + w_off[l], st);
         else e = wgrad<64, 64, false>(cur, X, nb, ny, nx, groups, wpartial, grad + w_off[l], st);
         if (e != cudaSuccess) return e;
         if ((e = bias_grad(cur, nb, ny, nx, 64, 0, bpartial, grad + b_off[l], st)) != cudaSuccess) return e;

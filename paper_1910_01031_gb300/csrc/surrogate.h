@@ -85,6 +85,7 @@ struct Surrogate {
     int init(int nx, int ny, int width, int depth);
     int ensure_batch(int nb);
     int wgrad_groups(int nb) const;
+    int wgrad9_groups(int nb) const;
     int layer_cin(int l) const;
     int layer_cout(int l) const;
     size_t layer_w(int l) const;
