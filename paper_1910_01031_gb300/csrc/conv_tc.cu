@@ -90,7 +90,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
     const uint32_t sbase = su32(smem);
 
     // weights of every tap, once per CTA (B operand, K-major, rows = output channels)
-    tc::stage_weights<CIN, COUT, TC_THREADS>(smem + L::W_OFF, W, tid);
+    tc::stage_weights<CIN, COUT, TC_THREADS, true>(smem + L::W_OFF, W, tid);
     for (int i = tid; i < COUT; i += TC_THREADS) sbias[i] = bias[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
@@ -188,6 +188,29 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
                 const uint64_t adesc = L::SW ? sdesc(a0, 16, 1024, 2) : sdesc(a0, PLANE, 128, 0);
                 const uint64_t bdesc = L::SW ? sdesc(sbase + L::W_OFF, 16, 1024, 2)
                                              : sdesc(sbase + L::W_OFF, COUT * 16, 128, 0);
+                if constexpr (L::SW) {
+                    // patch row p feeds output row r at ky = p - r; rows 1 and 2 feed
+                    // both output rows at the same pixel alignment, so each is one
+                    // product of N = 2 COUT into the two adjacent accumulators with the
+                    // weight blocks of ky and ky - 1 ([kx][ky = 2, 1, 0] order); rows 0
+                    // and 3 are single products.  The first product of each (kx, K
+                    // step) round is the row-1 pair, which at kx = 0, kc = 0
+                    // initialises both accumulators.
+                    constexpr uint32_t ID1 = idesc_bf16(TC_PX, COUT), ID2 = idesc_bf16(TC_PX, 2 * COUT);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                        for (int kc = 0; kc < CIN / 16; ++kc) {
+                            auto aoff = [&](int p) { return (uint32_t)(((p * TC_PCOLS + kx) * 128 + kc * 32) >> 4); };
+                            auto boff = [&](int ky_top) {
+                                return (uint32_t)((((kx * 3 + 2 - ky_top) * COUT) * 128 + kc * 32) >> 4);
+                            };
+                            tc::mma_bf16_ss(d0, adesc + aoff(1), bdesc + boff(1), ID2, (kx | kc) != 0);
+                            tc::mma_bf16_ss(d0, adesc + aoff(0), bdesc + boff(0), ID1, 1);
+                            tc::mma_bf16_ss(d0, adesc + aoff(2), bdesc + boff(2), ID2, 1);
+                            tc::mma_bf16_ss(d0 + (uint32_t)COUT, adesc + aoff(3), bdesc + boff(2), ID1, 1);
+                        }
+                } else {
 #pragma unroll
                 for (int r = 0; r < TC_ROWS; ++r)
 #pragma unroll
@@ -209,6 +232,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
                                              "l"(adesc + aoff), "l"(bdesc + boff), "r"(IDESC));
                         }
                     }
+                }
                 // the stage is free and the accumulators are ready once these MMAs complete
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                                  empty0 + 8 * s)

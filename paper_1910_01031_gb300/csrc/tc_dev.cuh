@@ -139,8 +139,10 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t adesc, uint64_t
 // output channels): 128-byte swizzled rows of 64 input channels, or core
 // matrices of 8 output channels x 16 bytes ([tap][chunk][co][8 ch]).  Every
 // thread issues all its loads before its first store, so the copy costs one
-// round trip to L2 rather than one per chunk.
-template <int CIN, int COUT, int NTHREADS>
+// round trip to L2 rather than one per chunk.  With KXMAJOR (64 input
+// channels) the tap blocks are ordered [kx][ky = 2, 1, 0], so that the
+// blocks of ky and ky - 1 at one kx are adjacent rows of one operand.
+template <int CIN, int COUT, int NTHREADS, bool KXMAJOR = false>
 __device__ __forceinline__ void stage_weights(unsigned char* wsm, const void* __restrict__ W, int tid)
 {
     constexpr int N = 9 * COUT * (CIN / 8);                 // 16-byte chunks
@@ -157,7 +159,8 @@ __device__ __forceinline__ void stage_weights(unsigned char* wsm, const void* __
         if (i < N) {
             // chunk i of W: row (tap, co), channels 8 c .. 8 c + 7
             const int c = i % (CIN / 8), co = (i / (CIN / 8)) % COUT, tap = i / ((CIN / 8) * COUT);
-            const int off = CIN == 64 ? (tap * COUT + co) * 128 + ((c ^ (co & 7)) << 4)
+            const int blk = KXMAJOR ? (tap % 3) * 3 + 2 - tap / 3 : tap;
+            const int off = CIN == 64 ? (blk * COUT + co) * 128 + ((c ^ (co & 7)) << 4)
                                       : ((tap * (CIN / 8) + c) * COUT + co) * 16;
             *reinterpret_cast<uint4*>(wsm + off) = r[k];
         }
