@@ -4,17 +4,17 @@
 // weight gradients.  Operands are staged by TMA, products by tcgen05.mma from
 // shared memory with FP32 accumulators in tensor memory.
 //
-// Forward and data passes (conv_tr_kernel): implicit GEMM over tiles of 4
-// output rows x 64 pixels.  Unlike the inference kernel (conv_tc.cu), whose
-// 128-pixel output rows make a shifted tap a shifted start address inside one
-// halo patch, a 64-pixel row is half an M = 128 accumulator, so one
-// accumulator spans two output rows and its 128 A rows must be the pixels of
-// both rows shifted by the same tap.  Each tile is therefore loaded as three
-// stages, one per column shift kx: the TMA box (CIN channels, 64 pixels,
-// 6 rows) starts at padded column x0 + kx, so the rows of a stage are
-// contiguous 64-pixel runs and A for (accumulator a, tap (ky, kx)) is the
-// 128 pixels from stage row 2a + ky.  The three stages of a tile accumulate
-// into one set of two accumulators (2 x 128 x COUT in tensor memory).
+// Forward and data passes (conv_tr_kernel): implicit GEMM over tiles of 16
+// output rows x 8 pixels.  The 64-pixel rows of the training fields are half
+// an M = 128 accumulator, so the tile is tall instead: each of its 16 rows is
+// one 8-row atom of the A operand (128-byte swizzle for 64 channels, one
+// core matrix for 16), and consecutive atoms lie one halo-patch row (10
+// pixels) apart, the descriptor's uniform atom stride.  One TMA box per tile
+// (CIN channels, 10 pixels, 18 rows) holds the tile and its halo, and a
+// shifted tap is a shifted start address; 9 taps x CIN / 16 products of
+// 128 x COUT x 16 fill one accumulator, two of them alternate in tensor
+// memory.  (A tile of 4 rows x 64 pixels needs the three column-shifted
+// copies of its patch, 3.1 times the bytes per output pixel.)
 //
 // Weight gradients (wgrad_tc_kernel): dW[tap][co][ci] = sum_p dZ[p][co]
 // X[p + off(tap)][ci] as a GEMM with K = pixels, both operands M/N-major (the
@@ -57,12 +57,12 @@ using tc::su32;
 using tc::tmem_ld16;
 using tc::tmem_ld32;
 
-constexpr int TR_PX = 64;                  // pixels of a tile row
-constexpr int TR_ROWS = 4;                 // output rows per tile
-constexpr int TR_PROWS = TR_ROWS + 2;      // stage rows
-constexpr int TR_NACC = TR_ROWS / 2;       // M = 128 accumulators per tile (two rows each)
-constexpr int TR_NS = 3;                   // shared-memory stages
-constexpr int TR_EPI_WARPS = 16;           // 4 lane quarters x 2 accumulators x 2 column halves
+constexpr int TR_TW = 8;                   // tile columns: one 8-row swizzle atom (or core matrix) per tile row
+constexpr int TR_TH = 16;                  // tile rows: 16 x 8 = 128 pixels = M
+constexpr int TR_PW = TR_TW + 2;           // halo patch columns
+constexpr int TR_PH = TR_TH + 2;           // halo patch rows
+constexpr int TR_NS = 4;                   // shared-memory stages
+constexpr int TR_EPI_WARPS = 8;            // 4 lane quarters x 2 column halves
 constexpr int TR_WARPS = 2 + TR_EPI_WARPS;
 constexpr int TR_THREADS = 32 * TR_WARPS;
 
@@ -70,18 +70,19 @@ enum TrMode : int { TR_HID = 0, TR_OUT = 1, TR_DGRAD = 2 };
 
 template <int CIN, int COUT>
 struct TrLayout {
-    static constexpr bool SW = CIN == 64;                          // 128-byte swizzle of the stages
+    static constexpr bool SW = CIN == 64;                          // 128-byte swizzle of the patches
     static constexpr int W_BYTES = 9 * COUT * CIN * 2;
-    static constexpr int STAGE = TR_PROWS * TR_PX * CIN * 2;       // bytes of one stage
+    static constexpr int STAGE = TR_PH * TR_PW * CIN * 2;          // bytes of one halo patch
     static constexpr int STAGE_ALLOC = (STAGE + 1023) / 1024 * 1024;
-    static constexpr int PLANE = TR_PROWS * TR_PX * 16;            // bytes of one 8-channel plane (no swizzle)
+    static constexpr int PLANE = TR_PH * TR_PW * 16;               // bytes of one 8-channel plane (no swizzle)
     static constexpr int A_OFF = (W_BYTES + 1023) / 1024 * 1024;
     static constexpr int BIAS_OFF = A_OFF + TR_NS * STAGE_ALLOC;
-    static constexpr int BAR_OFF = BIAS_OFF + COUT * 4;            // full[3] empty[3] tfull[2] tempty[2], abort, slot
-    static constexpr int TOTAL = BAR_OFF + 128;
-    // at least 120 KB so that one CTA runs per SM: it keeps its tensor memory
+    static constexpr int NBARS = 2 * TR_NS + 4;                    // full, empty, tfull[2], tempty[2]
+    static constexpr int BAR_OFF = BIAS_OFF + COUT * 4;            // then the abort flag and the tensor-memory slot
+    static constexpr int TOTAL = BAR_OFF + 8 * NBARS + 16;
+    // at least 120 KB so that one CTA runs per SM
     static constexpr int REQUEST = (TOTAL > 120 * 1024 ? TOTAL : 120 * 1024) + 1024;
-    static constexpr int TMEM_COLS = 2 * TR_NACC * COUT;
+    static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;
 };
 
 using tc::stage_weights;
@@ -119,8 +120,8 @@ conv_tr_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float* sbias = reinterpret_cast<float*>(smem + L::BIAS_OFF);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
-    volatile int* abort = reinterpret_cast<volatile int*>(smem + L::BAR_OFF + 80);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + 84);
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + L::BAR_OFF + 8 * L::NBARS);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + 8 * L::NBARS + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = su32(smem);
 
@@ -132,8 +133,8 @@ conv_tr_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        // full[3], empty[3]: one arrival; tfull[2]: one commit; tempty[2]: one per epilogue warp
-        for (int k = 0; k < 2 * TR_NS + 4; ++k) {
+        // full[NS], empty[NS]: one arrival; tfull[2]: one commit; tempty[2]: one per epilogue warp
+        for (int k = 0; k < L::NBARS; ++k) {
             const int count = (k >= 2 * TR_NS + 2) ? TR_EPI_WARPS : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(&bars[k])), "r"(count));
         }
@@ -148,7 +149,7 @@ conv_tr_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
     const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[TR_NS]), tfull0 = su32(&bars[2 * TR_NS]),
                    tempty0 = su32(&bars[2 * TR_NS + 2]);
 
-    const int tiles_x = nx / TR_PX, tiles_y = ny / TR_ROWS;
+    const int tiles_x = nx / TR_TW, tiles_y = ny / TR_TH;
     const long long ntiles = (long long)nb * tiles_x * tiles_y;
     const long long first = blockIdx.x, stride = gridDim.x;
     const int nloc = first < ntiles ? (int)((ntiles - 1 - first) / stride + 1) : 0;
@@ -156,86 +157,75 @@ conv_tr_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
         const long long t = first + (long long)i * stride;
         b = (int)(t / ((long long)tiles_x * tiles_y));
         const int rem = (int)(t % ((long long)tiles_x * tiles_y));
-        y0 = (rem / tiles_x) * TR_ROWS;
-        x0 = (rem % tiles_x) * TR_PX;
+        y0 = (rem / tiles_x) * TR_TH;
+        x0 = (rem % tiles_x) * TR_TW;
     };
 
     if (warp == 0) {
-        // ---- TMA producer: stage g = 3 i + kx holds tile i shifted by kx ----
+        // ---- TMA producer: the halo patch of tile i into stage i % NS ----
         int issued = 0;
         if (lane == 0) {
-            for (int g = 0; g < 3 * nloc; ++g) {
-                const int s = g % TR_NS;
-                const uint32_t k = (uint32_t)(g / TR_NS);
+            for (int i = 0; i < nloc; ++i) {
+                const int s = i % TR_NS;
+                const uint32_t k = (uint32_t)(i / TR_NS);
                 if (!mbar_wait(empty0 + 8 * s, (k & 1) ^ 1, abort)) break;
                 int b, y0, x0;
-                tile_coords(g / 3, b, y0, x0);
-                const int kx = g % 3;
+                tile_coords(i, b, y0, x0);
                 const uint32_t dst = sbase + L::A_OFF + s * L::STAGE_ALLOC;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full0 + 8 * s),
                              "r"(L::STAGE)
                              : "memory");
-                // padded coordinates: stage row 0 = padded row y0, stage column 0 = padded column x0 + kx
+                // padded coordinates: patch row 0 = padded row y0, patch column 0 = padded column x0
                 if (L::SW)
                     asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
                                  " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
-                                 "l"(reinterpret_cast<uint64_t>(&tmap_in)), "r"(0), "r"(x0 + kx), "r"(y0), "r"(b),
+                                 "l"(reinterpret_cast<uint64_t>(&tmap_in)), "r"(0), "r"(x0), "r"(y0), "r"(b),
                                  "r"(full0 + 8 * s)
                                  : "memory");
                 else
                     asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
                                  " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
-                                 "l"(reinterpret_cast<uint64_t>(&tmap_in)), "r"(0), "r"(x0 + kx), "r"(y0), "r"(0),
+                                 "l"(reinterpret_cast<uint64_t>(&tmap_in)), "r"(0), "r"(x0), "r"(y0), "r"(0),
                                  "r"(b), "r"(full0 + 8 * s)
                                  : "memory");
-                issued = g + 1;
+                issued = i + 1;
             }
             // after an abort, wait (bounded) for the copies in flight
             if (*abort)
-                for (int g = issued >= TR_NS ? issued - TR_NS : 0; g < issued; ++g)
-                    mbar_drain(full0 + 8 * (g % TR_NS), (uint32_t)((g / TR_NS) & 1));
+                for (int i = issued >= TR_NS ? issued - TR_NS : 0; i < issued; ++i)
+                    mbar_drain(full0 + 8 * (i % TR_NS), (uint32_t)((i / TR_NS) & 1));
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- MMA issuer ----
+        // ---- MMA issuer: 9 taps x CIN / 16 products of 128 x COUT x 16 per tile ----
         int committed = 0;
         if (lane == 0) {
             constexpr uint32_t IDESC = idesc_bf16(128, COUT);
             const uint64_t bdesc = L::SW ? sdesc(sbase, 16, 1024, 2) : sdesc(sbase, COUT * 16, 128, 0);
-            bool ok = true;
-            for (int i = 0; i < nloc && ok; ++i) {
-                const int as = i & 1;
-                const uint32_t ka = (uint32_t)(i >> 1);
-                if (!mbar_wait(tempty0 + 8 * as, (ka & 1) ^ 1, abort)) break;
-                const uint32_t d0 = tmem + (uint32_t)(as * TR_NACC * COUT);
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int g = 3 * i + kx, s = g % TR_NS;
-                    if (!mbar_wait(full0 + 8 * s, (uint32_t)((g / TR_NS) & 1), abort)) {
-                        ok = false;
-                        break;
+            for (int i = 0; i < nloc; ++i) {
+                const int s = i % TR_NS, as = i & 1;
+                if (!mbar_wait(tempty0 + 8 * as, (uint32_t)(((i >> 1) & 1) ^ 1), abort)) break;
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)((i / TR_NS) & 1), abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = sbase + L::A_OFF + s * L::STAGE_ALLOC;
+                // A: the tile's 128 pixels as 16 rows of 8, one 8-row atom (or core
+                // matrix) per tile row, atoms one patch row (TR_PW pixels) apart
+                const uint64_t adesc = L::SW ? sdesc(a0, 16, TR_PW * 128, 2) : sdesc(a0, L::PLANE, TR_PW * 16, 0);
+                const uint32_t d0 = tmem + (uint32_t)(as * COUT);
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+                    for (int kc = 0; kc < CIN / 16; ++kc) {
+                        const uint32_t aoff = L::SW ? ((ky * TR_PW + kx) * 128 + kc * 32) >> 4
+                                                    : (2 * kc * L::PLANE + (ky * TR_PW + kx) * 16) >> 4;
+                        const uint32_t boff = L::SW ? (tap * COUT * 128 + kc * 32) >> 4
+                                                    : ((tap * (CIN / 8) + 2 * kc) * COUT * 16) >> 4;
+                        mma_bf16_ss(d0, adesc + aoff, bdesc + boff, IDESC, (tap | kc) != 0);
                     }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t a0 = sbase + L::A_OFF + s * L::STAGE_ALLOC;
-                    const uint64_t adesc = L::SW ? sdesc(a0, 16, 1024, 2) : sdesc(a0, L::PLANE, 128, 0);
-#pragma unroll
-                    for (int a = 0; a < TR_NACC; ++a)
-#pragma unroll
-                        for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                            for (int kc = 0; kc < CIN / 16; ++kc) {
-                                const int tap = 3 * ky + kx;
-                                const uint32_t aoff = L::SW ? (((2 * a + ky) * TR_PX) * 128 + kc * 32) >> 4
-                                                            : (2 * kc * L::PLANE + ((2 * a + ky) * TR_PX) * 16) >> 4;
-                                const uint32_t boff = L::SW ? (tap * COUT * 128 + kc * 32) >> 4
-                                                            : ((tap * (CIN / 8) + 2 * kc) * COUT * 16) >> 4;
-                                mma_bf16_ss(d0 + (uint32_t)(a * COUT), adesc + aoff, bdesc + boff, IDESC,
-                                            (kx | ky | kc) != 0);
-                            }
-                    // the stage is free once these products complete
-                    mma_commit(empty0 + 8 * s);
                 }
-                if (!ok) break;
-                // the accumulators of tile i are ready
+                // the stage is free and the accumulator is ready once these products complete
+                mma_commit(empty0 + 8 * s);
                 mma_commit(tfull0 + 8 * as);
                 committed = i + 1;
             }
@@ -249,24 +239,22 @@ conv_tr_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warp 2 + e reads lane quarter (warp % 4) of
-        // accumulator (e / 8) and its columns 32 ((e / 4) % 2) + 0..31 ----
-        const int e = warp - 2, q = warp & 3, a = e >> 3, h = (e >> 2) & 1;
+        // ---- epilogue: warp 2 + e reads lane quarter (warp % 4) of the
+        // accumulator and its columns 32 (e / 4) + 0..31 ----
+        const int e = warp - 2, q = warp & 3, h = e >> 2;
         const bool active = MODE != TR_OUT || h == 0;     // the last layer has 16 columns
-        const int m = 32 * q + lane;
+        const int m = 32 * q + lane;                      // tile pixel: row m / 8, column m % 8
         for (int i = 0; i < nloc; ++i) {
             const int as = i & 1;
-            const uint32_t ka = (uint32_t)(i >> 1);
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(tfull0 + 8 * as, ka & 1, abort);
+            if (lane == 0) ok = mbar_wait(tfull0 + 8 * as, (uint32_t)((i >> 1) & 1), abort);
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             int b, y0, x0;
             tile_coords(i, b, y0, x0);
-            const int y = y0 + 2 * a + (m >> 6), x = x0 + (m & 63);
+            const int y = y0 + (m >> 3), x = x0 + (m & 7);
             const size_t pix = ((size_t)b * ny + y) * nx + x;
-            const uint32_t ta =
-                tmem + (uint32_t)(as * TR_NACC * COUT + a * COUT + 32 * h) + ((uint32_t)(32 * q) << 16);
+            const uint32_t ta = tmem + (uint32_t)(as * COUT + 32 * h) + ((uint32_t)(32 * q) << 16);
             if (MODE == TR_OUT) {
                 if (active) {
                     float v[16];
@@ -322,7 +310,10 @@ conv_tr_kernel(const __grid_constant__ CUtensorMap tmap_in, const __nv_bfloat16*
 // ---------------------------------------------------------------------------
 // weight gradients
 // ---------------------------------------------------------------------------
-constexpr int WG_PCOLS = TR_PX + 2;        // halo patch columns of X
+constexpr int WG_PX = 64;                  // pixels of a tile row
+constexpr int WG_ROWS = 4;                 // rows per tile
+constexpr int WG_PROWS = WG_ROWS + 2;      // halo patch rows of X
+constexpr int WG_PCOLS = WG_PX + 2;        // halo patch columns of X
 constexpr int WG_NS = 2;
 constexpr int WG_PAIRS = 5;
 constexpr int WG_THREADS = 32 * (2 + 4);
@@ -331,10 +322,10 @@ template <int COUT>
 struct WgLayout {
     static constexpr int ONES = 2048;                                  // 16 pixels x 64 channels of BF16 ones
     static constexpr int STAGE0 = ONES;                                // first stage
-    static constexpr int XSTAGE = TR_PROWS * WG_PCOLS * 128;           // X halo patch, 64 channels
+    static constexpr int XSTAGE = WG_PROWS * WG_PCOLS * 128;           // X halo patch, 64 channels
     static constexpr int XSTAGE_ALLOC = (XSTAGE + 1023) / 1024 * 1024;
-    static constexpr int DSTAGE = TR_ROWS * TR_PX * COUT * 2;          // dZ tile
-    static constexpr int DPLANE = TR_ROWS * TR_PX * 16;                // one 8-channel plane of dZ (COUT = 16)
+    static constexpr int DSTAGE = WG_ROWS * WG_PX * COUT * 2;          // dZ tile
+    static constexpr int DPLANE = WG_ROWS * WG_PX * 16;                // one 8-channel plane of dZ (COUT = 16)
     static constexpr int STAGE_ALLOC = XSTAGE_ALLOC + (DSTAGE + 1023) / 1024 * 1024;
     static constexpr int BAR_OFF = STAGE0 + WG_NS * STAGE_ALLOC;       // full[2] empty[2] done, abort, slot
     static constexpr int TOTAL = BAR_OFF + 64;
@@ -383,7 +374,7 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constan
     const uint32_t tmem = *tmem_slot;
     const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[WG_NS]), done = su32(&bars[2 * WG_NS]);
 
-    const int tiles_x = nx / TR_PX, tiles_y = ny / TR_ROWS;
+    const int tiles_x = nx / WG_PX, tiles_y = ny / WG_ROWS;
     const long long ntiles = (long long)nb * tiles_x * tiles_y;
     const long long t0 = (long long)blockIdx.x * tiles_per_group;
     const int nloc = t0 < ntiles ? (int)(min(ntiles, t0 + tiles_per_group) - t0) : 0;
@@ -399,7 +390,7 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constan
                 const long long t = t0 + i;
                 const int b = (int)(t / ((long long)tiles_x * tiles_y));
                 const int rem = (int)(t % ((long long)tiles_x * tiles_y));
-                const int y0 = (rem / tiles_x) * TR_ROWS, x0 = (rem % tiles_x) * TR_PX;
+                const int y0 = (rem / tiles_x) * WG_ROWS, x0 = (rem % tiles_x) * WG_PX;
                 const uint32_t xs = sbase + L::STAGE0 + s * L::STAGE_ALLOC, ds = xs + L::XSTAGE_ALLOC;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full0 + 8 * s),
                              "r"(L::XSTAGE + L::DSTAGE)
@@ -440,11 +431,11 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constan
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t xs = sbase + L::STAGE0 + s * L::STAGE_ALLOC, ds = xs + L::XSTAGE_ALLOC;
 #pragma unroll 1
-                for (int st = 0; st < TR_ROWS * TR_PX / 16; ++st) {
+                for (int st = 0; st < WG_ROWS * WG_PX / 16; ++st) {
                     const int r = st >> 2, xo = (st & 3) * 16;
                     // B = dZ^T (N = COUT channels, K = 16 pixels), M/N-major
-                    const uint64_t bdesc = COUT == 64 ? sdesc(ds + (uint32_t)((r * TR_PX + xo) * 128), 0, 1024, 2)
-                                                      : sdesc(ds + (uint32_t)((r * TR_PX + xo) * 16), 128, L::DPLANE, 0);
+                    const uint64_t bdesc = COUT == 64 ? sdesc(ds + (uint32_t)((r * WG_PX + xo) * 128), 0, 1024, 2)
+                                                      : sdesc(ds + (uint32_t)((r * WG_PX + xo) * 16), 128, L::DPLANE, 0);
 #pragma unroll
                     for (int j = 0; j < WG_PAIRS; ++j) {
                         const int ta = wg_t0(j), tb = ta + 1;
@@ -514,7 +505,7 @@ cudaError_t conv_tr(const CUtensorMap& map, const __nv_bfloat16* W, const float*
     static_assert(L::TMEM_COLS >= 32 && (L::TMEM_COLS & (L::TMEM_COLS - 1)) == 0, "tensor memory columns");
     cudaError_t e = tc::smem_attr_once<conv_tr_kernel<CIN, COUT, MODE>>(L::REQUEST);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)nb * (nx / TR_PX) * (ny / TR_ROWS);
+    const long long tiles = (long long)nb * (nx / TR_TW) * (ny / TR_TH);
     const int grid = (int)std::min<long long>(tiles, sm_count());
     if (grid < 1) return cudaSuccess;
     conv_tr_kernel<CIN, COUT, MODE><<<grid, TR_THREADS, L::REQUEST, st>>>(map, W, bias, nb, ny, nx, z, a, f, zprev,
@@ -538,7 +529,8 @@ cudaError_t wgrad_tc(const CUtensorMap& xm, const CUtensorMap& dm, int nb, int n
 
 bool conv_tr_supported(int nx, int ny)
 {
-    return nx > 0 && ny > 0 && nx % TR_PX == 0 && ny % TR_ROWS == 0 && nx + 2 <= 65536 && ny + 2 <= 65536;
+    return nx > 0 && ny > 0 && nx % WG_PX == 0 && ny % TR_TH == 0 && ny % WG_ROWS == 0 && nx + 2 <= 65536 &&
+           ny + 2 <= 65536;
 }
 
 cudaError_t launch_conv_tr(int kind, const CUtensorMap& in_map, const __nv_bfloat16* W, const float* bias, int nb,
@@ -578,7 +570,7 @@ int wgrad_tc_partial(int cout)
 
 void wgrad_tc_split(int nb, int ny, int nx, int* groups, int* tiles_per_group)
 {
-    const long long tiles = (long long)nb * (nx / TR_PX) * (ny / TR_ROWS);
+    const long long tiles = (long long)nb * (nx / WG_PX) * (ny / WG_ROWS);
     const long long g0 = std::max<long long>(1, std::min<long long>(tiles, sm_count()));
     const long long tpg = (tiles + g0 - 1) / g0;
     *tiles_per_group = (int)tpg;

@@ -899,13 +899,15 @@ int Surrogate::ensure_batch(int nb)
         // tensor maps of the padded buffers (boxes: conv_tr.cu's stages and tiles)
         tm_fwd.assign(depth, CUtensorMap{});
         tm_wx.assign(depth, CUtensorMap{});
-        bool ok = map16(&tm_in, x_in, nb, ny, nx, 64, 6) && map16(&tm_dout_f, dz_out, nb, ny, nx, 64, 6) &&
+        // forward and data passes: halo patches of 10 x 18 pixels; weight
+        // gradients: X halo patches of 66 x 6 and dZ tiles of 64 x 4
+        bool ok = map16(&tm_in, x_in, nb, ny, nx, 10, 18) && map16(&tm_dout_f, dz_out, nb, ny, nx, 10, 18) &&
                   map16(&tm_dout_w, dz_out, nb, ny, nx, 64, 4);
         for (int l = 0; l + 1 < depth && ok; ++l)
-            ok = map64(&tm_fwd[l], a[l], nb, ny, nx, 64, 6) && map64(&tm_wx[l], a[l], nb, ny, nx, 66, 6);
+            ok = map64(&tm_fwd[l], a[l], nb, ny, nx, 10, 18) && map64(&tm_wx[l], a[l], nb, ny, nx, 66, 6);
         __nv_bfloat16* dzs[2] = {dz_a, dz_b};
         for (int k = 0; k < 2 && ok; ++k)
-            ok = map64(&tm_dz_f[k], dzs[k], nb, ny, nx, 64, 6) && map64(&tm_dz_w[k], dzs[k], nb, ny, nx, 64, 4);
+            ok = map64(&tm_dz_f[k], dzs[k], nb, ny, nx, 10, 18) && map64(&tm_dz_w[k], dzs[k], nb, ny, nx, 64, 4);
         if (!ok) return IEWPF_ECUDA;
     }
     // launch attributes set now, outside any capture of a training step

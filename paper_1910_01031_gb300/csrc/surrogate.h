@@ -134,14 +134,15 @@ cudaError_t launch_conv_tc(int layer_kind, const CUtensorMap& in_map, const __nv
                            cudaStream_t st);
 
 // tcgen05 training convolutions (conv_tr.cu) on halo-padded activations,
-// tiles of 4 rows x 64 pixels (needs nx % 64 == 0, ny % 4 == 0).  kind 0 =
+// tiles of 16 rows x 8 pixels (with the weight gradients' tiles of 4 rows x
+// 64 pixels: needs nx % 64 == 0, ny % 16 == 0).  kind 0 =
 // 16 -> 64 and 1 = 64 -> 64 forward (z = conv + bias into z [b][ny][nx][64],
 // SiLU(z) into the padded a with its halo images); 2 = 64 -> 16 forward
 // (bias added, first 3 channels into f [b][ny][nx][3] FP32); 3 = 16 -> 64 and
 // 4 = 64 -> 64 data pass (conv with the flipped transposed weights times
 // SiLU'(zprev), zprev [b][ny][nx][64], into the padded a).  in_map: 16
-// channels as a 5-D map (8 ch, nx+2, ny+2, 2, b), box (8, 64, 6, 2, 1), no
-// swizzle; 64 channels as a 4-D map (64 ch, nx+2, ny+2, b), box (64, 64, 6,
+// channels as a 5-D map (8 ch, nx+2, ny+2, 2, b), box (8, 10, 18, 2, 1), no
+// swizzle; 64 channels as a 4-D map (64 ch, nx+2, ny+2, b), box (64, 10, 18,
 // 1), 128-byte swizzle.
 bool conv_tr_supported(int nx, int ny);
 cudaError_t launch_conv_tr(int kind, const CUtensorMap& in_map, const __nv_bfloat16* W, const float* bias, int nb,

@@ -323,11 +323,11 @@ def _oracle_grads(sur, p, X, Y):
     return L, g
 
 
-@pytest.mark.parametrize("nx,ny,n", [(64, 64, 3), (128, 8, 2), (192, 16, 1)])
+@pytest.mark.parametrize("nx,ny,n", [(64, 64, 3), (128, 16, 2), (192, 16, 1)])
 def test_tcgen05_training_matches_oracle(nx, ny, n):
-    # training on tcgen05: tiles of 4 rows x 64 pixels (one, two or three
-    # across), three column-shift stages per tile, weight gradients with tap
-    # pairs on M/N-major operands; the forward output as well
+    # training on tcgen05: forward and data passes over tiles of 16 rows x 8
+    # pixels (8, 16 or 24 across), weight gradients over tiles of 4 rows x 64
+    # pixels with tap pairs on M/N-major operands; the forward output as well
     sur, p = _net(nx=nx, ny=ny, seed=31)
     assert sur.uses_tcgen05_training()
     assert sur.uses_tcgen05() == (nx % 128 == 0)
@@ -340,9 +340,10 @@ def test_tcgen05_training_matches_oracle(nx, ny, n):
 
 
 def test_tcgen05_training_many_tiles_per_cta_match_mma_sync():
-    # 24 fields of 64 x 64: 384 tiles, two or three per CTA of the data passes
-    # (every shared-memory stage and both accumulator sets reused) and of the
-    # weight gradients; the same gradients on the mma.sync path
+    # 24 fields of 64 x 64: 768 tiles of the forward and data passes (five or
+    # six per CTA: every shared-memory stage and both accumulator sets
+    # reused) and 384 of the weight gradients; the same gradients on the
+    # mma.sync path
     sur, p = _net(nx=64, ny=64, seed=34)
     X = _fields(24, 64, 64, 35)
     Y = X + (_fields(24, 64, 64, 36) * np.array([0.05, 0.1, 0.1], np.float32)[None, :, None, None]).astype(np.float32)
@@ -359,10 +360,10 @@ def test_tcgen05_training_many_tiles_per_cta_match_mma_sync():
 
 
 def test_tcgen05_training_forward_is_bitwise_translation_equivariant():
-    # a shift by whole tiles (4 rows, 64 columns) moves every tile's work unchanged
+    # a shift by whole tiles (16 rows) moves every tile's work unchanged
     sur, _ = _net(nx=64, ny=64, seed=37)
     assert not sur.uses_tcgen05() and sur.uses_tcgen05_training()
     V = _fields(2, 64, 64, 39)
     a = sur.apply(V)
-    b = sur.apply(np.ascontiguousarray(np.roll(V, 8, axis=2)))
-    assert np.array_equal(np.roll(a, 8, axis=2), b)
+    b = sur.apply(np.ascontiguousarray(np.roll(V, 16, axis=2)))
+    assert np.array_equal(np.roll(a, 16, axis=2), b)
