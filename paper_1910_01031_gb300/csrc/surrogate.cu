@@ -10,6 +10,7 @@
 // Tensor layout: activations NHWC [batch][ny][nx][C] bf16 with C = 16
 // (network input, 3 used) or 64; weights [tap = 3 ky + kx][cout][cin] bf16.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -664,14 +665,14 @@ cudaError_t conv_setup(int* per_sm)
     const size_t sm = conv_smem<CIN, COUT, MODE>();
     cudaError_t e = tc::smem_attr_once<conv_kernel<CIN, COUT, MODE>>((int)sm);
     if (e != cudaSuccess) return e;
-    static int per_dev[64] = {0};
+    static std::atomic<int> per_dev[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    int per = dev < 64 ? per_dev[dev] : 0;
+    int per = dev < 64 ? per_dev[dev].load(std::memory_order_relaxed) : 0;
     if (per == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conv_kernel<CIN, COUT, MODE>, CONV_THREADS, sm);
         per = std::max(per, 1);
-        if (dev < 64) per_dev[dev] = per;
+        if (dev < 64) per_dev[dev].store(per, std::memory_order_relaxed);
     }
     if (per_sm) *per_sm = per;
     return cudaSuccess;

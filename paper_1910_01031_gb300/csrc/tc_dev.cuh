@@ -2,6 +2,7 @@
 // memory matrix descriptors, the instruction descriptor of a BF16 x BF16 ->
 // FP32 product, bounded mbarrier waits and tensor-memory loads.
 #pragma once
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -10,30 +11,34 @@ namespace iewpf {
 namespace tc {
 
 // host: the dynamic shared-memory limit of kernel K, set once per device
+// (setting it twice from two threads is harmless)
 template <auto K>
 inline cudaError_t smem_attr_once(int bytes)
 {
-    static unsigned long long done = 0;     // bit d: set on device d
+    static std::atomic<unsigned long long> done{0};     // bit d: set on device d
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
+    if (dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
     e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+    if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev, std::memory_order_release);
     return e;
 }
 
 // host: SM count of the current device (cached per device)
 inline int sm_count()
 {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (dev < 64 && cache[dev] > 0) return cache[dev];
+    if (dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms < 1) sms = 1;
-    if (dev < 64) cache[dev] = sms;
+    if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
 }
 
