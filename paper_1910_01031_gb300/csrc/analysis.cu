@@ -67,10 +67,11 @@ cholesky_small_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, i
 __global__ void solve_kernel(const double* __restrict__ L, const int* __restrict__ colptr,
                              const int* __restrict__ rowidx, const double* __restrict__ rdiag,
                              const int* __restrict__ plan, int n, const double* __restrict__ d,
-                             double* __restrict__ x, double* __restrict__ phi, int ne)
+                             double* __restrict__ x, double* __restrict__ phi, int ne, const int* __restrict__ perm,
+                             double* __restrict__ scratch)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp < ne) ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, warp);
+    if (warp < ne) ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, warp, perm, scratch);
 }
 
 __global__ void __launch_bounds__(ana::DOT_THREADS)
@@ -238,11 +239,13 @@ cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* fla
 }
 
 cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, const double* rdiag, const int* plan,
-                         int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st)
+                         int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st, const int* perm,
+                         double* scratch)
 {
+    if (perm && !scratch) return cudaErrorInvalidValue;
     const int threads = 128;
     const int blocks = (ne * 32 + threads - 1) / threads;
-    solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi, ne);
+    solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi, ne, perm, scratch);
     return cudaGetLastError();
 }
 
@@ -337,6 +340,96 @@ void block_levels(const int* block0, int nobs, int nRx, int nRy, std::vector<int
     order.assign(nobs, 0);
     std::vector<int> fill(level_off.begin(), level_off.end() - 1);
     for (int l = 0; l < nobs; ++l) order[fill[level[l]]++] = l;
+}
+
+namespace {
+
+// breadth-first levels from `root` over the nodes with mark[v] == stamp;
+// returns the levels (lists of nodes) and sets dist[v] for the reached ones
+std::vector<std::vector<int>> bfs_levels(const std::vector<std::vector<int>>& adj, const std::vector<int>& mark,
+                                         int stamp, int root, std::vector<int>& dist)
+{
+    std::vector<std::vector<int>> lev;
+    lev.push_back({root});
+    dist[root] = 0;
+    for (;;) {
+        std::vector<int> next;
+        for (int v : lev.back())
+            for (int w : adj[v])
+                if (mark[w] == stamp && dist[w] < 0) {
+                    dist[w] = (int)lev.size();
+                    next.push_back(w);
+                }
+        if (next.empty()) break;
+        lev.push_back(std::move(next));
+    }
+    return lev;
+}
+
+void nd_rec(const std::vector<std::vector<int>>& adj, std::vector<int> nodes, std::vector<int>& mark, int& stamp,
+            std::vector<int>& dist, std::vector<int>& out)
+{
+    if (nodes.size() <= 32) {
+        out.insert(out.end(), nodes.begin(), nodes.end());
+        return;
+    }
+    ++stamp;
+    for (int v : nodes) {
+        mark[v] = stamp;
+        dist[v] = -1;
+    }
+    // a far node of the component of nodes[0]: the last level of a search from it
+    std::vector<std::vector<int>> lev = bfs_levels(adj, mark, stamp, nodes[0], dist);
+    const int far = lev.back().front();
+    for (int v : nodes) dist[v] = -1;
+    lev = bfs_levels(adj, mark, stamp, far, dist);
+    std::vector<int> rest;                                  // other components
+    for (int v : nodes)
+        if (dist[v] < 0) rest.push_back(v);
+    const int D = (int)lev.size();
+    if (D < 3) {
+        // too shallow to split: this component as it is, then the rest
+        for (const auto& l : lev) out.insert(out.end(), l.begin(), l.end());
+        if (!rest.empty()) nd_rec(adj, rest, mark, stamp, dist, out);
+        return;
+    }
+    size_t reached = 0;
+    for (const auto& l : lev) reached += l.size();
+    int m = 1;
+    size_t below = lev[0].size();
+    while (m < D - 2 && below + lev[m].size() < reached / 2) below += lev[m++].size();
+    std::vector<int> a, b;
+    for (int k = 0; k < m; ++k) a.insert(a.end(), lev[k].begin(), lev[k].end());
+    for (int k = m + 1; k < D; ++k) b.insert(b.end(), lev[k].begin(), lev[k].end());
+    const std::vector<int> sep = lev[m];
+    nd_rec(adj, a, mark, stamp, dist, out);
+    nd_rec(adj, b, mark, stamp, dist, out);
+    if (!rest.empty()) nd_rec(adj, rest, mark, stamp, dist, out);
+    out.insert(out.end(), sep.begin(), sep.end());
+}
+
+}  // namespace
+
+void nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector<int>& order)
+{
+    auto near = [&](int d, int n) {
+        d = d < 0 ? -d : d;
+        d %= n;
+        return std::min(d, n - d) <= reach;
+    };
+    std::vector<std::vector<int>> adj(nobs);
+    for (int k = 0; k < nobs; ++k)
+        for (int l = k + 1; l < nobs; ++l)
+            if (near(cells[2 * k] - cells[2 * l], nx) && near(cells[2 * k + 1] - cells[2 * l + 1], ny)) {
+                adj[k].push_back(l);
+                adj[l].push_back(k);
+            }
+    std::vector<int> nodes(nobs), mark(nobs, 0), dist(nobs, -1);
+    for (int k = 0; k < nobs; ++k) nodes[k] = k;
+    int stamp = 0;
+    order.clear();
+    order.reserve(nobs);
+    nd_rec(adj, nodes, mark, stamp, dist, order);
 }
 
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,

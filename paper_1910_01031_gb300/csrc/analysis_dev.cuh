@@ -352,15 +352,22 @@ __device__ __forceinline__ void solve_plan_cta(const double* __restrict__ L, int
 // level schedule: a level of at least 8 rows gives one row per lane (the
 // row's sum in column order), a smaller one the whole warp to each row
 // (lane-strided partial sums, then the warp sum)
+// perm (may be null): the factor is that of P A P^T with unknown i of the
+// factored system = unknown perm[i] of the observations; the sweeps then run
+// in that order in scratch (n doubles per particle), d is read through perm
+// and the result written back through it
 __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, const int* __restrict__ colptr,
                                                   const int* __restrict__ rowidx, const double* __restrict__ rdiag,
                                                   const int* plan_base, int n, const double* __restrict__ d,
-                                                  double* __restrict__ x, double* __restrict__ phi, int w)
+                                                  double* __restrict__ x, double* __restrict__ phi, int w,
+                                                  const int* __restrict__ perm = nullptr,
+                                                  double* __restrict__ scratch = nullptr)
 {
     const SolvePlan P = solve_plan_view(const_cast<int*>(plan_base), n);
     const int lane = threadIdx.x & 31;
-    double* xp = x + (long long)w * n;
+    double* xp = (perm ? scratch : x) + (long long)w * n;
     const double* dp = d + (long long)w * n;
+    auto dval = [&](int i) { return perm ? dp[perm[i]] : dp[i]; };
     // forward: y_i = (d_i - sum_j L_ij y_j) / L_ii
     const int nf = P.nlev[0];
     for (int l = 0; l < nf; ++l) {
@@ -373,7 +380,7 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
                     const int j = P.colidx[q];
                     acc = fma(L[(long long)i * n + j], xp[j], acc);
                 }
-                xp[i] = (dp[i] - acc) * rdiag[i];
+                xp[i] = (dval(i) - acc) * rdiag[i];
             }
         } else {
             for (int t = a; t < b; ++t) {
@@ -384,7 +391,7 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
                     acc = fma(L[(long long)i * n + j], xp[j], acc);
                 }
                 acc = warp_sum(acc);
-                if (lane == 0) xp[i] = (dp[i] - acc) * rdiag[i];
+                if (lane == 0) xp[i] = (dval(i) - acc) * rdiag[i];
             }
         }
         __syncwarp();
@@ -419,9 +426,13 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
         __syncwarp();
     }
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) acc = fma(dp[i], xp[i], acc);
+    for (int i = lane; i < n; i += 32) acc = fma(dval(i), xp[i], acc);
     acc = warp_sum(acc);
     if (lane == 0) phi[w] = acc;
+    if (perm) {
+        double* out = x + (long long)w * n;
+        for (int i = lane; i < n; i += 32) out[perm[i]] = xp[i];
+    }
 }
 
 constexpr int DOT_THREADS = 256;

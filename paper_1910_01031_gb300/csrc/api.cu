@@ -84,6 +84,13 @@ struct iewpf_ctx {
     // no coarse point (block_levels), applied one level per launch
     int* d_border = nullptr;
     std::vector<int> blevel_off;
+    // fixed layouts of many observations: the factor is that of P A P^T in a
+    // nested-dissection order (d_perm_u: unknown i of the factor = unknown
+    // d_perm_u[i] of the observations; d_cell_perm: the cells in that order;
+    // d_xs: [ne][N_y] solve scratch); null for drifters and small layouts
+    int* d_perm_u = nullptr;
+    int* d_cell_perm = nullptr;
+    double* d_xs = nullptr;
     int ntiles = 0;
     int tile_cap = MAX_TILE_OBS;
     int* d_tile_cnt = nullptr;
@@ -447,7 +454,8 @@ int check_flags(iewpf_ctx* ctx, int f)
 int factor(iewpf_ctx* ctx, int nobs)
 {
     const int n = 2 * nobs;
-    KL(1, launch_hqht(ctx->d_K64, ctx->R, ctx->d_cell, nobs, ctx->G, ctx->P.dense_S,
+    KL(1, launch_hqht(ctx->d_K64, ctx->R, ctx->d_cell_perm ? ctx->d_cell_perm : ctx->d_cell, nobs, ctx->G,
+                      ctx->P.dense_S,
                    ctx->P.obs_sigma * ctx->P.obs_sigma, ctx->d_L, ctx->st));
     KL(1, launch_cholesky(ctx->d_L, n, ctx->d_colptr, ctx->d_rowidx, ctx->flag, ctx->d_rdiag, ctx->d_plan, ctx->st));
     ctx->n_fact = n;
@@ -852,9 +860,32 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
     if (P.n_drifters_max > 0 && (rc = dalloc(ctx, &ctx->d_xy, ne * 2 * (size_t)P.n_drifters_max)))
         return bail(rc);
     if (P.obs_kind == IEWPF_OBS_MOORING && nobs > 0) {
-        if ((rc = upload_obs_layout(ctx, mooring_xy, nobs)) || (rc = factor(ctx, nobs)) ||
-            (rc = read_flags(ctx)))
-            return bail(rc);
+        if ((rc = upload_obs_layout(ctx, mooring_xy, nobs))) return bail(rc);
+        if (nobs >= kNdMinObs) {
+            // many fixed observations: factor in a nested-dissection order of
+            // their coupling graph (wide levels for the triangular sweeps)
+            std::vector<int> cells(2 * (size_t)nobs), order;
+            if (cudaMemcpy(cells.data(), ctx->d_cell, sizeof(int) * 2 * nobs, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return bail(IEWPF_ECUDA);
+            nd_order(cells.data(), nobs, ctx->G.nx, ctx->G.ny, ctx->R, order);
+            std::vector<int> perm_u(2 * (size_t)nobs), cells_p(2 * (size_t)nobs);
+            for (int i = 0; i < nobs; ++i) {
+                perm_u[2 * i] = 2 * order[i];
+                perm_u[2 * i + 1] = 2 * order[i] + 1;
+                cells_p[2 * i] = cells[2 * order[i]];
+                cells_p[2 * i + 1] = cells[2 * order[i] + 1];
+            }
+            if ((rc = dalloc(ctx, &ctx->d_perm_u, 2 * (size_t)nobs)) ||
+                (rc = dalloc(ctx, &ctx->d_cell_perm, 2 * (size_t)nobs)) ||
+                (rc = dalloc(ctx, &ctx->d_xs, (size_t)ne * 2 * nobs)))
+                return bail(rc);
+            if (cudaMemcpy(ctx->d_perm_u, perm_u.data(), sizeof(int) * 2 * nobs, cudaMemcpyHostToDevice) !=
+                    cudaSuccess ||
+                cudaMemcpy(ctx->d_cell_perm, cells_p.data(), sizeof(int) * 2 * nobs, cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                return bail(IEWPF_ECUDA);
+        }
+        if ((rc = factor(ctx, nobs)) || (rc = read_flags(ctx))) return bail(rc);
         ctx->factored = true;
         // levels of the local blocks of the fixed layout
         std::vector<int> b0(2 * (size_t)nobs), order;
@@ -876,7 +907,8 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     void* ptrs[] = {ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->amax, ctx->maxsub, ctx->flag, ctx->work,
                     ctx->d_wtab, ctx->d_K32, ctx->d_K64, ctx->d_M49, ctx->d_xy, ctx->d_obs_xy, ctx->d_obs_y,
-                    ctx->d_cell, ctx->d_block0, ctx->d_border, ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
+                    ctx->d_cell, ctx->d_block0, ctx->d_border, ctx->d_perm_u, ctx->d_cell_perm, ctx->d_xs,
+                    ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
                     ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
                     ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
                     ctx->d_r, ctx->d_xi, ctx->d_soar};
@@ -987,7 +1019,7 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
                            ctx->P.H_eq, ctx->d_d, ctx->st));
         if (!mooring && (rc = factor(ctx, nobs))) return rc;
         KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, n, ctx->d_d, ctx->d_Sd,
-                           ctx->d_phi, ne, ctx->st));
+                           ctx->d_phi, ne, ctx->st, ctx->d_perm_u, ctx->d_xs));
     }
     // 3: random vectors
     Phase sub_("weights_and_update");
@@ -1718,6 +1750,8 @@ int iewpf_batch_create(const iewpf_params_t* params, const double* const* moorin
         I.plan = ctx->d_plan;
         I.colptr = ctx->d_colptr;
         I.rowidx = ctx->d_rowidx;
+        I.perm = ctx->d_perm_u;
+        I.xs = ctx->d_xs;
         I.d = ctx->d_d;
         I.Sd = ctx->d_Sd;
         I.phi = ctx->d_phi;

@@ -48,6 +48,8 @@ struct BInst {
     int* rowidx;
     double* rdiag;              // level-scheduled solves (ana::solve_plan_cta)
     int* plan;
+    const int* perm;            // elimination order of the factor (null: observation order)
+    double* xs;                 // [ne][2 nobs] solve scratch when perm is set
     double* d;
     double* Sd;
     double* phi;

@@ -22,6 +22,8 @@ cudaError_t launch_par_update(int* par, const int* nsub, int ne, unsigned long l
 // every step advance it and keep looping while it is below the largest n_sub
 // (and below kMaxSubSingle); the model-step counter of the model error
 constexpr int kMaxSubSingle = 100000;
+// fixed observation layouts from this size on are factored in a nested-dissection order
+constexpr int kNdMinObs = 256;
 cudaError_t launch_step_reset(int* s_dev, cudaStream_t st);
 cudaError_t launch_step_ctl(int* s_dev, const int* maxsub, cudaGraphConditionalHandle h, unsigned int* iters,
                             cudaStream_t st);
@@ -136,8 +138,10 @@ __host__ __device__ inline size_t solve_plan_ints(int n)
 // triangular sweeps (plan: ana::solve_plan_ints(n) ints)
 cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, double* rdiag, int* plan,
                             cudaStream_t st);
+// perm, scratch: see ana::solve_levels_warp (both null: observation order)
 cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, const double* rdiag, const int* plan,
-                         int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st);
+                         int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st,
+                         const int* perm = nullptr, double* scratch = nullptr);
 cudaError_t launch_rand_dots(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
                              double* partial, int nblk, cudaStream_t st);
 int rand_dots_blocks(int NR);
@@ -167,6 +171,13 @@ cudaError_t launch_block_level(float* r, int NR, int ne, const float* M49, const
 // within a level); level_off[v] .. level_off[v + 1] = the range of level v.
 void block_levels(const int* block0, int nobs, int nRx, int nRy, std::vector<int>& order,
                   std::vector<int>& level_off);
+// host: a nested-dissection elimination order of the observations (cells
+// [nobs][2] on the periodic nx x ny grid; two observations are coupled when
+// their cells are at most `reach` cells apart in both directions, minimum
+// image): recursive bisection of the coupling graph by breadth-first level
+// sets, each separator ordered after the two parts it separates.  order[k] =
+// the observation eliminated k-th.
+void nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector<int>& order);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,
                                  uint32_t* out, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n, double* o64,

@@ -87,7 +87,7 @@ def _mooring_analysis_full_size(cfg, cells, sample, coupled):
     n, nnz = ens.factor_info()
     assert n == 2 * len(cells)
     if coupled:
-        assert nnz > 100 * n        # the factor fills in between neighbouring moorings
+        assert nnz > 20 * n         # the factor fills in between neighbouring moorings
     else:
         assert nnz == n // 2        # 2 x 2 blocks: the moorings do not interact
     ens.set_state(U)
