@@ -410,8 +410,9 @@ void nd_rec(const std::vector<std::vector<int>>& adj, std::vector<int> nodes, st
 
 }  // namespace
 
-void nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector<int>& order)
+long long nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector<int>& order)
 {
+    long long pairs = 0;
     auto near = [&](int d, int n) {
         d = d < 0 ? -d : d;
         d %= n;
@@ -423,6 +424,7 @@ void nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector
             if (near(cells[2 * k] - cells[2 * l], nx) && near(cells[2 * k + 1] - cells[2 * l + 1], ny)) {
                 adj[k].push_back(l);
                 adj[l].push_back(k);
+                ++pairs;
             }
     std::vector<int> nodes(nobs), mark(nobs, 0), dist(nobs, -1);
     for (int k = 0; k < nobs; ++k) nodes[k] = k;
@@ -430,6 +432,7 @@ void nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector
     order.clear();
     order.reserve(nobs);
     nd_rec(adj, nodes, mark, stamp, dist, order);
+    return pairs;
 }
 
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,

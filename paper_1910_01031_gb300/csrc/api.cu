@@ -867,7 +867,8 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
             std::vector<int> cells(2 * (size_t)nobs), order;
             if (cudaMemcpy(cells.data(), ctx->d_cell, sizeof(int) * 2 * nobs, cudaMemcpyDeviceToHost) != cudaSuccess)
                 return bail(IEWPF_ECUDA);
-            nd_order(cells.data(), nobs, ctx->G.nx, ctx->G.ny, ctx->R, order);
+            // (no coupled pair: the factor is 2 x 2 blocks in any order)
+            const bool coupled = nd_order(cells.data(), nobs, ctx->G.nx, ctx->G.ny, ctx->R, order) > 0;
             std::vector<int> perm_u(2 * (size_t)nobs), cells_p(2 * (size_t)nobs);
             for (int i = 0; i < nobs; ++i) {
                 perm_u[2 * i] = 2 * order[i];
@@ -875,14 +876,15 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
                 cells_p[2 * i] = cells[2 * order[i]];
                 cells_p[2 * i + 1] = cells[2 * order[i] + 1];
             }
-            if ((rc = dalloc(ctx, &ctx->d_perm_u, 2 * (size_t)nobs)) ||
-                (rc = dalloc(ctx, &ctx->d_cell_perm, 2 * (size_t)nobs)) ||
-                (rc = dalloc(ctx, &ctx->d_xs, (size_t)ne * 2 * nobs)))
+            if (coupled && ((rc = dalloc(ctx, &ctx->d_perm_u, 2 * (size_t)nobs)) ||
+                            (rc = dalloc(ctx, &ctx->d_cell_perm, 2 * (size_t)nobs)) ||
+                            (rc = dalloc(ctx, &ctx->d_xs, (size_t)ne * 2 * nobs))))
                 return bail(rc);
-            if (cudaMemcpy(ctx->d_perm_u, perm_u.data(), sizeof(int) * 2 * nobs, cudaMemcpyHostToDevice) !=
-                    cudaSuccess ||
-                cudaMemcpy(ctx->d_cell_perm, cells_p.data(), sizeof(int) * 2 * nobs, cudaMemcpyHostToDevice) !=
-                    cudaSuccess)
+            if (coupled &&
+                (cudaMemcpy(ctx->d_perm_u, perm_u.data(), sizeof(int) * 2 * nobs, cudaMemcpyHostToDevice) !=
+                     cudaSuccess ||
+                 cudaMemcpy(ctx->d_cell_perm, cells_p.data(), sizeof(int) * 2 * nobs, cudaMemcpyHostToDevice) !=
+                     cudaSuccess))
                 return bail(IEWPF_ECUDA);
         }
         if ((rc = factor(ctx, nobs)) || (rc = read_flags(ctx))) return bail(rc);

@@ -176,8 +176,8 @@ void block_levels(const int* block0, int nobs, int nRx, int nRy, std::vector<int
 // their cells are at most `reach` cells apart in both directions, minimum
 // image): recursive bisection of the coupling graph by breadth-first level
 // sets, each separator ordered after the two parts it separates.  order[k] =
-// the observation eliminated k-th.
-void nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector<int>& order);
+// the observation eliminated k-th.  Returns the number of coupled pairs.
+long long nd_order(const int* cells, int nobs, int nx, int ny, int reach, std::vector<int>& order);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n,
                                  uint32_t* out, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t p, uint32_t t, uint32_t stream, long long n, double* o64,
