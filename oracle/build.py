@@ -1,7 +1,7 @@
 """Build the FP64 oracle shared library (test infrastructure only).
 
-The oracle is plain C compiled with gcc; it is the checker that the CUDA path
-is compared against, never a fallback for it.  Only tests/,
+The oracle is plain C compiled with gcc; it is the FP64 reference the CUDA
+path is compared against, never a fallback for it.  Only tests/,
 __graft_entry__.smoke() and bench.py's cpu_baseline leg may load it.
 """
 import os
