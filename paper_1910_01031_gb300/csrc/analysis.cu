@@ -111,20 +111,19 @@ __global__ void block_seq_kernel(float* __restrict__ r, int NR, const float* __r
     ana::block_seq_cta(r, NR, M49, block0, nobs, nRx, nRy, blockIdx.x);
 }
 
-// one level of blocks: warp w of the grid takes tasks (block, chunk of
-// BL_CHUNK particles) w, w + warps, ...: the block's 49 indices once per task,
-// then per particle lane t computes outputs t and t + 32 (< 49) with the FMA
-// order of block_seq_cta, its two rows of the 49 x 49 root held in registers
-// for all the warp's tasks, and the next particle's values loaded before the
-// current product
-constexpr int BL_CHUNK = 32;
-__global__ void __launch_bounds__(256, 2) block_level_kernel(float* __restrict__ r, int NR, int ne,
-                                                             const float* __restrict__ M49,
-                                                             const int* __restrict__ block0,
-                                                             const int* __restrict__ order, int lo, int nblk, int nRx,
-                                                             int nRy)
+// all levels of the local blocks of particle blockIdx.x: the CTA's warps
+// share the blocks of a level, a barrier separates the levels; lane t
+// computes outputs t and t + 32 (< 49) with the FMA order of block_seq_cta,
+// its two rows of the 49 x 49 root held in registers
+constexpr int BL_THREADS = 64;
+__global__ void __launch_bounds__(BL_THREADS) block_levels_kernel(float* __restrict__ r, int NR,
+                                                                  const float* __restrict__ M49,
+                                                                  const int* __restrict__ block0,
+                                                                  const int* __restrict__ order,
+                                                                  const int* __restrict__ level_off, int nlev,
+                                                                  int nRx, int nRy)
 {
-    __shared__ float v[8][49];
+    __shared__ float v[BL_THREADS / 32][49];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const bool two = lane + 32 < 49;
     float m0[49], m1[49];
@@ -133,26 +132,17 @@ __global__ void __launch_bounds__(256, 2) block_level_kernel(float* __restrict__
         m0[j] = __ldg(M49 + lane * 49 + j);
         m1[j] = two ? __ldg(M49 + (lane + 32) * 49 + j) : 0.0f;
     }
-    const int chunks = (ne + BL_CHUNK - 1) / BL_CHUNK;
-    const long long tasks = (long long)nblk * chunks;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long task = (long long)blockIdx.x * (blockDim.x >> 5) + wl; task < tasks; task += warps) {
-        const int ib = (int)(task / chunks), c = (int)(task - (long long)ib * chunks);
-        const int l = order[lo + ib];
-        const int cx = block0[2 * l], cy = block0[2 * l + 1];
-        const int i0 = pmod(cy + lane / 7 - 3, nRy) * nRx + pmod(cx + lane % 7 - 3, nRx);
-        const int t1 = two ? lane + 32 : 48;
-        const int i1 = pmod(cy + t1 / 7 - 3, nRy) * nRx + pmod(cx + t1 % 7 - 3, nRx);
-        const int p0 = c * BL_CHUNK, p1 = min(ne, p0 + BL_CHUNK);
-        float* rp = r + (long long)p0 * NR;
-        float x0 = rp[i0], x1 = two ? rp[i1] : 0.0f;
-        for (int p = p0; p < p1; ++p, rp += NR) {
-            v[wl][lane] = x0;
-            if (two) v[wl][lane + 32] = x1;
-            if (p + 1 < p1) {
-                x0 = rp[NR + i0];
-                if (two) x1 = rp[NR + i1];
-            }
+    float* rp = r + (long long)blockIdx.x * NR;
+    for (int lev = 0; lev < nlev; ++lev) {
+        const int lo = level_off[lev], hi = level_off[lev + 1];
+        for (int ib = lo + wl; ib < hi; ib += BL_THREADS / 32) {
+            const int l = order[ib];
+            const int cx = block0[2 * l], cy = block0[2 * l + 1];
+            const int i0 = pmod(cy + lane / 7 - 3, nRy) * nRx + pmod(cx + lane % 7 - 3, nRx);
+            const int t1 = two ? lane + 32 : 48;
+            const int i1 = pmod(cy + t1 / 7 - 3, nRy) * nRx + pmod(cx + t1 % 7 - 3, nRx);
+            v[wl][lane] = rp[i0];
+            if (two) v[wl][lane + 32] = rp[i1];
             __syncwarp();
             float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
@@ -165,6 +155,7 @@ __global__ void __launch_bounds__(256, 2) block_level_kernel(float* __restrict__
             rp[i0] = a0;
             if (two) rp[i1] = a1;
         }
+        __syncthreads();     // the next level reads what this one wrote
     }
 }
 
@@ -299,17 +290,11 @@ cudaError_t launch_block_seq(float* r, int NR, int ne, const float* M49, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_level(float* r, int NR, int ne, const float* M49, const int* obs_block0, const int* order,
-                               int lo, int hi, int nRx, int nRy, cudaStream_t st)
+cudaError_t launch_block_levels(float* r, int NR, int ne, const float* M49, const int* obs_block0, const int* order,
+                                const int* level_off, int nlev, int nRx, int nRy, cudaStream_t st)
 {
-    const int nblk = hi - lo;
-    if (nblk <= 0 || ne <= 0) return cudaSuccess;
-    const long long warps = (long long)nblk * ((ne + BL_CHUNK - 1) / BL_CHUNK);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long grid = std::min<long long>((warps + 7) / 8, (long long)std::max(sms, 1) * 8);
-    block_level_kernel<<<(unsigned)grid, 256, 0, st>>>(r, NR, ne, M49, obs_block0, order, lo, nblk, nRx, nRy);
+    if (nlev <= 0 || ne <= 0) return cudaSuccess;
+    block_levels_kernel<<<ne, BL_THREADS, 0, st>>>(r, NR, M49, obs_block0, order, level_off, nlev, nRx, nRy);
     return cudaGetLastError();
 }
 

@@ -83,7 +83,8 @@ struct iewpf_ctx {
     // fixed (mooring) layouts: the local blocks in levels of blocks that share
     // no coarse point (block_levels), applied one level per launch
     int* d_border = nullptr;
-    std::vector<int> blevel_off;
+    int* d_blevel = nullptr;     // level offsets of d_border (nblev + 1)
+    int nblev = 0;
     // fixed layouts of many observations: the factor is that of P A P^T in a
     // nested-dissection order (d_perm_u: unknown i of the factor = unknown
     // d_perm_u[i] of the observations; d_cell_perm: the cells in that order;
@@ -893,9 +894,13 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
         std::vector<int> b0(2 * (size_t)nobs), order;
         if (cudaMemcpy(b0.data(), ctx->d_block0, sizeof(int) * 2 * nobs, cudaMemcpyDeviceToHost) != cudaSuccess)
             return bail(IEWPF_ECUDA);
-        block_levels(b0.data(), nobs, ctx->C.nRx, ctx->C.nRy, order, ctx->blevel_off);
-        if ((rc = dalloc(ctx, &ctx->d_border, nobs)) ||
-            cudaMemcpy(ctx->d_border, order.data(), sizeof(int) * nobs, cudaMemcpyHostToDevice) != cudaSuccess)
+        std::vector<int> level_off;
+        block_levels(b0.data(), nobs, ctx->C.nRx, ctx->C.nRy, order, level_off);
+        ctx->nblev = (int)level_off.size() - 1;
+        if ((rc = dalloc(ctx, &ctx->d_border, nobs)) || (rc = dalloc(ctx, &ctx->d_blevel, level_off.size())) ||
+            cudaMemcpy(ctx->d_border, order.data(), sizeof(int) * nobs, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->d_blevel, level_off.data(), sizeof(int) * level_off.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
             return bail(rc ? rc : IEWPF_ECUDA);
     }
     *out = ctx;
@@ -909,7 +914,7 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     void* ptrs[] = {ctx->buf[0], ctx->buf[1], ctx->par, ctx->nsub, ctx->dtp, ctx->amax, ctx->maxsub, ctx->flag, ctx->work,
                     ctx->d_wtab, ctx->d_K32, ctx->d_K64, ctx->d_M49, ctx->d_xy, ctx->d_obs_xy, ctx->d_obs_y,
-                    ctx->d_cell, ctx->d_block0, ctx->d_border, ctx->d_perm_u, ctx->d_cell_perm, ctx->d_xs,
+                    ctx->d_cell, ctx->d_block0, ctx->d_border, ctx->d_blevel, ctx->d_perm_u, ctx->d_cell_perm, ctx->d_xs,
                     ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
                     ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
                     ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
@@ -1035,10 +1040,9 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
     // 6: posterior coarse field, local block roots, fused update with the pull
     KL(1, launch_form_r(ctx->P.seed, ctx->cycle, sb + 1, sb + 2, (int)ctx->NR, ne, ctx->d_coef, ctx->d_scal,
                      ctx->d_alpha, ctx->d_r, ctx->st));
-    if (mooring && !ctx->blevel_off.empty()) {
-        for (size_t v = 0; v + 1 < ctx->blevel_off.size(); ++v)
-            KL(1, launch_block_level(ctx->d_r, (int)ctx->NR, ne, ctx->d_M49, ctx->d_block0, ctx->d_border,
-                                     ctx->blevel_off[v], ctx->blevel_off[v + 1], ctx->C.nRx, ctx->C.nRy, ctx->st));
+    if (mooring && ctx->nblev > 0) {
+        KL(1, launch_block_levels(ctx->d_r, (int)ctx->NR, ne, ctx->d_M49, ctx->d_block0, ctx->d_border, ctx->d_blevel,
+                                  ctx->nblev, ctx->C.nRx, ctx->C.nRy, ctx->st));
     } else {
         KL(1, launch_block_seq(ctx->d_r, (int)ctx->NR, ne, ctx->d_M49, ctx->d_block0, nobs, ctx->C.nRx, ctx->C.nRy,
                                ctx->st));

@@ -158,12 +158,12 @@ cudaError_t launch_form_r(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_n
                           cudaStream_t st);
 cudaError_t launch_block_seq(float* r, int NR, int ne, const float* M49, const int* obs_block0, int nobs, int nRx,
                              int nRy, cudaStream_t st);
-// the same product for blocks order[lo..hi) that pairwise share no coarse
-// point (one level of block_levels), all particles at once: a warp per
-// (particle, block), the same arithmetic as block_seq, so a sequence of
-// levels gives block_seq's result bit for bit
-cudaError_t launch_block_level(float* r, int NR, int ne, const float* M49, const int* obs_block0, const int* order,
-                               int lo, int hi, int nRx, int nRy, cudaStream_t st);
+// the same products level by level (block_levels: order and level_off in
+// device memory, nlev levels; the blocks of a level pairwise share no coarse
+// point), one CTA per particle whose warps share each level's blocks, the
+// same arithmetic as block_seq, so the result is block_seq's bit for bit
+cudaError_t launch_block_levels(float* r, int NR, int ne, const float* M49, const int* obs_block0, const int* order,
+                                const int* level_off, int nlev, int nRx, int nRy, cudaStream_t st);
 // host: level of each block (0 when it shares no coarse point with an earlier
 // block, else one more than the highest level among the earlier blocks it
 // overlaps; blocks are 7 x 7 coarse points around block0 on the periodic
