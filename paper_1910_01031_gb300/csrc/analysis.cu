@@ -64,14 +64,30 @@ cholesky_small_kernel(double* __restrict__ A, int n, int* __restrict__ colptr, i
     if (threadIdx.x == 0 && bad) atomicOr(flag, FLAG_NOTPD);
 }
 
+// the factor's values below the diagonal in the order of the plan's CSR (Lr)
+// and of the CSC (Lc): a warp per row and per column of the dense factor
+__global__ void pack_factor_kernel(const double* __restrict__ L, int n, const int* __restrict__ colptr,
+                                   const int* __restrict__ rowidx, const int* plan, double* __restrict__ Lr,
+                                   double* __restrict__ Lc)
+{
+    const ana::SolvePlan P = ana::solve_plan_view(const_cast<int*>(plan), n);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        for (int q = P.rowptr[i] + lane; q < P.rowptr[i + 1]; q += 32) Lr[q] = L[(long long)i * n + P.colidx[q]];
+        for (int q = colptr[i] + lane; q < colptr[i + 1]; q += 32) Lc[q] = L[(long long)rowidx[q] * n + i];
+    }
+}
+
 __global__ void solve_kernel(const double* __restrict__ L, const int* __restrict__ colptr,
                              const int* __restrict__ rowidx, const double* __restrict__ rdiag,
                              const int* __restrict__ plan, int n, const double* __restrict__ d,
                              double* __restrict__ x, double* __restrict__ phi, int ne, const int* __restrict__ perm,
-                             double* __restrict__ scratch)
+                             double* __restrict__ scratch, const double* __restrict__ Lr, const double* __restrict__ Lc)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp < ne) ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, warp, perm, scratch);
+    if (warp < ne)
+        ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, warp, perm, scratch, Lr, Lc);
 }
 
 __global__ void __launch_bounds__(ana::DOT_THREADS)
@@ -231,12 +247,23 @@ cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* fla
 
 cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, const double* rdiag, const int* plan,
                          int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st, const int* perm,
-                         double* scratch)
+                         double* scratch, const double* Lr, const double* Lc)
 {
-    if (perm && !scratch) return cudaErrorInvalidValue;
+    if ((perm && !scratch) || (!Lr != !Lc)) return cudaErrorInvalidValue;
     const int threads = 128;
     const int blocks = (ne * 32 + threads - 1) / threads;
-    solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi, ne, perm, scratch);
+    solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi, ne, perm, scratch, Lr,
+                                             Lc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_factor(const double* L, int n, const int* colptr, const int* rowidx, const int* plan,
+                               double* Lr, double* Lc, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = std::min((n * 32 + threads - 1) / threads, 65535);
+    pack_factor_kernel<<<blocks, threads, 0, st>>>(L, n, colptr, rowidx, plan, Lr, Lc);
     return cudaGetLastError();
 }
 

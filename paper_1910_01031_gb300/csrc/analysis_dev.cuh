@@ -356,18 +356,26 @@ __device__ __forceinline__ void solve_plan_cta(const double* __restrict__ L, int
 // factored system = unknown perm[i] of the observations; the sweeps then run
 // in that order in scratch (n doubles per particle), d is read through perm
 // and the result written back through it
+// Lr, Lc (may be null): the factor's values below the diagonal in the order
+// of the plan's CSR (colidx) and of the CSC (rowidx), so that a row's or a
+// column's products read consecutive doubles instead of scattered entries of
+// the dense factor (pack_factor_values)
 __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, const int* __restrict__ colptr,
                                                   const int* __restrict__ rowidx, const double* __restrict__ rdiag,
                                                   const int* plan_base, int n, const double* __restrict__ d,
                                                   double* __restrict__ x, double* __restrict__ phi, int w,
                                                   const int* __restrict__ perm = nullptr,
-                                                  double* __restrict__ scratch = nullptr)
+                                                  double* __restrict__ scratch = nullptr,
+                                                  const double* __restrict__ Lr = nullptr,
+                                                  const double* __restrict__ Lc = nullptr)
 {
     const SolvePlan P = solve_plan_view(const_cast<int*>(plan_base), n);
     const int lane = threadIdx.x & 31;
     double* xp = (perm ? scratch : x) + (long long)w * n;
     const double* dp = d + (long long)w * n;
     auto dval = [&](int i) { return perm ? dp[perm[i]] : dp[i]; };
+    auto lrow = [&](int q, int i, int j) { return Lr ? Lr[q] : L[(long long)i * n + j]; };
+    auto lcol = [&](int q, int k, int i) { return Lc ? Lc[q] : L[(long long)k * n + i]; };
     // forward: y_i = (d_i - sum_j L_ij y_j) / L_ii
     const int nf = P.nlev[0];
     for (int l = 0; l < nf; ++l) {
@@ -376,9 +384,10 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
             for (int t = a + lane; t < b; t += 32) {
                 const int i = P.forder[t];
                 double acc = 0.0;
+#pragma unroll 4
                 for (int q = P.rowptr[i]; q < P.rowptr[i + 1]; ++q) {
                     const int j = P.colidx[q];
-                    acc = fma(L[(long long)i * n + j], xp[j], acc);
+                    acc = fma(lrow(q, i, j), xp[j], acc);
                 }
                 xp[i] = (dval(i) - acc) * rdiag[i];
             }
@@ -386,9 +395,10 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
             for (int t = a; t < b; ++t) {
                 const int i = P.forder[t];
                 double acc = 0.0;
+#pragma unroll 4
                 for (int q = P.rowptr[i] + lane; q < P.rowptr[i + 1]; q += 32) {
                     const int j = P.colidx[q];
-                    acc = fma(L[(long long)i * n + j], xp[j], acc);
+                    acc = fma(lrow(q, i, j), xp[j], acc);
                 }
                 acc = warp_sum(acc);
                 if (lane == 0) xp[i] = (dval(i) - acc) * rdiag[i];
@@ -404,9 +414,10 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
             for (int t = a + lane; t < b; t += 32) {
                 const int i = P.border[t];
                 double acc = 0.0;
+#pragma unroll 4
                 for (int q = colptr[i]; q < colptr[i + 1]; ++q) {
                     const int k = rowidx[q];
-                    acc = fma(L[(long long)k * n + i], xp[k], acc);
+                    acc = fma(lcol(q, k, i), xp[k], acc);
                 }
                 xp[i] = (xp[i] - acc) * rdiag[i];
             }
@@ -414,9 +425,10 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
             for (int t = a; t < b; ++t) {
                 const int i = P.border[t];
                 double acc = 0.0;
+#pragma unroll 4
                 for (int q = colptr[i] + lane; q < colptr[i + 1]; q += 32) {
                     const int k = rowidx[q];
-                    acc = fma(L[(long long)k * n + i], xp[k], acc);
+                    acc = fma(lcol(q, k, i), xp[k], acc);
                 }
                 acc = warp_sum(acc);
                 __syncwarp();

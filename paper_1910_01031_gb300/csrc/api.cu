@@ -101,6 +101,10 @@ struct iewpf_ctx {
     int* d_rowidx = nullptr;
     double* d_rdiag = nullptr;  // 1 / diagonal of the factor [Ny]
     int* d_plan = nullptr;      // level schedule of the triangular sweeps (ana::SolvePlan)
+    // a fixed layout's factor values below the diagonal in the order of the
+    // plan's rows and of the CSC (launch_pack_factor); null for drifters
+    double* d_Lr = nullptr;
+    double* d_Lc = nullptr;
     double* d_d = nullptr;      // innovations [ne][Ny]
     double* d_Sd = nullptr;     // [ne][Ny]
     double* d_phi = nullptr;
@@ -889,6 +893,13 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
                 return bail(IEWPF_ECUDA);
         }
         if ((rc = factor(ctx, nobs)) || (rc = read_flags(ctx))) return bail(rc);
+        int nnz = 0;
+        if (cudaMemcpy(&nnz, ctx->d_colptr + 2 * nobs, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(IEWPF_ECUDA);
+        if ((rc = dalloc(ctx, &ctx->d_Lr, (size_t)nnz)) || (rc = dalloc(ctx, &ctx->d_Lc, (size_t)nnz))) return bail(rc);
+        if (launch_pack_factor(ctx->d_L, 2 * nobs, ctx->d_colptr, ctx->d_rowidx, ctx->d_plan, ctx->d_Lr, ctx->d_Lc,
+                               ctx->st) != cudaSuccess)
+            return bail(IEWPF_ECUDA);
         ctx->factored = true;
         // levels of the local blocks of the fixed layout
         std::vector<int> b0(2 * (size_t)nobs), order;
@@ -916,7 +927,7 @@ int iewpf_destroy(iewpf_ctx_t* ctx)
                     ctx->d_wtab, ctx->d_K32, ctx->d_K64, ctx->d_M49, ctx->d_xy, ctx->d_obs_xy, ctx->d_obs_y,
                     ctx->d_cell, ctx->d_block0, ctx->d_border, ctx->d_blevel, ctx->d_perm_u, ctx->d_cell_perm, ctx->d_xs,
                     ctx->d_tile_cnt, ctx->d_tile_obs, ctx->d_L, ctx->d_colptr,
-                    ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
+                    ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, ctx->d_Lr, ctx->d_Lc, ctx->d_d, ctx->d_Sd, ctx->d_phi, ctx->d_c, ctx->d_gamma, ctx->d_zeta,
                     ctx->d_alpha, ctx->d_cstar, ctx->d_neglogw, ctx->d_coef, ctx->d_scal, ctx->d_partial,
                     ctx->d_r, ctx->d_xi, ctx->d_soar};
     for (void* p : ptrs)
@@ -1026,7 +1037,8 @@ int iewpf_assimilate(iewpf_ctx_t* ctx, const iewpf_obs_t* obs, iewpf_diag_t* dia
                            ctx->P.H_eq, ctx->d_d, ctx->st));
         if (!mooring && (rc = factor(ctx, nobs))) return rc;
         KL(1, launch_solve(ctx->d_L, ctx->d_colptr, ctx->d_rowidx, ctx->d_rdiag, ctx->d_plan, n, ctx->d_d, ctx->d_Sd,
-                           ctx->d_phi, ne, ctx->st, ctx->d_perm_u, ctx->d_xs));
+                           ctx->d_phi, ne, ctx->st, ctx->d_perm_u, ctx->d_xs, mooring ? ctx->d_Lr : nullptr,
+                           mooring ? ctx->d_Lc : nullptr));
     }
     // 3: random vectors
     Phase sub_("weights_and_update");
@@ -1758,6 +1770,8 @@ int iewpf_batch_create(const iewpf_params_t* params, const double* const* moorin
         I.rowidx = ctx->d_rowidx;
         I.perm = ctx->d_perm_u;
         I.xs = ctx->d_xs;
+        I.Lr = ctx->d_Lr;
+        I.Lc = ctx->d_Lc;
         I.d = ctx->d_d;
         I.Sd = ctx->d_Sd;
         I.phi = ctx->d_phi;

@@ -312,7 +312,7 @@ __global__ void b_solve(BatchDev B)
         const int i = find_inst(pre, B.n, w);
         const BInst& I = B.inst[i];
         ana::solve_levels_warp(I.L, I.colptr, I.rowidx, I.rdiag, I.plan, 2 * I.nobs, I.d, I.Sd, I.phi,
-                               (int)(w - pre[i]), I.perm, I.xs);
+                               (int)(w - pre[i]), I.perm, I.xs, I.Lr, I.Lc);
     }
 }
 

@@ -50,6 +50,8 @@ struct BInst {
     int* plan;
     const int* perm;            // elimination order of the factor (null: observation order)
     double* xs;                 // [ne][2 nobs] solve scratch when perm is set
+    const double* Lr;           // packed factor values of a fixed layout (launch_pack_factor; null: dense reads)
+    const double* Lc;
     double* d;
     double* Sd;
     double* phi;

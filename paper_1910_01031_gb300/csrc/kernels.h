@@ -138,10 +138,18 @@ __host__ __device__ inline size_t solve_plan_ints(int n)
 // triangular sweeps (plan: ana::solve_plan_ints(n) ints)
 cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, double* rdiag, int* plan,
                             cudaStream_t st);
-// perm, scratch: see ana::solve_levels_warp (both null: observation order)
+// perm, scratch: see ana::solve_levels_warp (both null: observation order);
+// Lr, Lc: the packed values of launch_pack_factor (both null: the sweeps
+// read the dense factor)
 cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, const double* rdiag, const int* plan,
                          int n, const double* d, double* Sd, double* phi, int ne, cudaStream_t st,
-                         const int* perm = nullptr, double* scratch = nullptr);
+                         const int* perm = nullptr, double* scratch = nullptr, const double* Lr = nullptr,
+                         const double* Lc = nullptr);
+// after launch_cholesky: the factor's values below the diagonal in the order
+// of the plan's rows (Lr) and of the CSC (Lc), n (n - 1) / 2 doubles each at
+// most
+cudaError_t launch_pack_factor(const double* L, int n, const int* colptr, const int* rowidx, const int* plan,
+                               double* Lr, double* Lc, cudaStream_t st);
 cudaError_t launch_rand_dots(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, int ne,
                              double* partial, int nblk, cudaStream_t st);
 int rand_dots_blocks(int NR);
