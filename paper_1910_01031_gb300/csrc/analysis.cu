@@ -90,6 +90,18 @@ __global__ void solve_kernel(const double* __restrict__ L, const int* __restrict
         ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, warp, perm, scratch, Lr, Lc);
 }
 
+// the same with a CTA of one warp per particle and its vector in shared
+// memory (n doubles)
+__global__ void __launch_bounds__(32)
+solve_smem_kernel(const double* __restrict__ L, const int* __restrict__ colptr, const int* __restrict__ rowidx,
+                  const double* __restrict__ rdiag, const int* __restrict__ plan, int n, const double* __restrict__ d,
+                  double* __restrict__ x, double* __restrict__ phi, const int* __restrict__ perm,
+                  const double* __restrict__ Lr, const double* __restrict__ Lc)
+{
+    extern __shared__ double sx[];
+    ana::solve_levels_warp(L, colptr, rowidx, rdiag, plan, n, d, x, phi, blockIdx.x, perm, nullptr, Lr, Lc, sx);
+}
+
 __global__ void __launch_bounds__(ana::DOT_THREADS)
 rand_dots_kernel(uint64_t seed, uint32_t t, uint32_t s_xi, uint32_t s_nu, int NR, double* __restrict__ partial,
                  int nblk)
@@ -250,6 +262,12 @@ cudaError_t launch_solve(const double* L, const int* colptr, const int* rowidx, 
                          double* scratch, const double* Lr, const double* Lc)
 {
     if ((perm && !scratch) || (!Lr != !Lc)) return cudaErrorInvalidValue;
+    if (ne <= 0) return cudaSuccess;
+    if (n > 0 && (size_t)n * sizeof(double) <= kSolveSmemBytes) {
+        solve_smem_kernel<<<ne, 32, (size_t)n * sizeof(double), st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi,
+                                                                       perm, Lr, Lc);
+        return cudaGetLastError();
+    }
     const int threads = 128;
     const int blocks = (ne * 32 + threads - 1) / threads;
     solve_kernel<<<blocks, threads, 0, st>>>(L, colptr, rowidx, rdiag, plan, n, d, Sd, phi, ne, perm, scratch, Lr,

@@ -253,8 +253,10 @@ __device__ __forceinline__ void solve_warp(const double* __restrict__ L, const i
 // not interact) give two levels each.  Int layout of `plan`, n = order:
 // rowptr[n+1] | forder[n] | fptr[n+1] | border[n] | bptr[n+1] | nlev[2] |
 // lev[n] | colidx[n(n-1)/2] (CSR below the diagonal, column order in a row).
+// rf, rb: per position t of the forward (backward) level order, the row
+// (column) and the bounds of its entries: {i, start, end}
 struct SolvePlan {
-    int *rowptr, *forder, *fptr, *border, *bptr, *nlev, *lev, *colidx;
+    int *rowptr, *forder, *fptr, *border, *bptr, *nlev, *lev, *rf, *rb, *colidx;
 };
 
 __host__ __device__ inline SolvePlan solve_plan_view(int* base, int n)
@@ -267,7 +269,9 @@ __host__ __device__ inline SolvePlan solve_plan_view(int* base, int n)
     P.bptr = P.border + n;
     P.nlev = P.bptr + n + 1;
     P.lev = P.nlev + 2;
-    P.colidx = P.lev + n;
+    P.rf = P.lev + n;
+    P.rb = P.rf + 3 * n;
+    P.colidx = P.rb + 3 * n;
     return P;
 }
 
@@ -346,12 +350,22 @@ __device__ __forceinline__ void solve_plan_cta(const double* __restrict__ L, int
         if (lane == 0) P.nlev[1] = level_sort(P.lev, n, P.border, P.bptr);
     }
     __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int i = P.forder[t], k = P.border[t];
+        P.rf[3 * t] = i;
+        P.rf[3 * t + 1] = P.rowptr[i];
+        P.rf[3 * t + 2] = P.rowptr[i + 1];
+        P.rb[3 * t] = k;
+        P.rb[3 * t + 1] = colptr[k];
+        P.rb[3 * t + 2] = colptr[k + 1];
+    }
+    __syncthreads();
 }
 
 // warp: S d = (L L^T)^{-1} d for particle w and phi_w = d^T S d along the
-// level schedule: a level of at least 8 rows gives one row per lane (the
-// row's sum in column order), a smaller one the whole warp to each row
-// (lane-strided partial sums, then the warp sum)
+// level schedule: a level of 32 rows or more gives one row per lane (the
+// row's sum in column order), a narrower one a group of lanes to each row
+// (lane-strided partial sums, then the group's sum)
 // perm (may be null): the factor is that of P A P^T with unknown i of the
 // factored system = unknown perm[i] of the observations; the sweeps then run
 // in that order in scratch (n doubles per particle), d is read through perm
@@ -359,7 +373,10 @@ __device__ __forceinline__ void solve_plan_cta(const double* __restrict__ L, int
 // Lr, Lc (may be null): the factor's values below the diagonal in the order
 // of the plan's CSR (colidx) and of the CSC (rowidx), so that a row's or a
 // column's products read consecutive doubles instead of scattered entries of
-// the dense factor (pack_factor_values)
+// the dense factor (launch_pack_factor)
+// sx (may be null): n doubles of shared memory owned by this warp; the sweeps
+// then run there instead of in scratch or x, so that the products of a level
+// wait on shared memory, not on L2, for the values of the levels before
 __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, const int* __restrict__ colptr,
                                                   const int* __restrict__ rowidx, const double* __restrict__ rdiag,
                                                   const int* plan_base, int n, const double* __restrict__ d,
@@ -367,83 +384,146 @@ __device__ __forceinline__ void solve_levels_warp(const double* __restrict__ L, 
                                                   const int* __restrict__ perm = nullptr,
                                                   double* __restrict__ scratch = nullptr,
                                                   const double* __restrict__ Lr = nullptr,
-                                                  const double* __restrict__ Lc = nullptr)
+                                                  const double* __restrict__ Lc = nullptr, double* sx = nullptr)
 {
     const SolvePlan P = solve_plan_view(const_cast<int*>(plan_base), n);
     const int lane = threadIdx.x & 31;
-    double* xp = (perm ? scratch : x) + (long long)w * n;
+    double* xp = sx ? sx : (perm ? scratch : x) + (long long)w * n;
     const double* dp = d + (long long)w * n;
     auto dval = [&](int i) { return perm ? dp[perm[i]] : dp[i]; };
+    // entry q of row i (column j) of the CSR; entry q of column i (row k) of the CSC
     auto lrow = [&](int q, int i, int j) { return Lr ? Lr[q] : L[(long long)i * n + j]; };
-    auto lcol = [&](int q, int k, int i) { return Lc ? Lc[q] : L[(long long)k * n + i]; };
+    auto lcol = [&](int q, int i, int k) { return Lc ? Lc[q] : L[(long long)k * n + i]; };
+    // the right-hand side in the order of the factored system; the forward
+    // sweep then overwrites it row by row
+    for (int i = lane; i < n; i += 32) xp[i] = dval(i);
+    __syncwarp();
+    // One sweep over the levels lv[0..nl] of a level order whose position t
+    // holds row (or column) ri[3t] with entries ri[3t+1]..ri[3t+2] (index
+    // idx[q], value val(q, i, idx[q])).  A level of m < 32 rows gives each row
+    // a group of g = 32 / 2^ceil(log2 m) lanes (lane-strided partial sums in
+    // entry order, then the group's sum), a wider one a lane per row, in
+    // rounds of 32 rows.  None of the loads but those of xp depends on an
+    // earlier level, so they are issued ahead: while level l is summed, the
+    // first batch of entries and the diagonal of level l+1, the row
+    // descriptors of level l+2 and the bounds of level l+3 are in flight.
+    constexpr int U = 8;
+    auto sweep = [&](const int* __restrict__ lv, int nl, const int* __restrict__ ri, const int* __restrict__ idx,
+                     auto val) {
+        auto bound = [&](int k) { return lv[k < nl ? k : nl]; };
+        auto log_group = [](int m) { return m >= 32 ? 0 : 5 - (m <= 1 ? 0 : 32 - __clz(m - 1)); };
+        // this lane's first row of a level: {i (-1: none), first entry, end}
+        auto fetch_row = [&](int lo, int hi, int& i, int& q0, int& q1) {
+            const int lg = log_group(hi - lo);
+            const int t = lo + (lane >> lg);
+            i = -1;
+            q0 = q1 = 0;
+            if (t < hi) {
+                i = ri[3 * t];
+                q0 = ri[3 * t + 1] + (lane & ((1 << lg) - 1));
+                q1 = ri[3 * t + 2];
+            }
+        };
+        auto fetch_batch = [&](int i, int q0, int q1, int g, int* jj, double* vv) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) jj[u] = q0 + u * g < q1 ? idx[q0 + u * g] : -1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) vv[u] = jj[u] >= 0 ? val(q0 + u * g, i, jj[u]) : 0.0;
+        };
+        auto sum_batch = [&](const int* jj, const double* vv, double acc) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (jj[u] >= 0) acc = fma(vv[u], xp[jj[u]], acc);
+            return acc;
+        };
+        // the row of one round: the prefetched first batch, then the rest
+        auto finish_row = [&](int lg, int i, int q0, int q1, const int* jj, const double* vv, double rd) {
+            const int g = 1 << lg;
+            double acc = 0.0;
+            if (i >= 0) {
+                // the next batch is in flight while the current one is summed
+                int cj[U];
+                double cv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    cj[u] = jj[u];
+                    cv[u] = vv[u];
+                }
+                for (int q = q0 + U * g;; q += U * g) {
+                    const bool more = q < q1;
+                    int kj[U];
+                    double kv[U];
+                    if (more) fetch_batch(i, q, q1, g, kj, kv);
+                    acc = sum_batch(cj, cv, acc);
+                    if (!more) break;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        cj[u] = kj[u];
+                        cv[u] = kv[u];
+                    }
+                }
+            }
+            for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (i >= 0 && (lane & (g - 1)) == 0) xp[i] = (xp[i] - acc) * rd;
+        };
+        // pipeline: level l (bounds, row, batch, diagonal), level l+1 (bounds,
+        // row), level l+2 (bounds)
+        int lo0 = bound(0), hi0 = bound(1), lo1 = hi0, hi1 = bound(2), lo2 = hi1, hi2 = bound(3);
+        int i0, a0, e0, i1, a1, e1;
+        fetch_row(lo0, hi0, i0, a0, e0);
+        fetch_row(lo1, hi1, i1, a1, e1);
+        int j0[U];
+        double v0[U];
+        fetch_batch(i0, a0, e0, 1 << log_group(hi0 - lo0), j0, v0);
+        double rd0 = i0 >= 0 ? rdiag[i0] : 0.0;
+        for (int l = 0; l < nl; ++l) {
+            // issue the loads of the levels ahead
+            int j1[U];
+            double v1[U];
+            fetch_batch(i1, a1, e1, 1 << log_group(hi1 - lo1), j1, v1);
+            const double rd1 = i1 >= 0 ? rdiag[i1] : 0.0;
+            int i2, a2, e2;
+            fetch_row(lo2, hi2, i2, a2, e2);
+            const int hi3 = bound(l + 4);
+            // level l: the first round from the prefetched values, further
+            // rounds (more than 32 rows) loaded here
+            const int lg = log_group(hi0 - lo0);
+            finish_row(lg, i0, a0, e0, j0, v0, rd0);
+            for (int t = lo0 + 32 + lane; t - lane < hi0; t += 32) {
+                int i = -1, q0 = 0, q1 = 0;
+                if (t < hi0) {
+                    i = ri[3 * t];
+                    q0 = ri[3 * t + 1];
+                    q1 = ri[3 * t + 2];
+                }
+                int jj[U];
+                double vv[U];
+                fetch_batch(i, q0, q1, 1, jj, vv);
+                finish_row(0, i, q0, q1, jj, vv, i >= 0 ? rdiag[i] : 0.0);
+            }
+            __syncwarp();
+            // advance the pipeline
+            lo0 = lo1; hi0 = hi1; i0 = i1; a0 = a1; e0 = e1; rd0 = rd1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                j0[u] = j1[u];
+                v0[u] = v1[u];
+            }
+            lo1 = lo2; hi1 = hi2; i1 = i2; a1 = a2; e1 = e2;
+            lo2 = hi2; hi2 = hi3;
+        }
+    };
     // forward: y_i = (d_i - sum_j L_ij y_j) / L_ii
-    const int nf = P.nlev[0];
-    for (int l = 0; l < nf; ++l) {
-        const int a = P.fptr[l], b = P.fptr[l + 1];
-        if (b - a >= 8) {
-            for (int t = a + lane; t < b; t += 32) {
-                const int i = P.forder[t];
-                double acc = 0.0;
-#pragma unroll 4
-                for (int q = P.rowptr[i]; q < P.rowptr[i + 1]; ++q) {
-                    const int j = P.colidx[q];
-                    acc = fma(lrow(q, i, j), xp[j], acc);
-                }
-                xp[i] = (dval(i) - acc) * rdiag[i];
-            }
-        } else {
-            for (int t = a; t < b; ++t) {
-                const int i = P.forder[t];
-                double acc = 0.0;
-#pragma unroll 4
-                for (int q = P.rowptr[i] + lane; q < P.rowptr[i + 1]; q += 32) {
-                    const int j = P.colidx[q];
-                    acc = fma(lrow(q, i, j), xp[j], acc);
-                }
-                acc = warp_sum(acc);
-                if (lane == 0) xp[i] = (dval(i) - acc) * rdiag[i];
-            }
-        }
-        __syncwarp();
-    }
+    sweep(P.fptr, P.nlev[0], P.rf, P.colidx, lrow);
     // backward: x_i = (y_i - sum_k L_ki x_k) / L_ii over k > i
-    const int nb = P.nlev[1];
-    for (int l = 0; l < nb; ++l) {
-        const int a = P.bptr[l], b = P.bptr[l + 1];
-        if (b - a >= 8) {
-            for (int t = a + lane; t < b; t += 32) {
-                const int i = P.border[t];
-                double acc = 0.0;
-#pragma unroll 4
-                for (int q = colptr[i]; q < colptr[i + 1]; ++q) {
-                    const int k = rowidx[q];
-                    acc = fma(lcol(q, k, i), xp[k], acc);
-                }
-                xp[i] = (xp[i] - acc) * rdiag[i];
-            }
-        } else {
-            for (int t = a; t < b; ++t) {
-                const int i = P.border[t];
-                double acc = 0.0;
-#pragma unroll 4
-                for (int q = colptr[i] + lane; q < colptr[i + 1]; q += 32) {
-                    const int k = rowidx[q];
-                    acc = fma(lcol(q, k, i), xp[k], acc);
-                }
-                acc = warp_sum(acc);
-                __syncwarp();
-                if (lane == 0) xp[i] = (xp[i] - acc) * rdiag[i];
-            }
-        }
-        __syncwarp();
-    }
+    sweep(P.bptr, P.nlev[1], P.rb, rowidx, lcol);
     double acc = 0.0;
     for (int i = lane; i < n; i += 32) acc = fma(dval(i), xp[i], acc);
     acc = warp_sum(acc);
     if (lane == 0) phi[w] = acc;
-    if (perm) {
+    if (perm || sx) {
         double* out = x + (long long)w * n;
-        for (int i = lane; i < n; i += 32) out[perm[i]] = xp[i];
+        for (int i = lane; i < n; i += 32) out[perm ? perm[i] : i] = xp[i];
     }
 }
 

@@ -131,13 +131,16 @@ cudaError_t launch_hqht(const double* K64, int R, const int* obs_cell, int nobs,
 // ints of the level schedule of the triangular sweeps of an n x n factor
 __host__ __device__ inline size_t solve_plan_ints(int n)
 {
-    return 6 * (size_t)n + 5 + (size_t)n * (n - 1) / 2;
+    return 12 * (size_t)n + 5 + (size_t)n * (n - 1) / 2;
 }
 // FP64 Cholesky of M (n x n) in place, the CSC of the factor below the
 // diagonal, its reciprocal diagonal and the level schedule of the two
 // triangular sweeps (plan: ana::solve_plan_ints(n) ints)
 cudaError_t launch_cholesky(double* M, int n, int* colptr, int* rowidx, int* flag, double* rdiag, int* plan,
                             cudaStream_t st);
+// largest vector a particle's solve keeps in shared memory (a CTA of one warp
+// per particle); larger systems sweep in global memory
+constexpr size_t kSolveSmemBytes = 48 * 1024;
 // perm, scratch: see ana::solve_levels_warp (both null: observation order);
 // Lr, Lc: the packed values of launch_pack_factor (both null: the sweeps
 // read the dense factor)
