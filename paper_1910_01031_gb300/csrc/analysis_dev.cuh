@@ -208,44 +208,6 @@ __device__ __forceinline__ void cholesky_cta(double* __restrict__ A, int n, int*
     if (threadIdx.x == 0 && bad) atomicOr(flag, FLAG_NOTPD);
 }
 
-// warp: S d = (L L^T)^{-1} d for particle w and phi_w = d^T S d
-__device__ __forceinline__ void solve_warp(const double* __restrict__ L, const int* __restrict__ colptr,
-                                           const int* __restrict__ rowidx, int n, const double* __restrict__ d,
-                                           double* __restrict__ x, double* __restrict__ phi, int w)
-{
-    const int lane = threadIdx.x & 31;
-    double* xp = x + (long long)w * n;
-    const double* dp = d + (long long)w * n;
-    for (int i = lane; i < n; i += 32) xp[i] = dp[i];
-    __syncwarp();
-    for (int k = 0; k < n; ++k) {
-        const double yk = xp[k] / L[(long long)k * n + k];
-        __syncwarp();
-        if (lane == 0) xp[k] = yk;
-        for (int q = colptr[k] + lane; q < colptr[k + 1]; q += 32) {
-            const int i = rowidx[q];
-            xp[i] = fma(-L[(long long)i * n + k], yk, xp[i]);
-        }
-        __syncwarp();
-    }
-    for (int k = n - 1; k >= 0; --k) {
-        double acc = 0.0;
-        for (int q = colptr[k] + lane; q < colptr[k + 1]; q += 32) {
-            const int i = rowidx[q];
-            acc = fma(L[(long long)i * n + k], xp[i], acc);
-        }
-        acc = warp_sum(acc);
-        const double xk = (xp[k] - acc) / L[(long long)k * n + k];
-        __syncwarp();
-        if (lane == 0) xp[k] = xk;
-        __syncwarp();
-    }
-    double acc = 0.0;
-    for (int i = lane; i < n; i += 32) acc = fma(dp[i], xp[i], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) phi[w] = acc;
-}
-
 // Level schedule of the triangular solves with the factor L (CSC below the
 // diagonal in colptr/rowidx).  Rows of one level of the forward sweep
 // L y = d depend only on rows of lower levels, and likewise columns of one
