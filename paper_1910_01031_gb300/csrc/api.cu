@@ -893,6 +893,7 @@ int iewpf_create(const iewpf_params_t* params, const double* mooring_xy, iewpf_c
                 return bail(IEWPF_ECUDA);
         }
         if ((rc = factor(ctx, nobs)) || (rc = read_flags(ctx))) return bail(rc);
+        // the factor's non-zeros below the diagonal (the stream is idle after read_flags)
         int nnz = 0;
         if (cudaMemcpy(&nnz, ctx->d_colptr + 2 * nobs, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return bail(IEWPF_ECUDA);
