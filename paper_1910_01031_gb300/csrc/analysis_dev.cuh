@@ -516,7 +516,10 @@ __device__ __forceinline__ void rand_dots_cta(uint64_t seed, uint32_t t, uint32_
                 const double d = ((double)nb[l] - (double)xb[l]) * 0x1p-31;   // 2u_b,nu - 2u_b,xi, exact
                 xx += rx2;
                 nn += rn2;
-                nx = fma(sqrt(rx2 * rn2), cospi(d), nx);
+                // nu~^T xi sets only the projection coefficient a of eq.
+                // nuPerpendicular, not gamma or zeta: its terms are formed in
+                // FP32 and summed in FP64
+                nx += (double)(sqrtf((float)(rx2 * rn2)) * cospif((float)d));
             }
         } else {
             double x[4], v[4];
