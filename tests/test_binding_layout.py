@@ -1,7 +1,8 @@
-"""The ctypes structures of the binding against the C structs of
-include/iewpf.h, on the CPU: a C program compiled with the host compiler
-prints every field's offset and size and each struct's size, which must
-equal the ctypes layout; and the configuration -> parameter mapping puts
+"""The binding's ABI against include/iewpf.h, on the CPU: a C program
+compiled with the host compiler prints every field's offset and size and
+each struct's size, which must equal the ctypes layout; every exported
+function's ctypes argument and return types match its prototype (pointer or
+scalar, width, signedness); and the configuration -> parameter mapping puts
 every value in its named field."""
 import ctypes
 import json
@@ -61,3 +62,42 @@ def test_params_from_config_fills_every_named_field():
     for k, v in expect.items():
         assert getattr(p, k) == v, k
     assert iewpf.params_from_config(cfg, n_obs_max=3).n_obs_max == 3
+
+
+_C_SCALARS = {"int": (4, "i"), "int64_t": (8, "i"), "uint64_t": (8, "u"), "uint32_t": (4, "u"),
+              "double": (8, "f"), "float": (4, "f"), "size_t": (8, "u")}
+
+
+def _c_kind(param):
+    """('ptr',) for a pointer parameter, else (size, signedness) of its type."""
+    p = " ".join(param.replace("const ", " ").split())
+    if "*" in p:
+        return ("ptr",)
+    base = p.rsplit(" ", 1)[0] if " " in p else p
+    return _C_SCALARS[base]
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return ("ptr",)
+    size = ctypes.sizeof(t)
+    if t in (ctypes.c_double, ctypes.c_float):
+        return (size, "f")
+    signed = t(-1).value < 0
+    return (size, "i" if signed else "u")
+
+
+def test_every_export_has_the_headers_argument_types():
+    import re
+    src = open(os.path.join(ROOT, "include", "iewpf.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    protos = re.findall(r"IEWPF_API\s+(int|const char\*)\s+([a-z_]+)\((.*?)\);", src, flags=re.S)
+    assert len(protos) == len(iewpf.EXPORTS)
+    L = iewpf.load()
+    for ret, name, args in protos:
+        fn = getattr(L, name)
+        params = [a.strip() for a in args.split(",") if a.strip() and a.strip() != "void"]
+        assert len(fn.argtypes) == len(params), name
+        for k, (p, t) in enumerate(zip(params, fn.argtypes)):
+            assert _c_kind(p) == _ctypes_kind(t), "%s argument %d (%s)" % (name, k, p)
+        assert fn.restype is (ctypes.c_int if ret == "int" else ctypes.c_char_p), name
