@@ -171,6 +171,17 @@ def _ptr(a, t=_dp):
     return None if a is None else a.ctypes.data_as(t)
 
 
+def _device_f32(t, shape, what):
+    """Refuses (ValueError) anything but a contiguous float32 CUDA tensor of
+    the given shape: the library reads or writes exactly that many floats at
+    the tensor's address."""
+    if not (hasattr(t, "data_ptr") and getattr(t, "is_cuda", False)):
+        raise ValueError("%s: a CUDA tensor is required" % what)
+    if str(t.dtype) != "torch.float32" or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError("%s: a contiguous float32 tensor of shape %s is required, not %s %s"
+                         % (what, tuple(shape), t.dtype, tuple(t.shape)))
+
+
 def _f64(a, shape=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
     if shape is not None:
@@ -254,7 +265,7 @@ class Ensemble:
     def set_state(self, U, stream=None):
         """U: numpy array or CUDA torch tensor [N_e][3][ny][nx] (float32)."""
         if hasattr(U, "data_ptr") and getattr(U, "is_cuda", False):
-            assert tuple(U.shape) == self.shape and U.is_contiguous() and str(U.dtype) == "torch.float32"
+            _device_f32(U, self.shape, "set_state")
             s = stream if stream is not None else _torch_stream()
             self._chk(self.L.iewpf_set_state(self.h, ctypes.c_void_p(U.data_ptr()), 1, s), "set_state")
             return
@@ -263,6 +274,7 @@ class Ensemble:
 
     def get_state(self, out=None, stream=None):
         if out is not None and hasattr(out, "data_ptr") and getattr(out, "is_cuda", False):
+            _device_f32(out, self.shape, "get_state")
             s = stream if stream is not None else _torch_stream()
             self._chk(self.L.iewpf_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 1, s), "get_state")
             return out
@@ -600,7 +612,9 @@ class Surrogate:
     def apply_device(self, U, out=None, stream=None):
         """U: CUDA torch tensor [n][3][ny][nx] float32; out (may be U) likewise."""
         out = U if out is None else out
-        assert U.is_cuda and U.is_contiguous() and out.is_contiguous() and tuple(out.shape) == tuple(U.shape)
+        shape = (U.shape[0] if len(U.shape) == 4 else -1, 3, self.ny, self.nx)
+        _device_f32(U, shape, "apply_device")
+        _device_f32(out, shape, "apply_device (out)")
         s = stream if stream is not None else _torch_stream()
         self._chk(self.L.iewpf_surrogate_apply_device(self.h, ctypes.c_void_p(U.data_ptr()), int(U.shape[0]),
                                                       ctypes.c_void_p(out.data_ptr()), s), "apply_device")

@@ -101,3 +101,35 @@ def test_every_export_has_the_headers_argument_types():
         for k, (p, t) in enumerate(zip(params, fn.argtypes)):
             assert _c_kind(p) == _ctypes_kind(t), "%s argument %d (%s)" % (name, k, p)
         assert fn.restype is (ctypes.c_int if ret == "int" else ctypes.c_char_p), name
+
+
+class _FakeTensor:
+    """Stands in for a CUDA torch tensor: only what the binding inspects."""
+
+    def __init__(self, shape, dtype="torch.float32", contiguous=True, cuda=True):
+        self.shape, self.dtype, self._c, self.is_cuda = tuple(shape), dtype, contiguous, cuda
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        raise AssertionError("the library must not be reached")
+
+
+def test_device_tensors_of_the_wrong_layout_are_refused_before_the_library():
+    e = iewpf.Ensemble.__new__(iewpf.Ensemble)
+    e.ne, e.nx, e.ny, e.L, e.h = 2, 16, 8, None, None
+    good = (2, 3, 8, 16)
+    for bad in (_FakeTensor((2, 3, 8, 15)), _FakeTensor((1, 3, 8, 16)), _FakeTensor(good, "torch.float64"),
+                _FakeTensor(good, contiguous=False)):
+        with pytest.raises(ValueError):
+            e.set_state(bad)
+        with pytest.raises(ValueError):
+            e.get_state(bad)
+    s = iewpf.Surrogate.__new__(iewpf.Surrogate)
+    s.nx, s.ny, s.L, s.h = 16, 8, None, None
+    for U, out in ((_FakeTensor((4, 3, 8, 15)), None), (_FakeTensor((4, 3, 8, 16), cuda=False), None),
+                   (_FakeTensor((4, 3, 8, 16)), _FakeTensor((3, 3, 8, 16))),
+                   (_FakeTensor((4, 3, 8, 16)), _FakeTensor((4, 3, 8, 16), "torch.bfloat16"))):
+        with pytest.raises(ValueError):
+            s.apply_device(U, out=out)
